@@ -1,0 +1,247 @@
+"""ctypes front end of the FP64 CPU oracle (oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU
+baseline leg import this package.  The product path never does, and it shares
+no code with the CUDA library (this module takes host numpy arrays, up-casts
+them to float64 and calls liboracle.so).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.cpp")
+
+_dp = C.POINTER(C.c_double)
+_u8p = C.POINTER(C.c_uint8)
+_i32p = C.POINTER(C.c_int32)
+
+
+def build(force: bool = False) -> str:
+    """Compile liboracle.so with g++ -O2 (no fast-math) and OpenMP."""
+    stale = not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
+        os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
+    if force or stale:
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+                               "-o", _SO, _SRC])
+    return _SO
+
+
+class ObParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("idm_amax", C.c_double), ("idm_b", C.c_double),
+                ("idm_T", C.c_double), ("idm_s0", C.c_double), ("idm_dq", C.c_double),
+                ("route_h", C.c_double), ("gap_min", C.c_double), ("band", C.c_double),
+                ("idm_K", C.c_int32), ("pad_", C.c_int32)]
+
+
+class ObBatch(C.Structure):
+    _fields_ = [("S", C.c_int32), ("N_tot", C.c_int32), ("T_log", C.c_int32), ("pad_", C.c_int32),
+                ("agent_off", _i32p), ("rg_off", _i32p),
+                ("L", _dp), ("W", _dp), ("idm_v0", _dp),
+                ("valid", _u8p), ("kind", _u8p),
+                ("route_off", _i32p), ("route_x", _dp), ("route_y", _dp),
+                ("rg_x", _dp), ("rg_y", _dp), ("rg_poly", _i32p), ("rg_type", _u8p), ("rg_valid", _u8p),
+                ("log_x", _dp), ("log_y", _dp)]
+
+
+class ObState(C.Structure):
+    _fields_ = [(k, _dp) for k in ("x", "y", "th", "vx", "vy", "s")]
+
+
+class ObMetrics(C.Structure):
+    _fields_ = [("ov", _dp), ("off", _dp), ("logdiv", _dp), ("flags", _u8p), ("reward", _i32p)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.POINTER
+        _lib.oracle_transition.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp,
+                                           _u8p, P(ObState), _u8p, _i32p]
+        _lib.oracle_metrics.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), C.c_int,
+                                        P(ObMetrics)]
+        _lib.oracle_rollout.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp,
+                                        C.c_int, C.c_int, P(ObMetrics), C.c_int]
+        _lib.oracle_box_depth.argtypes = [_dp, _dp]
+        _lib.oracle_box_depth.restype = C.c_double
+        _lib.oracle_point_sd.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_double, C.c_double,
+                                         P(C.c_int), _i32p]
+        _lib.oracle_point_sd.restype = C.c_double
+        _lib.oracle_loss.argtypes = [P(ObParams), P(ObBatch), C.c_int, P(ObState), _dp, C.c_int, C.c_int,
+                                     C.c_double, C.c_double]
+        _lib.oracle_loss.restype = C.c_double
+        _lib.oracle_loss_grad.argtypes = [P(ObParams), P(ObBatch), C.c_int, P(ObState), _dp, C.c_int,
+                                          C.c_int, C.c_double, C.c_double, C.c_int, _i32p, _i32p, _i32p, _dp]
+    return _lib
+
+
+@dataclass
+class Params:
+    """Method constants (same meaning and defaults as the GPU library's)."""
+    dt: float = 0.1
+    idm_amax: float = 2.0
+    idm_b: float = 3.0
+    idm_T: float = 1.5
+    idm_s0: float = 2.0
+    idm_dq: float = 2.0
+    route_h: float = 0.5
+    gap_min: float = 0.1
+    band: float = 1e-4
+    idm_K: int = 32
+
+    def c(self) -> ObParams:
+        return ObParams(self.dt, self.idm_amax, self.idm_b, self.idm_T, self.idm_s0, self.idm_dq,
+                        self.route_h, self.gap_min, self.band, self.idm_K, 0)
+
+
+def _ptr(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+STATE_KEYS = ("x", "y", "th", "vx", "vy", "s")
+
+
+class Oracle:
+    """FP64 view of a SceneBatch (arrays kept alive while the object lives)."""
+
+    def __init__(self, batch, params: Optional[Params] = None):
+        self.b = batch
+        self.p = params or Params()
+        self._cp = self.p.c()
+        keep = {}
+
+        def k(name, arr):
+            keep[name] = arr
+            return arr
+
+        self._batch = ObBatch(
+            batch.S, batch.N_tot, batch.log_x.shape[0], 0,
+            _ptr(k("ao", np.ascontiguousarray(batch.agent_off, np.int32)), _i32p),
+            _ptr(k("ro", np.ascontiguousarray(batch.rg_off, np.int32)), _i32p),
+            _ptr(k("L", _f64(batch.L)), _dp), _ptr(k("W", _f64(batch.W)), _dp),
+            _ptr(k("v0", _f64(batch.idm_v0)), _dp),
+            _ptr(k("valid", np.ascontiguousarray(batch.valid, np.uint8)), _u8p),
+            _ptr(k("kind", np.ascontiguousarray(batch.kind, np.uint8)), _u8p),
+            _ptr(k("rto", np.ascontiguousarray(batch.route_off, np.int32)), _i32p),
+            _ptr(k("rx", _f64(batch.route_x)), _dp), _ptr(k("ry", _f64(batch.route_y)), _dp),
+            _ptr(k("gx", _f64(batch.rg_x)), _dp), _ptr(k("gy", _f64(batch.rg_y)), _dp),
+            _ptr(k("gp", np.ascontiguousarray(batch.rg_poly, np.int32)), _i32p),
+            _ptr(k("gt", np.ascontiguousarray(batch.rg_type, np.uint8)), _u8p),
+            _ptr(k("gv", np.ascontiguousarray(batch.rg_valid, np.uint8)), _u8p),
+            _ptr(k("lx", _f64(batch.log_x)), _dp), _ptr(k("ly", _f64(batch.log_y)), _dp),
+        )
+        self._keep = keep
+
+    # -- state helpers -------------------------------------------------------
+    def initial_state(self) -> dict:
+        b = self.b
+        st = {k: _f64(getattr(b, k)).copy() for k in ("x", "y", "th", "vx", "vy")}
+        st["s"] = np.zeros(b.N_tot)
+        return st
+
+    @staticmethod
+    def _cstate(st: dict) -> ObState:
+        for k in STATE_KEYS:
+            assert st[k].dtype == np.float64 and st[k].flags.c_contiguous
+        return ObState(*[_ptr(st[k], _dp) for k in STATE_KEYS])
+
+    def _scenes(self, scenes):
+        return (0, self.b.S) if scenes is None else scenes
+
+    # -- calls ---------------------------------------------------------------
+    def transition(self, st: dict, act: np.ndarray, ctrl=None, scenes=None):
+        """State t -> t+1; act is [3][N_tot].  Returns (state, band_idm, lead)."""
+        N = self.b.N_tot
+        s0, s1 = self._scenes(scenes)
+        st = {k: _f64(st[k]) for k in STATE_KEYS}
+        out = {k: st[k].copy() for k in STATE_KEYS}
+        act = _f64(act).reshape(3, N)
+        band = np.zeros(N, np.uint8)
+        lead = np.full(N, -1, np.int32)
+        ctrl_p = None if ctrl is None else _ptr(np.ascontiguousarray(ctrl, np.uint8), _u8p)
+        rc = lib().oracle_transition(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(st)),
+                                     _ptr(act, _dp), ctrl_p, C.byref(self._cstate(out)),
+                                     _ptr(band, _u8p), _ptr(lead, _i32p))
+        if rc:
+            raise RuntimeError("oracle_transition failed")
+        return out, band, lead
+
+    def metrics(self, st: dict, t: int, scenes=None) -> dict:
+        N, S = self.b.N_tot, self.b.S
+        s0, s1 = self._scenes(scenes)
+        st = {k: _f64(st[k]) for k in STATE_KEYS}
+        m = dict(ov=np.zeros(N), off=np.zeros(N), logdiv=np.zeros(N), flags=np.zeros(N, np.uint8),
+                 reward=np.zeros(S, np.int32))
+        cm = ObMetrics(_ptr(m["ov"], _dp), _ptr(m["off"], _dp), _ptr(m["logdiv"], _dp),
+                       _ptr(m["flags"], _u8p), _ptr(m["reward"], _i32p))
+        rc = lib().oracle_metrics(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(st)),
+                                  t, C.byref(cm))
+        if rc:
+            raise RuntimeError("oracle_metrics failed")
+        return m
+
+    def rollout(self, st: dict, act_seq: np.ndarray, t0: int, T: int, scenes=None, nthreads: int = 0):
+        """Free-running FP64 rollout; returns (final state, metrics [T][...])."""
+        N, S = self.b.N_tot, self.b.S
+        s0, s1 = self._scenes(scenes)
+        st = {k: _f64(st[k]).copy() for k in STATE_KEYS}
+        act = _f64(act_seq).reshape(-1, 3, N)
+        m = dict(ov=np.zeros((T, N)), off=np.zeros((T, N)), logdiv=np.zeros((T, N)),
+                 flags=np.zeros((T, N), np.uint8), reward=np.zeros((T, S), np.int32))
+        cm = ObMetrics(_ptr(m["ov"], _dp), _ptr(m["off"], _dp), _ptr(m["logdiv"], _dp),
+                       _ptr(m["flags"], _u8p), _ptr(m["reward"], _i32p))
+        rc = lib().oracle_rollout(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(st)),
+                                  _ptr(act, _dp), t0, T, C.byref(cm), nthreads)
+        if rc:
+            raise RuntimeError("oracle_rollout failed")
+        return st, m
+
+    def point_sd(self, scene: int, px: float, py: float) -> Tuple[float, int, int]:
+        amb = C.c_int(0)
+        seg = C.c_int32(-1)
+        r = lib().oracle_point_sd(C.byref(self._cp), C.byref(self._batch), scene, px, py, C.byref(amb),
+                                  C.byref(seg))
+        return r, amb.value, seg.value
+
+    def loss(self, scene: int, st0: dict, act_seq: np.ndarray, t0: int, T: int, lam: float = 1.0,
+             tau: float = 0.25) -> float:
+        st = {k: _f64(st0[k]) for k in STATE_KEYS}
+        act = _f64(act_seq)
+        return lib().oracle_loss(C.byref(self._cp), C.byref(self._batch), scene, C.byref(self._cstate(st)),
+                                 _ptr(act, _dp), t0, T, lam, tau)
+
+    def loss_grad(self, scene: int, st0: dict, act_seq: np.ndarray, t0: int, T: int, dirs,
+                  lam: float = 1.0, tau: float = 0.25) -> np.ndarray:
+        """dL/dact[t][c][g] for dirs = iterable of (t, c, g) (dual numbers)."""
+        d = np.asarray(list(dirs), dtype=np.int32).reshape(-1, 3)
+        dt_, dc, dg = (np.ascontiguousarray(d[:, i]) for i in range(3))
+        out = np.zeros(len(d))
+        st = {k: _f64(st0[k]) for k in STATE_KEYS}
+        act = _f64(act_seq)
+        rc = lib().oracle_loss_grad(C.byref(self._cp), C.byref(self._batch), scene, C.byref(self._cstate(st)),
+                                    _ptr(act, _dp), t0, T, lam, tau, len(d), _ptr(dt_, _i32p), _ptr(dc, _i32p),
+                                    _ptr(dg, _i32p), _ptr(out, _dp))
+        if rc:
+            raise RuntimeError("oracle_loss_grad failed")
+        return out
+
+
+def box_depth(a, b) -> float:
+    """SAT depth of boxes given as (x, y, theta, L, W)."""
+    A, B = _f64(a), _f64(b)
+    return lib().oracle_box_depth(_ptr(A, _dp), _ptr(B, _dp))

@@ -1,0 +1,583 @@
+// FP64 CPU oracle for the batched closed-loop driving-simulator step
+// (Waymax, arXiv 2310.08710).  TEST INFRASTRUCTURE ONLY: see oracle.h.
+//
+// Plain definitions by brute force: every agent pair, every road-edge segment,
+// one dual-number pass per gradient direction.  Nothing is blocked, culled or
+// reordered beyond what the definitions state, so each function can be checked
+// against the paper by eye.  Readings of points the paper leaves open are
+// marked "Reading:" and repeated in the design notes.
+#include "oracle.h"
+
+#include <algorithm>
+#include <cmath>
+#include <limits>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+const double kInf = std::numeric_limits<double>::infinity();
+
+// ---------------------------------------------------------------------------
+// Forward-mode dual numbers (value, one tangent) for the loss gradient.
+// ---------------------------------------------------------------------------
+struct Dual {
+    double v, d;
+    Dual() : v(0), d(0) {}
+    Dual(double x) : v(x), d(0) {}  // NOLINT: implicit lift of constants
+    Dual(double x, double t) : v(x), d(t) {}
+};
+inline Dual operator+(Dual a, Dual b) { return {a.v + b.v, a.d + b.d}; }
+inline Dual operator-(Dual a, Dual b) { return {a.v - b.v, a.d - b.d}; }
+inline Dual operator-(Dual a) { return {-a.v, -a.d}; }
+inline Dual operator*(Dual a, Dual b) { return {a.v * b.v, a.d * b.v + a.v * b.d}; }
+inline Dual operator/(Dual a, Dual b) {
+    return {a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)};
+}
+inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
+inline Dual sqrt(Dual a) {
+    double r = std::sqrt(a.v);
+    return {r, r > 0 ? a.d / (2 * r) : 0.0};
+}
+inline Dual sin(Dual a) { return {std::sin(a.v), std::cos(a.v) * a.d}; }
+inline Dual cos(Dual a) { return {std::cos(a.v), -std::sin(a.v) * a.d}; }
+inline Dual exp(Dual a) { double e = std::exp(a.v); return {e, e * a.d}; }
+inline Dual log1p(Dual a) { return {std::log1p(a.v), a.d / (1 + a.v)}; }
+inline Dual fabs(Dual a) { return a.v < 0 ? -a : a; }
+inline double val(double x) { return x; }
+inline double val(Dual x) { return x.v; }
+template <class T> inline T tmin(T a, T b) { return val(b) < val(a) ? b : a; }
+template <class T> inline T tmax(T a, T b) { return val(b) > val(a) ? b : a; }
+
+using std::cos;
+using std::exp;
+using std::fabs;
+using std::log1p;
+using std::sin;
+using std::sqrt;
+
+// ---------------------------------------------------------------------------
+// Agent state and the two dynamics models of App. A.1.
+// ---------------------------------------------------------------------------
+template <class T> struct St { T x, y, th, vx, vy; };
+
+// App. A.1, bicycle action space, forward dynamics: position advanced with the
+// current velocity plus half the acceleration along the current heading; the
+// heading turns by kappa times the distance travelled; the new speed is put
+// along the new heading.  Reading: no clamp of v' (the equations have none).
+template <class T>
+St<T> bicycle_forward(const St<T>& s, T a, T kappa, double dt) {
+    T v = sqrt(s.vx * s.vx + s.vy * s.vy);
+    St<T> o;
+    o.x = s.x + s.vx * dt + 0.5 * a * cos(s.th) * dt * dt;
+    o.y = s.y + s.vy * dt + 0.5 * a * sin(s.th) * dt * dt;
+    o.th = s.th + kappa * (v * dt + 0.5 * a * dt * dt);
+    T vn = v + a * dt;
+    o.vx = vn * cos(o.th);
+    o.vy = vn * sin(o.th);
+    return o;
+}
+
+// App. A.1, delta action space: displacements added, velocity is the
+// displacement over the step length.
+template <class T>
+St<T> delta_forward(const St<T>& s, T dx, T dy, T dth, double dt) {
+    St<T> o;
+    o.x = s.x + dx;
+    o.y = s.y + dy;
+    o.th = s.th + dth;
+    o.vx = (o.x - s.x) / dt;
+    o.vy = (o.y - s.y) / dt;
+    return o;
+}
+
+// ---------------------------------------------------------------------------
+// Oriented boxes and the separating-axis overlap depth (Sec. 3.4, collision:
+// two top-down boxes at the same step overlap).
+// ---------------------------------------------------------------------------
+template <class T> struct Box { T cx, cy, c, s, hl, hw; };
+
+template <class T> Box<T> make_box(T x, T y, T th, double L, double W) {
+    Box<T> b;
+    b.cx = x; b.cy = y; b.c = cos(th); b.s = sin(th);
+    b.hl = T(0.5 * L); b.hw = T(0.5 * W);
+    return b;
+}
+
+// Signed depth d = min over the four edge normals of (rA + rB - |dc . axis|),
+// rX being box X's half extent projected on the axis.  d > 0 iff the boxes
+// overlap (no separating axis among the edge normals of two rectangles); then
+// d is the minimum translation distance.
+template <class T> T sat_depth(const Box<T>& A, const Box<T>& B) {
+    T dx = B.cx - A.cx, dy = B.cy - A.cy;
+    T ax[4] = {A.c, -A.s, B.c, -B.s};
+    T ay[4] = {A.s, A.c, B.s, B.c};
+    T best = T(kInf);
+    for (int k = 0; k < 4; ++k) {
+        T rA = A.hl * fabs(A.c * ax[k] + A.s * ay[k]) + A.hw * fabs(-A.s * ax[k] + A.c * ay[k]);
+        T rB = B.hl * fabs(B.c * ax[k] + B.s * ay[k]) + B.hw * fabs(-B.s * ax[k] + B.c * ay[k]);
+        T ov = rA + rB - fabs(dx * ax[k] + dy * ay[k]);
+        best = tmin(best, ov);
+    }
+    return best;
+}
+
+// Numerically stable softplus: max(x,0) + log(1 + exp(-|x|)).
+template <class T> T softplus(T x) { return tmax(x, T(0.0)) + log1p(exp(-fabs(x))); }
+
+// ---------------------------------------------------------------------------
+// Road-edge segments (Sec. 3.4 off-road: the vehicle must be on the left of the
+// oriented road edge).  Points k and k+1 form a segment iff both are valid road
+// edges of the same polyline; it is oriented k -> k+1.
+// ---------------------------------------------------------------------------
+struct Seg { double ax, ay, ux, uy; int k; int prev, next; };
+
+bool is_seg(const ob_batch* b, int r0, int r1, int k) {
+    if (k < r0 || k + 1 >= r1) return false;
+    return b->rg_valid[k] && b->rg_valid[k + 1] && b->rg_type[k] == 1 &&
+           b->rg_type[k + 1] == 1 && b->rg_poly[k] == b->rg_poly[k + 1];
+}
+
+std::vector<Seg> scene_segments(const ob_batch* b, int s) {
+    int r0 = b->rg_off[s], r1 = b->rg_off[s + 1];
+    std::vector<Seg> v;
+    for (int k = r0; k + 1 < r1; ++k) {
+        if (!is_seg(b, r0, r1, k)) continue;
+        Seg g;
+        g.ax = b->rg_x[k]; g.ay = b->rg_y[k];
+        g.ux = b->rg_x[k + 1] - b->rg_x[k];
+        g.uy = b->rg_y[k + 1] - b->rg_y[k];
+        g.k = k;
+        g.prev = is_seg(b, r0, r1, k - 1) ? (int)v.size() - 1 : -1;
+        g.next = -1;
+        if (g.prev >= 0) v[g.prev].next = (int)v.size();
+        v.push_back(g);
+    }
+    return v;
+}
+
+inline double cross(double ax, double ay, double bx, double by) { return ax * by - ay * bx; }
+
+// Which side of the nearest feature point p lies on: true = left = on road.
+// Interior nearest point (or an open polyline end): sign of u x (p - a).
+// Reading (the paper is silent on vertices): at a shared vertex with incoming
+// u1 and outgoing u2, a left turn (u1 x u2 > 0) keeps p on road iff it is left
+// of both lines, a right turn iff it is left of either, collinear uses u1.
+bool on_road_side(const std::vector<Seg>& g, int i, double traw, double px, double py) {
+    const Seg& e = g[i];
+    double vx, vy, u1x, u1y, u2x, u2y;
+    if (traw <= 0 && e.prev >= 0) {
+        vx = e.ax; vy = e.ay;
+        u1x = g[e.prev].ux; u1y = g[e.prev].uy; u2x = e.ux; u2y = e.uy;
+    } else if (traw >= 1 && e.next >= 0) {
+        vx = e.ax + e.ux; vy = e.ay + e.uy;
+        u1x = e.ux; u1y = e.uy; u2x = g[e.next].ux; u2y = g[e.next].uy;
+    } else {
+        return cross(e.ux, e.uy, px - e.ax, py - e.ay) > 0;
+    }
+    bool l1 = cross(u1x, u1y, px - vx, py - vy) > 0;
+    bool l2 = cross(u2x, u2y, px - vx, py - vy) > 0;
+    double turn = cross(u1x, u1y, u2x, u2y);
+    if (turn > 0) return l1 && l2;
+    if (turn < 0) return l1 || l2;
+    return l1;
+}
+
+// Distance of p to segment i; traw is the unclamped projection parameter.
+inline double seg_d2(const Seg& e, double px, double py, double* traw) {
+    double wx = px - e.ax, wy = py - e.ay;
+    double t = (wx * e.ux + wy * e.uy) / (e.ux * e.ux + e.uy * e.uy);
+    *traw = t;
+    double tc = std::min(1.0, std::max(0.0, t));
+    double ex = wx - tc * e.ux, ey = wy - tc * e.uy;
+    return ex * ex + ey * ey;
+}
+
+// Exhaustive nearest-segment scan (ties go to the lower roadgraph index) and
+// the signed distance: -dist on road, +dist off road.
+double point_sd(const std::vector<Seg>& g, double px, double py, double band,
+                int* ambiguous, int* seg_index) {
+    int best = -1;
+    double bd2 = kInf, bt = 0;
+    for (int i = 0; i < (int)g.size(); ++i) {
+        double t, d2 = seg_d2(g[i], px, py, &t);
+        if (d2 < bd2) { bd2 = d2; best = i; bt = t; }
+    }
+    if (seg_index) *seg_index = best;
+    if (best < 0) { if (ambiguous) *ambiguous = 0; return -kInf; }
+    bool on = on_road_side(g, best, bt, px, py);
+    double bd = std::sqrt(bd2);
+    if (ambiguous) {
+        // A near tie with a segment that shares no vertex with the winner and
+        // puts p on the other side: the sign is not decided robustly.
+        *ambiguous = 0;
+        for (int i = 0; i < (int)g.size(); ++i) {
+            if (i == best || i == g[best].prev || i == g[best].next) continue;
+            double t, d2 = seg_d2(g[i], px, py, &t);
+            if (std::sqrt(d2) > bd + band) continue;
+            if (on_road_side(g, i, t, px, py) != on) { *ambiguous = 1; break; }
+        }
+    }
+    return on ? -bd : bd;
+}
+
+// ---------------------------------------------------------------------------
+// IDM route following (Sec. 3.5: follow the logged path, IDM sets the speed).
+// The paper gives no equations; this is the textbook IDM of Treiber et al.
+// (2000), which the paper cites, with a lead search along the route.
+// ---------------------------------------------------------------------------
+struct RoutePt { double x, y, tx, ty; int seg; };
+
+// Position on the route polyline at parameter s: segment k = floor(s/h)
+// (clamped to the route, the last segment extrapolated), linear inside it.
+RoutePt route_eval(const double* rx, const double* ry, int P, double h, double s) {
+    double u = s / h;
+    int k = (int)std::floor(u);
+    if (k < 0) k = 0;
+    if (k > P - 2) k = P - 2;
+    double tau = u - k;
+    double dx = rx[k + 1] - rx[k], dy = ry[k + 1] - ry[k];
+    double n = std::sqrt(dx * dx + dy * dy);
+    RoutePt r;
+    r.x = rx[k] + tau * dx;
+    r.y = ry[k] + tau * dy;
+    r.tx = dx / n; r.ty = dy / n;
+    r.seg = k;
+    return r;
+}
+
+// True when s lies within eps (metres) of the boundary between two route
+// segments of different heading: the segment (hence heading) chosen at s is
+// then not decided robustly.
+bool boundary_ambiguous(const double* rx, const double* ry, int P, double h, double s, double eps) {
+    double u = s / h;
+    double j = std::nearbyint(u);
+    if (std::fabs(u - j) * h >= eps) return false;
+    int k = (int)j;
+    if (k <= 0 || k >= P - 1) return false;  // both sides clamp to the same segment
+    double ax = rx[k] - rx[k - 1], ay = ry[k] - ry[k - 1];
+    double bx = rx[k + 1] - rx[k], by = ry[k + 1] - ry[k];
+    return std::fabs(cross(ax, ay, bx, by)) > 1e-12 * (ax * ax + ay * ay);
+}
+
+struct IdmOut { St<double> st; double s; int lead; bool band; };
+
+IdmOut idm_agent(const ob_params* p, const ob_batch* b, int a0, int a1, int i,
+                 const ob_state* in) {
+    const double h = p->route_h, eps = p->band;
+    const int ro = b->route_off[i], P = b->route_off[i + 1] - ro;
+    const double* rx = b->route_x + ro;
+    const double* ry = b->route_y + ro;
+    const double xi = in->x[i], yi = in->y[i], si = in->s[i];
+    const double v = std::sqrt(in->vx[i] * in->vx[i] + in->vy[i] * in->vy[i]);
+    const double Li = b->L[i], Wi = b->W[i];
+    const int K = p->idm_K;
+    bool band = false;
+
+    // Lead-search samples ahead of the front bumper along the route.
+    std::vector<RoutePt> q(K + 1);
+    for (int k = 1; k <= K; ++k) q[k] = route_eval(rx, ry, P, h, si + 0.5 * Li + p->idm_dq * k);
+
+    // Candidates: another valid agent whose box, widened by half this agent's
+    // width, contains a sample.  first_hit = first such sample.
+    int lead = -1, lead_hit = -1;
+    double g1 = kInf, g2 = kInf, raw1 = kInf, raw2 = kInf;
+    std::vector<double> nonrobust_gaps;
+    for (int j = a0; j < a1; ++j) {
+        if (j == i || !b->valid[j]) continue;
+        double cj = std::cos(in->th[j]), sj = std::sin(in->th[j]);
+        int first = -1;
+        bool firm = false, maybe = false;
+        for (int k = 1; k <= K; ++k) {
+            double rxq = q[k].x - in->x[j], ryq = q[k].y - in->y[j];
+            double pu = std::fabs(rxq * cj + ryq * sj);
+            double pn = std::fabs(-rxq * sj + ryq * cj);
+            double m = std::min(0.5 * b->L[j] + 0.5 * Wi - pu, 0.5 * b->W[j] + 0.5 * Wi - pn);
+            if (m >= 0 && first < 0) first = k;
+            if (m >= eps) firm = true;
+            if (std::fabs(m) < eps) maybe = true;
+        }
+        double dist = std::sqrt((in->x[j] - xi) * (in->x[j] - xi) + (in->y[j] - yi) * (in->y[j] - yi));
+        double raw = dist - 0.5 * (Li + b->L[j]);
+        double g = std::max(p->gap_min, raw);
+        if (maybe && !firm) nonrobust_gaps.push_back(g);
+        if (first < 0) continue;
+        if (g < g1) {
+            g2 = g1; raw2 = raw1; g1 = g; raw1 = raw; lead = j; lead_hit = first;
+        } else if (g < g2) {
+            g2 = g; raw2 = raw;
+        }
+    }
+    // Ambiguity band: a candidate that a float32 test could add or drop and
+    // that could win; a near tie of the two smallest gaps (unless both sit on
+    // the clamp); an uncertain first-hit sample of the lead.
+    for (double g : nonrobust_gaps)
+        if (lead < 0 || g <= g1 + eps) band = true;
+    if (lead >= 0 && g2 - g1 < eps && !(raw1 < p->gap_min - eps && raw2 < p->gap_min - eps))
+        band = true;
+    double vlead = 0;
+    if (lead >= 0) {
+        double cj = std::cos(in->th[lead]), sj = std::sin(in->th[lead]);
+        for (int k = 1; k <= lead_hit; ++k) {
+            double rxq = q[k].x - in->x[lead], ryq = q[k].y - in->y[lead];
+            double pu = std::fabs(rxq * cj + ryq * sj);
+            double pn = std::fabs(-rxq * sj + ryq * cj);
+            double m = std::min(0.5 * b->L[lead] + 0.5 * Wi - pu, 0.5 * b->W[lead] + 0.5 * Wi - pn);
+            if (std::fabs(m) < eps) band = true;
+        }
+        if (boundary_ambiguous(rx, ry, P, h, si + 0.5 * Li + p->idm_dq * lead_hit, eps)) band = true;
+        vlead = in->vx[lead] * q[lead_hit].tx + in->vy[lead] * q[lead_hit].ty;
+    }
+
+    // Textbook IDM acceleration (delta = 4).
+    const double v0 = b->idm_v0[i];
+    double r4 = (v / v0) * (v / v0) * (v / v0) * (v / v0);
+    double acc;
+    if (lead >= 0) {
+        double dv = v - vlead;
+        double sstar = p->idm_s0 + std::max(0.0, v * p->idm_T + v * dv / (2 * std::sqrt(p->idm_amax * p->idm_b)));
+        acc = p->idm_amax * (1 - r4 - (sstar / g1) * (sstar / g1));
+    } else {
+        acc = p->idm_amax * (1 - r4);
+    }
+    // Advance along the route with the trapezoidal distance of the new speed.
+    double vn = std::max(0.0, v + acc * p->dt);
+    double sn = si + 0.5 * (v + vn) * p->dt;
+    RoutePt r = route_eval(rx, ry, P, h, sn);
+    if (boundary_ambiguous(rx, ry, P, h, sn, eps)) band = true;
+    IdmOut o;
+    o.st.x = r.x; o.st.y = r.y;
+    o.st.th = std::atan2(r.ty, r.tx);
+    o.st.vx = vn * std::cos(o.st.th);
+    o.st.vy = vn * std::sin(o.st.th);
+    o.s = sn;
+    o.lead = lead;
+    o.band = band;
+    return o;
+}
+
+void copy_agent(const ob_state* in, ob_state* out, int g) {
+    out->x[g] = in->x[g]; out->y[g] = in->y[g]; out->th[g] = in->th[g];
+    out->vx[g] = in->vx[g]; out->vy[g] = in->vy[g]; out->s[g] = in->s[g];
+}
+
+int transition_scene(const ob_params* p, const ob_batch* b, int s, const ob_state* in,
+                     const double* act, const uint8_t* ctrl, ob_state* out,
+                     uint8_t* band_idm, int32_t* lead_out) {
+    const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1], N = b->N_tot;
+    for (int g = a0; g < a1; ++g) {
+        if (band_idm) band_idm[g] = 0;
+        if (lead_out) lead_out[g] = -1;
+        const int kind = b->kind[g];
+        bool moves = b->valid[g] && (kind == 2 || !ctrl || ctrl[g]);
+        if (!moves) { copy_agent(in, out, g); continue; }
+        St<double> cur = {in->x[g], in->y[g], in->th[g], in->vx[g], in->vy[g]};
+        if (kind == 0) {
+            St<double> n = bicycle_forward(cur, act[g], act[N + g], p->dt);
+            out->x[g] = n.x; out->y[g] = n.y; out->th[g] = n.th; out->vx[g] = n.vx; out->vy[g] = n.vy;
+            out->s[g] = in->s[g];
+        } else if (kind == 1) {
+            St<double> n = delta_forward(cur, act[g], act[N + g], act[2 * N + g], p->dt);
+            out->x[g] = n.x; out->y[g] = n.y; out->th[g] = n.th; out->vx[g] = n.vx; out->vy[g] = n.vy;
+            out->s[g] = in->s[g];
+        } else if (kind == 2) {
+            if (b->route_off[g + 1] - b->route_off[g] < 2) return -1;
+            IdmOut o = idm_agent(p, b, a0, a1, g, in);
+            out->x[g] = o.st.x; out->y[g] = o.st.y; out->th[g] = o.st.th;
+            out->vx[g] = o.st.vx; out->vy[g] = o.st.vy; out->s[g] = o.s;
+            if (band_idm) band_idm[g] = o.band;
+            if (lead_out) lead_out[g] = o.lead;
+        } else {
+            return -1;
+        }
+    }
+    return 0;
+}
+
+// Metrics of one scene (Sec. 3.4) on state st, log row t.
+void metrics_scene(const ob_params* p, const ob_batch* b, int s, const ob_state* st, int t,
+                   double* ov, double* off, double* logdiv, uint8_t* flags, int32_t* reward) {
+    const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1], N = b->N_tot;
+    const double eps = p->band;
+    std::vector<Box<double>> box(a1 - a0);
+    for (int g = a0; g < a1; ++g) box[g - a0] = make_box(st->x[g], st->y[g], st->th[g], b->L[g], b->W[g]);
+    std::vector<Seg> segs = scene_segments(b, s);
+    int32_t r = 0;
+    for (int g = a0; g < a1; ++g) {
+        if (!b->valid[g]) { ov[g] = off[g] = logdiv[g] = 0; flags[g] = 0; continue; }
+        // Collision: largest SAT depth against any other valid agent.
+        double o = -kInf;
+        for (int j = a0; j < a1; ++j) {
+            if (j == g || !b->valid[j]) continue;
+            int lo = std::min(g, j), hi = std::max(g, j);
+            o = std::max(o, sat_depth(box[lo - a0], box[hi - a0]));
+        }
+        // Off-road: largest signed distance over the four box corners.
+        const Box<double>& B = box[g - a0];
+        double f = -kInf;
+        int amb_any = 0;
+        const double sl[4] = {1, 1, -1, -1}, sw[4] = {1, -1, -1, 1};
+        for (int c = 0; c < 4; ++c) {
+            double px = B.cx + sl[c] * B.hl * B.c - sw[c] * B.hw * B.s;
+            double py = B.cy + sl[c] * B.hl * B.s + sw[c] * B.hw * B.c;
+            int amb = 0;
+            f = std::max(f, point_sd(segs, px, py, eps, &amb, nullptr));
+            amb_any |= amb;
+        }
+        // Log divergence: L2 distance to the logged position at the same step.
+        double dx = st->x[g] - b->log_x[(size_t)t * N + g];
+        double dy = st->y[g] - b->log_y[(size_t)t * N + g];
+        ov[g] = o;
+        off[g] = f;
+        logdiv[g] = std::sqrt(dx * dx + dy * dy);
+        uint8_t fl = 0;
+        if (o > 0) fl |= 1;
+        if (f > 0) fl |= 2;
+        if (std::fabs(o) < eps) fl |= 4;
+        if (std::fabs(f) < eps || amb_any) fl |= 8;
+        flags[g] = fl;
+        r -= (o > 0) + (f > 0);
+    }
+    reward[s] = r;
+}
+
+// The differentiable loss of one scene, generic in the scalar type.
+template <class T, class ActFn>
+T scene_loss(const ob_params* p, const ob_batch* b, int s, const ob_state* st0, ActFn act,
+             int t0, int nsteps, double lambda, double tau) {
+    const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1], n = a1 - a0, N = b->N_tot;
+    std::vector<St<T>> cur(n);
+    for (int g = a0; g < a1; ++g)
+        cur[g - a0] = {T(st0->x[g]), T(st0->y[g]), T(st0->th[g]), T(st0->vx[g]), T(st0->vy[g])};
+    T loss = T(0.0);
+    std::vector<Box<T>> box(n);
+    for (int k = 0; k < nsteps; ++k) {
+        for (int g = a0; g < a1; ++g) {
+            if (!b->valid[g]) continue;
+            if (b->kind[g] == 0)
+                cur[g - a0] = bicycle_forward(cur[g - a0], act(k, 0, g), act(k, 1, g), p->dt);
+            else
+                cur[g - a0] = delta_forward(cur[g - a0], act(k, 0, g), act(k, 1, g), act(k, 2, g), p->dt);
+        }
+        const int tl = t0 + k + 1;
+        for (int g = a0; g < a1; ++g) {
+            if (!b->valid[g]) continue;
+            T dx = cur[g - a0].x - b->log_x[(size_t)tl * N + g];
+            T dy = cur[g - a0].y - b->log_y[(size_t)tl * N + g];
+            loss += dx * dx + dy * dy;
+            box[g - a0] = make_box(cur[g - a0].x, cur[g - a0].y, cur[g - a0].th, b->L[g], b->W[g]);
+        }
+        for (int i = a0; i < a1; ++i) {
+            if (!b->valid[i]) continue;
+            for (int j = i + 1; j < a1; ++j) {
+                if (!b->valid[j]) continue;
+                T d = sat_depth(box[i - a0], box[j - a0]);
+                loss += lambda * tau * softplus(d / tau);
+            }
+        }
+    }
+    return loss;
+}
+
+bool scene_differentiable(const ob_batch* b, int s) {
+    for (int g = b->agent_off[s]; g < b->agent_off[s + 1]; ++g)
+        if (b->valid[g] && b->kind[g] != 0 && b->kind[g] != 1) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int oracle_transition(const ob_params* p, const ob_batch* b, int s0, int s1,
+                      const ob_state* in, const double* act, const uint8_t* ctrl,
+                      ob_state* out, uint8_t* band_idm, int32_t* lead) {
+    if (!p || !b || !in || !out || s0 < 0 || s1 > b->S || s0 > s1) return -1;
+    for (int s = s0; s < s1; ++s)
+        if (transition_scene(p, b, s, in, act, ctrl, out, band_idm, lead)) return -1;
+    return 0;
+}
+
+int oracle_metrics(const ob_params* p, const ob_batch* b, int s0, int s1,
+                   const ob_state* st, int t, ob_metrics* m) {
+    if (!p || !b || !st || !m || s0 < 0 || s1 > b->S || s0 > s1 || t < 0 || t >= b->T_log) return -1;
+    for (int s = s0; s < s1; ++s)
+        metrics_scene(p, b, s, st, t, m->ov, m->off, m->logdiv, m->flags, m->reward);
+    return 0;
+}
+
+int oracle_rollout(const ob_params* p, const ob_batch* b, int s0, int s1, ob_state* st,
+                   const double* act_seq, int t0, int T, ob_metrics* mseq, int nthreads) {
+    if (!p || !b || !st || !act_seq || !mseq || s0 < 0 || s1 > b->S || s0 > s1) return -1;
+    if (t0 < 0 || t0 + T > b->T_log - 1) return -1;
+    const int N = b->N_tot, S = b->S;
+    int status = 0;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+    for (int s = s0; s < s1; ++s) {
+        const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1];
+        // Scratch next-state arrays indexed by the global agent index.
+        std::vector<double> buf(6 * (size_t)N);
+        ob_state nxt = {buf.data(), buf.data() + N, buf.data() + 2 * N, buf.data() + 3 * N,
+                        buf.data() + 4 * N, buf.data() + 5 * N};
+        for (int k = 0; k < T; ++k) {
+            if (transition_scene(p, b, s, st, act_seq + (size_t)k * 3 * N, nullptr, &nxt, nullptr, nullptr)) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                status = -1;
+                break;
+            }
+            for (int g = a0; g < a1; ++g) copy_agent(&nxt, st, g);
+            size_t o = (size_t)k * N;
+            metrics_scene(p, b, s, st, t0 + k + 1, mseq->ov + o, mseq->off + o, mseq->logdiv + o,
+                          mseq->flags + o, mseq->reward + (size_t)k * S);
+        }
+    }
+    return status;
+}
+
+double oracle_box_depth(const double* A, const double* B) {
+    Box<double> a = make_box(A[0], A[1], A[2], A[3], A[4]);
+    Box<double> c = make_box(B[0], B[1], B[2], B[3], B[4]);
+    return sat_depth(a, c);
+}
+
+double oracle_point_sd(const ob_params* p, const ob_batch* b, int s, double px, double py,
+                       int* ambiguous, int32_t* seg_out) {
+    std::vector<Seg> g = scene_segments(b, s);
+    int idx = -1;
+    double r = point_sd(g, px, py, p->band, ambiguous, &idx);
+    if (seg_out) *seg_out = idx >= 0 ? g[idx].k : -1;
+    return r;
+}
+
+double oracle_loss(const ob_params* p, const ob_batch* b, int s, const ob_state* st0,
+                   const double* act_seq, int t0, int T, double lambda, double tau) {
+    if (!scene_differentiable(b, s) || t0 < 0 || t0 + T > b->T_log - 1) return std::nan("");
+    const int N = b->N_tot;
+    auto act = [&](int k, int c, int g) { return act_seq[((size_t)k * 3 + c) * N + g]; };
+    return scene_loss<double>(p, b, s, st0, act, t0, T, lambda, tau);
+}
+
+int oracle_loss_grad(const ob_params* p, const ob_batch* b, int s, const ob_state* st0,
+                     const double* act_seq, int t0, int T, double lambda, double tau, int n,
+                     const int32_t* dir_t, const int32_t* dir_c, const int32_t* dir_g, double* grad) {
+    if (!scene_differentiable(b, s) || t0 < 0 || t0 + T > b->T_log - 1) return -1;
+    const int N = b->N_tot;
+    for (int q = 0; q < n; ++q) {
+        const int tq = dir_t[q], cq = dir_c[q], gq = dir_g[q];
+        auto act = [&](int k, int c, int g) {
+            double v = act_seq[((size_t)k * 3 + c) * N + g];
+            return Dual(v, (k == tq && c == cq && g == gq) ? 1.0 : 0.0);
+        };
+        grad[q] = scene_loss<Dual>(p, b, s, st0, act, t0, T, lambda, tau).d;
+    }
+    return 0;
+}
+
+}  // extern "C"

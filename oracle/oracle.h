@@ -1,0 +1,128 @@
+/*
+ * FP64 CPU oracle for the batched closed-loop driving-simulator step
+ * (Waymax, arXiv 2310.08710).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU
+ * baseline leg of the benchmark may load this library.  The product path (the
+ * CUDA library behind include/wsim.h) never calls it, shares no source with it
+ * and has no CPU fallback through it.
+ *
+ * Every quantity is IEEE double.  Inputs arrive as doubles that the caller
+ * up-casts from the same float32 arrays the GPU path reads, so both sides see
+ * identical inputs.  Functions are plain definitions by brute force (all pairs,
+ * all road-edge segments); the one heuristic (IDM route following) follows its
+ * steps in order.  Citations name the paper's section, equation or table.
+ *
+ * Pins: every function here is checked in tests/test_oracle_*.py against
+ * closed forms, brute force or invariants that do not reuse this code
+ * (analytic straight-line and constant-curvature trajectories, Sutherland-
+ * Hodgman clipping, dense point sampling of polylines, textbook IDM
+ * equilibria, central finite differences).
+ */
+#ifndef WSIM_ORACLE_H
+#define WSIM_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Method constants (the caller passes the same numbers to the GPU path). */
+typedef struct {
+    double dt;          /* step length, 0.1 s (Sec. 3.1 read as 10 Hz)          */
+    double idm_amax;    /* IDM maximum acceleration a (m/s^2)                   */
+    double idm_b;       /* IDM comfortable deceleration b (m/s^2)               */
+    double idm_T;       /* IDM time headway T (s)                               */
+    double idm_s0;      /* IDM minimum gap s0 (m)                               */
+    double idm_dq;      /* spacing of the lead-search samples along the route   */
+    double route_h;     /* parameter length of one route segment (m)            */
+    double gap_min;     /* lower clamp of the bumper gap (m)                    */
+    double band;        /* ambiguity band for discrete decisions (m)            */
+    int32_t idm_K;      /* number of lead-search samples                        */
+    int32_t pad_;
+} ob_params;
+
+/* A batch of scenes in CSR form.  Scene s owns agents [agent_off[s],
+ * agent_off[s+1]) and roadgraph points [rg_off[s], rg_off[s+1]).  Agent g
+ * owns route points [route_off[g], route_off[g+1]) (empty for policy agents).
+ * Logs are time-major: log_x[t * N_tot + g]. */
+typedef struct {
+    int32_t S, N_tot, T_log, pad_;
+    const int32_t *agent_off;          /* [S+1]  */
+    const int32_t *rg_off;             /* [S+1]  */
+    const double  *L, *W, *idm_v0;     /* [N_tot] */
+    const uint8_t *valid, *kind;       /* [N_tot] kind: 0 bicycle, 1 delta, 2 IDM */
+    const int32_t *route_off;          /* [N_tot+1] */
+    const double  *route_x, *route_y;  /* [route_off[N_tot]] */
+    const double  *rg_x, *rg_y;        /* [R_tot] */
+    const int32_t *rg_poly;            /* [R_tot] polyline id */
+    const uint8_t *rg_type, *rg_valid; /* [R_tot] type 1 = road edge */
+    const double  *log_x, *log_y;      /* [T_log][N_tot] */
+} ob_batch;
+
+/* Dynamic state per agent, [N_tot] each.  s is the IDM route cursor. */
+typedef struct { double *x, *y, *th, *vx, *vy, *s; } ob_state;
+
+/* Per-step metrics, [N_tot] each (reward [S]).
+ * flags: bit0 collision, bit1 off-road, bit2 overlap band, bit3 off-road
+ * band (boolean not gated in parity), bits 4.. reserved. */
+typedef struct {
+    double  *ov, *off, *logdiv;
+    uint8_t *flags;
+    int32_t *reward;
+} ob_metrics;
+
+/* One transition t -> t+1 for scenes [s0, s1) (Sec. 4 step(): all actions are
+ * resolved from state t, then every agent moves).  act is [3][N_tot]:
+ * (a, kappa, -) for bicycle agents, (dx, dy, dtheta) for delta agents;
+ * IDM agents ignore it.  ctrl may be NULL (all controlled); an uncontrolled
+ * or invalid agent keeps its state.  band_idm[g] (may be NULL) is set to 1
+ * when an IDM decision of agent g lies inside the ambiguity band; lead[g]
+ * (may be NULL) receives the chosen lead agent (global index) or -1. */
+int oracle_transition(const ob_params *p, const ob_batch *b, int s0, int s1,
+                      const ob_state *in, const double *act, const uint8_t *ctrl,
+                      ob_state *out, uint8_t *band_idm, int32_t *lead);
+
+/* Metrics of state st at time index t (log row t) for scenes [s0, s1):
+ * overlap (Sec. 3.4 collision), off-road (Sec. 3.4), log divergence
+ * (Sec. 3.4 displacement error) and the sparse reward (Sec. 5.2). */
+int oracle_metrics(const ob_params *p, const ob_batch *b, int s0, int s1,
+                   const ob_state *st, int t, ob_metrics *m);
+
+/* Free-running rollout of T steps from time index t0 for scenes [s0, s1):
+ * st holds state t0 on entry and state t0+T on exit; act_seq is
+ * [T][3][N_tot]; metric arrays are [T][N_tot] (reward [T][S]).  Scenes are
+ * split over nthreads OpenMP threads (<= 0: all cores). */
+int oracle_rollout(const ob_params *p, const ob_batch *b, int s0, int s1,
+                   ob_state *st, const double *act_seq, int t0, int T,
+                   ob_metrics *mseq, int nthreads);
+
+/* Signed SAT depth of two boxes (centre, heading, length, width):
+ * > 0 iff the boxes overlap (then it is the minimum translation distance). */
+double oracle_box_depth(const double *box_a, const double *box_b);
+
+/* Signed distance of point (px, py) to the road edges of scene s (> 0 means
+ * off road); *ambiguous is set when a near tie between non-adjacent
+ * segments of opposite sign lies inside the band.  Returns -inf when the
+ * scene has no road-edge segment; *seg_out (may be NULL) receives the global
+ * roadgraph index of the winning segment's start point, or -1. */
+double oracle_point_sd(const ob_params *p, const ob_batch *b, int s,
+                       double px, double py, int *ambiguous, int32_t *seg_out);
+
+/* Differentiable loss of one scene over T steps (bicycle / delta agents only):
+ * L = sum_t sum_i d_i(t)^2 + lambda * sum_t sum_{i<j} tau*softplus(d_ij/tau). */
+double oracle_loss(const ob_params *p, const ob_batch *b, int s,
+                   const ob_state *st0, const double *act_seq, int t0, int T,
+                   double lambda, double tau);
+
+/* dL/d act_seq[t][c][g] for n directions by forward-mode dual numbers
+ * (one pass per direction), written to grad[n]. */
+int oracle_loss_grad(const ob_params *p, const ob_batch *b, int s,
+                     const ob_state *st0, const double *act_seq, int t0, int T,
+                     double lambda, double tau, int n, const int32_t *dir_t,
+                     const int32_t *dir_c, const int32_t *dir_g, double *grad);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

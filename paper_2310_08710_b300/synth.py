@@ -1,0 +1,337 @@
+"""Seeded synthetic scenes shaped like the Waymo Open Motion Dataset workloads.
+
+The paper simulates WOMD scenes (Sec. 3.1: 9 s logs at 10 Hz, the first second
+is history, up to 128 objects per scene; roadgraph = sampled road/lane
+polylines, Sec. 3.2).  The dataset is not available here, so scenes are drawn
+from seeded distributions of the same shape.  This module holds no arithmetic
+of the simulated method: logs are integrated with the generator's own
+continuous-time unicycle model, and delta actions are a random walk, so neither
+side's dynamics is reused to make its own inputs.
+
+Every scene s of a batch is drawn from its own counter-based seed
+``splitmix64(base_seed ^ s)`` (SplitMix64 of Steele, Lea and Flood, 2014), so
+any subset of scenes can be regenerated bit-identically on its own.
+
+Arrays are float32 / int32 / uint8 in the layouts the C ABI takes:
+agents and roadgraph points in CSR over scenes, logs time-major
+``[T_log][N_tot]``, actions ``[T][3][N_tot]``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Dict, Optional, Sequence, Tuple, Union
+
+import numpy as np
+
+KIND_BICYCLE, KIND_DELTA, KIND_IDM = 0, 1, 2
+RG_EDGE, RG_LANE = 1, 2
+T_LOG = 91          # 9.1 s at 10 Hz: 11 history steps + 80 simulated
+T0 = 10             # index of the last history step (the simulation start)
+T_ROLLOUT = 80
+DT = 0.1
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x: int) -> int:
+    """One output of SplitMix64 for state x (Steele, Lea, Flood 2014)."""
+    x = (x + 0x9E3779B97F4A7C15) & _M64
+    z = x
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    return z ^ (z >> 31)
+
+
+def scene_rng(base_seed: int, scene: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(splitmix64((base_seed ^ scene) & _M64)))
+
+
+IntSpec = Union[int, Tuple[int, int]]
+
+
+@dataclass(frozen=True)
+class Workload:
+    """Shape of one workload (the five benchmark configurations below)."""
+    name: str
+    S: int                      # scenes
+    N: IntSpec                  # agents per scene, or inclusive range
+    R: IntSpec                  # roadgraph points per scene, or inclusive range
+    driver: str = "bicycle"     # "bicycle": all random bicycle; "idm": ego policy + IDM
+    ego_delta_half: bool = False  # scenes < S/2 drive the ego with delta actions
+    T: int = T_ROLLOUT
+
+
+WORKLOADS: Dict[int, Workload] = {
+    0: Workload("single scene 1x32x80, 2k roadgraph", 1, 32, 2000),
+    1: Workload("batch 1024x128x80, 20k roadgraph, IDM sim agents", 1024, 128, 20000, driver="idm"),
+    2: Workload("uneven 4096 x U{8..128} x80, U{1k..30k} roadgraph", 4096, (8, 128), (1000, 30000)),
+    3: Workload("differentiable 256x64x80, 2k roadgraph", 256, 64, 2000),
+    4: Workload("sweep 16384x128x80, 30k roadgraph, delta/bicycle ego + IDM", 16384, 128, 30000,
+                driver="idm", ego_delta_half=True),
+}
+
+
+def _draw(rng: np.random.Generator, spec: IntSpec) -> int:
+    if isinstance(spec, tuple):
+        return int(rng.integers(spec[0], spec[1] + 1))
+    return int(spec)
+
+
+def _polylines(rng, n_pts, start, heading, arc, radius, turn, spacing=0.5):
+    """Points of many polylines at fixed chord spacing: straight or circular arcs.
+
+    Vectorised over all points: polyline p has n_pts[p] points starting at
+    start[p] with initial heading heading[p]; arcs turn by 2*asin(spacing/2r)
+    per point so every chord has length `spacing`.
+    """
+    n_pts = np.asarray(n_pts, dtype=np.int64)
+    pid = np.repeat(np.arange(len(n_pts)), n_pts)
+    first = np.concatenate([[0], np.cumsum(n_pts)[:-1]])
+    k = np.arange(n_pts.sum()) - np.repeat(first, n_pts)
+    h = heading[pid]
+    x0, y0 = start[pid, 0], start[pid, 1]
+    r = radius[pid]
+    sg = turn[pid]
+    dphi = 2.0 * np.arcsin(spacing / (2.0 * r))
+    phi = h + sg * k * dphi
+    cx = x0 - sg * r * np.sin(h)
+    cy = y0 + sg * r * np.cos(h)
+    ax = cx + sg * r * np.sin(phi)
+    ay = cy - sg * r * np.cos(phi)
+    sx = x0 + spacing * k * np.cos(h)
+    sy = y0 + spacing * k * np.sin(h)
+    a = arc[pid]
+    px = np.where(k == 0, x0, np.where(a, ax, sx))
+    py = np.where(k == 0, y0, np.where(a, ay, sy))
+    return px, py, pid
+
+
+def _roadgraph(rng, R):
+    lens = []
+    tot = 0
+    while tot < R:
+        n = int(rng.integers(20, 201))
+        n = min(n, R - tot)
+        lens.append(n)
+        tot += n
+    P = len(lens)
+    start = rng.uniform(0.0, 200.0, size=(P, 2))
+    heading = rng.uniform(-np.pi, np.pi, size=P)
+    arc = rng.random(P) < 0.5
+    radius = rng.uniform(10.0, 100.0, size=P)
+    turn = np.where(rng.random(P) < 0.5, -1.0, 1.0)
+    edge = rng.random(P) < 0.3
+    x, y, pid = _polylines(rng, lens, start, heading, arc, radius, turn)
+    rtype = np.where(edge[pid], RG_EDGE, RG_LANE).astype(np.uint8)
+    return (x.astype(np.float32), y.astype(np.float32), pid.astype(np.int32), rtype,
+            np.ones(R, dtype=np.uint8))
+
+
+def _log_controls(rng, n):
+    """Per-agent parameters of the smooth log controls (see _integrate_logs)."""
+    return np.stack([rng.uniform(0.0, 2.0, n), rng.uniform(0.05, 0.2, n), rng.uniform(0.0, 2 * np.pi, n),
+                     rng.uniform(0.0, 0.05, n), rng.uniform(0.05, 0.2, n), rng.uniform(0.0, 2 * np.pi, n)])
+
+
+def _integrate_logs(ctl, x0, y0, th0, v0, T_log=T_LOG, t0=T0, sub=10):
+    """Logged x, y from a continuous unicycle with smooth seeded controls.
+
+    speed' = A sin(2 pi f t + phi) (speed kept >= 0), heading' = K sin(2 pi fk
+    t + phik) * speed, integrated with `sub` midpoint substeps per 0.1 s.
+    History steps before t0 hold the t0 pose.
+    """
+    A, f, ph, K, fk, phk = ctl
+    n = len(x0)
+    lx = np.empty((T_log, n), dtype=np.float32)
+    ly = np.empty((T_log, n), dtype=np.float32)
+    x, y, th, v = (np.asarray(a, dtype=np.float64).copy() for a in (x0, y0, th0, v0))
+    lx[: t0 + 1] = x
+    ly[: t0 + 1] = y
+    h = DT / sub
+    for t in range(t0 + 1, T_log):
+        for j in range(sub):
+            tm = (t - t0 - 1) * DT + (j + 0.5) * h
+            acc = A * np.sin(2 * np.pi * f * tm + ph)
+            kap = K * np.sin(2 * np.pi * fk * tm + phk)
+            vm = np.maximum(0.0, v + 0.5 * h * acc)
+            thm = th + 0.5 * h * kap * v
+            x += h * vm * np.cos(thm)
+            y += h * vm * np.sin(thm)
+            th += h * kap * vm
+            v = np.maximum(0.0, v + h * acc)
+        lx[t] = x
+        ly[t] = y
+    return lx, ly
+
+
+def _scene(rng, wl: Workload, s: int, N: Optional[int], R: Optional[int]):
+    N = _draw(rng, wl.N) if N is None else N
+    R = _draw(rng, wl.R) if R is None else R
+    T = wl.T
+    # Agents at the simulation start (t0).
+    x = rng.uniform(0.0, 200.0, N)
+    y = rng.uniform(0.0, 200.0, N)
+    th = rng.uniform(-np.pi, np.pi, N)
+    sp = rng.uniform(0.0, 20.0, N)
+    L = rng.uniform(4.0, 5.5, N)
+    W = rng.uniform(1.8, 2.2, N)
+    valid = (rng.random(N) >= 0.1).astype(np.uint8)
+    valid[0] = 1  # the ego
+    kind = np.full(N, KIND_BICYCLE, dtype=np.uint8)
+    if wl.driver == "idm":
+        kind[1:] = KIND_IDM
+    if wl.ego_delta_half and s < wl.S // 2:
+        kind[0] = KIND_DELTA
+    v0 = rng.uniform(8.0, 15.0, N)
+    # Positions are rounded to float32 first so that velocities, routes and
+    # logs start from the exact pose both sides see.
+    x = x.astype(np.float32).astype(np.float64)
+    y = y.astype(np.float32).astype(np.float64)
+    th = th.astype(np.float32).astype(np.float64)
+    vx = sp * np.cos(th)
+    vy = sp * np.sin(th)
+    # Roadgraph.
+    rg = _roadgraph(rng, R)
+    # IDM routes: each IDM agent's own lane from its start pose, 320 points.
+    idm = np.nonzero(kind == KIND_IDM)[0]
+    n_route = np.zeros(N, dtype=np.int64)
+    n_route[idm] = 320
+    if len(idm):
+        P = len(idm)
+        arc = rng.random(P) < 0.5
+        radius = rng.uniform(20.0, 200.0, P)
+        turn = np.where(rng.random(P) < 0.5, -1.0, 1.0)
+        rx, ry, _ = _polylines(rng, n_route[idm], np.stack([x[idm], y[idm]], 1), th[idm], arc, radius, turn)
+    else:
+        rx = ry = np.zeros(0)
+    # Log controls (integrated for the whole batch at once).
+    ctl = _log_controls(rng, N)
+    # Actions: bicycle a ~ U[-4,4] m/s^2, kappa ~ U[-0.3,0.3] 1/m; delta
+    # agents a random walk of displacements at speeds U[0,20] m/s.
+    act = np.zeros((T, 3, N), dtype=np.float32)
+    act[:, 0, :] = rng.uniform(-4.0, 4.0, (T, N))
+    act[:, 1, :] = rng.uniform(-0.3, 0.3, (T, N))
+    dl = np.nonzero(kind == KIND_DELTA)[0]
+    if len(dl):
+        psi = th[dl] + np.cumsum(rng.uniform(-0.05, 0.05, (T, len(dl))), axis=0)
+        spd = rng.uniform(0.0, 20.0, (T, len(dl)))
+        act[:, 0, dl] = spd * DT * np.cos(psi)
+        act[:, 1, dl] = spd * DT * np.sin(psi)
+        act[:, 2, dl] = rng.uniform(-0.05, 0.05, (T, len(dl)))
+    return dict(
+        N=N, R=R, x=x, y=y, th=th, vx=vx, vy=vy, L=L, W=W, valid=valid, kind=kind, v0=v0,
+        rg=rg, n_route=n_route, rx=rx, ry=ry, ctl=ctl, act=act,
+    )
+
+
+@dataclass
+class SceneBatch:
+    """A batch of scenes in the C ABI's layouts (host numpy arrays)."""
+    cfg: int
+    seed: int
+    scenes: np.ndarray            # scene ids of the source workload
+    S: int
+    N_tot: int
+    T: int
+    agent_off: np.ndarray         # int32 [S+1]
+    rg_off: np.ndarray            # int32 [S+1]
+    L: np.ndarray                 # float32 [N_tot]
+    W: np.ndarray
+    valid: np.ndarray             # uint8
+    kind: np.ndarray              # uint8
+    idm_v0: np.ndarray            # float32
+    route_off: np.ndarray         # int32 [N_tot+1]
+    route_x: np.ndarray           # float32
+    route_y: np.ndarray
+    rg_x: np.ndarray              # float32 [R_tot]
+    rg_y: np.ndarray
+    rg_poly: np.ndarray           # int32
+    rg_type: np.ndarray           # uint8
+    rg_valid: np.ndarray          # uint8
+    log_x: np.ndarray             # float32 [T_LOG][N_tot]
+    log_y: np.ndarray
+    x: np.ndarray                 # float32 [N_tot] state at t0
+    y: np.ndarray
+    th: np.ndarray
+    vx: np.ndarray
+    vy: np.ndarray
+    actions: np.ndarray           # float32 [T][3][N_tot]
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def T_log(self) -> int:
+        return self.log_x.shape[0]
+
+    @property
+    def R_tot(self) -> int:
+        return int(self.rg_off[-1])
+
+    def agent_steps(self) -> int:
+        return self.N_tot * self.T
+
+    def subset(self, idx: Sequence[int]) -> "SceneBatch":
+        """The scenes at positions idx of this batch, as a batch of their own."""
+        idx = np.asarray(idx, dtype=np.int64)
+        a0, a1 = self.agent_off[idx], self.agent_off[idx + 1]
+        r0, r1 = self.rg_off[idx], self.rg_off[idx + 1]
+        ag = np.concatenate([np.arange(a, b) for a, b in zip(a0, a1)]).astype(np.int64)
+        rg = np.concatenate([np.arange(a, b) for a, b in zip(r0, r1)]).astype(np.int64)
+        ro0, ro1 = self.route_off[ag], self.route_off[ag + 1]
+        rt = np.concatenate([np.arange(a, b) for a, b in zip(ro0, ro1)] + [np.zeros(0, np.int64)]).astype(np.int64)
+        off = lambda n: np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
+        return SceneBatch(
+            cfg=self.cfg, seed=self.seed, scenes=self.scenes[idx], S=len(idx), N_tot=len(ag), T=self.T,
+            agent_off=off(a1 - a0), rg_off=off(r1 - r0),
+            L=self.L[ag], W=self.W[ag], valid=self.valid[ag], kind=self.kind[ag], idm_v0=self.idm_v0[ag],
+            route_off=off(ro1 - ro0), route_x=self.route_x[rt], route_y=self.route_y[rt],
+            rg_x=self.rg_x[rg], rg_y=self.rg_y[rg], rg_poly=self.rg_poly[rg], rg_type=self.rg_type[rg],
+            rg_valid=self.rg_valid[rg],
+            log_x=np.ascontiguousarray(self.log_x[:, ag]), log_y=np.ascontiguousarray(self.log_y[:, ag]),
+            x=self.x[ag], y=self.y[ag], th=self.th[ag], vx=self.vx[ag], vy=self.vy[ag],
+            actions=np.ascontiguousarray(self.actions[:, :, ag]),
+        )
+
+
+def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
+               N: Optional[int] = None, R: Optional[int] = None, S: Optional[int] = None,
+               T: Optional[int] = None) -> SceneBatch:
+    """Scenes of workload `cfg` (0-4).
+
+    scenes: ids of the workload's scenes to draw (default all S); a scene's
+    content depends only on (seed, id), so subsets reproduce the full batch.
+    N, R: override agents / roadgraph points per scene (tests use tiny scenes).
+    S: override the scene count of the workload; T: rollout length.
+    """
+    wl = WORKLOADS[cfg]
+    if S is not None:
+        wl = Workload(wl.name, S, wl.N, wl.R, wl.driver, wl.ego_delta_half, wl.T)
+    if T is not None:
+        wl = Workload(wl.name, wl.S, wl.N, wl.R, wl.driver, wl.ego_delta_half, T)
+    ids = np.arange(wl.S) if scenes is None else np.asarray(scenes, dtype=np.int64)
+    parts = [_scene(scene_rng(seed, int(s)), wl, int(s), N, R) for s in ids]
+    Ns = np.array([p["N"] for p in parts], dtype=np.int64)
+    Rs = np.array([p["R"] for p in parts], dtype=np.int64)
+    agent_off = np.concatenate([[0], np.cumsum(Ns)]).astype(np.int32)
+    rg_off = np.concatenate([[0], np.cumsum(Rs)]).astype(np.int32)
+    cat = lambda k, dt: np.concatenate([p[k] for p in parts]).astype(dt)
+    n_route = np.concatenate([p["n_route"] for p in parts])
+    route_off = np.concatenate([[0], np.cumsum(n_route)]).astype(np.int32)
+    x, y, th = cat("x", np.float32), cat("y", np.float32), cat("th", np.float32)
+    vx, vy = cat("vx", np.float32), cat("vy", np.float32)
+    ctl = np.concatenate([p["ctl"] for p in parts], axis=1)
+    log_x, log_y = _integrate_logs(ctl, x, y, th, np.hypot(vx.astype(np.float64), vy.astype(np.float64)))
+    return SceneBatch(
+        cfg=cfg, seed=seed, scenes=ids, S=len(ids), N_tot=int(Ns.sum()), T=wl.T,
+        agent_off=agent_off, rg_off=rg_off,
+        L=cat("L", np.float32), W=cat("W", np.float32), valid=cat("valid", np.uint8),
+        kind=cat("kind", np.uint8), idm_v0=cat("v0", np.float32),
+        route_off=route_off,
+        route_x=np.concatenate([p["rx"] for p in parts]).astype(np.float32),
+        route_y=np.concatenate([p["ry"] for p in parts]).astype(np.float32),
+        rg_x=np.concatenate([p["rg"][0] for p in parts]),
+        rg_y=np.concatenate([p["rg"][1] for p in parts]),
+        rg_poly=np.concatenate([p["rg"][2] for p in parts]),
+        rg_type=np.concatenate([p["rg"][3] for p in parts]),
+        rg_valid=np.concatenate([p["rg"][4] for p in parts]),
+        log_x=log_x, log_y=log_y, x=x, y=y, th=th, vx=vx, vy=vy,
+        actions=np.ascontiguousarray(np.concatenate([p["act"] for p in parts], axis=2)),
+    )
