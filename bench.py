@@ -1,0 +1,303 @@
+#!/usr/bin/env python
+"""Throughput of the batched closed-loop rollout on B300.
+
+One step = one 80-step rollout of the whole scene batch: per step of it,
+action resolution, IDM sim agents, bicycle/delta dynamics, pairwise box
+overlap, off-road signed distance, log divergence and reward (the Step of the
+paper's runtime benchmark, Sec. 5.1, driven for a full episode as in its
+Rollout column).  Metric: agent-steps/s (agent slots x simulated steps per
+second), all scenes on one GPU, inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wsim|reference]
+
+Under torchrun every rank simulates its own batch (different seeds) and the
+value is the total over ranks divided by the slowest rank's time.
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "agent-steps/s (step+overlap+offroad) on 1 B300; BPTT grad steps/s vs plain"
+UNIT = "agent-steps/s"
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
+# FP32 operations per unit of counted work (roofline section).
+FLOPS_PER_EVAL = 15      # corner x road-edge segment distance
+FLOPS_PER_TILE = 10      # culling-tile bound test
+FLOPS_PER_PAIR = 44      # ordered SAT pair
+FLOPS_PER_TEST = 16      # IDM look-ahead sample x box test
+FLOPS_PER_AGENT = 60     # dynamics + log divergence per agent-step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wsim", choices=["wsim", "reference"])
+    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.rows = []
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) == 8:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.t.join(timeout=2)
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        pw = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "wsim" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return ws, rank, local, pg
+
+
+def workload_desc(cfg):
+    from paper_2310_08710_b300 import synth
+    wl = synth.WORKLOADS[cfg]
+    return wl
+
+
+def cpu_baseline(b, seconds: float, reps: int = 1) -> dict:
+    """The FP64 oracle's free-running rollout on host cores, bounded sample."""
+    import oracle
+    cores = os.cpu_count() or 1
+    # about 6e3 agent-steps/s per core on 128-agent IDM scenes
+    per_scene = 0.0
+    probe = b.subset([0])
+    o = oracle.Oracle(probe)
+    t = time.perf_counter()
+    o.rollout(o.initial_state(), probe.actions, 10, 8, nthreads=1)
+    per_scene = (time.perf_counter() - t) * (b.T / 8)
+    n = int(max(1, min(b.S, round(seconds * cores / max(per_scene, 1e-3)))))
+    sub = b.subset(list(range(n)))
+    o = oracle.Oracle(sub)
+    st = o.initial_state()
+    times = []
+    for _ in range(reps):
+        t = time.perf_counter()
+        o.rollout(st, sub.actions, 10, b.T, nthreads=cores)
+        times.append(time.perf_counter() - t)
+    dt = statistics.median(times)
+    return {"value": sub.N_tot * b.T / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {b.S} scenes x {b.T} steps (free-running FP64 rollout, OpenMP over scenes)",
+            "seconds": dt}
+
+
+def run_reference(args, ws, rank, pg):
+    from paper_2310_08710_b300 import synth
+    if rank != 0:
+        return
+    b = synth.make_batch(args.config, seed=args.seed)
+    import oracle
+    cores = os.cpu_count() or 1
+    # size each step so that the whole run stays within a few minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    probe = b.subset([0])
+    o = oracle.Oracle(probe)
+    t = time.perf_counter()
+    o.rollout(o.initial_state(), probe.actions, 10, 8, nthreads=1)
+    per_scene = (time.perf_counter() - t) * (b.T / 8)
+    n = int(max(1, min(b.S, budget * cores / max(per_scene, 1e-3) * 0.8)))
+    sub = b.subset(list(range(n)))
+    o = oracle.Oracle(sub)
+    st = o.initial_state()
+    for _ in range(args.warmup):
+        o.rollout(st, sub.actions, 10, b.T, nthreads=cores)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        o.rollout(st, sub.actions, 10, b.T, nthreads=cores)
+    dt = (time.perf_counter() - t) / args.steps
+    v = sub.N_tot * b.T / dt
+    sample = f"{n} of {b.S} scenes x {b.T} steps per step (free-running FP64 rollout, OpenMP over scenes)"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(args, b),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args, b):
+    wl = workload_desc(args.config)
+    return {"workload": f"config {args.config}: {wl.name}", "scenes": int(b.S),
+            "agents": int(b.N_tot), "rollout_steps": int(b.T), "roadgraph_points": int(b.R_tot),
+            "dt_s": 0.1, "rollout_mode": "persistent step kernel x80, CUDA graph",
+            "l2": "inputs larger than L2 (road-edge segments + routes + logs streamed every rollout)"}
+
+
+def main():
+    args = parse()
+    ws, rank, local, pg = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank, pg)
+        return
+    import torch
+    from paper_2310_08710_b300 import synth, wsim
+    torch.cuda.set_device(local)
+    b = synth.make_batch(args.config, seed=args.seed + 1000 * rank)
+    T, N, S = b.T, b.N_tot, b.S
+    db = wsim.DeviceBatch(b)
+    sim = wsim.Sim(db)
+    st0 = wsim.State.from_batch(b)
+    st = st0.clone()
+    act = torch.as_tensor(b.actions).cuda().contiguous()
+    m = wsim.Metrics(N, S, rows=T)
+    stream = torch.cuda.current_stream()
+
+    def rollout():
+        st.data.copy_(st0.data)
+        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_GRAPH)
+
+    # Work counters of one rollout (untimed) for the roofline numerator.
+    sim.set_counting(True)
+    rollout()
+    cnt = sim.counters()
+    sim.set_counting(False)
+    for _ in range(max(3, args.warmup)):
+        rollout()
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+
+    clk = ClockSampler(local)
+    time.sleep(0.5)
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        rollout()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    if pg:
+        pg.barrier()
+    clocks = clk.stop()
+    assert sim.status() == 0
+
+    # End to end through the public API: pinned host inputs in, metrics out.
+    h_act = torch.as_tensor(b.actions).pin_memory()
+    h_st = st0.data.cpu().pin_memory()
+    h_rew = torch.empty((T, S), dtype=torch.int32).pin_memory()
+    h_flags = torch.empty((T, N), dtype=torch.uint8).pin_memory()
+    for _ in range(2):
+        act.copy_(h_act, non_blocking=True)
+        st.data.copy_(h_st, non_blocking=True)
+        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_GRAPH)
+        h_rew.copy_(m.reward, non_blocking=True)
+        h_flags.copy_(m.flags, non_blocking=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        act.copy_(h_act, non_blocking=True)
+        st.data.copy_(h_st, non_blocking=True)
+        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_GRAPH)
+        h_rew.copy_(m.reward, non_blocking=True)
+        h_flags.copy_(m.flags, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+    h2d = h_act.numel() * 4 + h_st.numel() * 4
+    d2h = h_rew.numel() * 4 + h_flags.numel()
+
+    units = N * T
+    if pg:
+        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms, ms_e2e = t.tolist()
+        u = torch.tensor([units], dtype=torch.float64, device="cuda")
+        pg.all_reduce(u)
+        units = u.item()
+    if rank != 0:
+        return
+    value = units / (ms / 1e3)
+    flops = (FLOPS_PER_EVAL * cnt[0] + FLOPS_PER_TILE * cnt[1] + FLOPS_PER_PAIR * cnt[2] + FLOPS_PER_TEST * cnt[3]
+             + FLOPS_PER_AGENT * N * T) / T
+    launch_ms = ms / T  # whole graph per step kernel: includes the tiny memset nodes
+    achieved = flops / (launch_ms / 1e3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "config": config_dict(args, b),
+        "roofline": {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
+                     "flops_per_launch": flops, "launch_ms": launch_ms,
+                     "counts_per_rollout": {"corner_segment_evals": int(cnt[0]), "tile_tests": int(cnt[1]),
+                                            "sat_pairs": int(cnt[2]), "idm_sample_tests": int(cnt[3])}},
+        "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": args.steps * T,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(b, args.cpu_sample_seconds)
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * wsim: batched closed-loop driving-simulator step on one B300 (sm_103a).
+ *
+ * C ABI of libwsim.so.  It implements the data-parallel hot path of the
+ * Waymax simulator (arXiv 2310.08710): per agent, bicycle and delta dynamics
+ * (App. A.1) and IDM route-following sim agents (Sec. 3.5); per scene, the
+ * pairwise rotated-box overlap (Sec. 3.4, collision), the signed distance of
+ * each box corner to the oriented road edges (Sec. 3.4, off-road), the log
+ * divergence (Sec. 3.4, displacement error) and the sparse reward (Sec. 5.2);
+ * an 80-step rollout (Sec. 5.1, Rollout) and its adjoint for BPTT (the
+ * differentiable simulation of Sec. 6).
+ *
+ * Calling conventions shared by every entry point
+ * -----------------------------------------------
+ *  - Pointers named in the structs below are DEVICE pointers into memory the
+ *    caller owns (e.g. torch tensors).  The library never frees them and keeps
+ *    no reference to them after a call returns, except the scene batch given
+ *    to wsim_init, which must stay alive and unchanged until wsim_destroy.
+ *  - Layouts are structure-of-arrays of float32 / int32 / uint8.  Agents and
+ *    roadgraph points are in CSR form over scenes (agent_off, rg_off).
+ *    Per-step arrays are indexed by the global agent index g in [0, N_tot).
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default
+ *    stream.  Calls enqueue work and return without synchronising, except
+ *    wsim_init, wsim_status and wsim_destroy, which synchronise the stream.
+ *  - Every call returns WSIM_OK (0) or a negative WSIM_E* code.  Errors found
+ *    on the host (bad sizes, null pointers) are returned before any work is
+ *    enqueued.  Errors found on the device (non-finite input, a bounded wait
+ *    that expired) are recorded in a sticky status word that wsim_status
+ *    reads; no kernel traps.
+ *  - A context may be used from one host thread at a time.
+ */
+#ifndef WSIM_H
+#define WSIM_H
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define WSIM_OK 0
+#define WSIM_EINVAL (-1)      /* null pointer, bad enum, inconsistent CSR       */
+#define WSIM_ESIZE (-2)       /* a size beyond the documented limits            */
+#define WSIM_ECUDA (-3)       /* a CUDA runtime call failed                      */
+#define WSIM_ENONFINITE (-4)  /* a non-finite action or state reached a kernel   */
+#define WSIM_ETIMEOUT (-5)    /* a bounded device-side wait gave up              */
+#define WSIM_ENOMEM (-6)      /* device allocation failed                        */
+#define WSIM_ESTATE (-7)      /* call out of order (e.g. backward before rollout)*/
+
+#define WSIM_MAX_AGENTS 256   /* agents per scene                                */
+#define WSIM_LOOKAHEAD 32     /* IDM look-ahead samples (one per warp lane)      */
+
+/* Agent kinds. */
+#define WSIM_KIND_BICYCLE 0   /* policy agent, action (a [m/s^2], kappa [1/m])    */
+#define WSIM_KIND_DELTA 1     /* policy agent, action (dx [m], dy [m], dtheta)    */
+#define WSIM_KIND_IDM 2       /* IDM sim agent following its route               */
+
+/* Roadgraph point types: only RG_EDGE points form road-edge segments. */
+#define WSIM_RG_EDGE 1
+
+/* Metric flag bits (wsim_metric_buf.flags). */
+#define WSIM_FLAG_COLLISION 1
+#define WSIM_FLAG_OFFROAD 2
+
+/* Rollout modes. */
+#define WSIM_MODE_GRAPH 0      /* persistent step kernel per step, CUDA graph   */
+#define WSIM_MODE_STREAM 1     /* persistent step kernel per step, no graph     */
+#define WSIM_MODE_PLAIN 2      /* one launch per scene per phase (baseline)     */
+
+/* Method constants.  wsim_default_config fills the values used throughout. */
+typedef struct {
+    float dt;          /* step length [s]: 0.1 (Sec. 3.1, 10 Hz)                 */
+    float idm_amax;    /* IDM maximum acceleration a [m/s^2]: 2.0                */
+    float idm_b;       /* IDM comfortable deceleration b [m/s^2]: 3.0            */
+    float idm_T;       /* IDM time headway T [s]: 1.5                            */
+    float idm_s0;      /* IDM minimum gap s0 [m]: 2.0                            */
+    float idm_dq;      /* spacing of the look-ahead samples along the route [m]: 2 */
+    float route_h;     /* parameter length of one route segment [m]: 0.5         */
+    float gap_min;     /* lower clamp of the bumper gap [m]: 0.1                 */
+    float loss_lambda; /* weight of the overlap penalty in the BPTT loss: 1.0    */
+    float loss_tau;    /* softplus temperature of the overlap penalty [m]: 0.25  */
+    int32_t ckpt_every;/* BPTT checkpoint interval in steps (1 = store all): 10  */
+    int32_t tile_segs; /* road-edge segments per culling tile (0 = default)      */
+} wsim_config;
+
+/* A batch of S scenes (all device pointers; sizes on the host).
+ * Scene s owns agents [agent_off[s], agent_off[s+1]) and roadgraph points
+ * [rg_off[s], rg_off[s+1]).  Agent g owns route points [route_off[g],
+ * route_off[g+1]) (>= 2 for IDM agents, may be empty otherwise).  Logs are
+ * time-major [T_log][N_tot].  Points k and k+1 of a scene form a road-edge
+ * segment, oriented k -> k+1, iff both are valid, both have type
+ * WSIM_RG_EDGE and both carry the same polyline id (Sec. 3.4, off-road: the
+ * road lies on the left of an oriented edge). */
+typedef struct {
+    int32_t S, N_tot, T_log, pad_;
+    int64_t R_tot;                     /* roadgraph points in the batch       */
+    int64_t route_tot;                 /* route points in the batch           */
+    const int32_t *agent_off, *rg_off; /* [S+1]                               */
+    const float *L, *W, *idm_v0;       /* [N_tot] box length, width; IDM v0   */
+    const uint8_t *valid, *kind;       /* [N_tot]                             */
+    const int32_t *route_off;          /* [N_tot+1]                           */
+    const float *route_x, *route_y;    /* [route_tot]                         */
+    const float *rg_x, *rg_y;          /* [R_tot]                             */
+    const int32_t *rg_poly;            /* [R_tot] polyline id                 */
+    const uint8_t *rg_type, *rg_valid; /* [R_tot]                             */
+    const float *log_x, *log_y;        /* [T_log][N_tot] logged positions     */
+} wsim_batch;
+
+/* Agent state, [N_tot] each.  Positions, heading and route cursor are
+ * float32 pairs (hi, lo) whose exact sum is the value (compensated
+ * summation keeps positions near 400 m inside 1e-5 m).  s is the arc-length
+ * parameter of an IDM agent on its route (unused by policy agents). */
+typedef struct {
+    float *x, *y, *x_lo, *y_lo, *th, *th_lo, *vx, *vy, *s, *s_lo;
+} wsim_state;
+
+/* Per-step metrics.  ov: largest SAT overlap depth against another valid
+ * agent (> 0 = collision; -inf if none).  off: largest signed distance of a
+ * box corner to the nearest road edge (> 0 = off road; -inf if the scene has
+ * no edge).  logdiv: distance to the logged position.  flags: bit0 collision,
+ * bit1 off road.  reward[s] = -(collisions + off-road agents) of scene s.
+ * Invalid agents report 0 everywhere.  In wsim_rollout each pointer is the
+ * base of a [T][N_tot] (reward [T][S]) array. */
+typedef struct {
+    float *ov, *off, *logdiv;
+    uint8_t *flags;
+    int32_t *reward;
+} wsim_metric_buf;
+
+typedef struct wsim_ctx wsim_ctx;
+
+/* Fills *cfg with the default constants listed in wsim_config. */
+void wsim_default_config(wsim_config *cfg);
+
+/* reset() of Sec. 4 (the initialisation half): validates the batch, builds
+ * the packed road-edge segments and their culling tiles on the device and
+ * the cost-ordered scene work list.  Allocates device scratch owned by the
+ * context.  Synchronises `stream`.  Limits: agents per scene <=
+ * WSIM_MAX_AGENTS, S >= 1, T_log >= 2. */
+int wsim_init(wsim_ctx **out, const wsim_config *cfg, const wsim_batch *b, void *stream);
+
+/* step() of Sec. 4: state t -> t+1 for every scene, then the metrics of t+1
+ * against log row t+1.  act is [3][N_tot]: (a, kappa, unused) for bicycle
+ * agents, (dx, dy, dtheta) for delta agents; IDM agents ignore it.
+ * ctrl [N_tot] may be NULL (all policy agents controlled); a policy agent
+ * with ctrl = 0, and every invalid agent, keeps its state.  `in` and `out`
+ * must not alias.  m may be NULL (transition only).  Requires 0 <= t and
+ * t+1 < T_log. */
+int wsim_step(wsim_ctx *ctx, const wsim_state *in, const float *act, const uint8_t *ctrl,
+              wsim_state *out, const wsim_metric_buf *m, int t, void *stream);
+
+/* The metrics of state st against log row t (Sec. 3.4). */
+int wsim_metrics(wsim_ctx *ctx, const wsim_state *st, const wsim_metric_buf *m, int t, void *stream);
+
+/* Rollout (Sec. 5.1): T steps from time index t0.  st holds state t0 on
+ * entry and state t0+T on return (device order); act_seq is [T][3][N_tot];
+ * mseq arrays are [T][N_tot] ([T][S] for reward), row k holding the metrics
+ * of time t0+k+1.  mode: WSIM_MODE_GRAPH replays a CUDA graph of T step
+ * launches (captured on the first call and re-captured when pointers or T
+ * change), WSIM_MODE_STREAM launches the same kernels directly,
+ * WSIM_MODE_PLAIN launches one kernel per scene and phase.  All three give
+ * bit-identical results.  traj (may be NULL) receives the states of times
+ * t0+1..t0+T as [T] consecutive wsim_state-shaped blocks: traj[k] pointers
+ * are the base pointers advanced by k*N_tot. */
+int wsim_rollout(wsim_ctx *ctx, wsim_state *st, const float *act_seq, const uint8_t *ctrl, int t0,
+                 int T, int mode, const wsim_metric_buf *mseq, const wsim_state *traj, void *stream);
+
+/* Sticky device status: synchronises `stream`, writes the first device error
+ * code recorded since the last call (WSIM_OK if none) to *device_status and
+ * clears it. */
+int wsim_status(wsim_ctx *ctx, int *device_status, void *stream);
+
+/* Work counters of the last rollout (for roofline accounting; 0 unless
+ * wsim_set_counting(ctx, 1) was called before it): [0] corner-segment
+ * distance evaluations, [1] culling-tile bound tests, [2] SAT pair
+ * evaluations, [3] IDM look-ahead sample-box tests.  Synchronises. */
+int wsim_set_counting(wsim_ctx *ctx, int on);
+int wsim_counters(wsim_ctx *ctx, int64_t out[4], void *stream);
+
+/* Message for a WSIM_E* code. */
+const char *wsim_strerror(int code);
+
+/* Frees the context's device scratch; synchronises its last stream. */
+void wsim_destroy(wsim_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,435 @@
+// Host side of the wsim C ABI (include/wsim.h).
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "wsim_internal.h"
+
+using namespace wsim;
+
+struct RolloutKey {
+    wsim_state st, traj;
+    const float* act;
+    const uint8_t* ctrl;
+    wsim_metric_buf m;
+    int t0, T, has_traj;
+};
+
+struct wsim_ctx {
+    wsim_config cfg;
+    wsim_batch b;
+    Params p;
+    int S = 0, N_tot = 0, grid = 1, count = 0;
+    std::vector<int32_t> h_agent_off;
+    // device scratch owned by the context
+    int32_t *seg_off = nullptr, *seg_cnt = nullptr, *order = nullptr, *queue = nullptr, *status = nullptr;
+    int queue_len = 0;
+    float4* seg_geo = nullptr;
+    float* seg_inv = nullptr;
+    uint8_t* seg_flags = nullptr;
+    unsigned long long* counters = nullptr;
+    float* tmp = nullptr;  // ping-pong state, 10 x N_tot
+    // captured rollout
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    RolloutKey key{};
+    bool have_key = false;
+    cudaStream_t last = nullptr;
+};
+
+namespace {
+
+inline cudaStream_t S_(void* s) { return static_cast<cudaStream_t>(s); }
+
+#define CK(expr)                                   \
+    do {                                           \
+        if ((expr) != cudaSuccess) {               \
+            cudaGetLastError();                    \
+            return WSIM_ECUDA;                     \
+        }                                          \
+    } while (0)
+
+template <class T> int dalloc(T** p, size_t n) {
+    if (n == 0) n = 1;
+    if (cudaMalloc(reinterpret_cast<void**>(p), n * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        return WSIM_ENOMEM;
+    }
+    return WSIM_OK;
+}
+
+bool state_ok(const wsim_state* s) {
+    return s && s->x && s->y && s->x_lo && s->y_lo && s->th && s->th_lo && s->vx && s->vy && s->s && s->s_lo;
+}
+bool metrics_ok(const wsim_metric_buf* m) { return m && m->ov && m->off && m->logdiv && m->flags && m->reward; }
+
+CStateP cstate(const wsim_state* s) {
+    return CStateP{s->x, s->y, s->x_lo, s->y_lo, s->th, s->th_lo, s->vx, s->vy, s->s, s->s_lo};
+}
+StateP mstate(const wsim_state* s) {
+    return StateP{s->x, s->y, s->x_lo, s->y_lo, s->th, s->th_lo, s->vx, s->vy, s->s, s->s_lo};
+}
+wsim_state offset(const wsim_state& s, size_t k) {
+    return wsim_state{s.x + k, s.y + k, s.x_lo + k, s.y_lo + k, s.th + k,
+                      s.th_lo + k, s.vx + k, s.vy + k, s.s + k, s.s_lo + k};
+}
+wsim_state tmp_state(const wsim_ctx* c) {
+    float* t = c->tmp;
+    size_t n = static_cast<size_t>(c->N_tot);
+    return wsim_state{t, t + n, t + 2 * n, t + 3 * n, t + 4 * n, t + 5 * n, t + 6 * n, t + 7 * n, t + 8 * n, t + 9 * n};
+}
+
+StepArgs base_args(const wsim_ctx* c) {
+    StepArgs a;
+    std::memset(&a, 0, sizeof(a));
+    const wsim_batch& b = c->b;
+    a.S = b.S;
+    a.N_tot = b.N_tot;
+    a.T_log = b.T_log;
+    a.agent_off = b.agent_off;
+    a.L = b.L;
+    a.W = b.W;
+    a.v0 = b.idm_v0;
+    a.valid = b.valid;
+    a.kind = b.kind;
+    a.route_off = b.route_off;
+    a.route_x = b.route_x;
+    a.route_y = b.route_y;
+    a.log_x = b.log_x;
+    a.log_y = b.log_y;
+    a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags};
+    a.order = c->order;
+    a.status = c->status;
+    a.counters = c->counters;
+    a.count = c->count;
+    a.p = c->p;
+    return a;
+}
+
+int ensure_queue(wsim_ctx* c, int n) {
+    if (n <= c->queue_len) return WSIM_OK;
+    if (c->exec) {  // the captured graph holds the old counters
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+        c->have_key = false;
+    }
+    if (c->queue) cudaFree(c->queue);
+    c->queue = nullptr;
+    c->queue_len = 0;
+    int rc = dalloc(&c->queue, static_cast<size_t>(n));
+    if (rc) return rc;
+    c->queue_len = n;
+    return WSIM_OK;
+}
+
+// One step (or metrics pass when in == out == nullptr for the transition).
+int enqueue_step(wsim_ctx* c, const CStateP& in, const StateP* out, const float* act, const uint8_t* ctrl,
+                 const wsim_metric_buf* m, int t_log, int32_t* queue, bool plain, cudaStream_t st) {
+    StepArgs a = base_args(c);
+    a.in = in;
+    if (out) a.out = *out;
+    a.act = act;
+    a.ctrl = ctrl;
+    a.do_transition = out != nullptr;
+    a.do_metrics = m != nullptr;
+    if (m) a.m = MetricsP{m->ov, m->off, m->logdiv, m->flags, m->reward};
+    a.t_log = t_log;
+    a.queue = queue;
+    if (plain) {
+        for (int s = 0; s < c->S; ++s) CK(launch_plain_scene(a, s, st));
+    } else {
+        CK(cudaMemsetAsync(queue, 0, sizeof(int32_t), st));
+        CK(launch_step(a, c->grid, st));
+    }
+    return WSIM_OK;
+}
+
+int enqueue_rollout(wsim_ctx* c, const RolloutKey& k, bool plain, cudaStream_t st) {
+    const size_t N = static_cast<size_t>(c->N_tot);
+    const wsim_state tmp = tmp_state(c);
+    wsim_state prev = k.st;
+    for (int i = 0; i < k.T; ++i) {
+        wsim_state out;
+        if (k.has_traj)
+            out = offset(k.traj, static_cast<size_t>(i) * N);
+        else
+            out = (i % 2 == 0) ? tmp : k.st;
+        wsim_metric_buf m = k.m;
+        m.ov += static_cast<size_t>(i) * N;
+        m.off += static_cast<size_t>(i) * N;
+        m.logdiv += static_cast<size_t>(i) * N;
+        m.flags += static_cast<size_t>(i) * N;
+        m.reward += static_cast<size_t>(i) * c->S;
+        StateP o = mstate(&out);
+        int rc = enqueue_step(c, cstate(&prev), &o, k.act + static_cast<size_t>(i) * 3 * N, k.ctrl, &m, k.t0 + i + 1,
+                              c->queue + i, plain, st);
+        if (rc) return rc;
+        prev = out;
+    }
+    if (prev.x != k.st.x) {
+        float* const src[10] = {prev.x, prev.y, prev.x_lo, prev.y_lo, prev.th, prev.th_lo, prev.vx, prev.vy, prev.s, prev.s_lo};
+        float* const dst[10] = {k.st.x, k.st.y, k.st.x_lo, k.st.y_lo, k.st.th, k.st.th_lo, k.st.vx, k.st.vy, k.st.s, k.st.s_lo};
+        for (int j = 0; j < 10; ++j) CK(cudaMemcpyAsync(dst[j], src[j], N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    return WSIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void wsim_default_config(wsim_config* cfg) {
+    if (!cfg) return;
+    cfg->dt = 0.1f;
+    cfg->idm_amax = 2.0f;
+    cfg->idm_b = 3.0f;
+    cfg->idm_T = 1.5f;
+    cfg->idm_s0 = 2.0f;
+    cfg->idm_dq = 2.0f;
+    cfg->route_h = 0.5f;
+    cfg->gap_min = 0.1f;
+    cfg->loss_lambda = 1.0f;
+    cfg->loss_tau = 0.25f;
+    cfg->ckpt_every = 10;
+    cfg->tile_segs = 0;
+}
+
+const char* wsim_strerror(int code) {
+    switch (code) {
+        case WSIM_OK: return "ok";
+        case WSIM_EINVAL: return "invalid argument (null pointer, bad enum or inconsistent CSR offsets)";
+        case WSIM_ESIZE: return "size outside the documented limits";
+        case WSIM_ECUDA: return "a CUDA runtime call failed";
+        case WSIM_ENONFINITE: return "a non-finite action or state reached a kernel";
+        case WSIM_ETIMEOUT: return "a bounded device-side wait expired";
+        case WSIM_ENOMEM: return "device allocation failed";
+        case WSIM_ESTATE: return "call out of order";
+        default: return "unknown wsim error";
+    }
+}
+
+int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void* stream) {
+    if (!out || !cfg || !b) return WSIM_EINVAL;
+    *out = nullptr;
+    if (b->S < 1 || b->N_tot < 0 || b->T_log < 2 || b->R_tot < 0 || b->route_tot < 0) return WSIM_ESIZE;
+    if (!b->agent_off || !b->rg_off || !b->L || !b->W || !b->idm_v0 || !b->valid || !b->kind || !b->route_off ||
+        !b->log_x || !b->log_y)
+        return WSIM_EINVAL;
+    if (b->R_tot > 0 && (!b->rg_x || !b->rg_y || !b->rg_poly || !b->rg_type || !b->rg_valid)) return WSIM_EINVAL;
+    if (b->route_tot > 0 && (!b->route_x || !b->route_y)) return WSIM_EINVAL;
+    if (!(cfg->dt > 0.f) || !(cfg->route_h > 0.f) || !(cfg->idm_amax > 0.f) || !(cfg->idm_b > 0.f))
+        return WSIM_EINVAL;
+    cudaStream_t st = S_(stream);
+    const int S = b->S, N = b->N_tot;
+
+    // Validate the CSR offsets and the IDM routes on the host.
+    std::vector<int32_t> ao(S + 1), ro(S + 1), rto(static_cast<size_t>(N) + 1);
+    std::vector<uint8_t> kind(static_cast<size_t>(N) + 1), valid(static_cast<size_t>(N) + 1);
+    CK(cudaMemcpyAsync(ao.data(), b->agent_off, sizeof(int32_t) * (S + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ro.data(), b->rg_off, sizeof(int32_t) * (S + 1), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(rto.data(), b->route_off, sizeof(int32_t) * (N + 1), cudaMemcpyDeviceToHost, st));
+    if (N > 0) {
+        CK(cudaMemcpyAsync(kind.data(), b->kind, N, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(valid.data(), b->valid, N, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    if (ao[0] != 0 || ao[S] != N || ro[0] != 0 || ro[S] != b->R_tot || rto[0] != 0 || rto[N] != b->route_tot)
+        return WSIM_EINVAL;
+    for (int s = 0; s < S; ++s) {
+        const int n = ao[s + 1] - ao[s];
+        if (n < 0 || ro[s + 1] < ro[s]) return WSIM_EINVAL;
+        if (n > WSIM_MAX_AGENTS) return WSIM_ESIZE;
+    }
+    for (int g = 0; g < N; ++g) {
+        if (rto[g + 1] < rto[g]) return WSIM_EINVAL;
+        if (kind[g] > WSIM_KIND_IDM) return WSIM_EINVAL;
+        if (kind[g] == WSIM_KIND_IDM && valid[g] && rto[g + 1] - rto[g] < 2) return WSIM_EINVAL;
+    }
+
+    wsim_ctx* c = new wsim_ctx();
+    c->cfg = *cfg;
+    c->b = *b;
+    c->S = S;
+    c->N_tot = N;
+    c->h_agent_off = ao;
+    c->p = Params{cfg->dt,     cfg->idm_amax,         cfg->idm_b,  cfg->idm_T,
+                  cfg->idm_s0, cfg->idm_dq,           cfg->route_h, 1.0f / cfg->route_h,
+                  cfg->gap_min, 2.0f * sqrtf(cfg->idm_amax * cfg->idm_b)};
+    int rc = WSIM_OK;
+    auto fail = [&](int code) {
+        wsim_destroy(c);
+        return code;
+    };
+    if ((rc = dalloc(&c->seg_off, S + 1)) || (rc = dalloc(&c->seg_cnt, S)) || (rc = dalloc(&c->order, S)) ||
+        (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->counters, 4)) ||
+        (rc = dalloc(&c->tmp, static_cast<size_t>(N) * 10)) || (rc = ensure_queue(c, 128)))
+        return fail(rc);
+    if (cudaMemsetAsync(c->status, 0, sizeof(int32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess)
+        return fail(WSIM_ECUDA);
+
+    // Road-edge segments: count, pad each scene to kSegAlign, pack.
+    if (launch_seg_count(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, S, c->seg_cnt, st) !=
+        cudaSuccess)
+        return fail(WSIM_ECUDA);
+    std::vector<int32_t> cnt(S), off(S + 1, 0);
+    if (cudaMemcpyAsync(cnt.data(), c->seg_cnt, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(WSIM_ECUDA);
+    for (int s = 0; s < S; ++s) off[s + 1] = off[s] + ((cnt[s] + kSegAlign - 1) / kSegAlign) * kSegAlign;
+    const size_t E = static_cast<size_t>(off[S]);
+    if ((rc = dalloc(&c->seg_geo, E)) || (rc = dalloc(&c->seg_inv, E)) || (rc = dalloc(&c->seg_flags, E)))
+        return fail(rc);
+    if (cudaMemsetAsync(c->seg_geo, 0, std::max<size_t>(E, 1) * sizeof(float4), st) != cudaSuccess ||
+        cudaMemsetAsync(c->seg_inv, 0, std::max<size_t>(E, 1) * sizeof(float), st) != cudaSuccess ||
+        cudaMemsetAsync(c->seg_flags, 0, std::max<size_t>(E, 1), st) != cudaSuccess ||
+        cudaMemcpyAsync(c->seg_off, off.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return fail(WSIM_ECUDA);
+    if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, S, c->seg_off, c->seg_geo,
+                        c->seg_inv, c->seg_flags, st) != cudaSuccess)
+        return fail(WSIM_ECUDA);
+
+    // Scene work list, most expensive first (longest-processing-time order).
+    std::vector<double> cost(S);
+    for (int s = 0; s < S; ++s) {
+        const double n = ao[s + 1] - ao[s];
+        cost[s] = 4.0 * n * cnt[s] + 32.0 * n * n + 64.0;
+    }
+    std::vector<int32_t> order(S);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    if (cudaMemcpyAsync(c->order, order.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(WSIM_ECUDA);
+
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    c->grid = std::min(S, sms * step_blocks_per_sm());
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(WSIM_ECUDA);
+    c->last = st;
+    *out = c;
+    return WSIM_OK;
+}
+
+int wsim_step(wsim_ctx* c, const wsim_state* in, const float* act, const uint8_t* ctrl, wsim_state* out,
+              const wsim_metric_buf* m, int t, void* stream) {
+    if (!c || !state_ok(in) || !state_ok(out) || !act || (m && !metrics_ok(m))) return WSIM_EINVAL;
+    if (in->x == out->x) return WSIM_EINVAL;
+    if (t < 0 || t + 1 >= c->b.T_log) return WSIM_ESIZE;
+    c->last = S_(stream);
+    StateP o = mstate(out);
+    return enqueue_step(c, cstate(in), &o, act, ctrl, m, t + 1, c->queue, false, S_(stream));
+}
+
+int wsim_metrics(wsim_ctx* c, const wsim_state* st, const wsim_metric_buf* m, int t, void* stream) {
+    if (!c || !state_ok(st) || !metrics_ok(m)) return WSIM_EINVAL;
+    if (t < 0 || t >= c->b.T_log) return WSIM_ESIZE;
+    c->last = S_(stream);
+    return enqueue_step(c, cstate(st), nullptr, nullptr, nullptr, m, t, c->queue, false, S_(stream));
+}
+
+int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_t* ctrl, int t0, int T, int mode,
+                 const wsim_metric_buf* mseq, const wsim_state* traj, void* stream) {
+    if (!c || !state_ok(st) || !act_seq || !metrics_ok(mseq) || (traj && !state_ok(traj))) return WSIM_EINVAL;
+    if (mode < WSIM_MODE_GRAPH || mode > WSIM_MODE_PLAIN) return WSIM_EINVAL;
+    if (T < 1 || t0 < 0 || t0 + T >= c->b.T_log) return WSIM_ESIZE;
+    cudaStream_t s = S_(stream);
+    c->last = s;
+    int rc = ensure_queue(c, T);
+    if (rc) return rc;
+    RolloutKey k{};
+    std::memset(&k, 0, sizeof(k));
+    k.st = *st;
+    if (traj) k.traj = *traj;
+    k.act = act_seq;
+    k.ctrl = ctrl;
+    k.m = *mseq;
+    k.t0 = t0;
+    k.T = T;
+    k.has_traj = traj != nullptr;
+    if (mode != WSIM_MODE_GRAPH) return enqueue_rollout(c, k, mode == WSIM_MODE_PLAIN, s);
+
+    if (!c->exec || !c->have_key || std::memcmp(&k, &c->key, sizeof(k)) != 0) {
+        if (c->exec) {
+            cudaGraphExecDestroy(c->exec);
+            c->exec = nullptr;
+        }
+        c->have_key = false;
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_rollout(c, k, false, c->cap);
+        cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+        if (rc || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return rc ? rc : WSIM_ECUDA;
+        }
+        e = cudaGraphInstantiate(&c->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->exec = nullptr;
+            return WSIM_ECUDA;
+        }
+        c->key = k;
+        c->have_key = true;
+    }
+    CK(cudaGraphLaunch(c->exec, s));
+    return WSIM_OK;
+}
+
+int wsim_status(wsim_ctx* c, int* device_status, void* stream) {
+    if (!c || !device_status) return WSIM_EINVAL;
+    cudaStream_t s = S_(stream);
+    int v = 0;
+    CK(cudaMemcpyAsync(&v, c->status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    *device_status = v;
+    return WSIM_OK;
+}
+
+int wsim_set_counting(wsim_ctx* c, int on) {
+    if (!c) return WSIM_EINVAL;
+    c->count = on ? 1 : 0;
+    if (c->exec) {
+        cudaGraphExecDestroy(c->exec);
+        c->exec = nullptr;
+        c->have_key = false;
+    }
+    CK(cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->last));
+    return WSIM_OK;
+}
+
+int wsim_counters(wsim_ctx* c, int64_t out[4], void* stream) {
+    if (!c || !out) return WSIM_EINVAL;
+    unsigned long long v[4];
+    cudaStream_t s = S_(stream);
+    CK(cudaMemcpyAsync(v, c->counters, sizeof(v), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int k = 0; k < 4; ++k) out[k] = static_cast<int64_t>(v[k]);
+    return WSIM_OK;
+}
+
+void wsim_destroy(wsim_ctx* c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->last);
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->cap) cudaStreamDestroy(c->cap);
+    cudaFree(c->seg_off);
+    cudaFree(c->seg_cnt);
+    cudaFree(c->order);
+    cudaFree(c->queue);
+    cudaFree(c->status);
+    cudaFree(c->counters);
+    cudaFree(c->tmp);
+    cudaFree(c->seg_geo);
+    cudaFree(c->seg_inv);
+    cudaFree(c->seg_flags);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,228 @@
+"""Python binding of libwsim.so (include/wsim.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+kernels of the library.  PyTorch provides device memory (tensors) and
+streams.  Importing this module loads libwsim.so and raises if it is missing;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libwsim.so")
+
+OK, EINVAL, ESIZE, ECUDA, ENONFINITE, ETIMEOUT, ENOMEM, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+MODE_GRAPH, MODE_STREAM, MODE_PLAIN = 0, 1, 2
+MAX_AGENTS = 256
+FLAG_COLLISION, FLAG_OFFROAD = 1, 2
+
+_fp = C.POINTER(C.c_float)
+_u8p = C.POINTER(C.c_uint8)
+_i32p = C.POINTER(C.c_int32)
+
+
+class WsimConfig(C.Structure):
+    _fields_ = [("dt", C.c_float), ("idm_amax", C.c_float), ("idm_b", C.c_float), ("idm_T", C.c_float),
+                ("idm_s0", C.c_float), ("idm_dq", C.c_float), ("route_h", C.c_float), ("gap_min", C.c_float),
+                ("loss_lambda", C.c_float), ("loss_tau", C.c_float), ("ckpt_every", C.c_int32),
+                ("tile_segs", C.c_int32)]
+
+
+class WsimBatch(C.Structure):
+    _fields_ = [("S", C.c_int32), ("N_tot", C.c_int32), ("T_log", C.c_int32), ("pad_", C.c_int32),
+                ("R_tot", C.c_int64), ("route_tot", C.c_int64),
+                ("agent_off", C.c_void_p), ("rg_off", C.c_void_p),
+                ("L", C.c_void_p), ("W", C.c_void_p), ("idm_v0", C.c_void_p),
+                ("valid", C.c_void_p), ("kind", C.c_void_p), ("route_off", C.c_void_p),
+                ("route_x", C.c_void_p), ("route_y", C.c_void_p), ("rg_x", C.c_void_p), ("rg_y", C.c_void_p),
+                ("rg_poly", C.c_void_p), ("rg_type", C.c_void_p), ("rg_valid", C.c_void_p),
+                ("log_x", C.c_void_p), ("log_y", C.c_void_p)]
+
+
+STATE_FIELDS = ("x", "y", "x_lo", "y_lo", "th", "th_lo", "vx", "vy", "s", "s_lo")
+
+
+class WsimState(C.Structure):
+    _fields_ = [(k, C.c_void_p) for k in STATE_FIELDS]
+
+
+class WsimMetricBuf(C.Structure):
+    _fields_ = [("ov", C.c_void_p), ("off", C.c_void_p), ("logdiv", C.c_void_p), ("flags", C.c_void_p),
+                ("reward", C.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libwsim.so is not built ({LIB_PATH}); run paper_2310_08710_b300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    vp = C.c_void_p
+    lib.wsim_default_config.argtypes = [P(WsimConfig)]
+    lib.wsim_default_config.restype = None
+    lib.wsim_init.argtypes = [P(vp), P(WsimConfig), P(WsimBatch), vp]
+    lib.wsim_step.argtypes = [vp, P(WsimState), vp, vp, P(WsimState), P(WsimMetricBuf), C.c_int, vp]
+    lib.wsim_metrics.argtypes = [vp, P(WsimState), P(WsimMetricBuf), C.c_int, vp]
+    lib.wsim_rollout.argtypes = [vp, P(WsimState), vp, vp, C.c_int, C.c_int, C.c_int, P(WsimMetricBuf),
+                                 P(WsimState), vp]
+    lib.wsim_status.argtypes = [vp, P(C.c_int), vp]
+    lib.wsim_set_counting.argtypes = [vp, C.c_int]
+    lib.wsim_counters.argtypes = [vp, P(C.c_int64), vp]
+    lib.wsim_strerror.argtypes = [C.c_int]
+    lib.wsim_strerror.restype = C.c_char_p
+    lib.wsim_destroy.argtypes = [vp]
+    lib.wsim_destroy.restype = None
+    return lib
+
+
+lib = _load()
+
+EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
+            "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy")
+
+
+class WsimError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {lib.wsim_strerror(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise WsimError(rc, where)
+
+
+def default_config(**over) -> WsimConfig:
+    c = WsimConfig()
+    lib.wsim_default_config(C.byref(c))
+    for k, v in over.items():
+        setattr(c, k, v)
+    return c
+
+
+def _stream(stream: Optional[torch.cuda.Stream]) -> C.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+class DeviceBatch:
+    """A SceneBatch copied into device tensors, plus its wsim_batch view."""
+
+    def __init__(self, b, device="cuda"):
+        dev = torch.device(device)
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt).to(dev)
+        self.S, self.N_tot, self.T_log = b.S, b.N_tot, b.log_x.shape[0]
+        self.agent_off = t(b.agent_off, torch.int32)
+        self.rg_off = t(b.rg_off, torch.int32)
+        self.L, self.W, self.idm_v0 = t(b.L, torch.float32), t(b.W, torch.float32), t(b.idm_v0, torch.float32)
+        self.valid, self.kind = t(b.valid, torch.uint8), t(b.kind, torch.uint8)
+        self.route_off = t(b.route_off, torch.int32)
+        self.route_x, self.route_y = t(b.route_x, torch.float32), t(b.route_y, torch.float32)
+        self.rg_x, self.rg_y = t(b.rg_x, torch.float32), t(b.rg_y, torch.float32)
+        self.rg_poly = t(b.rg_poly, torch.int32)
+        self.rg_type, self.rg_valid = t(b.rg_type, torch.uint8), t(b.rg_valid, torch.uint8)
+        self.log_x, self.log_y = t(b.log_x, torch.float32), t(b.log_y, torch.float32)
+        self.c = WsimBatch(self.S, self.N_tot, self.T_log, 0, int(b.rg_off[-1]), int(b.route_off[-1]),
+                           *[_ptr(getattr(self, k)) for k in (
+                               "agent_off", "rg_off", "L", "W", "idm_v0", "valid", "kind", "route_off",
+                               "route_x", "route_y", "rg_x", "rg_y", "rg_poly", "rg_type", "rg_valid",
+                               "log_x", "log_y")])
+
+
+class State:
+    """Agent state in one [10, n_rows * N] float32 tensor (rows of N agents)."""
+
+    def __init__(self, N: int, rows: int = 1, device="cuda", data: Optional[torch.Tensor] = None):
+        self.N, self.rows = N, rows
+        self.data = data if data is not None else torch.zeros((10, rows * N), dtype=torch.float32, device=device)
+
+    @classmethod
+    def from_batch(cls, b, device="cuda") -> "State":
+        st = cls(b.N_tot, device=device)
+        for k in ("x", "y", "th", "vx", "vy"):
+            st.data[STATE_FIELDS.index(k)] = torch.as_tensor(getattr(b, k)).to(device)
+        return st
+
+    def field(self, k: str) -> torch.Tensor:
+        return self.data[STATE_FIELDS.index(k)].view(self.rows, self.N)
+
+    def c(self, row: int = 0) -> WsimState:
+        base = row * self.N
+        return WsimState(*[self.data[i, base:].data_ptr() for i in range(10)])
+
+    def clone(self) -> "State":
+        return State(self.N, self.rows, data=self.data.clone())
+
+
+class Metrics:
+    """Metric arrays for `rows` steps: [rows, N] (reward [rows, S])."""
+
+    def __init__(self, N: int, S: int, rows: int = 1, device="cuda"):
+        f = lambda: torch.zeros((rows, N), dtype=torch.float32, device=device)
+        self.ov, self.off, self.logdiv = f(), f(), f()
+        self.flags = torch.zeros((rows, N), dtype=torch.uint8, device=device)
+        self.reward = torch.zeros((rows, S), dtype=torch.int32, device=device)
+
+    def c(self) -> WsimMetricBuf:
+        return WsimMetricBuf(self.ov.data_ptr(), self.off.data_ptr(), self.logdiv.data_ptr(),
+                             self.flags.data_ptr(), self.reward.data_ptr())
+
+
+class Sim:
+    """A wsim context over one device batch."""
+
+    def __init__(self, batch: DeviceBatch, cfg: Optional[WsimConfig] = None, stream=None):
+        self.batch = batch
+        self.cfg = cfg if cfg is not None else default_config()
+        self._h = C.c_void_p()
+        _check(lib.wsim_init(C.byref(self._h), C.byref(self.cfg), C.byref(batch.c), _stream(stream)), "wsim_init")
+
+    def close(self):
+        if self._h:
+            lib.wsim_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, st_in: State, act: torch.Tensor, st_out: State, m: Optional[Metrics], t: int,
+             ctrl: Optional[torch.Tensor] = None, stream=None):
+        mc = m.c() if m is not None else None
+        _check(lib.wsim_step(self._h, C.byref(st_in.c()), act.data_ptr(), _ptr(ctrl), C.byref(st_out.c()),
+                             C.byref(mc) if mc is not None else None, t, _stream(stream)), "wsim_step")
+
+    def metrics(self, st: State, m: Metrics, t: int, stream=None):
+        _check(lib.wsim_metrics(self._h, C.byref(st.c()), C.byref(m.c()), t, _stream(stream)), "wsim_metrics")
+
+    def rollout(self, st: State, act_seq: torch.Tensor, mseq: Metrics, t0: int, T: int, mode: int = MODE_GRAPH,
+                ctrl: Optional[torch.Tensor] = None, traj: Optional[State] = None, stream=None):
+        tc = traj.c() if traj is not None else None
+        _check(lib.wsim_rollout(self._h, C.byref(st.c()), act_seq.data_ptr(), _ptr(ctrl), t0, T, mode,
+                                C.byref(mseq.c()), C.byref(tc) if tc is not None else None, _stream(stream)),
+               "wsim_rollout")
+
+    def status(self, stream=None) -> int:
+        v = C.c_int(0)
+        _check(lib.wsim_status(self._h, C.byref(v), _stream(stream)), "wsim_status")
+        return v.value
+
+    def set_counting(self, on: bool):
+        _check(lib.wsim_set_counting(self._h, int(on)), "wsim_set_counting")
+
+    def counters(self, stream=None) -> np.ndarray:
+        out = (C.c_int64 * 4)()
+        _check(lib.wsim_counters(self._h, out, _stream(stream)), "wsim_counters")
+        return np.array(out[:], dtype=np.int64)

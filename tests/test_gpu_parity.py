@@ -1,0 +1,146 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a B300).
+
+Teacher-forced parity per step and per quantity (positions 1e-5 m, heading
+1e-6 rad, velocity 1e-5 m/s, log divergence 1e-5 m, overlap depth and
+off-road distance 2e-5 m, or 4 float32 ulps of larger values); collision and
+off-road booleans and the reward bit-exact outside the oracle's ambiguity
+bands.  The three rollout modes must agree bit for bit.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2310_08710_b300 import synth
+from tests import gpu_harness as H
+from tests.scenes import straight_route, tiny_batch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def wsim():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_08710_b300 import wsim as w
+    return w
+
+
+def test_config0_every_step(wsim):
+    b = synth.make_batch(0, seed=1)
+    g = H.run_rollout(b)
+    assert g["status"] == 0
+    c = H.teacher_forced(b, g, [0], range(b.T))
+    assert c["steps"] == 80
+    print("config0", c)
+
+
+def test_config0_modes_bit_identical_and_deterministic(wsim):
+    b = synth.make_batch(0, seed=2)
+    ref = H.run_rollout(b, mode=wsim.MODE_GRAPH)
+    for mode in (wsim.MODE_GRAPH, wsim.MODE_STREAM, wsim.MODE_PLAIN):
+        g = H.run_rollout(b, mode=mode)
+        for k in ("traj", "final", "ov", "off", "logdiv", "flags", "reward"):
+            assert np.array_equal(g[k].view(np.uint8), ref[k].view(np.uint8)), (mode, k)
+
+
+def test_config1_sampled_scenes_full_size(wsim):
+    # Full 1024-scene batch in the benchmark's launch configuration (graph);
+    # the oracle checks a spread of scenes at every step.
+    b = synth.make_batch(1, seed=0)
+    g = H.run_rollout(b)
+    assert g["status"] == 0
+    scenes = [0, 333, 700, 1023]
+    c = H.teacher_forced(b, g, scenes, range(b.T))
+    print("config1", c)
+    assert c["band_idm"] <= 0.02 * c["agent_steps"]
+
+
+def test_config2_uneven_against_plain_and_oracle(wsim):
+    b = synth.make_batch(2, seed=0, S=512)
+    g = H.run_rollout(b, mode=wsim.MODE_GRAPH)
+    p = H.run_rollout(b, mode=wsim.MODE_PLAIN)
+    for k in ("traj", "ov", "off", "logdiv", "flags", "reward"):
+        assert np.array_equal(g[k].view(np.uint8), p[k].view(np.uint8)), k
+    rng = np.random.default_rng(0)
+    scenes = sorted(rng.choice(b.S, 8, replace=False).tolist())
+    big = int(np.argmax(np.diff(b.rg_off)))
+    c = H.teacher_forced(b, g, sorted(set(scenes + [big])), [0, 1, 2, 17, 40, 79])
+    print("config2", c)
+
+
+def test_edge_cases_tiny_scenes(wsim):
+    # scenes with 1 agent, 2 agents, no road edges, all agents invalid, an
+    # empty scene, and a box touching an edge
+    edge = np.stack([np.arange(-20, 20.5, 0.5), np.zeros(81)], 1)
+    scenes = [
+        tiny_batch([dict(x=0.0, y=1.0, th=0.2, v=3.0)], roadgraph=[(edge, 1)]),
+        tiny_batch([dict(x=0.0, y=3.0, v=5.0), dict(x=3.0, y=3.5, th=0.3, v=1.0)], roadgraph=[(edge, 2)]),
+        tiny_batch([dict(x=0.0, y=1.0, valid=0), dict(x=3.0, y=1.0, valid=0)], roadgraph=[(edge, 1)]),
+    ]
+    b = _concat(scenes + [_empty_scene()], T=20)
+    g = H.run_rollout(b)
+    assert g["status"] == 0
+    H.teacher_forced(b, g, list(range(b.S)), range(b.T))
+    assert np.isneginf(g["ov"][0][0])                    # a lone agent has no pair
+    assert np.isneginf(g["off"][0][1]) and np.isneginf(g["off"][0][2])  # no road edge
+    assert (g["ov"][:, 3:5] == 0).all() and (g["flags"][:, 3:5] == 0).all()  # invalid agents
+
+
+def test_max_agents_per_scene(wsim):
+    b = synth.make_batch(0, seed=4, N=256, S=2, R=3000)
+    g = H.run_rollout(b, T=12)
+    H.teacher_forced(b, g, [0, 1], range(12))
+    bad = synth.make_batch(0, seed=4, N=257, S=1, R=100)
+    with pytest.raises(wsim.WsimError) as e:
+        wsim.Sim(wsim.DeviceBatch(bad))
+    assert e.value.code == wsim.ESIZE
+
+
+def test_idm_scene_with_routes_every_step(wsim):
+    b = synth.make_batch(1, seed=3, S=6, R=4000)
+    g = H.run_rollout(b)
+    c = H.teacher_forced(b, g, list(range(6)), range(b.T))
+    print("idm", c)
+    assert c["band_idm"] <= 0.02 * c["agent_steps"]
+
+
+def test_ctrl_mask_and_nonfinite_status(wsim):
+    b = synth.make_batch(0, seed=5)
+    ctrl = (np.arange(b.N_tot) % 3 != 0).astype(np.uint8)
+    g = H.run_rollout(b, ctrl=ctrl, T=5)
+    r0 = H.initial_rows(b)
+    held = ctrl == 0
+    assert np.array_equal(g["traj"][:, 4, held], r0[:, held])
+    b.actions[2, 0, 5] = np.nan
+    g = H.run_rollout(b, T=5)
+    assert g["status"] == wsim.ENONFINITE
+
+
+def _empty_scene():
+    b = tiny_batch([dict(x=0.0, y=0.0)])
+    return synth.SceneBatch(**{**b.__dict__, "N_tot": 0, "agent_off": np.array([0, 0], np.int32),
+                               "L": b.L[:0], "W": b.W[:0], "valid": b.valid[:0], "kind": b.kind[:0],
+                               "idm_v0": b.idm_v0[:0], "route_off": np.zeros(1, np.int32),
+                               "log_x": b.log_x[:, :0], "log_y": b.log_y[:, :0], "x": b.x[:0], "y": b.y[:0],
+                               "th": b.th[:0], "vx": b.vx[:0], "vy": b.vy[:0], "actions": b.actions[:, :, :0]})
+
+
+def _concat(bs, T):
+    """Concatenate single-scene batches; random actions for T steps."""
+    rng = np.random.default_rng(0)
+    cat = lambda k: np.concatenate([getattr(x, k) for x in bs])
+    off = lambda n: np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
+    N = [x.N_tot for x in bs]
+    R = [x.R_tot for x in bs]
+    rt = [int(x.route_off[-1]) for x in bs]
+    route_off = np.concatenate([[0]] + [x.route_off[1:] + sum(rt[:i]) for i, x in enumerate(bs)]).astype(np.int32)
+    polys = np.concatenate([x.rg_poly + 1000 * i for i, x in enumerate(bs)]).astype(np.int32)
+    act = np.stack([rng.uniform(-4, 4, (T, sum(N))), rng.uniform(-0.3, 0.3, (T, sum(N))),
+                    np.zeros((T, sum(N)))], 1).astype(np.float32)
+    return synth.SceneBatch(
+        cfg=-1, seed=0, scenes=np.arange(len(bs)), S=len(bs), N_tot=sum(N), T=T,
+        agent_off=off(N), rg_off=off(R), L=cat("L"), W=cat("W"), valid=cat("valid"), kind=cat("kind"),
+        idm_v0=cat("idm_v0"), route_off=route_off, route_x=cat("route_x"), route_y=cat("route_y"),
+        rg_x=cat("rg_x"), rg_y=cat("rg_y"), rg_poly=polys, rg_type=cat("rg_type"), rg_valid=cat("rg_valid"),
+        log_x=np.concatenate([x.log_x for x in bs], 1), log_y=np.concatenate([x.log_y for x in bs], 1),
+        x=cat("x"), y=cat("y"), th=cat("th"), vx=cat("vx"), vy=cat("vy"), actions=act)
