@@ -168,7 +168,7 @@ __device__ void idm_agent(Smem& sm, const StepArgs& A, int a0, int N, int i, int
         const float ex = xjh - cx, ey = yjh - cy;
         const float reach = rq + hlj + hwj + 2.f * wi + 0.05f;
         if (ex * ex + ey * ey > reach * reach) continue;
-        n_tests += 32;
+        if (lane == 0) n_tests += 32;
         const float rxq = (Px - xjh) + (qox - sm.xl[j]);
         const float ryq = (Py - yjh) + (qoy - sm.yl[j]);
         const float cj = sm.c[j], sj = sm.s[j];
