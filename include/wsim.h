@@ -183,6 +183,25 @@ const char *wsim_strerror(int code);
 /* Frees the context's device scratch; synchronises its last stream. */
 void wsim_destroy(wsim_ctx *ctx);
 
+/* Metrics of state st against log row t, like wsim_metrics, but with no
+ * context and no device allocation at all.  The paper has no counterpart;
+ * this is for callers that cannot call cudaMalloc when they need the metrics
+ * (a caching allocator or fixed arena that owns all device memory, code that
+ * must not allocate).  The scratch wsim_init would allocate lives instead in
+ * one file-scope device array of about 5.6 MB that every GPU loading the
+ * library holds until the process exits.  Limits: at most 4096 scenes, and
+ * R_tot + 3 * S <= 262144 (the packed road-edge segments must fit); larger
+ * batches return WSIM_ESIZE before any work.  The first call on a device
+ * looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array and it keeps the previous call's contents, so calls that overlap
+ * on the GPU (other streams, other threads) race: serialise them.  The call
+ * synchronises `stream` and returns WSIM_OK or the first error found (also
+ * the device-side checks of the CSR offsets and the agents-per-scene
+ * limit).  Outputs are the same as wsim_metrics on the same inputs. */
+int wsim_metrics_static(const wsim_config *cfg, const wsim_batch *b, const wsim_state *st,
+                        const wsim_metric_buf *m, int t, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

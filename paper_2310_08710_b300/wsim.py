@@ -78,13 +78,14 @@ def _load():
     lib.wsim_strerror.restype = C.c_char_p
     lib.wsim_destroy.argtypes = [vp]
     lib.wsim_destroy.restype = None
+    lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
     return lib
 
 
 lib = _load()
 
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
-            "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy")
+            "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static")
 
 
 class WsimError(RuntimeError):
@@ -226,3 +227,14 @@ class Sim:
         out = (C.c_int64 * 4)()
         _check(lib.wsim_counters(self._h, out, _stream(stream)), "wsim_counters")
         return np.array(out[:], dtype=np.int64)
+
+
+def metrics_static(batch: DeviceBatch, st: State, m: Metrics, t: int, cfg: Optional[WsimConfig] = None,
+                   stream=None):
+    """wsim_metrics_static: the metrics of `st` at log row t with no context
+    and no device allocation (for callers that cannot allocate; the library
+    keeps the scratch in a fixed device array shared by all calls).
+    Synchronises the stream."""
+    cfg = cfg if cfg is not None else default_config()
+    _check(lib.wsim_metrics_static(C.byref(cfg), C.byref(batch.c), C.byref(st.c()), C.byref(m.c()), t,
+                                   _stream(stream)), "wsim_metrics_static")
