@@ -185,7 +185,7 @@ def config_dict(args, b):
     wl = workload_desc(args.config)
     return {"workload": f"config {args.config}: {wl.name}", "scenes": int(b.S),
             "agents": int(b.N_tot), "rollout_steps": int(b.T), "roadgraph_points": int(b.R_tot),
-            "dt_s": 0.1, "rollout_mode": "persistent step kernel x80, CUDA graph",
+            "dt_s": 0.1, "rollout_mode": "scene-resident rollout kernel (one launch per rollout)",
             "l2": "inputs larger than L2 (road-edge segments + routes + logs streamed every rollout)"}
 
 
@@ -210,7 +210,7 @@ def main():
 
     def rollout():
         st.data.copy_(st0.data)
-        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_GRAPH)
+        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_FUSED)
 
     # Work counters of one rollout (untimed) for the roofline numerator.
     sim.set_counting(True)
@@ -247,7 +247,7 @@ def main():
     for _ in range(2):
         act.copy_(h_act, non_blocking=True)
         st.data.copy_(h_st, non_blocking=True)
-        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_GRAPH)
+        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_FUSED)
         h_rew.copy_(m.reward, non_blocking=True)
         h_flags.copy_(m.flags, non_blocking=True)
     torch.cuda.synchronize()
@@ -255,7 +255,7 @@ def main():
     for _ in range(args.steps):
         act.copy_(h_act, non_blocking=True)
         st.data.copy_(h_st, non_blocking=True)
-        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_GRAPH)
+        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_FUSED)
         h_rew.copy_(m.reward, non_blocking=True)
         h_flags.copy_(m.flags, non_blocking=True)
     e1.record(stream)
@@ -263,6 +263,23 @@ def main():
     ms_e2e = e0.elapsed_time(e1) / args.steps
     h2d = h_act.numel() * 4 + h_st.numel() * 4
     d2h = h_rew.numel() * 4 + h_flags.numel()
+
+    # The same rollout through the per-step paths, one timed rollout each:
+    # a CUDA graph of T persistent step launches, and one launch per scene
+    # and phase (the plain baseline).
+    modes = {}
+    for name, mode in (("graph_of_steps", wsim.MODE_GRAPH), ("plain_per_scene", wsim.MODE_PLAIN)):
+        st.data.copy_(st0.data)
+        sim.rollout(st, act, m, synth.T0, T, mode=mode)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st.data.copy_(st0.data)
+        sim.rollout(st, act, m, synth.T0, T, mode=mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mm = e0.elapsed_time(e1)
+        modes[name] = {"value": N * T / (mm / 1e3), "unit": UNIT, "ms_per_rollout": mm}
+    assert sim.status() == 0
 
     units = N * T
     if pg:
@@ -276,14 +293,14 @@ def main():
         return
     value = units / (ms / 1e3)
     flops = (FLOPS_PER_EVAL * cnt[0] + FLOPS_PER_TILE * cnt[1] + FLOPS_PER_PAIR * cnt[2] + FLOPS_PER_TEST * cnt[3]
-             + FLOPS_PER_AGENT * N * T) / T
-    launch_ms = ms / T  # whole graph per step kernel: includes the tiny memset nodes
+             + FLOPS_PER_AGENT * N * T)
+    launch_ms = ms  # one scene-resident launch per rollout (plus one 4-byte memset)
     achieved = flops / (launch_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config_dict(args, b),
-        "roofline": {"bound": "alu", "kernel": "k_step", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "kernel": "k_rollout", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
                      "flops_per_launch": flops, "launch_ms": launch_ms,
@@ -291,7 +308,8 @@ def main():
                                             "sat_pairs": int(cnt[2]), "idm_sample_tests": int(cnt[3])}},
         "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": args.steps * T,
+        "gpu_launches": args.steps,
+        "modes": modes,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

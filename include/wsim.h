@@ -66,6 +66,7 @@ extern "C" {
 #define WSIM_MODE_GRAPH 0      /* persistent step kernel per step, CUDA graph   */
 #define WSIM_MODE_STREAM 1     /* persistent step kernel per step, no graph     */
 #define WSIM_MODE_PLAIN 2      /* one launch per scene per phase (baseline)     */
+#define WSIM_MODE_FUSED 3      /* one scene-resident launch for all T steps     */
 
 /* Method constants.  wsim_default_config fills the values used throughout. */
 typedef struct {
@@ -155,10 +156,13 @@ int wsim_metrics(wsim_ctx *ctx, const wsim_state *st, const wsim_metric_buf *m, 
 /* Rollout (Sec. 5.1): T steps from time index t0.  st holds state t0 on
  * entry and state t0+T on return (device order); act_seq is [T][3][N_tot];
  * mseq arrays are [T][N_tot] ([T][S] for reward), row k holding the metrics
- * of time t0+k+1.  mode: WSIM_MODE_GRAPH replays a CUDA graph of T step
- * launches (captured on the first call and re-captured when pointers or T
- * change), WSIM_MODE_STREAM launches the same kernels directly,
- * WSIM_MODE_PLAIN launches one kernel per scene and phase.  All three give
+ * of time t0+k+1.  mode: WSIM_MODE_FUSED (fastest) runs one persistent
+ * launch in which each CTA carries whole scenes through all T steps with
+ * the state and the scene's road-edge segments resident in shared memory;
+ * WSIM_MODE_GRAPH replays a CUDA graph of T per-step launches (captured on
+ * the first call and re-captured when pointers or T change);
+ * WSIM_MODE_STREAM launches the same per-step kernels directly;
+ * WSIM_MODE_PLAIN launches one kernel per scene and phase.  All four give
  * bit-identical results.  traj (may be NULL) receives the states of times
  * t0+1..t0+T as [T] consecutive wsim_state-shaped blocks: traj[k] pointers
  * are the base pointers advanced by k*N_tot. */
@@ -188,9 +192,9 @@ void wsim_destroy(wsim_ctx *ctx);
  * this is for callers that cannot call cudaMalloc when they need the metrics
  * (a caching allocator or fixed arena that owns all device memory, code that
  * must not allocate).  The scratch wsim_init would allocate lives instead in
- * one file-scope device array of about 5.6 MB that every GPU loading the
+ * one file-scope device array of about 5.8 MB that every GPU loading the
  * library holds until the process exits.  Limits: at most 4096 scenes, and
- * R_tot + 3 * S <= 262144 (the packed road-edge segments must fit); larger
+ * R_tot + 31 * S <= 262144 (the packed road-edge segments must fit); larger
  * batches return WSIM_ESIZE before any work.  The first call on a device
  * looks up the array's device address (once per device, with that device
  * current); make that first call before any stream capture.  All calls share

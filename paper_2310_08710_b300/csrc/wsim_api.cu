@@ -20,7 +20,7 @@ struct wsim_ctx {
     wsim_config cfg;
     wsim_batch b;
     Params p;
-    int S = 0, N_tot = 0, grid = 1, count = 0;
+    int S = 0, N_tot = 0, grid = 1, roll_grid = 1, seg_cap = 0, count = 0;
     std::vector<int32_t> h_agent_off;
     // device scratch owned by the context
     int32_t *seg_off = nullptr, *seg_cnt = nullptr, *order = nullptr, *queue = nullptr, *status = nullptr;
@@ -28,6 +28,8 @@ struct wsim_ctx {
     float4* seg_geo = nullptr;
     float* seg_inv = nullptr;
     uint8_t* seg_flags = nullptr;
+    float4* seg_tiles = nullptr;
+    int32_t* hint = nullptr;  // [N_tot][4] nearest-segment cache of the per-step kernels
     unsigned long long* counters = nullptr;
     float* tmp = nullptr;  // ping-pong state, 10 x N_tot
     // captured rollout
@@ -98,7 +100,9 @@ StepArgs base_args(const wsim_ctx* c) {
     a.route_y = b.route_y;
     a.log_x = b.log_x;
     a.log_y = b.log_y;
-    a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags};
+    a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags, c->seg_tiles};
+    a.hint = c->hint;
+    a.seg_cap = c->seg_cap;
     a.order = c->order;
     a.status = c->status;
     a.counters = c->counters;
@@ -263,8 +267,11 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     };
     if ((rc = dalloc(&c->seg_off, S + 1)) || (rc = dalloc(&c->seg_cnt, S)) || (rc = dalloc(&c->order, S)) ||
         (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->counters, 4)) ||
-        (rc = dalloc(&c->tmp, static_cast<size_t>(N) * 10)) || (rc = ensure_queue(c, 128)))
+        (rc = dalloc(&c->tmp, static_cast<size_t>(N) * 10)) || (rc = ensure_queue(c, 128)) ||
+        (rc = dalloc(&c->hint, static_cast<size_t>(N) * 4)))
         return fail(rc);
+    if (cudaMemsetAsync(c->hint, 0xff, std::max<size_t>(N, 1) * 4 * sizeof(int32_t), st) != cudaSuccess)
+        return fail(WSIM_ECUDA);
     if (cudaMemsetAsync(c->status, 0, sizeof(int32_t), st) != cudaSuccess ||
         cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess)
         return fail(WSIM_ECUDA);
@@ -279,7 +286,8 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
         return fail(WSIM_ECUDA);
     for (int s = 0; s < S; ++s) off[s + 1] = off[s] + ((cnt[s] + kSegAlign - 1) / kSegAlign) * kSegAlign;
     const size_t E = static_cast<size_t>(off[S]);
-    if ((rc = dalloc(&c->seg_geo, E)) || (rc = dalloc(&c->seg_inv, E)) || (rc = dalloc(&c->seg_flags, E)))
+    if ((rc = dalloc(&c->seg_geo, E)) || (rc = dalloc(&c->seg_inv, E)) || (rc = dalloc(&c->seg_flags, E)) ||
+        (rc = dalloc(&c->seg_tiles, 2 * (E / kTile))))
         return fail(rc);
     if (cudaMemsetAsync(c->seg_geo, 0, std::max<size_t>(E, 1) * sizeof(float4), st) != cudaSuccess ||
         cudaMemsetAsync(c->seg_inv, 0, std::max<size_t>(E, 1) * sizeof(float), st) != cudaSuccess ||
@@ -287,7 +295,8 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
         cudaMemcpyAsync(c->seg_off, off.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return fail(WSIM_ECUDA);
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, S, c->seg_off, c->seg_geo,
-                        c->seg_inv, c->seg_flags, st) != cudaSuccess)
+                        c->seg_inv, c->seg_flags, st) != cudaSuccess ||
+        launch_tile_build(S, c->seg_off, c->seg_cnt, c->seg_geo, c->seg_tiles, st) != cudaSuccess)
         return fail(WSIM_ECUDA);
 
     // Scene work list, most expensive first (longest-processing-time order).
@@ -307,6 +316,13 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     c->grid = std::min(S, sms * step_blocks_per_sm());
+    // Scene-resident rollout: stage up to the largest scene's segments.
+    int need = 0;
+    for (int s = 0; s < S; ++s) need = std::max(need, off[s + 1] - off[s]);
+    c->seg_cap = std::min(need, rollout_max_seg_cap());
+    int rbps = 1;
+    if (rollout_prepare(c->seg_cap, &rbps) != cudaSuccess) return fail(WSIM_ECUDA);
+    c->roll_grid = std::min(S, sms * rbps);
     if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(WSIM_ECUDA);
     c->last = st;
     *out = c;
@@ -333,7 +349,7 @@ int wsim_metrics(wsim_ctx* c, const wsim_state* st, const wsim_metric_buf* m, in
 int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_t* ctrl, int t0, int T, int mode,
                  const wsim_metric_buf* mseq, const wsim_state* traj, void* stream) {
     if (!c || !state_ok(st) || !act_seq || !metrics_ok(mseq) || (traj && !state_ok(traj))) return WSIM_EINVAL;
-    if (mode < WSIM_MODE_GRAPH || mode > WSIM_MODE_PLAIN) return WSIM_EINVAL;
+    if (mode < WSIM_MODE_GRAPH || mode > WSIM_MODE_FUSED) return WSIM_EINVAL;
     if (T < 1 || t0 < 0 || t0 + T >= c->b.T_log) return WSIM_ESIZE;
     cudaStream_t s = S_(stream);
     c->last = s;
@@ -349,6 +365,23 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
     k.t0 = t0;
     k.T = T;
     k.has_traj = traj != nullptr;
+    if (mode == WSIM_MODE_FUSED) {
+        StepArgs a = base_args(c);
+        a.in = cstate(st);
+        a.out = mstate(st);
+        a.act = act_seq;
+        a.ctrl = ctrl;
+        a.m = MetricsP{mseq->ov, mseq->off, mseq->logdiv, mseq->flags, mseq->reward};
+        a.t_log = t0 + 1;
+        a.T = T;
+        if (traj) a.traj = mstate(traj);
+        a.do_transition = 1;
+        a.do_metrics = 1;
+        a.queue = c->queue;
+        CK(cudaMemsetAsync(c->queue, 0, sizeof(int32_t), s));
+        CK(launch_rollout(a, c->roll_grid, s));
+        return WSIM_OK;
+    }
     if (mode != WSIM_MODE_GRAPH) return enqueue_rollout(c, k, mode == WSIM_MODE_PLAIN, s);
 
     if (!c->exec || !c->have_key || std::memcmp(&k, &c->key, sizeof(k)) != 0) {
@@ -429,6 +462,8 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->seg_geo);
     cudaFree(c->seg_inv);
     cudaFree(c->seg_flags);
+    cudaFree(c->seg_tiles);
+    cudaFree(c->hint);
     delete c;
 }
 

@@ -8,21 +8,24 @@
 namespace wsim {
 
 constexpr int kMaxN = WSIM_MAX_AGENTS;  // agents per scene
-constexpr int kThreads = 256;           // threads per step CTA (8 warps)
-constexpr int kWarps = kThreads / 32;
-constexpr int kChunk = 512;             // road-edge segments per staged chunk
-constexpr int kSegAlign = 4;            // per-scene segment arrays start on 16 B
+constexpr int kStepThreads = 256;       // threads per CTA of the per-step kernels
+constexpr int kRollThreads = 512;       // threads per CTA of the scene-resident rollout kernel
+constexpr int kTile = 32;               // road-edge segments per culling tile (one per lane)
+constexpr int kSegAlign = kTile;        // per-scene segment arrays start on a tile boundary
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
 
-// Packed road-edge segments of the whole batch (built by wsim_init).
-// Scene s owns entries [seg_off[s], seg_off[s] + seg_cnt[s]); seg_off is a
-// multiple of kSegAlign and the region is zero-padded up to the next one.
+// Packed road-edge segments of the whole batch (built by wsim_init).  Scene s
+// owns segments [off[s], off[s] + cnt[s]); off[s] is a multiple of kTile and
+// the region is zero-padded to the next multiple.  Tile t of the batch covers
+// segments [t kTile, (t+1) kTile) and has two float4 records: its bounding box
+// (xmin, ymin, xmax, ymax) and two points that lie on its segments.
 struct Segs {
-    const int32_t* off;     // [S+1] padded offsets
-    const int32_t* cnt;     // [S]
-    const float4* geo;      // (ax, ay, ux, uy): start point and k -> k+1 vector
-    const float* inv;       // 1 / |u|^2
-    const uint8_t* flags;   // bit0: a segment ends where this one starts; bit1: one starts where it ends
+    const int32_t* off;    // [S+1]
+    const int32_t* cnt;    // [S]
+    const float4* geo;     // (ax, ay, ux, uy): start point and k -> k+1 vector
+    const float* inv;      // 1 / |u|^2
+    const uint8_t* flags;  // bit0: a segment ends where this one starts; bit1: one starts where it ends
+    const float4* tiles;   // [2 * tiles]
 };
 
 struct StateP {
@@ -42,7 +45,7 @@ struct Params {
     float dt, amax, b, T, s0, dq, h, inv_h, gap_min, idm_sqrt_ab2;  // 2 sqrt(a b)
 };
 
-// Everything one step kernel needs.
+// Everything a step or rollout kernel needs.
 struct StepArgs {
     int S, N_tot, T_log;
     const int32_t* agent_off;
@@ -52,30 +55,41 @@ struct StepArgs {
     const float *route_x, *route_y;
     const float *log_x, *log_y;
     Segs segs;
+    int32_t* hint;    // [N_tot][4] nearest-segment cache of the per-step kernels (may be null)
     CStateP in;       // state t (transition) or the state measured (metrics only)
-    StateP out;       // state t+1 (transition)
-    const float* act; // [3][N_tot]
+    StateP out;       // state t+1 (per-step) / final state (rollout)
+    const float* act; // [3][N_tot] (per step) or [T][3][N_tot] (rollout)
     const uint8_t* ctrl;
-    MetricsP m;       // metrics of `out` (or of `in` when do_transition == 0)
-    int t_log;        // log row of the metrics
+    MetricsP m;       // metrics of `out` (or of `in` when do_transition == 0); rollout: [T][...]
+    int t_log;        // log row of the metrics (rollout: of the first step)
+    int T;            // rollout steps (scene-resident kernel)
+    StateP traj;      // rollout: states of every step, [T][N_tot] blocks (x == nullptr: none)
     int do_transition, do_metrics;
     const int32_t* order;  // cost-ordered scene ids
     int32_t* queue;        // scene work counter (zeroed before each launch)
     int32_t* status;       // sticky device status
     unsigned long long* counters;  // [4] work counters (when count != 0)
     int count;
+    int seg_cap;           // rollout: segments that fit in the shared-memory stage
     Params p;
 };
 
-// Launchers (kernels.cu).
+// Launchers (wsim_kernels.cu, wsim_rollout.cu).
 cudaError_t launch_seg_count(const int32_t* rg_off, const float* rg_x, const float* rg_y, const int32_t* rg_poly,
                              const uint8_t* rg_type, const uint8_t* rg_valid, int S, int32_t* cnt,
                              cudaStream_t st);
 cudaError_t launch_seg_pack(const int32_t* rg_off, const float* rg_x, const float* rg_y, const int32_t* rg_poly,
                             const uint8_t* rg_type, const uint8_t* rg_valid, int S, const int32_t* seg_off,
                             float4* geo, float* inv, uint8_t* flags, cudaStream_t st);
+cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const float4* geo,
+                              float4* tiles, cudaStream_t st);
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_plain_scene(const StepArgs& a, int scene, cudaStream_t st);
 int step_blocks_per_sm();
+// Scene-resident rollout: dynamic shared memory for `seg_cap` staged segments.
+size_t rollout_smem_bytes(int seg_cap);
+int rollout_max_seg_cap();
+cudaError_t rollout_prepare(int seg_cap, int* blocks_per_sm);
+cudaError_t launch_rollout(const StepArgs& a, int grid, cudaStream_t st);
 
 }  // namespace wsim

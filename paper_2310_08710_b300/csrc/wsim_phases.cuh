@@ -1,0 +1,617 @@
+// Phases of one simulated step of one scene, shared by the per-step kernel,
+// the plain per-scene kernels and the scene-resident rollout kernel.  A CTA
+// of NT threads owns one scene; agent data lives in an AgentSmem block.
+#pragma once
+#include <math_constants.h>
+
+#include "wsim_device.cuh"
+
+namespace wsim {
+
+#define WSIM_INF CUDART_INF_F
+constexpr unsigned kFull = 0xffffffffu;
+
+struct __align__(16) AgentSmem {
+    uint64_t bar[2];
+    unsigned long long cnt[4];
+    // current state (t during the transition, t+1 after the writeback)
+    float xh[kMaxN], xl[kMaxN], yh[kMaxN], yl[kMaxN], c[kMaxN], s[kMaxN], hl[kMaxN], hw[kMaxN];
+    float vx[kMaxN], vy[kMaxN], thh[kMaxN], thl[kMaxN], sh[kMaxN], sl[kMaxN];
+    // next state
+    float nxh[kMaxN], nxl[kMaxN], nyh[kMaxN], nyl[kMaxN], nth[kMaxN], ntl[kMaxN];
+    float nvx[kMaxN], nvy[kMaxN], nsh[kMaxN], nsl[kMaxN];
+    float ov[kMaxN], off[kMaxN];
+    int32_t hint[4 * kMaxN];  // scene-resident nearest-segment cache
+    uint8_t valid[kMaxN];
+    int scene;
+    int reward;
+};
+
+// Work counters of one thread (flushed into the CTA's AgentSmem::cnt).
+struct Counts {
+    unsigned long long evals = 0, tiles = 0, pairs = 0, tests = 0;
+};
+
+// One scene's packed road-edge segments, in global or shared memory.
+struct SegView {
+    const float4* geo;
+    const float* inv;
+    const uint8_t* flags;
+    const float4* tiles;  // 2 per tile: bounding box, two points on segments
+    int E, nt;
+};
+
+template <class T> __device__ __forceinline__ T pick4(const T (&a)[4], int k) {
+    return k == 0 ? a[0] : (k == 1 ? a[1] : (k == 2 ? a[2] : a[3]));
+}
+
+// ---------------------------------------------------------------------------
+// Loading and storing agent state.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, int a0, int N) {
+    for (int i = threadIdx.x; i < N; i += NT) {
+        const int g = a0 + i;
+        sm.xh[i] = st.x[g];
+        sm.xl[i] = st.x_lo[g];
+        sm.yh[i] = st.y[g];
+        sm.yl[i] = st.y_lo[g];
+        const float th = st.th[g], tl = st.th_lo[g];
+        sm.thh[i] = th;
+        sm.thl[i] = tl;
+        float c, s;
+        comp_sincos(th, tl, c, s);
+        sm.c[i] = c;
+        sm.s[i] = s;
+        sm.hl[i] = 0.5f * A.L[g];
+        sm.hw[i] = 0.5f * A.W[g];
+        sm.vx[i] = st.vx[g];
+        sm.vy[i] = st.vy[g];
+        sm.sh[i] = st.s[g];
+        sm.sl[i] = st.s_lo[g];
+        sm.valid[i] = A.valid[g];
+    }
+}
+
+// Make the next state current; optionally store it to global memory.
+template <int NT>
+__device__ void writeback(AgentSmem& sm, const StateP* out, int a0, int N) {
+    for (int i = threadIdx.x; i < N; i += NT) {
+        if (out) {
+            const int g = a0 + i;
+            out->x[g] = sm.nxh[i];
+            out->x_lo[g] = sm.nxl[i];
+            out->y[g] = sm.nyh[i];
+            out->y_lo[g] = sm.nyl[i];
+            out->th[g] = sm.nth[i];
+            out->th_lo[g] = sm.ntl[i];
+            out->vx[g] = sm.nvx[i];
+            out->vy[g] = sm.nvy[i];
+            out->s[g] = sm.nsh[i];
+            out->s_lo[g] = sm.nsl[i];
+        }
+        sm.xh[i] = sm.nxh[i];
+        sm.xl[i] = sm.nxl[i];
+        sm.yh[i] = sm.nyh[i];
+        sm.yl[i] = sm.nyl[i];
+        sm.thh[i] = sm.nth[i];
+        sm.thl[i] = sm.ntl[i];
+        float c, s;
+        comp_sincos(sm.nth[i], sm.ntl[i], c, s);
+        sm.c[i] = c;
+        sm.s[i] = s;
+        sm.vx[i] = sm.nvx[i];
+        sm.vy[i] = sm.nvy[i];
+        sm.sh[i] = sm.nsh[i];
+        sm.sl[i] = sm.nsl[i];
+    }
+}
+
+// Store the current state to global memory.
+template <int NT>
+__device__ void store_state(const AgentSmem& sm, const StateP& out, int a0, int N) {
+    for (int i = threadIdx.x; i < N; i += NT) {
+        const int g = a0 + i;
+        out.x[g] = sm.xh[i];
+        out.x_lo[g] = sm.xl[i];
+        out.y[g] = sm.yh[i];
+        out.y_lo[g] = sm.yl[i];
+        out.th[g] = sm.thh[i];
+        out.th_lo[g] = sm.thl[i];
+        out.vx[g] = sm.vx[i];
+        out.vy[g] = sm.vy[i];
+        out.s[g] = sm.sh[i];
+        out.s_lo[g] = sm.sl[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Route polyline: parameter (hi + lo) -> segment index and fraction.
+// Segment k = floor(s / h), clamped to the route; beyond either end the
+// fraction leaves [0, 1) so the end segment is extrapolated.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void route_locate(float hi, float lo, const Params& p, int P, int& seg, float& tau) {
+    const float u = hi * p.inv_h;
+    const float fl = floorf(u);
+    tau = fmaf(lo, p.inv_h, u - fl);
+    seg = static_cast<int>(fl);
+    if (tau < 0.f) {
+        seg -= 1;
+        tau += 1.f;
+    } else if (tau >= 1.f) {
+        seg += 1;
+        tau -= 1.f;
+    }
+    if (seg < 0) {
+        tau += static_cast<float>(seg);
+        seg = 0;
+    }
+    if (seg > P - 2) {
+        tau += static_cast<float>(seg - (P - 2));
+        seg = P - 2;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// IDM route following of agent i (Sec. 3.5; textbook IDM of Treiber et al.).
+// Warp-cooperative: lane k holds look-ahead sample k+1 at route parameter
+// s + L/2 + dq (k+1).  Candidate agents are found 32 at a time (one per lane)
+// by a bounding-circle test; for each candidate the warp tests all 32
+// samples against its box widened by half this agent's width, and the
+// ballot's lowest set bit is the first hit.  The lead is the hit agent with
+// the smallest bumper gap (ties: lower index).
+// ---------------------------------------------------------------------------
+static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N, int i, int lane, Counts& cnt) {
+    const Params& p = A.p;
+    const int g = a0 + i;
+    const int ro = A.route_off[g];
+    const int P = A.route_off[g + 1] - ro;
+    const float* rx = A.route_x + ro;
+    const float* ry = A.route_y + ro;
+    const float s_hi = sm.sh[i], s_lo = sm.sl[i];
+    const float vxi = sm.vx[i], vyi = sm.vy[i];
+    const float v = sqrtf(fmaf(vxi, vxi, vyi * vyi));
+    const float hli = sm.hl[i], wi = sm.hw[i];
+
+    // This lane's look-ahead sample.
+    float bh, bl;
+    two_sum(s_hi, fmaf(p.dq, static_cast<float>(lane + 1), hli), bh, bl);
+    bl = __fadd_rn(bl, s_lo);
+    int seg;
+    float tau;
+    route_locate(bh, bl, p, P, seg, tau);
+    const float Px = rx[seg], Py = ry[seg];
+    const float dx = rx[seg + 1] - Px, dy = ry[seg + 1] - Py;
+    const float qox = tau * dx, qoy = tau * dy;
+    const float rn = rsqrtf(fmaf(dx, dx, dy * dy));
+    const float tx = dx * rn, ty = dy * rn;
+
+    // Bounding circle of the samples.
+    const float qx = Px + qox, qy = Py + qoy;
+    const float cx = __shfl_sync(kFull, qx, 15), cy = __shfl_sync(kFull, qy, 15);
+    float rq = sqrtf((qx - cx) * (qx - cx) + (qy - cy) * (qy - cy));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rq = fmaxf(rq, __shfl_xor_sync(kFull, rq, o));
+
+    const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
+    int lead = -1, lead_hit = 0;
+    float gbest = WSIM_INF;
+    for (int jb = 0; jb < N; jb += 32) {
+        const int jl = jb + lane;
+        bool cand = false;
+        if (jl < N && jl != i && sm.valid[jl]) {
+            const float ex = sm.xh[jl] - cx, ey = sm.yh[jl] - cy;
+            const float reach = rq + sm.hl[jl] + sm.hw[jl] + 2.f * wi + 0.05f;
+            cand = ex * ex + ey * ey <= reach * reach;
+        }
+        unsigned cm = __ballot_sync(kFull, cand);
+        while (cm) {
+            const int j = jb + __ffs(cm) - 1;
+            cm &= cm - 1;
+            if (lane == 0) cnt.tests += 32;
+            const float xjh = sm.xh[j], yjh = sm.yh[j];
+            const float hlj = sm.hl[j], hwj = sm.hw[j];
+            const float rxq = (Px - xjh) + (qox - sm.xl[j]);
+            const float ryq = (Py - yjh) + (qoy - sm.yl[j]);
+            const float cj = sm.c[j], sj = sm.s[j];
+            const float pu = fabsf(fmaf(rxq, cj, ryq * sj));
+            const float pn = fabsf(fmaf(-rxq, sj, ryq * cj));
+            const float m = fminf(hlj + wi - pu, hwj + wi - pn);
+            const unsigned hits = __ballot_sync(kFull, m >= 0.f);
+            if (!hits) continue;
+            const float ddx = comp_diff(xjh, sm.xl[j], xih, xil);
+            const float ddy = comp_diff(yjh, sm.yl[j], yih, yil);
+            const float gap = fmaxf(p.gap_min, sqrtf(fmaf(ddx, ddx, ddy * ddy)) - (hli + hlj));
+            if (gap < gbest) {
+                gbest = gap;
+                lead = j;
+                lead_hit = __ffs(hits) - 1;
+            }
+        }
+    }
+
+    // IDM acceleration (exponent 4).
+    const float r = v / A.v0[g];
+    const float r2 = r * r;
+    const float r4 = r2 * r2;
+    float acc;
+    if (lead >= 0) {
+        const float tlx = __shfl_sync(kFull, tx, lead_hit);
+        const float tly = __shfl_sync(kFull, ty, lead_hit);
+        const float vl = fmaf(sm.vx[lead], tlx, sm.vy[lead] * tly);
+        const float sstar = p.s0 + fmaxf(0.f, fmaf(v, p.T, v * (v - vl) / p.idm_sqrt_ab2));
+        const float q = sstar / gbest;
+        acc = p.amax * (1.f - r4 - q * q);
+    } else {
+        acc = p.amax * (1.f - r4);
+    }
+    // Advance along the route by the trapezoidal distance of the new speed.
+    const float vn = fmaxf(0.f, fmaf(acc, p.dt, v));
+    float sh = s_hi, sl = s_lo;
+    comp_add(sh, sl, 0.5f * (v + vn) * p.dt);
+    int sg;
+    float ta;
+    route_locate(sh, sl, p, P, sg, ta);
+    const float Qx = rx[sg], Qy = ry[sg];
+    const float ux = rx[sg + 1] - Qx, uy = ry[sg + 1] - Qy;
+    if (lane == 0) {
+        float xh, xe, yh, ye;
+        two_sum(Qx, ta * ux, xh, xe);
+        two_sum(Qy, ta * uy, yh, ye);
+        const float un = rsqrtf(fmaf(ux, ux, uy * uy));
+        sm.nxh[i] = xh;
+        sm.nxl[i] = xe;
+        sm.nyh[i] = yh;
+        sm.nyl[i] = ye;
+        sm.nth[i] = atan2f(uy, ux);
+        sm.ntl[i] = 0.f;
+        sm.nvx[i] = vn * ux * un;
+        sm.nvy[i] = vn * uy * un;
+        sm.nsh[i] = sh;
+        sm.nsl[i] = sl;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Transition t -> t+1 of one scene into the n* arrays.  act is [3][N_tot].
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* act, int a0, int N, Counts& cnt) {
+    constexpr int NW = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < N; i += NW) {
+        if (A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i]) idm_agent(sm, A, a0, N, i, lane, cnt);
+    }
+    const Params& p = A.p;
+    for (int i = threadIdx.x; i < N; i += NT) {
+        const int g = a0 + i;
+        const int kind = A.kind[g];
+        if (kind == WSIM_KIND_IDM && sm.valid[i]) continue;
+        float xh = sm.xh[i], xl = sm.xl[i], yh = sm.yh[i], yl = sm.yl[i];
+        float thh = sm.thh[i], thl = sm.thl[i];
+        float vx = sm.vx[i], vy = sm.vy[i];
+        const bool moves = sm.valid[i] && kind != WSIM_KIND_IDM && (A.ctrl == nullptr || A.ctrl[g]);
+        if (moves && kind == WSIM_KIND_BICYCLE) {
+            // App. A.1 bicycle forward dynamics.
+            const float a = act[g], k = act[A.N_tot + g];
+            if (!isfinite(a) || !isfinite(k)) set_status(A.status, WSIM_ENONFINITE);
+            const float v = sqrtf(fmaf(vx, vx, vy * vy));
+            const float ah = a * (0.5f * p.dt * p.dt);
+            comp_add(xh, xl, fmaf(vx, p.dt, ah * sm.c[i]));
+            comp_add(yh, yl, fmaf(vy, p.dt, ah * sm.s[i]));
+            comp_add(thh, thl, k * fmaf(v, p.dt, ah));
+            const float vn = fmaf(a, p.dt, v);
+            float cn, sn;
+            comp_sincos(thh, thl, cn, sn);
+            vx = vn * cn;
+            vy = vn * sn;
+        } else if (moves && kind == WSIM_KIND_DELTA) {
+            // App. A.1 delta dynamics.
+            const float ddx = act[g], ddy = act[A.N_tot + g], dth = act[2 * A.N_tot + g];
+            if (!isfinite(ddx) || !isfinite(ddy) || !isfinite(dth)) set_status(A.status, WSIM_ENONFINITE);
+            comp_add(xh, xl, ddx);
+            comp_add(yh, yl, ddy);
+            comp_add(thh, thl, dth);
+            vx = ddx / p.dt;
+            vy = ddy / p.dt;
+        }
+        sm.nxh[i] = xh;
+        sm.nxl[i] = xl;
+        sm.nyh[i] = yh;
+        sm.nyl[i] = yl;
+        sm.nth[i] = thh;
+        sm.ntl[i] = thl;
+        sm.nvx[i] = vx;
+        sm.nvy[i] = vy;
+        sm.nsh[i] = sm.sh[i];
+        sm.nsl[i] = sm.sl[i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Overlap of agent i (warp): ov_i = max over valid j != i of the SAT depth
+// d_ij, computed in the canonical order (min(i,j), max(i,j)) so that
+// d_ij == d_ji bit for bit.  Returns the value in every lane.
+// ---------------------------------------------------------------------------
+static __device__ float overlap_agent(const AgentSmem& sm, int N, int i, int lane, Counts& cnt) {
+    float best = -WSIM_INF;
+    for (int j = lane; j < N; j += 32) {
+        if (j == i || !sm.valid[j]) continue;
+        const int lo = min(i, j), hi = max(i, j);
+        const float dx = comp_diff(sm.xh[hi], sm.xl[hi], sm.xh[lo], sm.xl[lo]);
+        const float dy = comp_diff(sm.yh[hi], sm.yl[hi], sm.yh[lo], sm.yl[lo]);
+        best = fmaxf(best, sat_depth(dx, dy, sm.c[lo], sm.s[lo], sm.hl[lo], sm.hw[lo], sm.c[hi], sm.s[hi],
+                                     sm.hl[hi], sm.hw[hi]));
+        ++cnt.pairs;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
+    return best;
+}
+
+// Squared distance from corner (ch + cl) to segment G; raw projection in *traw.
+__device__ __forceinline__ float seg_dist2(float4 G, float iv, float cxh, float cxl, float cyh, float cyl,
+                                           float* traw = nullptr) {
+    const float wx = (cxh - G.x) + cxl;
+    const float wy = (cyh - G.y) + cyl;
+    const float dot = fmaf(wx, G.z, wy * G.w) * iv;
+    if (traw) *traw = dot;
+    const float t = __saturatef(dot);
+    const float ex = fmaf(-t, G.z, wx), ey = fmaf(-t, G.w, wy);
+    return fmaf(ex, ex, ey * ey);
+}
+
+// ---------------------------------------------------------------------------
+// Off-road of agent i (warp; Sec. 3.4: the road lies left of an oriented road
+// edge).  For each box corner: the nearest road-edge segment (exact, ties to
+// the lower index) and the side of its nearest feature, with the vertex rule
+// where that feature is a vertex shared by two segments.  Returns
+// max over corners of the signed distance (+ = off road) in every lane.
+//
+// Culling: an upper bound U_k on corner k's nearest distance comes from the
+// segment that was nearest at the previous step (hint) or, without one, from
+// points known to lie on segments (two per tile).  Only tiles whose bounding
+// box lies within U_k of corner k are scanned (lane = segment of the tile),
+// so the result equals the exhaustive scan.  hint (may be null) is read and
+// updated with the winners.
+// ---------------------------------------------------------------------------
+static __device__ float offroad_agent(const SegView& V, int lane, float xh, float xl, float yh, float yl, float c, float s,
+                               float hl, float hw, int32_t* hint, Counts& cnt) {
+    if (V.E == 0) {
+        if (hint && lane < 4) hint[lane] = -1;
+        return -WSIM_INF;
+    }
+    float cxl[4], cyl[4], px[4], py[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float a = (k < 2 ? 1.f : -1.f) * hl;
+        const float b = (k == 0 || k == 3 ? 1.f : -1.f) * hw;
+        cxl[k] = xl + fmaf(a, c, -b * s);
+        cyl[k] = yl + fmaf(a, s, b * c);
+        px[k] = xh + cxl[k];
+        py[k] = yh + cyl[k];
+    }
+    // Upper bounds from the previous winners (lane k evaluates corner k).
+    float dh = WSIM_INF;
+    if (hint && lane < 4) {
+        const int e = hint[lane];
+        if (e >= 0 && e < V.E) dh = seg_dist2(V.geo[e], V.inv[e], xh, pick4(cxl, lane), yh, pick4(cyl, lane));
+    }
+    float u2[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) u2[k] = __shfl_sync(kFull, dh, k);
+    if (!(u2[0] < WSIM_INF && u2[1] < WSIM_INF && u2[2] < WSIM_INF && u2[3] < WSIM_INF)) {
+        // Bounds from points on segments (two per tile).
+        float m[4] = {WSIM_INF, WSIM_INF, WSIM_INF, WSIM_INF};
+        for (int t = lane; t < V.nt; t += 32) {
+            const float4 P = V.tiles[2 * t + 1];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float ax = P.x - px[k], ay = P.y - py[k], bx = P.z - px[k], by = P.w - py[k];
+                m[k] = fminf(m[k], fminf(fmaf(ax, ax, ay * ay), fmaf(bx, bx, by * by)));
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) m[k] = fminf(m[k], __shfl_xor_sync(kFull, m[k], o));
+            u2[k] = fminf(u2[k], m[k]);
+        }
+        if (lane == 0) cnt.tiles += V.nt;
+    }
+    // Float32 corner positions in the box tests and bounds: 2 mm of slack.
+    float lim2[4], ucap = 0.f;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float u = sqrtf(u2[k]) + 2e-3f;
+        lim2[k] = u * u;
+        ucap = fmaxf(ucap, u);
+    }
+    // Agent-level pre-test: the centre's distance to the box minus the half
+    // diagonal bounds every corner's distance from below.
+    const float ccx = xh + xl, ccy = yh + yl;
+    const float rad = sqrtf(fmaf(hl, hl, hw * hw)) + 1e-3f;
+    const float clim = (ucap + rad) * (ucap + rad);
+
+    float bd[4] = {WSIM_INF, WSIM_INF, WSIM_INF, WSIM_INF};
+    int bi[4] = {-1, -1, -1, -1};
+    for (int base = 0; base < V.nt; base += 32) {
+        const int t = base + lane;
+        unsigned cm = 0;
+        if (t < V.nt) {
+            const float4 B = V.tiles[2 * t];
+            float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
+            float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
+            if (fmaf(dx, dx, dy * dy) <= clim) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    dx = fmaxf(fmaxf(B.x - px[k], px[k] - B.z), 0.f);
+                    dy = fmaxf(fmaxf(B.y - py[k], py[k] - B.w), 0.f);
+                    if (fmaf(dx, dx, dy * dy) <= lim2[k]) cm |= 1u << k;
+                }
+            }
+        }
+        if (lane == 0) cnt.tiles += min(32, V.nt - base);
+        unsigned want = __ballot_sync(kFull, cm != 0);
+        while (want) {
+            const int l = __ffs(want) - 1;
+            want &= want - 1;
+            const unsigned km = __shfl_sync(kFull, cm, l);
+            const int e = (base + l) * kTile + lane;
+            if (lane == 0) cnt.evals += 32 * __popc(km);
+            if (e < V.E) {
+                const float4 G = V.geo[e];
+                const float iv = V.inv[e];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if ((km >> k) & 1u) {
+                        const float d2 = seg_dist2(G, iv, xh, cxl[k], yh, cyl[k]);
+                        if (d2 < bd[k]) {
+                            bd[k] = d2;
+                            bi[k] = e;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    // Nearest segment per corner: lexicographic (distance, index) minimum.
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float od = __shfl_xor_sync(kFull, bd[k], o);
+            const int oi = __shfl_xor_sync(kFull, bi[k], o);
+            if (od < bd[k] || (od == bd[k] && static_cast<unsigned>(oi) < static_cast<unsigned>(bi[k]))) {
+                bd[k] = od;
+                bi[k] = oi;
+            }
+        }
+    }
+    // Side of the nearest feature (lane k: corner k).
+    float sd = -WSIM_INF;
+    if (lane < 4) {
+        const int e = pick4(bi, lane);
+        if (e >= 0) {
+            const float4 G = V.geo[e];
+            const uint8_t fl = V.flags[e];
+            float traw;
+            const float cl = pick4(cxl, lane), dl = pick4(cyl, lane);
+            seg_dist2(G, V.inv[e], xh, cl, yh, dl, &traw);
+            const float wx = (xh - G.x) + cl, wy = (yh - G.y) + dl;
+            bool on;
+            if (traw <= 0.f && (fl & 1)) {
+                const float4 Gp = V.geo[e - 1];
+                const bool l1 = fmaf(Gp.z, wy, -Gp.w * wx) > 0.f;
+                const bool l2 = fmaf(G.z, wy, -G.w * wx) > 0.f;
+                const float turn = fmaf(Gp.z, G.w, -Gp.w * G.z);
+                on = turn > 0.f ? (l1 && l2) : (turn < 0.f ? (l1 || l2) : l1);
+            } else if (traw >= 1.f && (fl & 2)) {
+                const float4 Gn = V.geo[e + 1];
+                const float qx = wx - G.z, qy = wy - G.w;
+                const bool l1 = fmaf(G.z, qy, -G.w * qx) > 0.f;
+                const bool l2 = fmaf(Gn.z, qy, -Gn.w * qx) > 0.f;
+                const float turn = fmaf(G.z, Gn.w, -G.w * Gn.z);
+                on = turn > 0.f ? (l1 && l2) : (turn < 0.f ? (l1 || l2) : l1);
+            } else {
+                on = fmaf(G.z, wy, -G.w * wx) > 0.f;
+            }
+            const float d = sqrtf(pick4(bd, lane));
+            sd = on ? -d : d;
+        }
+        if (hint) hint[lane] = e;
+    }
+    sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 1));
+    sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 2));
+    return __shfl_sync(kFull, sd, 0);
+}
+
+// ---------------------------------------------------------------------------
+// Overlap and off-road of every agent (warp per agent).
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_base, int N, bool do_ov, bool do_off,
+                              Counts& cnt) {
+    constexpr int NW = NT / 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < N; i += NW) {
+        if (!sm.valid[i]) continue;
+        if (do_ov) {
+            const float o = overlap_agent(sm, N, i, lane, cnt);
+            if (lane == 0) sm.ov[i] = o;
+        }
+        if (do_off) {
+            const float f = offroad_agent(V, lane, sm.xh[i], sm.xl[i], sm.yh[i], sm.yl[i], sm.c[i], sm.s[i], sm.hl[i],
+                                          sm.hw[i], hint_base ? hint_base + 4 * i : nullptr, cnt);
+            if (lane == 0) sm.off[i] = f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Log divergence, flags, metric stores and the scene reward.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void phase_finish(AgentSmem& sm, const StepArgs& A, const MetricsP& m, int32_t* reward, int t_log, int a0,
+                             int N) {
+    if (threadIdx.x == 0) sm.reward = 0;
+    __syncthreads();
+    int r = 0;
+    for (int i = threadIdx.x; i < N; i += NT) {
+        const int g = a0 + i;
+        float ov = 0.f, off = 0.f, ld = 0.f;
+        uint8_t fl = 0;
+        if (sm.valid[i]) {
+            const size_t li = static_cast<size_t>(t_log) * A.N_tot + g;
+            const float dx = (sm.xh[i] - A.log_x[li]) + sm.xl[i];
+            const float dy = (sm.yh[i] - A.log_y[li]) + sm.yl[i];
+            ld = sqrtf(fmaf(dx, dx, dy * dy));
+            ov = sm.ov[i];
+            off = sm.off[i];
+            fl = (ov > 0.f ? WSIM_FLAG_COLLISION : 0) | (off > 0.f ? WSIM_FLAG_OFFROAD : 0);
+            r -= (ov > 0.f) + (off > 0.f);
+        }
+        m.ov[g] = ov;
+        m.off[g] = off;
+        m.logdiv[g] = ld;
+        m.flags[g] = fl;
+    }
+    if (r) atomicAdd(&sm.reward, r);
+    __syncthreads();
+    if (threadIdx.x == 0) *reward = sm.reward;
+}
+
+// ---------------------------------------------------------------------------
+// CTA setup and counters.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void init_cta(AgentSmem& sm) {
+    if (threadIdx.x == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+        for (int k = 0; k < 4; ++k) sm.cnt[k] = 0;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void publish_counts(AgentSmem& sm, const StepArgs& A, const Counts& c) {
+    if (A.count) {
+        if (c.evals) atomicAdd(&sm.cnt[0], c.evals);
+        if (c.tiles) atomicAdd(&sm.cnt[1], c.tiles);
+        if (c.pairs) atomicAdd(&sm.cnt[2], c.pairs);
+        if (c.tests) atomicAdd(&sm.cnt[3], c.tests);
+    }
+    __syncthreads();
+    if (A.count && threadIdx.x == 0)
+        for (int k = 0; k < 4; ++k)
+            if (sm.cnt[k]) atomicAdd(&A.counters[k], sm.cnt[k]);
+}
+
+// Scene s's segments in global memory.
+__device__ __forceinline__ SegView global_view(const Segs& G, int s) {
+    const int e0 = G.off[s];
+    const int E = G.cnt[s];
+    return SegView{G.geo + e0, G.inv + e0, G.flags + e0, G.tiles + 2 * (e0 / kTile), E, (E + kTile - 1) / kTile};
+}
+
+}  // namespace wsim

@@ -1,0 +1,128 @@
+// Scene-resident rollout kernel (sm_103a).
+//
+// Scenes never exchange data during a rollout, so one CTA can run a scene's
+// whole episode (Sec. 5.1, Rollout: T steps of step()) without any global
+// synchronisation: the agent state stays in shared memory from step to step
+// and only the per-step metrics (and, on request, the per-step states) go to
+// global memory.  At the start of each scene one thread stages the scene's
+// packed road-edge segments, their flags and culling tiles into shared
+// memory with four bulk async copies (TMA) completing on one mbarrier, so
+// every off-road query of the episode reads shared memory.  Scenes whose
+// segments do not fit read them from global memory instead.  CTAs are
+// persistent and take scenes from an atomic counter over a cost-ordered
+// list.  Per step the phases are the same device functions as the per-step
+// kernel, so the results are bit-identical to it.
+#include "wsim_phases.cuh"
+
+namespace wsim {
+
+constexpr int NTr = kRollThreads;
+constexpr size_t kAgentBytes = (sizeof(AgentSmem) + 127) / 128 * 128;
+constexpr size_t kBytesPerTile = kTile * (16 + 4 + 1) + 32;  // geo + inv + flags + tile records
+
+__device__ __forceinline__ StateP offset_state(const StateP& s, size_t k) {
+    return StateP{s.x + k, s.y + k, s.x_lo + k, s.y_lo + k, s.th + k,
+                  s.th_lo + k, s.vx + k, s.vy + k, s.s + k, s.s_lo + k};
+}
+
+__global__ void __launch_bounds__(NTr, 1) k_rollout(const StepArgs A) {
+    extern __shared__ __align__(128) unsigned char dyn[];
+    AgentSmem& sm = *reinterpret_cast<AgentSmem*>(dyn);
+    unsigned char* stage = dyn + kAgentBytes;
+    init_cta(sm);
+    Counts cnt;
+    uint32_t parity = 0;
+    const size_t N_tot = static_cast<size_t>(A.N_tot);
+    for (;;) {
+        if (threadIdx.x == 0) sm.scene = atomicAdd(A.queue, 1);
+        __syncthreads();
+        const int w = sm.scene;
+        if (w >= A.S) break;
+        const int s = A.order[w];
+        const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
+        SegView V = global_view(A.segs, s);
+        const bool staged = V.nt > 0 && V.nt * kTile <= A.seg_cap;
+        if (staged) {
+            const int e0 = A.segs.off[s];
+            const int ns = V.nt * kTile;
+            float4* geo = reinterpret_cast<float4*>(stage);
+            float* inv = reinterpret_cast<float*>(geo + ns);
+            uint8_t* fl = reinterpret_cast<uint8_t*>(inv + ns);
+            float4* tiles = reinterpret_cast<float4*>(fl + ns);
+            if (threadIdx.x == 0) {
+                const uint32_t bg = ns * 16u, bi = ns * 4u, bf = ns * 1u, bt = V.nt * 32u;
+                fence_proxy_async();
+                mbar_expect_tx(&sm.bar[0], bg + bi + bf + bt);
+                bulk_g2s(geo, A.segs.geo + e0, bg, &sm.bar[0]);
+                bulk_g2s(inv, A.segs.inv + e0, bi, &sm.bar[0]);
+                bulk_g2s(fl, A.segs.flags + e0, bf, &sm.bar[0]);
+                bulk_g2s(tiles, A.segs.tiles + 2 * (e0 / kTile), bt, &sm.bar[0]);
+            }
+            V = SegView{geo, inv, fl, tiles, V.E, V.nt};
+        }
+        load_state<NTr>(sm, A, A.in, a0, N);
+        for (int j = threadIdx.x; j < 4 * N; j += NTr) sm.hint[j] = -1;
+        if (staged) {
+            const bool ok = mbar_wait_bounded(&sm.bar[0], parity, kWaitLimitNs);
+            parity ^= 1u;
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) set_status(A.status, WSIM_ETIMEOUT);
+                mbar_wait_bounded(&sm.bar[0], parity ^ 1u, kWaitLimitNs);
+                __syncthreads();
+                break;
+            }
+        }
+        __syncthreads();
+        for (int k = 0; k < A.T; ++k) {
+            phase_transition<NTr>(sm, A, A.act + static_cast<size_t>(k) * 3 * N_tot, a0, N, cnt);
+            __syncthreads();
+            if (A.traj.x) {
+                const StateP tr = offset_state(A.traj, static_cast<size_t>(k) * N_tot);
+                writeback<NTr>(sm, &tr, a0, N);
+            } else {
+                writeback<NTr>(sm, nullptr, a0, N);
+            }
+            __syncthreads();
+            phase_metrics<NTr>(sm, V, sm.hint, N, true, true, cnt);
+            __syncthreads();
+            const size_t r = static_cast<size_t>(k) * N_tot;
+            const MetricsP m{A.m.ov + r, A.m.off + r, A.m.logdiv + r, A.m.flags + r, nullptr};
+            phase_finish<NTr>(sm, A, m, A.m.reward + static_cast<size_t>(k) * A.S + s, A.t_log + k, a0, N);
+            __syncthreads();
+        }
+        store_state<NTr>(sm, A.out, a0, N);
+        __syncthreads();
+    }
+    publish_counts(sm, A, cnt);
+}
+
+size_t rollout_smem_bytes(int seg_cap) { return kAgentBytes + static_cast<size_t>(seg_cap / kTile) * kBytesPerTile; }
+
+int rollout_max_seg_cap() {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (static_cast<size_t>(optin) <= kAgentBytes) return 0;
+    return static_cast<int>((static_cast<size_t>(optin) - kAgentBytes) / kBytesPerTile) * kTile;
+}
+
+cudaError_t rollout_prepare(int seg_cap, int* blocks_per_sm) {
+    const size_t bytes = rollout_smem_bytes(seg_cap);
+    cudaError_t e = cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(bytes));
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout, NTr, bytes);
+    *blocks_per_sm = n > 0 ? n : 1;
+    return e;
+}
+
+cudaError_t launch_rollout(const StepArgs& a, int grid, cudaStream_t st) {
+    k_rollout<<<grid, NTr, rollout_smem_bytes(a.seg_cap), st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace wsim

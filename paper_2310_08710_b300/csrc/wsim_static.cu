@@ -25,6 +25,7 @@ struct StaticScratch {
     float4 geo[kStaticMaxSegs];
     float inv[kStaticMaxSegs];
     uint8_t flags[kStaticMaxSegs];
+    float4 tiles[2 * (kStaticMaxSegs / kTile)];
     int32_t seg_off[kStaticMaxScenes + 1];
     int32_t seg_cnt[kStaticMaxScenes];
     int32_t order[kStaticMaxScenes];
@@ -32,7 +33,7 @@ struct StaticScratch {
     int32_t status;
 };
 
-// Every GPU that loads the library holds this array (about 5.6 MB) until
+// Every GPU that loads the library holds this array (about 5.8 MB) until
 // the process exits.  All calls share it.
 static __device__ __align__(256) StaticScratch g_scratch;
 
@@ -162,7 +163,8 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
     rc = read_status(sc, s);
     if (rc) return rc;
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, b->S, sc->seg_off,
-                        sc->geo, sc->inv, sc->flags, s) != cudaSuccess)
+                        sc->geo, sc->inv, sc->flags, s) != cudaSuccess ||
+        launch_tile_build(b->S, sc->seg_off, sc->seg_cnt, sc->geo, sc->tiles, s) != cudaSuccess)
         return WSIM_ECUDA;
 
     StepArgs a;
@@ -176,7 +178,8 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
     a.valid = b->valid;
     a.log_x = b->log_x;
     a.log_y = b->log_y;
-    a.segs = Segs{sc->seg_off, sc->seg_cnt, sc->geo, sc->inv, sc->flags};
+    a.segs = Segs{sc->seg_off, sc->seg_cnt, sc->geo, sc->inv, sc->flags, sc->tiles};
+    a.hint = nullptr;  // no nearest-segment cache: bounds come from the tiles
     a.in = CStateP{st->x, st->y, st->x_lo, st->y_lo, st->th, st->th_lo, st->vx, st->vy, st->s, st->s_lo};
     a.m = MetricsP{m->ov, m->off, m->logdiv, m->flags, m->reward};
     a.t_log = t;

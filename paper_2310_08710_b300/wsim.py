@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libwsim.so")
 
 OK, EINVAL, ESIZE, ECUDA, ENONFINITE, ETIMEOUT, ENOMEM, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
-MODE_GRAPH, MODE_STREAM, MODE_PLAIN = 0, 1, 2
+MODE_GRAPH, MODE_STREAM, MODE_PLAIN, MODE_FUSED = 0, 1, 2, 3
 MAX_AGENTS = 256
 FLAG_COLLISION, FLAG_OFFROAD = 1, 2
 

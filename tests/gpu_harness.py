@@ -25,7 +25,7 @@ ULP_SLACK = 4       # float32 ulps of the value for large magnitudes
 
 def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None):
     from paper_2310_08710_b300 import wsim
-    mode = wsim.MODE_GRAPH if mode is None else mode
+    mode = wsim.MODE_FUSED if mode is None else mode
     T = b.T if T is None else T
     db = wsim.DeviceBatch(b)
     sim = wsim.Sim(db, cfg)

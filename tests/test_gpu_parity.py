@@ -4,7 +4,7 @@ Teacher-forced parity per step and per quantity (positions 1e-5 m, heading
 1e-6 rad, velocity 1e-5 m/s, log divergence 1e-5 m, overlap depth and
 off-road distance 2e-5 m, or 4 float32 ulps of larger values); collision and
 off-road booleans and the reward bit-exact outside the oracle's ambiguity
-bands.  The three rollout modes must agree bit for bit.
+bands.  The four rollout modes must agree bit for bit.
 """
 import numpy as np
 import pytest
@@ -36,18 +36,22 @@ def test_config0_every_step(wsim):
 
 def test_config0_modes_bit_identical_and_deterministic(wsim):
     b = synth.make_batch(0, seed=2)
-    ref = H.run_rollout(b, mode=wsim.MODE_GRAPH)
-    for mode in (wsim.MODE_GRAPH, wsim.MODE_STREAM, wsim.MODE_PLAIN):
+    ref = H.run_rollout(b, mode=wsim.MODE_FUSED)
+    for mode in (wsim.MODE_FUSED, wsim.MODE_GRAPH, wsim.MODE_STREAM, wsim.MODE_PLAIN):
         g = H.run_rollout(b, mode=mode)
         for k in ("traj", "final", "ov", "off", "logdiv", "flags", "reward"):
             assert np.array_equal(g[k].view(np.uint8), ref[k].view(np.uint8)), (mode, k)
 
 
 def test_config1_sampled_scenes_full_size(wsim):
-    # Full 1024-scene batch in the benchmark's launch configuration (graph);
-    # the oracle checks a spread of scenes at every step.
+    # Full 1024-scene batch in the benchmark's launch configuration (the
+    # scene-resident rollout); the oracle checks a spread of scenes at every
+    # step, and the per-step graph path must agree bit for bit.
     b = synth.make_batch(1, seed=0)
-    g = H.run_rollout(b)
+    g = H.run_rollout(b, mode=wsim.MODE_FUSED)
+    gg = H.run_rollout(b, mode=wsim.MODE_GRAPH)
+    for k in ("traj", "final", "ov", "off", "logdiv", "flags", "reward"):
+        assert np.array_equal(g[k].view(np.uint8), gg[k].view(np.uint8)), k
     assert g["status"] == 0
     scenes = [0, 333, 700, 1023]
     c = H.teacher_forced(b, g, scenes, range(b.T))
@@ -56,11 +60,14 @@ def test_config1_sampled_scenes_full_size(wsim):
 
 
 def test_config2_uneven_against_plain_and_oracle(wsim):
+    # Scenes of 1k-30k roadgraph points: the largest do not fit the
+    # shared-memory stage and read their segments from global memory.
     b = synth.make_batch(2, seed=0, S=512)
-    g = H.run_rollout(b, mode=wsim.MODE_GRAPH)
-    p = H.run_rollout(b, mode=wsim.MODE_PLAIN)
-    for k in ("traj", "ov", "off", "logdiv", "flags", "reward"):
-        assert np.array_equal(g[k].view(np.uint8), p[k].view(np.uint8)), k
+    g = H.run_rollout(b, mode=wsim.MODE_FUSED)
+    for mode in (wsim.MODE_GRAPH, wsim.MODE_PLAIN):
+        p = H.run_rollout(b, mode=mode)
+        for k in ("traj", "ov", "off", "logdiv", "flags", "reward"):
+            assert np.array_equal(g[k].view(np.uint8), p[k].view(np.uint8)), (mode, k)
     rng = np.random.default_rng(0)
     scenes = sorted(rng.choice(b.S, 8, replace=False).tolist())
     big = int(np.argmax(np.diff(b.rg_off)))
