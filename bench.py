@@ -52,6 +52,11 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--mode", default="fused", choices=["fused", "graph"],
+                    help="rollout path timed: scene-resident kernel or graph of per-step launches")
+    ap.add_argument("--scenes", type=int, default=None, help="override the scene count (profiling only)")
+    ap.add_argument("--profile", action="store_true",
+                    help="time the main path only (no mode comparison, end-to-end or CPU legs)")
     return ap.parse_args()
 
 
@@ -185,7 +190,8 @@ def config_dict(args, b):
     wl = workload_desc(args.config)
     return {"workload": f"config {args.config}: {wl.name}", "scenes": int(b.S),
             "agents": int(b.N_tot), "rollout_steps": int(b.T), "roadgraph_points": int(b.R_tot),
-            "dt_s": 0.1, "rollout_mode": "scene-resident rollout kernel (one launch per rollout)",
+            "dt_s": 0.1, "rollout_mode": ("scene-resident rollout kernel (one launch per rollout)"
+                                          if args.mode == "fused" else "persistent step kernel x80, CUDA graph"),
             "l2": "inputs larger than L2 (road-edge segments + routes + logs streamed every rollout)"}
 
 
@@ -198,8 +204,9 @@ def main():
     import torch
     from paper_2310_08710_b300 import synth, wsim
     torch.cuda.set_device(local)
-    b = synth.make_batch(args.config, seed=args.seed + 1000 * rank)
+    b = synth.make_batch(args.config, seed=args.seed + 1000 * rank, S=args.scenes)
     T, N, S = b.T, b.N_tot, b.S
+    main_mode = wsim.MODE_FUSED if args.mode == "fused" else wsim.MODE_GRAPH
     db = wsim.DeviceBatch(b)
     sim = wsim.Sim(db)
     st0 = wsim.State.from_batch(b)
@@ -210,12 +217,12 @@ def main():
 
     def rollout():
         st.data.copy_(st0.data)
-        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_FUSED)
+        sim.rollout(st, act, m, synth.T0, T, mode=main_mode)
 
     # Work counters of one rollout (untimed) for the roofline numerator.
     sim.set_counting(True)
     rollout()
-    cnt = sim.counters()
+    cnt = [int(x) for x in sim.counters()]
     sim.set_counting(False)
     for _ in range(max(3, args.warmup)):
         rollout()
@@ -239,6 +246,11 @@ def main():
     clocks = clk.stop()
     assert sim.status() == 0
 
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": True, "mode": args.mode, "ms_per_step": ms, "scenes": S,
+                              "value": N * T / (ms / 1e3), "counts": cnt}), flush=True)
+        return
     # End to end through the public API: pinned host inputs in, metrics out.
     h_act = torch.as_tensor(b.actions).pin_memory()
     h_st = st0.data.cpu().pin_memory()
@@ -247,7 +259,7 @@ def main():
     for _ in range(2):
         act.copy_(h_act, non_blocking=True)
         st.data.copy_(h_st, non_blocking=True)
-        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_FUSED)
+        sim.rollout(st, act, m, synth.T0, T, mode=main_mode)
         h_rew.copy_(m.reward, non_blocking=True)
         h_flags.copy_(m.flags, non_blocking=True)
     torch.cuda.synchronize()
@@ -255,7 +267,7 @@ def main():
     for _ in range(args.steps):
         act.copy_(h_act, non_blocking=True)
         st.data.copy_(h_st, non_blocking=True)
-        sim.rollout(st, act, m, synth.T0, T, mode=wsim.MODE_FUSED)
+        sim.rollout(st, act, m, synth.T0, T, mode=main_mode)
         h_rew.copy_(m.reward, non_blocking=True)
         h_flags.copy_(m.flags, non_blocking=True)
     e1.record(stream)
@@ -293,14 +305,18 @@ def main():
         return
     value = units / (ms / 1e3)
     flops = (FLOPS_PER_EVAL * cnt[0] + FLOPS_PER_TILE * cnt[1] + FLOPS_PER_PAIR * cnt[2] + FLOPS_PER_TEST * cnt[3]
-             + FLOPS_PER_AGENT * N * T)
-    launch_ms = ms  # one scene-resident launch per rollout (plus one 4-byte memset)
+             + FLOPS_PER_AGENT * N * T) / launches
+    fused = args.mode == "fused"
+    # fused: one scene-resident launch per rollout; graph: T step launches
+    # (each preceded by a 4-byte memset node, counted in the launch time)
+    launch_ms = ms if fused else ms / T
+    launches = 1 if fused else T
     achieved = flops / (launch_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": config_dict(args, b),
-        "roofline": {"bound": "alu", "kernel": "k_rollout", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+        "roofline": {"bound": "alu", "kernel": "k_rollout" if fused else "k_step", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
                      "flops_per_launch": flops, "launch_ms": launch_ms,
@@ -308,7 +324,7 @@ def main():
                                             "sat_pairs": int(cnt[2]), "idm_sample_tests": int(cnt[3])}},
         "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches,
         "modes": modes,
         "clocks": clocks,
     }
