@@ -192,7 +192,7 @@ void wsim_destroy(wsim_ctx *ctx);
  * this is for callers that cannot call cudaMalloc when they need the metrics
  * (a caching allocator or fixed arena that owns all device memory, code that
  * must not allocate).  The scratch wsim_init would allocate lives instead in
- * one file-scope device array of about 5.8 MB that every GPU loading the
+ * one file-scope device array of about 5.9 MB that every GPU loading the
  * library holds until the process exits.  Limits: at most 4096 scenes, and
  * R_tot + 31 * S <= 262144 (the packed road-edge segments must fit); larger
  * batches return WSIM_ESIZE before any work.  The first call on a device

@@ -29,6 +29,8 @@ struct wsim_ctx {
     float* seg_inv = nullptr;
     uint8_t* seg_flags = nullptr;
     float4* seg_tiles = nullptr;
+    int32_t* seg_soff = nullptr;
+    float4* seg_sup = nullptr;
     int32_t* hint = nullptr;  // [N_tot][4] nearest-segment cache of the per-step kernels
     unsigned long long* counters = nullptr;
     float* tmp = nullptr;  // ping-pong state, 10 x N_tot
@@ -100,7 +102,7 @@ StepArgs base_args(const wsim_ctx* c) {
     a.route_y = b.route_y;
     a.log_x = b.log_x;
     a.log_y = b.log_y;
-    a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags, c->seg_tiles};
+    a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags, c->seg_tiles, c->seg_soff, c->seg_sup};
     a.hint = c->hint;
     a.seg_cap = c->seg_cap;
     a.order = c->order;
@@ -284,11 +286,20 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     if (cudaMemcpyAsync(cnt.data(), c->seg_cnt, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(WSIM_ECUDA);
-    for (int s = 0; s < S; ++s) off[s + 1] = off[s] + ((cnt[s] + kSegAlign - 1) / kSegAlign) * kSegAlign;
+    std::vector<int32_t> soff(S + 1, 0);
+    for (int s = 0; s < S; ++s) {
+        off[s + 1] = off[s] + ((cnt[s] + kSegAlign - 1) / kSegAlign) * kSegAlign;
+        const int nt = (cnt[s] + kTile - 1) / kTile;
+        soff[s + 1] = soff[s] + (nt + kSuper - 1) / kSuper;
+    }
     const size_t E = static_cast<size_t>(off[S]);
     if ((rc = dalloc(&c->seg_geo, E)) || (rc = dalloc(&c->seg_inv, E)) || (rc = dalloc(&c->seg_flags, E)) ||
-        (rc = dalloc(&c->seg_tiles, 2 * (E / kTile))))
+        (rc = dalloc(&c->seg_tiles, 2 * (E / kTile))) || (rc = dalloc(&c->seg_soff, S + 1)) ||
+        (rc = dalloc(&c->seg_sup, static_cast<size_t>(soff[S]))))
         return fail(rc);
+    if (cudaMemcpyAsync(c->seg_soff, soff.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess)
+        return fail(WSIM_ECUDA);
     if (cudaMemsetAsync(c->seg_geo, 0, std::max<size_t>(E, 1) * sizeof(float4), st) != cudaSuccess ||
         cudaMemsetAsync(c->seg_inv, 0, std::max<size_t>(E, 1) * sizeof(float), st) != cudaSuccess ||
         cudaMemsetAsync(c->seg_flags, 0, std::max<size_t>(E, 1), st) != cudaSuccess ||
@@ -296,7 +307,8 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
         return fail(WSIM_ECUDA);
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, S, c->seg_off, c->seg_geo,
                         c->seg_inv, c->seg_flags, st) != cudaSuccess ||
-        launch_tile_build(S, c->seg_off, c->seg_cnt, c->seg_geo, c->seg_tiles, st) != cudaSuccess)
+        launch_tile_build(S, c->seg_off, c->seg_cnt, c->seg_geo, c->seg_tiles, st) != cudaSuccess ||
+        launch_super_build(S, c->seg_off, c->seg_cnt, c->seg_soff, c->seg_tiles, c->seg_sup, st) != cudaSuccess)
         return fail(WSIM_ECUDA);
 
     // Scene work list, most expensive first (longest-processing-time order).
@@ -463,6 +475,8 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->seg_inv);
     cudaFree(c->seg_flags);
     cudaFree(c->seg_tiles);
+    cudaFree(c->seg_soff);
+    cudaFree(c->seg_sup);
     cudaFree(c->hint);
     delete c;
 }

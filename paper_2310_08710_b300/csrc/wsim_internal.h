@@ -12,6 +12,7 @@ constexpr int kStepThreads = 256;       // threads per CTA of the per-step kerne
 constexpr int kRollThreads = 512;       // threads per CTA of the scene-resident rollout kernel
 constexpr int kTile = 32;               // road-edge segments per culling tile (one per lane)
 constexpr int kSegAlign = kTile;        // per-scene segment arrays start on a tile boundary
+constexpr int kSuper = 8;               // tiles per super-tile (first culling level)
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
 
 // Packed road-edge segments of the whole batch (built by wsim_init).  Scene s
@@ -26,6 +27,8 @@ struct Segs {
     const float* inv;      // 1 / |u|^2
     const uint8_t* flags;  // bit0: a segment ends where this one starts; bit1: one starts where it ends
     const float4* tiles;   // [2 * tiles]
+    const int32_t* soff;   // [S+1] first super-tile of each scene
+    const float4* sup;     // super-tile bounding boxes: super-tile j of scene s covers its tiles 8j .. 8j+7
 };
 
 struct StateP {
@@ -83,6 +86,8 @@ cudaError_t launch_seg_pack(const int32_t* rg_off, const float* rg_x, const floa
                             float4* geo, float* inv, uint8_t* flags, cudaStream_t st);
 cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const float4* geo,
                               float4* tiles, cudaStream_t st);
+cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const int32_t* soff,
+                               const float4* tiles, float4* sup, cudaStream_t st);
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_plain_scene(const StepArgs& a, int scene, cudaStream_t st);
 int step_blocks_per_sm();

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(NTs) k_plain_overlap(const StepArgs A, int s) 
     phase_metrics<NTs>(sm, SegView{}, nullptr, N, true, false, cnt);
     __syncthreads();
     for (int i = threadIdx.x; i < N; i += NTs)
-        if (sm.valid[i]) A.m.ov[a0 + i] = sm.ov[i];
+        if (sm.valid[i]) A.m.ov[a0 + i] = merged_ov(sm, i);
     publish_counts(sm, A, cnt);
 }
 
@@ -197,6 +197,26 @@ __global__ void __launch_bounds__(256) k_tile_build(const int32_t* seg_off, cons
     }
 }
 
+// Per super-tile: bounding box of its kSuper tiles.
+__global__ void __launch_bounds__(256) k_super_build(const int32_t* seg_off, const int32_t* seg_cnt,
+                                                     const int32_t* soff, const float4* tiles, float4* sup) {
+    const int s = blockIdx.x;
+    const int e0 = seg_off[s], E = seg_cnt[s];
+    const int nt = (E + kTile - 1) / kTile;
+    const int ns = (nt + kSuper - 1) / kSuper;
+    for (int j = threadIdx.x; j < ns; j += 256) {
+        float x0 = WSIM_INF, y0 = WSIM_INF, x1 = -WSIM_INF, y1 = -WSIM_INF;
+        for (int t = j * kSuper; t < min(nt, (j + 1) * kSuper); ++t) {
+            const float4 B = tiles[2 * (static_cast<size_t>(e0 / kTile) + t)];
+            x0 = fminf(x0, B.x);
+            y0 = fminf(y0, B.y);
+            x1 = fmaxf(x1, B.z);
+            y1 = fmaxf(y1, B.w);
+        }
+        sup[soff[s] + j] = make_float4(x0, y0, x1, y1);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Launchers.
 // ---------------------------------------------------------------------------
@@ -219,6 +239,12 @@ cudaError_t launch_seg_pack(const int32_t* rg_off, const float* rg_x, const floa
 cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const float4* geo,
                               float4* tiles, cudaStream_t st) {
     k_tile_build<<<S, 256, 0, st>>>(seg_off, seg_cnt, geo, tiles);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const int32_t* soff,
+                               const float4* tiles, float4* sup, cudaStream_t st) {
+    k_super_build<<<S, 256, 0, st>>>(seg_off, seg_cnt, soff, tiles, sup);
     return cudaGetLastError();
 }
 

@@ -21,10 +21,12 @@ struct __align__(16) AgentSmem {
     float nxh[kMaxN], nxl[kMaxN], nyh[kMaxN], nyl[kMaxN], nth[kMaxN], ntl[kMaxN];
     float nvx[kMaxN], nvy[kMaxN], nsh[kMaxN], nsl[kMaxN];
     float ov[kMaxN], off[kMaxN];
+    int32_t ovk[kMaxN];       // column maxima of the pair depths, as ordered keys
     int32_t hint[4 * kMaxN];  // scene-resident nearest-segment cache
     uint8_t valid[kMaxN];
     int scene;
     int reward;
+    int work[2];              // agent counters of the warp phases (transition, metrics)
 };
 
 // Work counters of one thread (flushed into the CTA's AgentSmem::cnt).
@@ -38,8 +40,23 @@ struct SegView {
     const float* inv;
     const uint8_t* flags;
     const float4* tiles;  // 2 per tile: bounding box, two points on segments
-    int E, nt;
+    const float4* sup;    // bounding box per super-tile of kSuper tiles
+    int E, nt, ns;
 };
+
+// Order-preserving int key of a float (for atomicMax on shared memory).
+__device__ __forceinline__ int32_t fkey(float f) {
+    const int32_t b = __float_as_int(f);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+__device__ __forceinline__ float funkey(int32_t k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+
+// Next agent of a warp phase (dynamic assignment balances uneven agents).
+__device__ __forceinline__ int next_agent(AgentSmem& sm, int slot, int lane) {
+    int i = 0;
+    if (lane == 0) i = atomicAdd(&sm.work[slot], 1);
+    return __shfl_sync(0xffffffffu, i, 0);
+}
 
 template <class T> __device__ __forceinline__ T pick4(const T (&a)[4], int k) {
     return k == 0 ? a[0] : (k == 1 ? a[1] : (k == 2 ? a[2] : a[3]));
@@ -70,7 +87,9 @@ __device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, 
         sm.sh[i] = st.s[g];
         sm.sl[i] = st.s_lo[g];
         sm.valid[i] = A.valid[g];
+        sm.ovk[i] = fkey(-WSIM_INF);
     }
+    if (threadIdx.x == 0) sm.work[0] = sm.work[1] = 0;
 }
 
 // Make the next state current; optionally store it to global memory.
@@ -104,6 +123,7 @@ __device__ void writeback(AgentSmem& sm, const StateP* out, int a0, int N) {
         sm.vy[i] = sm.nvy[i];
         sm.sh[i] = sm.nsh[i];
         sm.sl[i] = sm.nsl[i];
+        sm.ovk[i] = fkey(-WSIM_INF);
     }
 }
 
@@ -277,9 +297,9 @@ static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* act, int a0, int N, Counts& cnt) {
-    constexpr int NW = NT / 32;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < N; i += NW) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) sm.work[1] = 0;  // the metrics phase starts after two barriers
+    for (int i = next_agent(sm, 0, lane); i < N; i = next_agent(sm, 0, lane)) {
         if (A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i]) idm_agent(sm, A, a0, N, i, lane, cnt);
     }
     const Params& p = A.p;
@@ -329,20 +349,24 @@ __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* 
 }
 
 // ---------------------------------------------------------------------------
-// Overlap of agent i (warp): ov_i = max over valid j != i of the SAT depth
-// d_ij, computed in the canonical order (min(i,j), max(i,j)) so that
-// d_ij == d_ji bit for bit.  Returns the value in every lane.
+// Overlap, row i (warp): the SAT depth d_ij of every valid j > i, computed once
+// per unordered pair with i as the first box (the canonical order, so that
+// d_ij is one value for both agents).  Returns max_j d_ij of the row in every
+// lane and folds each d_ij into agent j's column maximum (ovk).  ov_i is
+// then max(row i, column i) = max over all valid j != i.
 // ---------------------------------------------------------------------------
-static __device__ float overlap_agent(const AgentSmem& sm, int N, int i, int lane, Counts& cnt) {
+static __device__ float overlap_row(AgentSmem& sm, int N, int i, int lane, Counts& cnt) {
     float best = -WSIM_INF;
-    for (int j = lane; j < N; j += 32) {
-        if (j == i || !sm.valid[j]) continue;
-        const int lo = min(i, j), hi = max(i, j);
-        const float dx = comp_diff(sm.xh[hi], sm.xl[hi], sm.xh[lo], sm.xl[lo]);
-        const float dy = comp_diff(sm.yh[hi], sm.yl[hi], sm.yh[lo], sm.yl[lo]);
-        best = fmaxf(best, sat_depth(dx, dy, sm.c[lo], sm.s[lo], sm.hl[lo], sm.hw[lo], sm.c[hi], sm.s[hi],
-                                     sm.hl[hi], sm.hw[hi]));
-        ++cnt.pairs;
+    const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
+    const float ci = sm.c[i], si = sm.s[i], hli = sm.hl[i], hwi = sm.hw[i];
+    for (int j = i + 1 + lane; j < N; j += 32) {
+        if (!sm.valid[j]) continue;
+        const float dx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
+        const float dy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
+        const float d = sat_depth(dx, dy, ci, si, hli, hwi, sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
+        best = fmaxf(best, d);
+        atomicMax(&sm.ovk[j], fkey(d));
+        cnt.pairs += 2;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
@@ -370,13 +394,13 @@ __device__ __forceinline__ float seg_dist2(float4 G, float iv, float cxh, float 
 //
 // Culling: an upper bound U_k on corner k's nearest distance comes from the
 // segment that was nearest at the previous step (hint) or, without one, from
-// points known to lie on segments (two per tile).  Only tiles whose bounding
-// box lies within U_k of corner k are scanned (lane = segment of the tile),
-// so the result equals the exhaustive scan.  hint (may be null) is read and
-// updated with the winners.
+// points known to lie on segments (two per tile).  Super-tiles (kSuper tiles)
+// and then tiles whose bounding box lies farther than U_k from corner k are
+// skipped; the rest are scanned with one segment per lane, so the result
+// equals the exhaustive scan.  hint (may be null) is read and updated.
 // ---------------------------------------------------------------------------
-static __device__ float offroad_agent(const SegView& V, int lane, float xh, float xl, float yh, float yl, float c, float s,
-                               float hl, float hw, int32_t* hint, Counts& cnt) {
+static __device__ float offroad_agent(const SegView& V, int lane, float xh, float xl, float yh, float yl, float c,
+                                      float s, float hl, float hw, int32_t* hint, Counts& cnt) {
     if (V.E == 0) {
         if (hint && lane < 4) hint[lane] = -1;
         return -WSIM_INF;
@@ -413,8 +437,7 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) m[k] = fminf(m[k], __shfl_xor_sync(kFull, m[k], o));
+            m[k] = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(m[k])));
             u2[k] = fminf(u2[k], m[k]);
         }
         if (lane == 0) cnt.tiles += V.nt;
@@ -427,66 +450,77 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
         lim2[k] = u * u;
         ucap = fmaxf(ucap, u);
     }
-    // Agent-level pre-test: the centre's distance to the box minus the half
-    // diagonal bounds every corner's distance from below.
+    // Agent-level test: the centre's distance to a box minus the half
+    // diagonal bounds every corner's distance to it from below.
     const float ccx = xh + xl, ccy = yh + yl;
     const float rad = sqrtf(fmaf(hl, hl, hw * hw)) + 1e-3f;
     const float clim = (ucap + rad) * (ucap + rad);
 
     float bd[4] = {WSIM_INF, WSIM_INF, WSIM_INF, WSIM_INF};
     int bi[4] = {-1, -1, -1, -1};
-    for (int base = 0; base < V.nt; base += 32) {
-        const int t = base + lane;
-        unsigned cm = 0;
-        if (t < V.nt) {
-            const float4 B = V.tiles[2 * t];
-            float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
-            float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
-            if (fmaf(dx, dx, dy * dy) <= clim) {
+    for (int sb = 0; sb < V.ns; sb += 32) {
+        bool pass = false;
+        if (sb + lane < V.ns) {
+            const float4 B = V.sup[sb + lane];
+            const float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
+            const float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
+            pass = fmaf(dx, dx, dy * dy) <= clim;
+        }
+        if (lane == 0) cnt.tiles += min(32, V.ns - sb);
+        unsigned sup = __ballot_sync(kFull, pass);
+        while (sup) {
+            const int t0 = (sb + __ffs(sup) - 1) * kSuper;
+            sup &= sup - 1;
+            // Lanes 0..kSuper-1 test the super-tile's tiles corner by corner.
+            unsigned cm = 0;
+            const int t = t0 + lane;
+            if (lane < kSuper && t < V.nt) {
+                const float4 B = V.tiles[2 * t];
+                float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
+                float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
+                if (fmaf(dx, dx, dy * dy) <= clim) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    dx = fmaxf(fmaxf(B.x - px[k], px[k] - B.z), 0.f);
-                    dy = fmaxf(fmaxf(B.y - py[k], py[k] - B.w), 0.f);
-                    if (fmaf(dx, dx, dy * dy) <= lim2[k]) cm |= 1u << k;
+                    for (int k = 0; k < 4; ++k) {
+                        dx = fmaxf(fmaxf(B.x - px[k], px[k] - B.z), 0.f);
+                        dy = fmaxf(fmaxf(B.y - py[k], py[k] - B.w), 0.f);
+                        if (fmaf(dx, dx, dy * dy) <= lim2[k]) cm |= 1u << k;
+                    }
                 }
             }
-        }
-        if (lane == 0) cnt.tiles += min(32, V.nt - base);
-        unsigned want = __ballot_sync(kFull, cm != 0);
-        while (want) {
-            const int l = __ffs(want) - 1;
-            want &= want - 1;
-            const unsigned km = __shfl_sync(kFull, cm, l);
-            const int e = (base + l) * kTile + lane;
-            if (lane == 0) cnt.evals += 32 * __popc(km);
-            if (e < V.E) {
-                const float4 G = V.geo[e];
-                const float iv = V.inv[e];
+            if (lane == 0) cnt.tiles += kSuper;
+            unsigned want = __ballot_sync(kFull, cm != 0);
+            while (want) {
+                const int l = __ffs(want) - 1;
+                want &= want - 1;
+                const unsigned km = __shfl_sync(kFull, cm, l);
+                const int e = (t0 + l) * kTile + lane;
+                if (lane == 0) cnt.evals += 32 * __popc(km);
+                if (e < V.E) {
+                    const float4 G = V.geo[e];
+                    const float iv = V.inv[e];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    if ((km >> k) & 1u) {
-                        const float d2 = seg_dist2(G, iv, xh, cxl[k], yh, cyl[k]);
-                        if (d2 < bd[k]) {
-                            bd[k] = d2;
-                            bi[k] = e;
+                    for (int k = 0; k < 4; ++k) {
+                        if ((km >> k) & 1u) {
+                            const float d2 = seg_dist2(G, iv, xh, cxl[k], yh, cyl[k]);
+                            if (d2 < bd[k]) {
+                                bd[k] = d2;
+                                bi[k] = e;
+                            }
                         }
                     }
                 }
             }
         }
     }
-    // Nearest segment per corner: lexicographic (distance, index) minimum.
+    // Nearest segment per corner: the lexicographic (distance, index)
+    // minimum over lanes (distances >= 0 order like their bit patterns).
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            const float od = __shfl_xor_sync(kFull, bd[k], o);
-            const int oi = __shfl_xor_sync(kFull, bi[k], o);
-            if (od < bd[k] || (od == bd[k] && static_cast<unsigned>(oi) < static_cast<unsigned>(bi[k]))) {
-                bd[k] = od;
-                bi[k] = oi;
-            }
-        }
+        const unsigned key = __float_as_uint(bd[k]);
+        const unsigned mn = __reduce_min_sync(kFull, key);
+        const unsigned id = __reduce_min_sync(kFull, key == mn ? static_cast<unsigned>(bi[k]) : 0xffffffffu);
+        bd[k] = __uint_as_float(mn);
+        bi[k] = static_cast<int>(id);
     }
     // Side of the nearest feature (lane k: corner k).
     float sd = -WSIM_INF;
@@ -527,17 +561,18 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
 }
 
 // ---------------------------------------------------------------------------
-// Overlap and off-road of every agent (warp per agent).
+// Overlap rows and off-road of every agent, one warp per agent taken from a
+// shared counter.  sm.ov receives the row maxima; finish merges the columns.
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_base, int N, bool do_ov, bool do_off,
                               Counts& cnt) {
-    constexpr int NW = NT / 32;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < N; i += NW) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) sm.work[0] = 0;  // the next transition starts after two barriers
+    for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane)) {
         if (!sm.valid[i]) continue;
         if (do_ov) {
-            const float o = overlap_agent(sm, N, i, lane, cnt);
+            const float o = overlap_row(sm, N, i, lane, cnt);
             if (lane == 0) sm.ov[i] = o;
         }
         if (do_off) {
@@ -547,6 +582,9 @@ __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_bas
         }
     }
 }
+
+// ov_i of a valid agent after phase_metrics: max(row i, column i).
+__device__ __forceinline__ float merged_ov(const AgentSmem& sm, int i) { return fmaxf(sm.ov[i], funkey(sm.ovk[i])); }
 
 // ---------------------------------------------------------------------------
 // Log divergence, flags, metric stores and the scene reward.
@@ -566,7 +604,7 @@ __device__ void phase_finish(AgentSmem& sm, const StepArgs& A, const MetricsP& m
             const float dx = (sm.xh[i] - A.log_x[li]) + sm.xl[i];
             const float dy = (sm.yh[i] - A.log_y[li]) + sm.yl[i];
             ld = sqrtf(fmaf(dx, dx, dy * dy));
-            ov = sm.ov[i];
+            ov = merged_ov(sm, i);
             off = sm.off[i];
             fl = (ov > 0.f ? WSIM_FLAG_COLLISION : 0) | (off > 0.f ? WSIM_FLAG_OFFROAD : 0);
             r -= (ov > 0.f) + (off > 0.f);
@@ -611,7 +649,9 @@ __device__ __forceinline__ void publish_counts(AgentSmem& sm, const StepArgs& A,
 __device__ __forceinline__ SegView global_view(const Segs& G, int s) {
     const int e0 = G.off[s];
     const int E = G.cnt[s];
-    return SegView{G.geo + e0, G.inv + e0, G.flags + e0, G.tiles + 2 * (e0 / kTile), E, (E + kTile - 1) / kTile};
+    const int nt = (E + kTile - 1) / kTile;
+    return SegView{G.geo + e0, G.inv + e0, G.flags + e0, G.tiles + 2 * (e0 / kTile), G.sup + G.soff[s],
+                   E, nt, (nt + kSuper - 1) / kSuper};
 }
 
 }  // namespace wsim

@@ -5,8 +5,8 @@
 // synchronisation: the agent state stays in shared memory from step to step
 // and only the per-step metrics (and, on request, the per-step states) go to
 // global memory.  At the start of each scene one thread stages the scene's
-// packed road-edge segments, their flags and culling tiles into shared
-// memory with four bulk async copies (TMA) completing on one mbarrier, so
+// packed road-edge segments, their flags, culling tiles and super-tiles into
+// shared memory with five bulk async copies (TMA) completing on one mbarrier, so
 // every off-road query of the episode reads shared memory.  Scenes whose
 // segments do not fit read them from global memory instead.  CTAs are
 // persistent and take scenes from an atomic counter over a cost-ordered
@@ -19,6 +19,7 @@ namespace wsim {
 constexpr int NTr = kRollThreads;
 constexpr size_t kAgentBytes = (sizeof(AgentSmem) + 127) / 128 * 128;
 constexpr size_t kBytesPerTile = kTile * (16 + 4 + 1) + 32;  // geo + inv + flags + tile records
+constexpr size_t kBytesPerSuper = 16;
 
 __device__ __forceinline__ StateP offset_state(const StateP& s, size_t k) {
     return StateP{s.x + k, s.y + k, s.x_lo + k, s.y_lo + k, s.th + k,
@@ -49,16 +50,18 @@ __global__ void __launch_bounds__(NTr, 1) k_rollout(const StepArgs A) {
             float* inv = reinterpret_cast<float*>(geo + ns);
             uint8_t* fl = reinterpret_cast<uint8_t*>(inv + ns);
             float4* tiles = reinterpret_cast<float4*>(fl + ns);
+            float4* sup = tiles + 2 * V.nt;
             if (threadIdx.x == 0) {
-                const uint32_t bg = ns * 16u, bi = ns * 4u, bf = ns * 1u, bt = V.nt * 32u;
+                const uint32_t bg = ns * 16u, bi = ns * 4u, bf = ns * 1u, bt = V.nt * 32u, bs = V.ns * 16u;
                 fence_proxy_async();
-                mbar_expect_tx(&sm.bar[0], bg + bi + bf + bt);
+                mbar_expect_tx(&sm.bar[0], bg + bi + bf + bt + bs);
                 bulk_g2s(geo, A.segs.geo + e0, bg, &sm.bar[0]);
                 bulk_g2s(inv, A.segs.inv + e0, bi, &sm.bar[0]);
                 bulk_g2s(fl, A.segs.flags + e0, bf, &sm.bar[0]);
                 bulk_g2s(tiles, A.segs.tiles + 2 * (e0 / kTile), bt, &sm.bar[0]);
+                bulk_g2s(sup, A.segs.sup + A.segs.soff[s], bs, &sm.bar[0]);
             }
-            V = SegView{geo, inv, fl, tiles, V.E, V.nt};
+            V = SegView{geo, inv, fl, tiles, sup, V.E, V.nt, V.ns};
         }
         load_state<NTr>(sm, A, A.in, a0, N);
         for (int j = threadIdx.x; j < 4 * N; j += NTr) sm.hint[j] = -1;
@@ -96,7 +99,10 @@ __global__ void __launch_bounds__(NTr, 1) k_rollout(const StepArgs A) {
     publish_counts(sm, A, cnt);
 }
 
-size_t rollout_smem_bytes(int seg_cap) { return kAgentBytes + static_cast<size_t>(seg_cap / kTile) * kBytesPerTile; }
+size_t rollout_smem_bytes(int seg_cap) {
+    const size_t nt = static_cast<size_t>(seg_cap / kTile);
+    return kAgentBytes + nt * kBytesPerTile + (nt + kSuper - 1) / kSuper * kBytesPerSuper;
+}
 
 int rollout_max_seg_cap() {
     int dev = 0, optin = 0;
@@ -105,8 +111,10 @@ int rollout_max_seg_cap() {
         cudaGetLastError();
         return 0;
     }
-    if (static_cast<size_t>(optin) <= kAgentBytes) return 0;
-    return static_cast<int>((static_cast<size_t>(optin) - kAgentBytes) / kBytesPerTile) * kTile;
+    if (static_cast<size_t>(optin) <= kAgentBytes + kBytesPerSuper) return 0;
+    size_t nt = (static_cast<size_t>(optin) - kAgentBytes - kBytesPerSuper) / (kBytesPerTile + kBytesPerSuper / kSuper);
+    while (nt > 0 && rollout_smem_bytes(static_cast<int>(nt * kTile)) > static_cast<size_t>(optin)) --nt;
+    return static_cast<int>(nt) * kTile;
 }
 
 cudaError_t rollout_prepare(int seg_cap, int* blocks_per_sm) {

@@ -26,14 +26,16 @@ struct StaticScratch {
     float inv[kStaticMaxSegs];
     uint8_t flags[kStaticMaxSegs];
     float4 tiles[2 * (kStaticMaxSegs / kTile)];
+    float4 sup[kStaticMaxSegs / kTile / kSuper + kStaticMaxScenes];
     int32_t seg_off[kStaticMaxScenes + 1];
+    int32_t soff[kStaticMaxScenes + 1];
     int32_t seg_cnt[kStaticMaxScenes];
     int32_t order[kStaticMaxScenes];
     int32_t queue;
     int32_t status;
 };
 
-// Every GPU that loads the library holds this array (about 5.8 MB) until
+// Every GPU that loads the library holds this array (about 5.9 MB) until
 // the process exits.  All calls share it.
 static __device__ __align__(256) StaticScratch g_scratch;
 
@@ -61,57 +63,69 @@ int scratch_address(StaticScratch** out) {
     return WSIM_OK;
 }
 
+// Exclusive prefix sum over one 1024-thread block with a running carry.
+__device__ int block_excl_scan(int v, int* wsum, int* carry) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += u;
+    }
+    if (lane == 31) wsum[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int w = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += u;
+        }
+        wsum[lane] = w;
+    }
+    __syncthreads();
+    const int incl = x + (warp > 0 ? wsum[warp - 1] : 0) + *carry;
+    __syncthreads();
+    if (threadIdx.x == 1023) *carry = incl;
+    __syncthreads();
+    return incl - v;
+}
+
 // One CTA: checks the CSR offsets and the agents-per-scene limit, turns the
-// per-scene segment counts into padded offsets, and writes the identity work
-// order.  Any violation is recorded in the status word.
+// per-scene segment counts into padded segment offsets and super-tile
+// offsets, and writes the identity work order.  Violations go to the status
+// word.
 __global__ void __launch_bounds__(1024) k_static_offsets(const int32_t* agent_off, const int32_t* rg_off, int S,
                                                          int N_tot, int64_t R_tot, StaticScratch* sc) {
-    __shared__ int32_t carry;
+    __shared__ int32_t carry[2];
     __shared__ int32_t wsum[32];
     if (threadIdx.x == 0) {
-        carry = 0;
+        carry[0] = carry[1] = 0;
         if (agent_off[0] != 0 || agent_off[S] != N_tot || rg_off[0] != 0 || rg_off[S] != R_tot)
             atomicCAS(&sc->status, 0, WSIM_EINVAL);
     }
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int base = 0; base < S; base += 1024) {
         const int s = base + threadIdx.x;
-        int padded = 0;
+        int padded = 0, nsup = 0;
         if (s < S) {
             const int n = agent_off[s + 1] - agent_off[s];
             if (n < 0 || rg_off[s + 1] < rg_off[s]) atomicCAS(&sc->status, 0, WSIM_EINVAL);
             if (n > kMaxN) atomicCAS(&sc->status, 0, WSIM_ESIZE);
             padded = (sc->seg_cnt[s] + kSegAlign - 1) / kSegAlign * kSegAlign;
+            nsup = (padded / kTile + kSuper - 1) / kSuper;
             sc->order[s] = s;
         }
-        // block-wide inclusive scan of `padded`
-        int v = padded;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        if (lane == 31) wsum[warp] = v;
-        __syncthreads();
-        if (warp == 0) {
-            int w = wsum[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int u = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += u;
-            }
-            wsum[lane] = w;
-        }
-        __syncthreads();
-        const int incl = v + (warp > 0 ? wsum[warp - 1] : 0) + carry;
+        const int e = block_excl_scan(padded, wsum, &carry[0]);
+        const int u = block_excl_scan(nsup, wsum, &carry[1]);
         if (s < S) {
-            sc->seg_off[s] = incl - padded;
-            if (s == S - 1) sc->seg_off[S] = incl;
+            sc->seg_off[s] = e;
+            sc->soff[s] = u;
+            if (s == S - 1) {
+                sc->seg_off[S] = e + padded;
+                sc->soff[S] = u + nsup;
+            }
         }
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = incl;
-        __syncthreads();
     }
 }
 
@@ -164,7 +178,8 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
     if (rc) return rc;
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, b->S, sc->seg_off,
                         sc->geo, sc->inv, sc->flags, s) != cudaSuccess ||
-        launch_tile_build(b->S, sc->seg_off, sc->seg_cnt, sc->geo, sc->tiles, s) != cudaSuccess)
+        launch_tile_build(b->S, sc->seg_off, sc->seg_cnt, sc->geo, sc->tiles, s) != cudaSuccess ||
+        launch_super_build(b->S, sc->seg_off, sc->seg_cnt, sc->soff, sc->tiles, sc->sup, s) != cudaSuccess)
         return WSIM_ECUDA;
 
     StepArgs a;
@@ -178,7 +193,7 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
     a.valid = b->valid;
     a.log_x = b->log_x;
     a.log_y = b->log_y;
-    a.segs = Segs{sc->seg_off, sc->seg_cnt, sc->geo, sc->inv, sc->flags, sc->tiles};
+    a.segs = Segs{sc->seg_off, sc->seg_cnt, sc->geo, sc->inv, sc->flags, sc->tiles, sc->soff, sc->sup};
     a.hint = nullptr;  // no nearest-segment cache: bounds come from the tiles
     a.in = CStateP{st->x, st->y, st->x_lo, st->y_lo, st->th, st->th_lo, st->vx, st->vy, st->s, st->s_lo};
     a.m = MetricsP{m->ov, m->off, m->logdiv, m->flags, m->reward};
