@@ -219,6 +219,9 @@ def main():
         st.data.copy_(st0.data)
         sim.rollout(st, act, m, synth.T0, T, mode=main_mode)
 
+    # Launch shapes per scene-size bucket, tuned on this workload (untimed).
+    tune = sim.autotune(st0, act, synth.T0, 8) if main_mode == wsim.MODE_FUSED else None
+
     # Work counters of one rollout (untimed) for the roofline numerator.
     sim.set_counting(True)
     rollout()
@@ -248,7 +251,7 @@ def main():
 
     if args.profile:
         if rank == 0:
-            print(json.dumps({"profile": True, "mode": args.mode, "ms_per_step": ms, "scenes": S,
+            print(json.dumps({"profile": True, "mode": args.mode, "ms_per_step": ms, "scenes": S, "tune": tune,
                               "value": N * T / (ms / 1e3), "counts": cnt}), flush=True)
         return
     # End to end through the public API: pinned host inputs in, metrics out.
@@ -315,7 +318,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic", "config": config_dict(args, b),
+        "data": "synthetic", "config": {**config_dict(args, b), "rollout_tuning": tune},
         "roofline": {"bound": "alu", "kernel": "k_rollout" if fused else "k_step", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
                      "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",

@@ -169,6 +169,28 @@ int wsim_metrics(wsim_ctx *ctx, const wsim_state *st, const wsim_metric_buf *m, 
 int wsim_rollout(wsim_ctx *ctx, wsim_state *st, const float *act_seq, const uint8_t *ctrl, int t0,
                  int T, int mode, const wsim_metric_buf *mseq, const wsim_state *traj, void *stream);
 
+/* Autotuner of the scene-resident rollout (WSIM_MODE_FUSED).  Scenes are
+ * grouped at wsim_init into size buckets by their road-edge segment count:
+ * bucket 0 fits the small shared-memory stage, bucket 1 the large one,
+ * bucket 2 neither.  Three launch shapes exist: 0 = 512 threads, one CTA per
+ * SM, large stage; 1 = 256 threads, two CTAs per SM, small stage; 2 = 256
+ * threads, four CTAs per SM, segments read from global memory (L2).  For
+ * every non-empty bucket this times a T-step rollout of that bucket's scenes
+ * from state st (copied; st is not modified) with each shape, after one
+ * warm-up run, and keeps the fastest for later WSIM_MODE_FUSED rollouts.
+ * shapes_out[b] receives the chosen shape (-1 for an empty bucket);
+ * ms_out[3*b + shape] the measured milliseconds (-1 when not run).  All
+ * shapes give bit-identical results.  Allocates and frees scratch for the
+ * metric rows; synchronises `stream`. */
+int wsim_autotune(wsim_ctx *ctx, const wsim_state *st, const float *act_seq, int t0, int T, int shapes_out[3],
+                  float ms_out[9], void *stream);
+
+/* Sets the launch shape of each bucket (-1 keeps the current one), e.g. a
+ * tuning saved from an earlier wsim_autotune; wsim_get_shapes reads them and
+ * the scene count of each bucket (bucket_scenes_out may be NULL). */
+int wsim_set_shapes(wsim_ctx *ctx, const int shapes[3]);
+int wsim_get_shapes(wsim_ctx *ctx, int shapes_out[3], int bucket_scenes_out[3]);
+
 /* Sticky device status: synchronises `stream`, writes the first device error
  * code recorded since the last call (WSIM_OK if none) to *device_status and
  * clears it. */
@@ -192,9 +214,9 @@ void wsim_destroy(wsim_ctx *ctx);
  * this is for callers that cannot call cudaMalloc when they need the metrics
  * (a caching allocator or fixed arena that owns all device memory, code that
  * must not allocate).  The scratch wsim_init would allocate lives instead in
- * one file-scope device array of about 5.9 MB that every GPU loading the
+ * one file-scope device array of about 6.2 MB that every GPU loading the
  * library holds until the process exits.  Limits: at most 4096 scenes, and
- * R_tot + 31 * S <= 262144 (the packed road-edge segments must fit); larger
+ * R_tot + 15 * S <= 262144 (the packed road-edge segments must fit); larger
  * batches return WSIM_ESIZE before any work.  The first call on a device
  * looks up the array's device address (once per device, with that device
  * current); make that first call before any stream capture.  All calls share

@@ -20,7 +20,14 @@ struct wsim_ctx {
     wsim_config cfg;
     wsim_batch b;
     Params p;
-    int S = 0, N_tot = 0, grid = 1, roll_grid = 1, seg_cap = 0, count = 0;
+    int S = 0, N_tot = 0, grid = 1, count = 0;
+    // scene-resident rollout: scenes in size buckets, each with a launch shape
+    int shape_cap[kRollShapes] = {0, 0, 0};   // staged segments per shape
+    int shape_grid[kRollShapes] = {1, 1, 1};  // persistent grid per shape
+    int bucket_n[kRollShapes] = {0, 0, 0};    // scenes per bucket
+    int bucket_at[kRollShapes] = {0, 0, 0};   // first entry of the bucket in border
+    int bucket_shape[kRollShapes] = {1, 0, 2};
+    int32_t* border = nullptr;                // cost-ordered scene ids, grouped by bucket
     std::vector<int32_t> h_agent_off;
     // device scratch owned by the context
     int32_t *seg_off = nullptr, *seg_cnt = nullptr, *order = nullptr, *queue = nullptr, *status = nullptr;
@@ -32,6 +39,8 @@ struct wsim_ctx {
     int32_t* seg_soff = nullptr;
     float4* seg_sup = nullptr;
     int32_t* hint = nullptr;  // [N_tot][4] nearest-segment cache of the per-step kernels
+    uint16_t* tlist = nullptr;  // [N_tot][kList] candidate-tile lists of the per-step kernels
+    float4* tmeta = nullptr;    // [N_tot] their centre, radius and count
     unsigned long long* counters = nullptr;
     float* tmp = nullptr;  // ping-pong state, 10 x N_tot
     // captured rollout
@@ -103,8 +112,10 @@ StepArgs base_args(const wsim_ctx* c) {
     a.log_x = b.log_x;
     a.log_y = b.log_y;
     a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags, c->seg_tiles, c->seg_soff, c->seg_sup};
+    a.n_work = b.S;
     a.hint = c->hint;
-    a.seg_cap = c->seg_cap;
+    a.tlist = c->tlist;
+    a.tmeta = c->tmeta;
     a.order = c->order;
     a.status = c->status;
     a.counters = c->counters;
@@ -177,6 +188,34 @@ int enqueue_rollout(wsim_ctx* c, const RolloutKey& k, bool plain, cudaStream_t s
         float* const src[10] = {prev.x, prev.y, prev.x_lo, prev.y_lo, prev.th, prev.th_lo, prev.vx, prev.vy, prev.s, prev.s_lo};
         float* const dst[10] = {k.st.x, k.st.y, k.st.x_lo, k.st.y_lo, k.st.th, k.st.th_lo, k.st.vx, k.st.vy, k.st.s, k.st.s_lo};
         for (int j = 0; j < 10; ++j) CK(cudaMemcpyAsync(dst[j], src[j], N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    return WSIM_OK;
+}
+
+// Scene-resident rollout of every bucket (or of one bucket with one shape).
+int enqueue_fused(wsim_ctx* c, const wsim_state* st, const float* act_seq, const uint8_t* ctrl, int t0, int T,
+                  const wsim_metric_buf* mseq, const wsim_state* traj, int only_bucket, int force_shape,
+                  cudaStream_t s) {
+    StepArgs a = base_args(c);
+    a.in = cstate(st);
+    a.out = mstate(st);
+    a.act = act_seq;
+    a.ctrl = ctrl;
+    a.m = MetricsP{mseq->ov, mseq->off, mseq->logdiv, mseq->flags, mseq->reward};
+    a.t_log = t0 + 1;
+    a.T = T;
+    if (traj) a.traj = mstate(traj);
+    a.do_transition = 1;
+    a.do_metrics = 1;
+    CK(cudaMemsetAsync(c->queue, 0, kRollShapes * sizeof(int32_t), s));
+    for (int bk = 0; bk < kRollShapes; ++bk) {
+        if (c->bucket_n[bk] == 0 || (only_bucket >= 0 && bk != only_bucket)) continue;
+        const int sh = force_shape >= 0 ? force_shape : c->bucket_shape[bk];
+        a.order = c->border + c->bucket_at[bk];
+        a.n_work = c->bucket_n[bk];
+        a.queue = c->queue + bk;
+        a.seg_cap = c->shape_cap[sh];
+        CK(launch_rollout(sh, a, std::min(c->bucket_n[bk], c->shape_grid[sh]), s));
     }
     return WSIM_OK;
 }
@@ -268,11 +307,15 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
         return code;
     };
     if ((rc = dalloc(&c->seg_off, S + 1)) || (rc = dalloc(&c->seg_cnt, S)) || (rc = dalloc(&c->order, S)) ||
+        (rc = dalloc(&c->border, S)) ||
         (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->counters, 4)) ||
         (rc = dalloc(&c->tmp, static_cast<size_t>(N) * 10)) || (rc = ensure_queue(c, 128)) ||
-        (rc = dalloc(&c->hint, static_cast<size_t>(N) * 4)))
+        (rc = dalloc(&c->hint, static_cast<size_t>(N) * 4)) ||
+        (rc = dalloc(&c->tlist, static_cast<size_t>(N) * kList)) || (rc = dalloc(&c->tmeta, static_cast<size_t>(N))))
         return fail(rc);
-    if (cudaMemsetAsync(c->hint, 0xff, std::max<size_t>(N, 1) * 4 * sizeof(int32_t), st) != cudaSuccess)
+    // all-ones: no nearest segment known, list count -1 (no list yet)
+    if (cudaMemsetAsync(c->hint, 0xff, std::max<size_t>(N, 1) * 4 * sizeof(int32_t), st) != cudaSuccess ||
+        cudaMemsetAsync(c->tmeta, 0xff, std::max<size_t>(N, 1) * sizeof(float4), st) != cudaSuccess)
         return fail(WSIM_ECUDA);
     if (cudaMemsetAsync(c->status, 0, sizeof(int32_t), st) != cudaSuccess ||
         cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess)
@@ -328,13 +371,29 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     c->grid = std::min(S, sms * step_blocks_per_sm());
-    // Scene-resident rollout: stage up to the largest scene's segments.
+    // Scene-resident rollout.  Buckets by staged size: 0 = fits the small
+    // stage (shape 1), 1 = fits the large stage (shape 0), 2 = neither.
     int need = 0;
     for (int s = 0; s < S; ++s) need = std::max(need, off[s + 1] - off[s]);
-    c->seg_cap = std::min(need, rollout_max_seg_cap());
-    int rbps = 1;
-    if (rollout_prepare(c->seg_cap, &rbps) != cudaSuccess) return fail(WSIM_ECUDA);
-    c->roll_grid = std::min(S, sms * rbps);
+    for (int sh = 0; sh < kRollShapes; ++sh) c->shape_cap[sh] = std::min(need, shape_max_seg_cap(sh));
+    std::vector<int32_t> border;
+    for (int bk = 0; bk < kRollShapes; ++bk) {
+        c->bucket_at[bk] = static_cast<int>(border.size());
+        for (int w = 0; w < S; ++w) {
+            const int s = order[w], segs = off[s + 1] - off[s];
+            const int b = segs <= shape_max_seg_cap(1) ? 0 : (segs <= shape_max_seg_cap(0) ? 1 : 2);
+            if (b == bk) border.push_back(s);
+        }
+        c->bucket_n[bk] = static_cast<int>(border.size()) - c->bucket_at[bk];
+    }
+    for (int sh = 0; sh < kRollShapes; ++sh) {
+        int bps = 1;
+        if (shape_prepare(sh, c->shape_cap[sh], &bps) != cudaSuccess) return fail(WSIM_ECUDA);
+        c->shape_grid[sh] = sms * bps;
+    }
+    if (cudaMemcpyAsync(c->border, border.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return fail(WSIM_ECUDA);
     if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(WSIM_ECUDA);
     c->last = st;
     *out = c;
@@ -377,23 +436,7 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
     k.t0 = t0;
     k.T = T;
     k.has_traj = traj != nullptr;
-    if (mode == WSIM_MODE_FUSED) {
-        StepArgs a = base_args(c);
-        a.in = cstate(st);
-        a.out = mstate(st);
-        a.act = act_seq;
-        a.ctrl = ctrl;
-        a.m = MetricsP{mseq->ov, mseq->off, mseq->logdiv, mseq->flags, mseq->reward};
-        a.t_log = t0 + 1;
-        a.T = T;
-        if (traj) a.traj = mstate(traj);
-        a.do_transition = 1;
-        a.do_metrics = 1;
-        a.queue = c->queue;
-        CK(cudaMemsetAsync(c->queue, 0, sizeof(int32_t), s));
-        CK(launch_rollout(a, c->roll_grid, s));
-        return WSIM_OK;
-    }
+    if (mode == WSIM_MODE_FUSED) return enqueue_fused(c, st, act_seq, ctrl, t0, T, mseq, traj, -1, -1, s);
     if (mode != WSIM_MODE_GRAPH) return enqueue_rollout(c, k, mode == WSIM_MODE_PLAIN, s);
 
     if (!c->exec || !c->have_key || std::memcmp(&k, &c->key, sizeof(k)) != 0) {
@@ -422,6 +465,88 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
         c->have_key = true;
     }
     CK(cudaGraphLaunch(c->exec, s));
+    return WSIM_OK;
+}
+
+int wsim_autotune(wsim_ctx* c, const wsim_state* st, const float* act_seq, int t0, int T, int shapes_out[3],
+                  float ms_out[9], void* stream) {
+    if (!c || !state_ok(st) || !act_seq) return WSIM_EINVAL;
+    if (T < 1 || t0 < 0 || t0 + T >= c->b.T_log) return WSIM_ESIZE;
+    cudaStream_t s = S_(stream);
+    c->last = s;
+    int rc = ensure_queue(c, 128);
+    if (rc) return rc;
+    const size_t N = static_cast<size_t>(c->N_tot), S = static_cast<size_t>(c->S);
+    // Scratch metric rows for T steps; the caller's state is copied, not changed.
+    unsigned char* buf = nullptr;
+    const size_t bytes = static_cast<size_t>(T) * (N * (3 * sizeof(float) + 1) + S * sizeof(int32_t)) + 64;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return WSIM_ENOMEM;
+    }
+    wsim_metric_buf m;
+    float* f = reinterpret_cast<float*>(buf);
+    m.ov = f;
+    m.off = f + T * N;
+    m.logdiv = f + 2 * T * N;
+    m.reward = reinterpret_cast<int32_t*>(f + 3 * T * N);
+    m.flags = reinterpret_cast<uint8_t*>(m.reward + T * S);
+    const wsim_state tmp = tmp_state(c);
+    float* const src[10] = {st->x, st->y, st->x_lo, st->y_lo, st->th, st->th_lo, st->vx, st->vy, st->s, st->s_lo};
+    float* const dst[10] = {tmp.x, tmp.y, tmp.x_lo, tmp.y_lo, tmp.th, tmp.th_lo, tmp.vx, tmp.vy, tmp.s, tmp.s_lo};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    rc = WSIM_OK;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = WSIM_ECUDA;
+    for (int k = 0; k < 9; ++k) ms_out[k] = -1.f;
+    for (int bk = 0; bk < kRollShapes && rc == WSIM_OK; ++bk) {
+        shapes_out[bk] = c->bucket_n[bk] ? c->bucket_shape[bk] : -1;
+        if (!c->bucket_n[bk]) continue;
+        float best = 1e30f;
+        for (int sh = 0; sh < kRollShapes && rc == WSIM_OK; ++sh) {
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && rc == WSIM_OK; ++rep) {  // first run warms up
+                for (int j = 0; j < 10; ++j)
+                    if (cudaMemcpyAsync(dst[j], src[j], N * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                        rc = WSIM_ECUDA;
+                if (rc) break;
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = WSIM_ECUDA;
+                if (!rc) rc = enqueue_fused(c, &tmp, act_seq, nullptr, t0, T, &m, nullptr, bk, sh, s);
+                if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                    rc = WSIM_ECUDA;
+            }
+            if (rc) break;
+            ms_out[3 * bk + sh] = ms;
+            if (ms < best) {
+                best = ms;
+                c->bucket_shape[bk] = sh;
+            }
+        }
+        shapes_out[bk] = c->bucket_shape[bk];
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (rc) cudaGetLastError();
+    return rc;
+}
+
+int wsim_set_shapes(wsim_ctx* c, const int shapes[3]) {
+    if (!c || !shapes) return WSIM_EINVAL;
+    for (int b = 0; b < kRollShapes; ++b)
+        if (shapes[b] < -1 || shapes[b] >= kRollShapes) return WSIM_EINVAL;
+    for (int b = 0; b < kRollShapes; ++b)
+        if (shapes[b] >= 0) c->bucket_shape[b] = shapes[b];
+    return WSIM_OK;
+}
+
+int wsim_get_shapes(wsim_ctx* c, int shapes_out[3], int bucket_scenes_out[3]) {
+    if (!c || !shapes_out) return WSIM_EINVAL;
+    for (int b = 0; b < kRollShapes; ++b) {
+        shapes_out[b] = c->bucket_shape[b];
+        if (bucket_scenes_out) bucket_scenes_out[b] = c->bucket_n[b];
+    }
     return WSIM_OK;
 }
 
@@ -467,6 +592,7 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->seg_off);
     cudaFree(c->seg_cnt);
     cudaFree(c->order);
+    cudaFree(c->border);
     cudaFree(c->queue);
     cudaFree(c->status);
     cudaFree(c->counters);
@@ -478,6 +604,8 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->seg_soff);
     cudaFree(c->seg_sup);
     cudaFree(c->hint);
+    cudaFree(c->tlist);
+    cudaFree(c->tmeta);
     delete c;
 }
 

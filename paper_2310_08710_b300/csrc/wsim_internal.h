@@ -9,10 +9,12 @@ namespace wsim {
 
 constexpr int kMaxN = WSIM_MAX_AGENTS;  // agents per scene
 constexpr int kStepThreads = 256;       // threads per CTA of the per-step kernels
-constexpr int kRollThreads = 512;       // threads per CTA of the scene-resident rollout kernel
-constexpr int kTile = 32;               // road-edge segments per culling tile (one per lane)
+constexpr int kRollShapes = 3;          // launch shapes of the scene-resident rollout kernel
+constexpr int kTile = 16;               // road-edge segments per culling tile (half a warp)
 constexpr int kSegAlign = kTile;        // per-scene segment arrays start on a tile boundary
 constexpr int kSuper = 8;               // tiles per super-tile (first culling level)
+constexpr int kList = 32;               // tiles in an agent's cached candidate list (one per lane)
+constexpr float kSkin = 4.0f;           // extra radius of a candidate list beyond the current need (m)
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
 
 // Packed road-edge segments of the whole batch (built by wsim_init).  Scene s
@@ -51,6 +53,7 @@ struct Params {
 // Everything a step or rollout kernel needs.
 struct StepArgs {
     int S, N_tot, T_log;
+    int n_work;       // scenes in the work list `order`
     const int32_t* agent_off;
     const float *L, *W, *v0;
     const uint8_t *valid, *kind;
@@ -59,6 +62,8 @@ struct StepArgs {
     const float *log_x, *log_y;
     Segs segs;
     int32_t* hint;    // [N_tot][4] nearest-segment cache of the per-step kernels (may be null)
+    uint16_t* tlist;  // [N_tot][kList] candidate-tile cache of the per-step kernels (may be null)
+    float4* tmeta;    // [N_tot] (centre x, centre y, radius, count) of each candidate list
     CStateP in;       // state t (transition) or the state measured (metrics only)
     StateP out;       // state t+1 (per-step) / final state (rollout)
     const float* act; // [3][N_tot] (per step) or [T][3][N_tot] (rollout)
@@ -91,10 +96,11 @@ cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_plain_scene(const StepArgs& a, int scene, cudaStream_t st);
 int step_blocks_per_sm();
-// Scene-resident rollout: dynamic shared memory for `seg_cap` staged segments.
-size_t rollout_smem_bytes(int seg_cap);
-int rollout_max_seg_cap();
-cudaError_t rollout_prepare(int seg_cap, int* blocks_per_sm);
-cudaError_t launch_rollout(const StepArgs& a, int grid, cudaStream_t st);
+// Scene-resident rollout, launch shape 0 (512 threads, 1 CTA/SM, large stage),
+// 1 (256 threads, 2 CTAs/SM, small stage) or 2 (256 threads, 4 CTAs/SM, no
+// stage).  seg_cap: staged segments (a.seg_cap at launch).
+int shape_max_seg_cap(int shape);
+cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm);
+cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st);
 
 }  // namespace wsim

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(NTs) k_step(const StepArgs A) {
         if (threadIdx.x == 0) sm.scene = atomicAdd(A.queue, 1);
         __syncthreads();
         const int w = sm.scene;
-        if (w >= A.S) break;
+        if (w >= A.n_work) break;
         const int s = A.order[w];
         const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
         load_state<NTs>(sm, A, A.in, a0, N);
@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(NTs) k_step(const StepArgs A) {
         }
         if (A.do_metrics) {
             const SegView V = global_view(A.segs, s);
-            phase_metrics<NTs>(sm, V, A.hint ? A.hint + 4 * a0 : nullptr, N, true, true, cnt);
+            phase_metrics<NTs>(sm, V, A.hint ? A.hint + 4 * a0 : nullptr, A.tlist ? A.tlist + kList * a0 : nullptr,
+                               A.tmeta ? A.tmeta + a0 : nullptr, N, true, true, cnt);
             __syncthreads();
             phase_finish<NTs>(sm, A, A.m, A.m.reward + s, A.t_log, a0, N);
         }
@@ -78,7 +79,7 @@ __global__ void __launch_bounds__(NTs) k_plain_overlap(const StepArgs A, int s) 
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
     load_state<NTs>(sm, A, A.do_transition ? as_const(A.out) : A.in, a0, N);
     __syncthreads();
-    phase_metrics<NTs>(sm, SegView{}, nullptr, N, true, false, cnt);
+    phase_metrics<NTs>(sm, SegView{}, nullptr, nullptr, nullptr, N, true, false, cnt);
     __syncthreads();
     for (int i = threadIdx.x; i < N; i += NTs)
         if (sm.valid[i]) A.m.ov[a0 + i] = merged_ov(sm, i);
@@ -92,7 +93,9 @@ __global__ void __launch_bounds__(NTs) k_plain_offroad(const StepArgs A, int s) 
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
     load_state<NTs>(sm, A, A.do_transition ? as_const(A.out) : A.in, a0, N);
     __syncthreads();
-    phase_metrics<NTs>(sm, global_view(A.segs, s), A.hint ? A.hint + 4 * a0 : nullptr, N, false, true, cnt);
+    phase_metrics<NTs>(sm, global_view(A.segs, s), A.hint ? A.hint + 4 * a0 : nullptr,
+                       A.tlist ? A.tlist + kList * a0 : nullptr, A.tmeta ? A.tmeta + a0 : nullptr, N, false, true,
+                       cnt);
     __syncthreads();
     for (int i = threadIdx.x; i < N; i += NTs)
         if (sm.valid[i]) A.m.off[a0 + i] = sm.off[i];

@@ -385,6 +385,50 @@ __device__ __forceinline__ float seg_dist2(float4 G, float iv, float cxh, float 
     return fmaf(ex, ex, ey * ey);
 }
 
+// Scan two tiles at once (lanes 0-15: tile ta, lanes 16-31: tile tb) for the
+// corners in their masks, updating each lane's (distance, index) minima.
+__device__ __forceinline__ void scan_pair(const SegView& V, int lane, int ta, unsigned ma, int tb, unsigned mb,
+                                          float xh, float yh, const float (&cxl)[4], const float (&cyl)[4],
+                                          float (&bd)[4], int (&bi)[4], Counts& cnt) {
+    const bool upper = lane >= kTile;
+    const int t = upper ? tb : ta;
+    const unsigned m = upper ? mb : ma;
+    const unsigned u = ma | mb;
+    const int e = t * kTile + (lane & (kTile - 1));
+    if (lane == 0) cnt.evals += kTile * (__popc(ma) + __popc(mb));
+    if (m && e < V.E) {
+        const float4 G = V.geo[e];
+        const float iv = V.inv[e];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if ((u >> k) & 1u) {
+                const float d2 = seg_dist2(G, iv, xh, cxl[k], yh, cyl[k]);
+                if (((m >> k) & 1u) && d2 < bd[k]) {
+                    bd[k] = d2;
+                    bi[k] = e;
+                }
+            }
+        }
+    }
+}
+
+// Takes up to two tiles from the ballot `want` (lane l's tile and corner mask
+// in t_l, cm_l) and scans them.
+__device__ __forceinline__ void scan_next_two(const SegView& V, int lane, unsigned& want, int tl_lane,
+                                              unsigned cm_lane, float xh, float yh, const float (&cxl)[4],
+                                              const float (&cyl)[4], float (&bd)[4], int (&bi)[4], Counts& cnt) {
+    const int l1 = __ffs(want) - 1;
+    want &= want - 1;
+    const int l2 = want ? __ffs(want) - 1 : l1;
+    const bool two = want != 0;
+    want &= want - 1;
+    const unsigned m1 = __shfl_sync(kFull, cm_lane, l1);
+    const int t1 = __shfl_sync(kFull, tl_lane, l1);
+    const unsigned m2 = __shfl_sync(kFull, cm_lane, l2);
+    const int t2 = __shfl_sync(kFull, tl_lane, l2);
+    scan_pair(V, lane, t1, m1, t2, two ? m2 : 0u, xh, yh, cxl, cyl, bd, bi, cnt);
+}
+
 // ---------------------------------------------------------------------------
 // Off-road of agent i (warp; Sec. 3.4: the road lies left of an oriented road
 // edge).  For each box corner: the nearest road-edge segment (exact, ties to
@@ -400,7 +444,8 @@ __device__ __forceinline__ float seg_dist2(float4 G, float iv, float cxh, float 
 // equals the exhaustive scan.  hint (may be null) is read and updated.
 // ---------------------------------------------------------------------------
 static __device__ float offroad_agent(const SegView& V, int lane, float xh, float xl, float yh, float yl, float c,
-                                      float s, float hl, float hw, int32_t* hint, Counts& cnt) {
+                                      float s, float hl, float hw, int32_t* hint, uint16_t* tl, float4* meta,
+                                      Counts& cnt) {
     if (V.E == 0) {
         if (hint && lane < 4) hint[lane] = -1;
         return -WSIM_INF;
@@ -458,59 +503,99 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
 
     float bd[4] = {WSIM_INF, WSIM_INF, WSIM_INF, WSIM_INF};
     int bi[4] = {-1, -1, -1, -1};
-    for (int sb = 0; sb < V.ns; sb += 32) {
-        bool pass = false;
-        if (sb + lane < V.ns) {
-            const float4 B = V.sup[sb + lane];
-            const float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
-            const float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
-            pass = fmaf(dx, dx, dy * dy) <= clim;
-        }
-        if (lane == 0) cnt.tiles += min(32, V.ns - sb);
-        unsigned sup = __ballot_sync(kFull, pass);
-        while (sup) {
-            const int t0 = (sb + __ffs(sup) - 1) * kSuper;
-            sup &= sup - 1;
-            // Lanes 0..kSuper-1 test the super-tile's tiles corner by corner.
+    bool done = false;
+    if (tl) {
+        // Cached candidate tiles: every tile whose box lies within radius r0
+        // of centre c0.  A segment outside them is farther than
+        // r0 - |p - c0| from corner p, so a best distance below that bound
+        // is the exact nearest distance.
+        const float4 M = *meta;
+        const int n = __float_as_int(M.w);
+        if (n >= 0) {
             unsigned cm = 0;
-            const int t = t0 + lane;
-            if (lane < kSuper && t < V.nt) {
+            int t = 0;
+            if (lane < n) {
+                t = tl[lane];
                 const float4 B = V.tiles[2 * t];
-                float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
-                float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
-                if (fmaf(dx, dx, dy * dy) <= clim) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        dx = fmaxf(fmaxf(B.x - px[k], px[k] - B.z), 0.f);
-                        dy = fmaxf(fmaxf(B.y - py[k], py[k] - B.w), 0.f);
-                        if (fmaf(dx, dx, dy * dy) <= lim2[k]) cm |= 1u << k;
-                    }
+                for (int k = 0; k < 4; ++k) {
+                    const float dx = fmaxf(fmaxf(B.x - px[k], px[k] - B.z), 0.f);
+                    const float dy = fmaxf(fmaxf(B.y - py[k], py[k] - B.w), 0.f);
+                    if (fmaf(dx, dx, dy * dy) <= lim2[k]) cm |= 1u << k;
                 }
             }
-            if (lane == 0) cnt.tiles += kSuper;
+            if (lane == 0) cnt.tiles += n;
             unsigned want = __ballot_sync(kFull, cm != 0);
-            while (want) {
-                const int l = __ffs(want) - 1;
-                want &= want - 1;
-                const unsigned km = __shfl_sync(kFull, cm, l);
-                const int e = (t0 + l) * kTile + lane;
-                if (lane == 0) cnt.evals += 32 * __popc(km);
-                if (e < V.E) {
-                    const float4 G = V.geo[e];
-                    const float iv = V.inv[e];
+            while (want) scan_next_two(V, lane, want, t, cm, xh, yh, cxl, cyl, bd, bi, cnt);
+            // The check is on per-lane values; all lanes agree after the vote.
+            bool ok = true;
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        if ((km >> k) & 1u) {
-                            const float d2 = seg_dist2(G, iv, xh, cxl[k], yh, cyl[k]);
-                            if (d2 < bd[k]) {
-                                bd[k] = d2;
-                                bi[k] = e;
-                            }
+            for (int k = 0; k < 4; ++k) {
+                const float b = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(bd[k])));
+                const float dx = px[k] - M.x, dy = py[k] - M.y;
+                ok = ok && sqrtf(b) + sqrtf(fmaf(dx, dx, dy * dy)) <= M.z - 1e-3f;
+            }
+            done = ok;
+            if (!done) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    bd[k] = WSIM_INF;
+                    bi[k] = -1;
+                }
+            }
+        }
+    }
+    if (!done) {
+        // Full search over the super-tiles; on the way, collect the tiles
+        // within R of the centre as the next candidate list.
+        const float R = ucap + rad + kSkin;
+        const float R2 = (R + 1e-3f) * (R + 1e-3f);
+        const float slim = fmaxf(clim, R2);
+        int nl = 0;
+        for (int sb = 0; sb < V.ns; sb += 32) {
+            bool pass = false;
+            if (sb + lane < V.ns) {
+                const float4 B = V.sup[sb + lane];
+                const float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
+                const float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
+                pass = fmaf(dx, dx, dy * dy) <= slim;
+            }
+            if (lane == 0) cnt.tiles += min(32, V.ns - sb);
+            unsigned sup = __ballot_sync(kFull, pass);
+            while (sup) {
+                const int t0 = (sb + __ffs(sup) - 1) * kSuper;
+                sup &= sup - 1;
+                // Lanes 0..kSuper-1 test the super-tile's tiles corner by corner.
+                unsigned cm = 0;
+                bool inl = false;
+                const int t = t0 + lane;
+                if (lane < kSuper && t < V.nt) {
+                    const float4 B = V.tiles[2 * t];
+                    float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
+                    float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
+                    const float dc = fmaf(dx, dx, dy * dy);
+                    inl = dc <= R2;
+                    if (dc <= clim) {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            dx = fmaxf(fmaxf(B.x - px[k], px[k] - B.z), 0.f);
+                            dy = fmaxf(fmaxf(B.y - py[k], py[k] - B.w), 0.f);
+                            if (fmaf(dx, dx, dy * dy) <= lim2[k]) cm |= 1u << k;
                         }
                     }
                 }
+                if (lane == 0) cnt.tiles += kSuper;
+                if (tl) {
+                    const unsigned lb = __ballot_sync(kFull, inl);
+                    const int pos = nl + __popc(lb & ((1u << lane) - 1u));
+                    if (inl && pos < kList) tl[pos] = static_cast<uint16_t>(t);
+                    nl += __popc(lb);
+                }
+                unsigned want = __ballot_sync(kFull, cm != 0);
+                while (want) scan_next_two(V, lane, want, t, cm, xh, yh, cxl, cyl, bd, bi, cnt);
             }
         }
+        if (tl && lane == 0) *meta = make_float4(ccx, ccy, R, __int_as_float(nl <= kList ? nl : -1));
     }
     // Nearest segment per corner: the lexicographic (distance, index)
     // minimum over lanes (distances >= 0 order like their bit patterns).
@@ -565,8 +650,8 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
 // shared counter.  sm.ov receives the row maxima; finish merges the columns.
 // ---------------------------------------------------------------------------
 template <int NT>
-__device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_base, int N, bool do_ov, bool do_off,
-                              Counts& cnt) {
+__device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
+                              float4* meta_base, int N, bool do_ov, bool do_off, Counts& cnt) {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) sm.work[0] = 0;  // the next transition starts after two barriers
     for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane)) {
@@ -577,7 +662,9 @@ __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_bas
         }
         if (do_off) {
             const float f = offroad_agent(V, lane, sm.xh[i], sm.xl[i], sm.yh[i], sm.yl[i], sm.c[i], sm.s[i], sm.hl[i],
-                                          sm.hw[i], hint_base ? hint_base + 4 * i : nullptr, cnt);
+                                          sm.hw[i], hint_base ? hint_base + 4 * i : nullptr,
+                                          tl_base ? tl_base + kList * i : nullptr, tl_base ? meta_base + i : nullptr,
+                                          cnt);
             if (lane == 0) sm.off[i] = f;
         }
     }

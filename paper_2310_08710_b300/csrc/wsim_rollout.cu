@@ -1,34 +1,46 @@
-// Scene-resident rollout kernel (sm_103a).
+// Scene-resident rollout kernels (sm_103a).
 //
 // Scenes never exchange data during a rollout, so one CTA can run a scene's
 // whole episode (Sec. 5.1, Rollout: T steps of step()) without any global
 // synchronisation: the agent state stays in shared memory from step to step
 // and only the per-step metrics (and, on request, the per-step states) go to
-// global memory.  At the start of each scene one thread stages the scene's
-// packed road-edge segments, their flags, culling tiles and super-tiles into
-// shared memory with five bulk async copies (TMA) completing on one mbarrier, so
-// every off-road query of the episode reads shared memory.  Scenes whose
-// segments do not fit read them from global memory instead.  CTAs are
-// persistent and take scenes from an atomic counter over a cost-ordered
-// list.  Per step the phases are the same device functions as the per-step
-// kernel, so the results are bit-identical to it.
+// global memory.  In the staged shapes one thread copies the scene's packed
+// road-edge segments, their flags, culling tiles and super-tiles into shared
+// memory with five bulk async copies (TMA) completing on one mbarrier, so
+// every off-road query of the episode reads shared memory; scenes too large
+// for the stage, and the unstaged shape, read them from global memory (L2).
+// CTAs are persistent and take scenes from an atomic counter over a
+// cost-ordered work list.  Per step the phases are the same device functions
+// as the per-step kernel, so every shape gives bit-identical results.
+//
+// Launch shapes (threads per CTA x resident CTAs per SM, staged or not) are
+// picked per scene-size bucket; wsim_autotune times them on the workload.
 #include "wsim_phases.cuh"
 
 namespace wsim {
 
-constexpr int NTr = kRollThreads;
-constexpr size_t kAgentBytes = (sizeof(AgentSmem) + 127) / 128 * 128;
+constexpr size_t kCacheBytes = kMaxN * (kList * sizeof(uint16_t) + sizeof(float4));  // candidate-tile lists
+constexpr size_t kAgentBytes = (sizeof(AgentSmem) + kCacheBytes + 127) / 128 * 128;
 constexpr size_t kBytesPerTile = kTile * (16 + 4 + 1) + 32;  // geo + inv + flags + tile records
 constexpr size_t kBytesPerSuper = 16;
+
+struct ShapeDesc {
+    int threads, min_blocks;
+    bool stage;
+};
+constexpr ShapeDesc kShapes[kRollShapes] = {{512, 1, true}, {256, 2, true}, {256, 4, false}};
 
 __device__ __forceinline__ StateP offset_state(const StateP& s, size_t k) {
     return StateP{s.x + k, s.y + k, s.x_lo + k, s.y_lo + k, s.th + k,
                   s.th_lo + k, s.vx + k, s.vy + k, s.s + k, s.s_lo + k};
 }
 
-__global__ void __launch_bounds__(NTr, 1) k_rollout(const StepArgs A) {
+template <int NT, int MINB, bool STAGE>
+__global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
     extern __shared__ __align__(128) unsigned char dyn[];
     AgentSmem& sm = *reinterpret_cast<AgentSmem*>(dyn);
+    float4* tmeta = reinterpret_cast<float4*>(dyn + (sizeof(AgentSmem) + 15) / 16 * 16);
+    uint16_t* tlist = reinterpret_cast<uint16_t*>(tmeta + kMaxN);
     unsigned char* stage = dyn + kAgentBytes;
     init_cta(sm);
     Counts cnt;
@@ -38,11 +50,11 @@ __global__ void __launch_bounds__(NTr, 1) k_rollout(const StepArgs A) {
         if (threadIdx.x == 0) sm.scene = atomicAdd(A.queue, 1);
         __syncthreads();
         const int w = sm.scene;
-        if (w >= A.S) break;
+        if (w >= A.n_work) break;
         const int s = A.order[w];
         const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
         SegView V = global_view(A.segs, s);
-        const bool staged = V.nt > 0 && V.nt * kTile <= A.seg_cap;
+        const bool staged = STAGE && V.nt > 0 && V.nt * kTile <= A.seg_cap;
         if (staged) {
             const int e0 = A.segs.off[s];
             const int ns = V.nt * kTile;
@@ -63,8 +75,9 @@ __global__ void __launch_bounds__(NTr, 1) k_rollout(const StepArgs A) {
             }
             V = SegView{geo, inv, fl, tiles, sup, V.E, V.nt, V.ns};
         }
-        load_state<NTr>(sm, A, A.in, a0, N);
-        for (int j = threadIdx.x; j < 4 * N; j += NTr) sm.hint[j] = -1;
+        load_state<NT>(sm, A, A.in, a0, N);
+        for (int j = threadIdx.x; j < 4 * N; j += NT) sm.hint[j] = -1;
+        for (int j = threadIdx.x; j < N; j += NT) tmeta[j] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
         if (staged) {
             const bool ok = mbar_wait_bounded(&sm.bar[0], parity, kWaitLimitNs);
             parity ^= 1u;
@@ -77,59 +90,71 @@ __global__ void __launch_bounds__(NTr, 1) k_rollout(const StepArgs A) {
         }
         __syncthreads();
         for (int k = 0; k < A.T; ++k) {
-            phase_transition<NTr>(sm, A, A.act + static_cast<size_t>(k) * 3 * N_tot, a0, N, cnt);
+            phase_transition<NT>(sm, A, A.act + static_cast<size_t>(k) * 3 * N_tot, a0, N, cnt);
             __syncthreads();
             if (A.traj.x) {
                 const StateP tr = offset_state(A.traj, static_cast<size_t>(k) * N_tot);
-                writeback<NTr>(sm, &tr, a0, N);
+                writeback<NT>(sm, &tr, a0, N);
             } else {
-                writeback<NTr>(sm, nullptr, a0, N);
+                writeback<NT>(sm, nullptr, a0, N);
             }
             __syncthreads();
-            phase_metrics<NTr>(sm, V, sm.hint, N, true, true, cnt);
+            phase_metrics<NT>(sm, V, sm.hint, tlist, tmeta, N, true, true, cnt);
             __syncthreads();
             const size_t r = static_cast<size_t>(k) * N_tot;
             const MetricsP m{A.m.ov + r, A.m.off + r, A.m.logdiv + r, A.m.flags + r, nullptr};
-            phase_finish<NTr>(sm, A, m, A.m.reward + static_cast<size_t>(k) * A.S + s, A.t_log + k, a0, N);
+            phase_finish<NT>(sm, A, m, A.m.reward + static_cast<size_t>(k) * A.S + s, A.t_log + k, a0, N);
             __syncthreads();
         }
-        store_state<NTr>(sm, A.out, a0, N);
+        store_state<NT>(sm, A.out, a0, N);
         __syncthreads();
     }
     publish_counts(sm, A, cnt);
 }
 
-size_t rollout_smem_bytes(int seg_cap) {
+using KernelFn = void (*)(StepArgs);
+constexpr KernelFn kKernels[kRollShapes] = {k_rollout<512, 1, true>, k_rollout<256, 2, true>,
+                                            k_rollout<256, 4, false>};
+
+static size_t stage_bytes(int seg_cap) {
     const size_t nt = static_cast<size_t>(seg_cap / kTile);
-    return kAgentBytes + nt * kBytesPerTile + (nt + kSuper - 1) / kSuper * kBytesPerSuper;
+    return nt * kBytesPerTile + (nt + kSuper - 1) / kSuper * kBytesPerSuper;
 }
 
-int rollout_max_seg_cap() {
-    int dev = 0, optin = 0;
+// Largest stage (in segments, a multiple of kTile) of a shape on this device.
+int shape_max_seg_cap(int shape) {
+    if (!kShapes[shape].stage) return 0;
+    int dev = 0, per_sm = 0, optin = 0;
     cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    if (static_cast<size_t>(optin) <= kAgentBytes + kBytesPerSuper) return 0;
-    size_t nt = (static_cast<size_t>(optin) - kAgentBytes - kBytesPerSuper) / (kBytesPerTile + kBytesPerSuper / kSuper);
-    while (nt > 0 && rollout_smem_bytes(static_cast<int>(nt * kTile)) > static_cast<size_t>(optin)) --nt;
+    // per-CTA budget when min_blocks CTAs share the SM (1 KB reserved per CTA)
+    size_t budget = static_cast<size_t>(per_sm) / kShapes[shape].min_blocks;
+    budget = budget > 1024 ? budget - 1024 : 0;
+    if (budget > static_cast<size_t>(optin)) budget = static_cast<size_t>(optin);
+    if (budget <= kAgentBytes + kBytesPerSuper) return 0;
+    size_t nt = (budget - kAgentBytes - kBytesPerSuper) / (kBytesPerTile + kBytesPerSuper / kSuper);
+    while (nt > 0 && kAgentBytes + stage_bytes(static_cast<int>(nt * kTile)) > budget) --nt;
     return static_cast<int>(nt) * kTile;
 }
 
-cudaError_t rollout_prepare(int seg_cap, int* blocks_per_sm) {
-    const size_t bytes = rollout_smem_bytes(seg_cap);
-    cudaError_t e = cudaFuncSetAttribute(k_rollout, cudaFuncAttributeMaxDynamicSharedMemorySize,
+cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm) {
+    const size_t bytes = kAgentBytes + stage_bytes(kShapes[shape].stage ? seg_cap : 0);
+    cudaError_t e = cudaFuncSetAttribute(kKernels[shape], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(bytes));
     if (e != cudaSuccess) return e;
     int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout, NTr, bytes);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kKernels[shape], kShapes[shape].threads, bytes);
     *blocks_per_sm = n > 0 ? n : 1;
     return e;
 }
 
-cudaError_t launch_rollout(const StepArgs& a, int grid, cudaStream_t st) {
-    k_rollout<<<grid, NTr, rollout_smem_bytes(a.seg_cap), st>>>(a);
+cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st) {
+    const size_t bytes = kAgentBytes + stage_bytes(kShapes[shape].stage ? a.seg_cap : 0);
+    kKernels[shape]<<<grid, kShapes[shape].threads, bytes, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -35,7 +35,7 @@ struct StaticScratch {
     int32_t status;
 };
 
-// Every GPU that loads the library holds this array (about 5.9 MB) until
+// Every GPU that loads the library holds this array (about 6.2 MB) until
 // the process exits.  All calls share it.
 static __device__ __align__(256) StaticScratch g_scratch;
 
@@ -185,6 +185,7 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
     StepArgs a;
     std::memset(&a, 0, sizeof(a));
     a.S = b->S;
+    a.n_work = b->S;
     a.N_tot = b->N_tot;
     a.T_log = b->T_log;
     a.agent_off = b->agent_off;

@@ -78,6 +78,9 @@ def _load():
     lib.wsim_strerror.restype = C.c_char_p
     lib.wsim_destroy.argtypes = [vp]
     lib.wsim_destroy.restype = None
+    lib.wsim_autotune.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, P(C.c_int), P(C.c_float), vp]
+    lib.wsim_set_shapes.argtypes = [vp, P(C.c_int)]
+    lib.wsim_get_shapes.argtypes = [vp, P(C.c_int), P(C.c_int)]
     lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
     return lib
 
@@ -85,7 +88,8 @@ def _load():
 lib = _load()
 
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
-            "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static")
+            "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static",
+            "wsim_autotune", "wsim_set_shapes", "wsim_get_shapes")
 
 
 class WsimError(RuntimeError):
@@ -214,6 +218,24 @@ class Sim:
         _check(lib.wsim_rollout(self._h, C.byref(st.c()), act_seq.data_ptr(), _ptr(ctrl), t0, T, mode,
                                 C.byref(mseq.c()), C.byref(tc) if tc is not None else None, _stream(stream)),
                "wsim_rollout")
+
+    def autotune(self, st: State, act_seq: torch.Tensor, t0: int = 10, T: int = 8, stream=None) -> dict:
+        """Times the rollout launch shapes per scene-size bucket on this
+        workload and keeps the fastest (see wsim_autotune)."""
+        shapes = (C.c_int * 3)()
+        ms = (C.c_float * 9)()
+        _check(lib.wsim_autotune(self._h, C.byref(st.c()), act_seq.data_ptr(), t0, T, shapes, ms, _stream(stream)),
+               "wsim_autotune")
+        return {"shapes": list(shapes), "ms": [[ms[3 * b + k] for k in range(3)] for b in range(3)]}
+
+    def set_shapes(self, shapes):
+        arr = (C.c_int * 3)(*shapes)
+        _check(lib.wsim_set_shapes(self._h, arr), "wsim_set_shapes")
+
+    def get_shapes(self) -> dict:
+        sh, n = (C.c_int * 3)(), (C.c_int * 3)()
+        _check(lib.wsim_get_shapes(self._h, sh, n), "wsim_get_shapes")
+        return {"shapes": list(sh), "bucket_scenes": list(n)}
 
     def status(self, stream=None) -> int:
         v = C.c_int(0)

@@ -75,6 +75,42 @@ def test_config2_uneven_against_plain_and_oracle(wsim):
     print("config2", c)
 
 
+def test_every_launch_shape_on_every_bucket_bit_identical(wsim):
+    # Uneven scenes span the three size buckets; each of the three launch
+    # shapes of the scene-resident rollout must give the same bits on each.
+    b = synth.make_batch(2, seed=7, S=96, T=12)
+    sim = wsim.Sim(wsim.DeviceBatch(b))
+    info = sim.get_shapes()
+    sim.close()
+    print("buckets", info)
+    assert sum(info["bucket_scenes"]) == b.S and min(info["bucket_scenes"][:2]) > 0
+    ref = H.run_rollout(b, mode=wsim.MODE_GRAPH)
+    for sh in range(3):
+        g = H.run_rollout(b, mode=wsim.MODE_FUSED, shapes=[sh, sh, sh])
+        for k in ("traj", "final", "ov", "off", "logdiv", "flags", "reward"):
+            assert np.array_equal(g[k].view(np.uint8), ref[k].view(np.uint8)), (sh, k)
+
+
+def test_autotune_keeps_results(wsim):
+    import torch
+    b = synth.make_batch(2, seed=8, S=64, T=10)
+    db = wsim.DeviceBatch(b)
+    sim = wsim.Sim(db)
+    st = wsim.State.from_batch(b)
+    act = torch.as_tensor(b.actions).cuda().contiguous()
+    res = sim.autotune(st, act, 10, 6)
+    print("autotune", res)
+    assert torch.equal(st.data, wsim.State.from_batch(b).data)  # input state untouched
+    for bk, sh in enumerate(res["shapes"]):
+        if sh >= 0:
+            assert res["ms"][bk][sh] == min(v for v in res["ms"][bk] if v >= 0)
+    sim.close()
+    g1 = H.run_rollout(b)
+    g2 = H.run_rollout(b, shapes=res["shapes"])
+    for k in ("traj", "ov", "off", "flags", "reward"):
+        assert np.array_equal(g1[k].view(np.uint8), g2[k].view(np.uint8)), k
+
+
 def test_edge_cases_tiny_scenes(wsim):
     # scenes with 1 agent, 2 agents, no road edges, all agents invalid, an
     # empty scene, and a box touching an edge
