@@ -169,27 +169,39 @@ int wsim_metrics(wsim_ctx *ctx, const wsim_state *st, const wsim_metric_buf *m, 
 int wsim_rollout(wsim_ctx *ctx, wsim_state *st, const float *act_seq, const uint8_t *ctrl, int t0,
                  int T, int mode, const wsim_metric_buf *mseq, const wsim_state *traj, void *stream);
 
-/* Autotuner of the scene-resident rollout (WSIM_MODE_FUSED).  Scenes are
- * grouped at wsim_init into size buckets by their road-edge segment count:
- * bucket 0 fits the small shared-memory stage, bucket 1 the large one,
- * bucket 2 neither.  Three launch shapes exist: 0 = 512 threads, one CTA per
- * SM, large stage; 1 = 256 threads, two CTAs per SM, small stage; 2 = 256
- * threads, four CTAs per SM, segments read from global memory (L2).  For
- * every non-empty bucket this times a T-step rollout of that bucket's scenes
- * from state st (copied; st is not modified) with each shape, after one
- * warm-up run, and keeps the fastest for later WSIM_MODE_FUSED rollouts.
- * shapes_out[b] receives the chosen shape (-1 for an empty bucket);
- * ms_out[3*b + shape] the measured milliseconds (-1 when not run).  All
- * shapes give bit-identical results.  Allocates and frees scratch for the
- * metric rows; synchronises `stream`. */
-int wsim_autotune(wsim_ctx *ctx, const wsim_state *st, const float *act_seq, int t0, int T, int shapes_out[3],
-                  float ms_out[9], void *stream);
+/* Launch configuration of the scene-resident rollout (WSIM_MODE_FUSED).
+ * Three launch shapes exist: 0 = 512 threads, one CTA per SM, large
+ * shared-memory stage for the scene's road-edge segments; 1 = 256 threads,
+ * two CTAs per SM, small stage; 2 = 256 threads, four CTAs per SM, segments
+ * read from global memory (L2).  Scenes are grouped at wsim_init into size
+ * buckets by road-edge segment count: bucket 0 fits the small stage, bucket
+ * 1 the large one, bucket 2 neither.  Either one shape runs the whole
+ * cost-ordered batch (split = 0, single_shape) or each bucket runs its own
+ * shape on its own stream, concurrently (split = 1, bucket_shape).  Every
+ * configuration gives bit-identical results. */
+typedef struct {
+    int32_t split;            /* 0: one launch of single_shape; 1: per bucket   */
+    int32_t single_shape;
+    int32_t bucket_shape[3];
+    int32_t bucket_scenes[3]; /* filled by wsim_get_tuning / wsim_autotune      */
+    float ms_single[3];       /* wsim_autotune: T-step time of each shape       */
+    float ms_bucket[3][3];    /* ... of each shape on each bucket alone (-1: n/a) */
+    float ms_split;           /* ... of the split configuration (-1: n/a)       */
+} wsim_tuning;
 
-/* Sets the launch shape of each bucket (-1 keeps the current one), e.g. a
- * tuning saved from an earlier wsim_autotune; wsim_get_shapes reads them and
- * the scene count of each bucket (bucket_scenes_out may be NULL). */
-int wsim_set_shapes(wsim_ctx *ctx, const int shapes[3]);
-int wsim_get_shapes(wsim_ctx *ctx, int shapes_out[3], int bucket_scenes_out[3]);
+/* Autotuner: times a T-step rollout from state st (copied; st is not
+ * modified) for each single shape, for each shape on each non-empty bucket,
+ * and for the split configuration built from the best shape of each bucket,
+ * after one warm-up run each; keeps the fastest configuration for later
+ * WSIM_MODE_FUSED rollouts and reports all times in *out.  Allocates and
+ * frees scratch for the metric rows; synchronises `stream`. */
+int wsim_autotune(wsim_ctx *ctx, const wsim_state *st, const float *act_seq, int t0, int T, wsim_tuning *out,
+                  void *stream);
+
+/* Set a configuration (e.g. one saved from an earlier wsim_autotune; only
+ * split, single_shape and bucket_shape are read) / read the current one. */
+int wsim_set_tuning(wsim_ctx *ctx, const wsim_tuning *t);
+int wsim_get_tuning(wsim_ctx *ctx, wsim_tuning *out);
 
 /* Sticky device status: synchronises `stream`, writes the first device error
  * code recorded since the last call (WSIM_OK if none) to *device_status and

@@ -27,7 +27,10 @@ struct wsim_ctx {
     int bucket_n[kRollShapes] = {0, 0, 0};    // scenes per bucket
     int bucket_at[kRollShapes] = {0, 0, 0};   // first entry of the bucket in border
     int bucket_shape[kRollShapes] = {1, 0, 2};
+    int split = 0, single_shape = 0;          // one launch of single_shape, or one per bucket
     int32_t* border = nullptr;                // cost-ordered scene ids, grouped by bucket
+    cudaStream_t side[kRollShapes] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork = nullptr, join[kRollShapes] = {nullptr, nullptr, nullptr};
     std::vector<int32_t> h_agent_off;
     // device scratch owned by the context
     int32_t *seg_off = nullptr, *seg_cnt = nullptr, *order = nullptr, *queue = nullptr, *status = nullptr;
@@ -192,10 +195,11 @@ int enqueue_rollout(wsim_ctx* c, const RolloutKey& k, bool plain, cudaStream_t s
     return WSIM_OK;
 }
 
-// Scene-resident rollout of every bucket (or of one bucket with one shape).
+// Scene-resident rollout.  how: -1 = the context's configuration; 0..2 =
+// whole batch with that shape; 3 = split with the context's bucket shapes;
+// 10 + 3*b + shape = bucket b alone with that shape.
 int enqueue_fused(wsim_ctx* c, const wsim_state* st, const float* act_seq, const uint8_t* ctrl, int t0, int T,
-                  const wsim_metric_buf* mseq, const wsim_state* traj, int only_bucket, int force_shape,
-                  cudaStream_t s) {
+                  const wsim_metric_buf* mseq, const wsim_state* traj, int how, cudaStream_t s) {
     StepArgs a = base_args(c);
     a.in = cstate(st);
     a.out = mstate(st);
@@ -207,15 +211,36 @@ int enqueue_fused(wsim_ctx* c, const wsim_state* st, const float* act_seq, const
     if (traj) a.traj = mstate(traj);
     a.do_transition = 1;
     a.do_metrics = 1;
+    if (how < 0) how = c->split ? 3 : c->single_shape;
     CK(cudaMemsetAsync(c->queue, 0, kRollShapes * sizeof(int32_t), s));
+    if (how < kRollShapes) {  // whole batch, one shape
+        a.order = c->order;
+        a.n_work = c->S;
+        a.queue = c->queue;
+        a.seg_cap = c->shape_cap[how];
+        CK(launch_rollout(how, a, std::min(c->S, c->shape_grid[how]), s));
+        return WSIM_OK;
+    }
+    const bool split = how == 3;
+    if (split) CK(cudaEventRecord(c->fork, s));
     for (int bk = 0; bk < kRollShapes; ++bk) {
-        if (c->bucket_n[bk] == 0 || (only_bucket >= 0 && bk != only_bucket)) continue;
-        const int sh = force_shape >= 0 ? force_shape : c->bucket_shape[bk];
+        if (c->bucket_n[bk] == 0) continue;
+        int sh = c->bucket_shape[bk];
+        if (!split) {
+            if ((how - 10) / kRollShapes != bk) continue;
+            sh = (how - 10) % kRollShapes;
+        }
         a.order = c->border + c->bucket_at[bk];
         a.n_work = c->bucket_n[bk];
         a.queue = c->queue + bk;
         a.seg_cap = c->shape_cap[sh];
-        CK(launch_rollout(sh, a, std::min(c->bucket_n[bk], c->shape_grid[sh]), s));
+        cudaStream_t q = split ? c->side[bk] : s;
+        if (split) CK(cudaStreamWaitEvent(q, c->fork, 0));
+        CK(launch_rollout(sh, a, std::min(c->bucket_n[bk], c->shape_grid[sh]), q));
+        if (split) {
+            CK(cudaEventRecord(c->join[bk], q));
+            CK(cudaStreamWaitEvent(s, c->join[bk], 0));
+        }
     }
     return WSIM_OK;
 }
@@ -394,7 +419,16 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     if (cudaMemcpyAsync(c->border, border.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(WSIM_ECUDA);
-    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(WSIM_ECUDA);
+    if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess)
+        return fail(WSIM_ECUDA);
+    for (int b = 0; b < kRollShapes; ++b)
+        if (cudaStreamCreateWithFlags(&c->side[b], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->join[b], cudaEventDisableTiming) != cudaSuccess)
+            return fail(WSIM_ECUDA);
+    // Default until tuned: one launch with the large stage if any scene uses
+    // it, else the small-stage shape.
+    c->single_shape = c->bucket_n[1] + c->bucket_n[2] > 0 ? 0 : 1;
     c->last = st;
     *out = c;
     return WSIM_OK;
@@ -436,7 +470,7 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
     k.t0 = t0;
     k.T = T;
     k.has_traj = traj != nullptr;
-    if (mode == WSIM_MODE_FUSED) return enqueue_fused(c, st, act_seq, ctrl, t0, T, mseq, traj, -1, -1, s);
+    if (mode == WSIM_MODE_FUSED) return enqueue_fused(c, st, act_seq, ctrl, t0, T, mseq, traj, -1, s);
     if (mode != WSIM_MODE_GRAPH) return enqueue_rollout(c, k, mode == WSIM_MODE_PLAIN, s);
 
     if (!c->exec || !c->have_key || std::memcmp(&k, &c->key, sizeof(k)) != 0) {
@@ -468,9 +502,9 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
     return WSIM_OK;
 }
 
-int wsim_autotune(wsim_ctx* c, const wsim_state* st, const float* act_seq, int t0, int T, int shapes_out[3],
-                  float ms_out[9], void* stream) {
-    if (!c || !state_ok(st) || !act_seq) return WSIM_EINVAL;
+int wsim_autotune(wsim_ctx* c, const wsim_state* st, const float* act_seq, int t0, int T, wsim_tuning* out,
+                  void* stream) {
+    if (!c || !state_ok(st) || !act_seq || !out) return WSIM_EINVAL;
     if (T < 1 || t0 < 0 || t0 + T >= c->b.T_log) return WSIM_ESIZE;
     cudaStream_t s = S_(stream);
     c->last = s;
@@ -495,35 +529,61 @@ int wsim_autotune(wsim_ctx* c, const wsim_state* st, const float* act_seq, int t
     float* const src[10] = {st->x, st->y, st->x_lo, st->y_lo, st->th, st->th_lo, st->vx, st->vy, st->s, st->s_lo};
     float* const dst[10] = {tmp.x, tmp.y, tmp.x_lo, tmp.y_lo, tmp.th, tmp.th_lo, tmp.vx, tmp.vy, tmp.s, tmp.s_lo};
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    rc = WSIM_OK;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) rc = WSIM_ECUDA;
-    for (int k = 0; k < 9; ++k) ms_out[k] = -1.f;
-    for (int bk = 0; bk < kRollShapes && rc == WSIM_OK; ++bk) {
-        shapes_out[bk] = c->bucket_n[bk] ? c->bucket_shape[bk] : -1;
-        if (!c->bucket_n[bk]) continue;
-        float best = 1e30f;
-        for (int sh = 0; sh < kRollShapes && rc == WSIM_OK; ++sh) {
-            float ms = 0.f;
-            for (int rep = 0; rep < 2 && rc == WSIM_OK; ++rep) {  // first run warms up
-                for (int j = 0; j < 10; ++j)
-                    if (cudaMemcpyAsync(dst[j], src[j], N * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-                        rc = WSIM_ECUDA;
-                if (rc) break;
-                if (cudaEventRecord(e0, s) != cudaSuccess) rc = WSIM_ECUDA;
-                if (!rc) rc = enqueue_fused(c, &tmp, act_seq, nullptr, t0, T, &m, nullptr, bk, sh, s);
-                if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-                            cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+    // Time one configuration (first run warms up).
+    auto timeit = [&](int how, float* ms) {
+        for (int rep = 0; rep < 2 && rc == WSIM_OK; ++rep) {
+            for (int j = 0; j < 10; ++j)
+                if (cudaMemcpyAsync(dst[j], src[j], N * sizeof(float), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
                     rc = WSIM_ECUDA;
-            }
-            if (rc) break;
-            ms_out[3 * bk + sh] = ms;
-            if (ms < best) {
-                best = ms;
+            if (!rc && cudaEventRecord(e0, s) != cudaSuccess) rc = WSIM_ECUDA;
+            if (!rc) rc = enqueue_fused(c, &tmp, act_seq, nullptr, t0, T, &m, nullptr, how, s);
+            if (!rc && (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+                rc = WSIM_ECUDA;
+        }
+    };
+    std::memset(out, 0, sizeof(*out));
+    float best = 1e30f;
+    int best_how = 0;
+    for (int sh = 0; sh < kRollShapes; ++sh) {
+        out->ms_single[sh] = -1.f;
+        timeit(sh, &out->ms_single[sh]);
+        if (!rc && out->ms_single[sh] < best) {
+            best = out->ms_single[sh];
+            best_how = sh;
+        }
+    }
+    int used = 0;
+    for (int bk = 0; bk < kRollShapes; ++bk) {
+        out->bucket_scenes[bk] = c->bucket_n[bk];
+        float bb = 1e30f;
+        for (int sh = 0; sh < kRollShapes; ++sh) {
+            out->ms_bucket[bk][sh] = -1.f;
+            if (!c->bucket_n[bk] || rc) continue;
+            timeit(10 + kRollShapes * bk + sh, &out->ms_bucket[bk][sh]);
+            if (!rc && out->ms_bucket[bk][sh] < bb) {
+                bb = out->ms_bucket[bk][sh];
                 c->bucket_shape[bk] = sh;
             }
         }
-        shapes_out[bk] = c->bucket_shape[bk];
+        used += c->bucket_n[bk] > 0;
     }
+    out->ms_split = -1.f;
+    if (used > 1 && !rc) {
+        timeit(3, &out->ms_split);
+        if (!rc && out->ms_split < best) {
+            best = out->ms_split;
+            best_how = 3;
+        }
+    }
+    if (!rc) {
+        c->split = best_how == 3;
+        if (!c->split) c->single_shape = best_how;
+    }
+    out->split = c->split;
+    out->single_shape = c->single_shape;
+    for (int bk = 0; bk < kRollShapes; ++bk) out->bucket_shape[bk] = c->bucket_shape[bk];
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(s);
@@ -532,21 +592,29 @@ int wsim_autotune(wsim_ctx* c, const wsim_state* st, const float* act_seq, int t
     return rc;
 }
 
-int wsim_set_shapes(wsim_ctx* c, const int shapes[3]) {
-    if (!c || !shapes) return WSIM_EINVAL;
+int wsim_set_tuning(wsim_ctx* c, const wsim_tuning* t) {
+    if (!c || !t) return WSIM_EINVAL;
+    if (t->single_shape < 0 || t->single_shape >= kRollShapes) return WSIM_EINVAL;
     for (int b = 0; b < kRollShapes; ++b)
-        if (shapes[b] < -1 || shapes[b] >= kRollShapes) return WSIM_EINVAL;
-    for (int b = 0; b < kRollShapes; ++b)
-        if (shapes[b] >= 0) c->bucket_shape[b] = shapes[b];
+        if (t->bucket_shape[b] < 0 || t->bucket_shape[b] >= kRollShapes) return WSIM_EINVAL;
+    c->split = t->split ? 1 : 0;
+    c->single_shape = t->single_shape;
+    for (int b = 0; b < kRollShapes; ++b) c->bucket_shape[b] = t->bucket_shape[b];
     return WSIM_OK;
 }
 
-int wsim_get_shapes(wsim_ctx* c, int shapes_out[3], int bucket_scenes_out[3]) {
-    if (!c || !shapes_out) return WSIM_EINVAL;
+int wsim_get_tuning(wsim_ctx* c, wsim_tuning* out) {
+    if (!c || !out) return WSIM_EINVAL;
+    std::memset(out, 0, sizeof(*out));
+    out->split = c->split;
+    out->single_shape = c->single_shape;
     for (int b = 0; b < kRollShapes; ++b) {
-        shapes_out[b] = c->bucket_shape[b];
-        if (bucket_scenes_out) bucket_scenes_out[b] = c->bucket_n[b];
+        out->bucket_shape[b] = c->bucket_shape[b];
+        out->bucket_scenes[b] = c->bucket_n[b];
+        out->ms_single[b] = -1.f;
+        for (int k = 0; k < kRollShapes; ++k) out->ms_bucket[b][k] = -1.f;
     }
+    out->ms_split = -1.f;
     return WSIM_OK;
 }
 
@@ -589,6 +657,11 @@ void wsim_destroy(wsim_ctx* c) {
     cudaStreamSynchronize(c->last);
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->fork) cudaEventDestroy(c->fork);
+    for (int b = 0; b < kRollShapes; ++b) {
+        if (c->side[b]) cudaStreamDestroy(c->side[b]);
+        if (c->join[b]) cudaEventDestroy(c->join[b]);
+    }
     cudaFree(c->seg_off);
     cudaFree(c->seg_cnt);
     cudaFree(c->order);

@@ -53,6 +53,19 @@ class WsimState(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in STATE_FIELDS]
 
 
+class WsimTuning(C.Structure):
+    _fields_ = [("split", C.c_int32), ("single_shape", C.c_int32), ("bucket_shape", C.c_int32 * 3),
+                ("bucket_scenes", C.c_int32 * 3), ("ms_single", C.c_float * 3), ("ms_bucket", (C.c_float * 3) * 3),
+                ("ms_split", C.c_float)]
+
+    def as_dict(self) -> dict:
+        return {"split": bool(self.split), "single_shape": self.single_shape,
+                "bucket_shape": list(self.bucket_shape), "bucket_scenes": list(self.bucket_scenes),
+                "ms_single": [round(v, 4) for v in self.ms_single],
+                "ms_bucket": [[round(v, 4) for v in row] for row in self.ms_bucket],
+                "ms_split": round(self.ms_split, 4)}
+
+
 class WsimMetricBuf(C.Structure):
     _fields_ = [("ov", C.c_void_p), ("off", C.c_void_p), ("logdiv", C.c_void_p), ("flags", C.c_void_p),
                 ("reward", C.c_void_p)]
@@ -78,9 +91,9 @@ def _load():
     lib.wsim_strerror.restype = C.c_char_p
     lib.wsim_destroy.argtypes = [vp]
     lib.wsim_destroy.restype = None
-    lib.wsim_autotune.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, P(C.c_int), P(C.c_float), vp]
-    lib.wsim_set_shapes.argtypes = [vp, P(C.c_int)]
-    lib.wsim_get_shapes.argtypes = [vp, P(C.c_int), P(C.c_int)]
+    lib.wsim_autotune.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, P(WsimTuning), vp]
+    lib.wsim_set_tuning.argtypes = [vp, P(WsimTuning)]
+    lib.wsim_get_tuning.argtypes = [vp, P(WsimTuning)]
     lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
     return lib
 
@@ -89,7 +102,7 @@ lib = _load()
 
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
             "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static",
-            "wsim_autotune", "wsim_set_shapes", "wsim_get_shapes")
+            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning")
 
 
 class WsimError(RuntimeError):
@@ -220,22 +233,24 @@ class Sim:
                "wsim_rollout")
 
     def autotune(self, st: State, act_seq: torch.Tensor, t0: int = 10, T: int = 8, stream=None) -> dict:
-        """Times the rollout launch shapes per scene-size bucket on this
-        workload and keeps the fastest (see wsim_autotune)."""
-        shapes = (C.c_int * 3)()
-        ms = (C.c_float * 9)()
-        _check(lib.wsim_autotune(self._h, C.byref(st.c()), act_seq.data_ptr(), t0, T, shapes, ms, _stream(stream)),
+        """Times the rollout launch configurations on this workload and keeps
+        the fastest (see wsim_autotune)."""
+        t = WsimTuning()
+        _check(lib.wsim_autotune(self._h, C.byref(st.c()), act_seq.data_ptr(), t0, T, C.byref(t), _stream(stream)),
                "wsim_autotune")
-        return {"shapes": list(shapes), "ms": [[ms[3 * b + k] for k in range(3)] for b in range(3)]}
+        return t.as_dict()
 
-    def set_shapes(self, shapes):
-        arr = (C.c_int * 3)(*shapes)
-        _check(lib.wsim_set_shapes(self._h, arr), "wsim_set_shapes")
+    def set_tuning(self, split: bool = False, single_shape: int = 0, bucket_shape=(1, 0, 2)):
+        t = WsimTuning()
+        t.split, t.single_shape = int(split), single_shape
+        for i, v in enumerate(bucket_shape):
+            t.bucket_shape[i] = v
+        _check(lib.wsim_set_tuning(self._h, C.byref(t)), "wsim_set_tuning")
 
-    def get_shapes(self) -> dict:
-        sh, n = (C.c_int * 3)(), (C.c_int * 3)()
-        _check(lib.wsim_get_shapes(self._h, sh, n), "wsim_get_shapes")
-        return {"shapes": list(sh), "bucket_scenes": list(n)}
+    def get_tuning(self) -> dict:
+        t = WsimTuning()
+        _check(lib.wsim_get_tuning(self._h, C.byref(t)), "wsim_get_tuning")
+        return t.as_dict()
 
     def status(self, stream=None) -> int:
         v = C.c_int(0)

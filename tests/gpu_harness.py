@@ -23,14 +23,14 @@ TOL_DEPTH = 2e-5    # m, overlap depth and off-road distance
 ULP_SLACK = 4       # float32 ulps of the value for large magnitudes
 
 
-def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None, shapes=None):
+def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None, tuning=None):
     from paper_2310_08710_b300 import wsim
     mode = wsim.MODE_FUSED if mode is None else mode
     T = b.T if T is None else T
     db = wsim.DeviceBatch(b)
     sim = wsim.Sim(db, cfg)
-    if shapes is not None:
-        sim.set_shapes(shapes)
+    if tuning is not None:
+        sim.set_tuning(**tuning)
     st = wsim.State.from_batch(b)
     act = torch.as_tensor(b.actions[:T]).cuda().contiguous()
     traj = wsim.State(b.N_tot, rows=T)

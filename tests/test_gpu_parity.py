@@ -75,20 +75,23 @@ def test_config2_uneven_against_plain_and_oracle(wsim):
     print("config2", c)
 
 
-def test_every_launch_shape_on_every_bucket_bit_identical(wsim):
-    # Uneven scenes span the three size buckets; each of the three launch
-    # shapes of the scene-resident rollout must give the same bits on each.
+def test_every_launch_configuration_bit_identical(wsim):
+    # Uneven scenes span the three size buckets; every single launch shape
+    # and every split configuration of the scene-resident rollout must give
+    # the same bits as the per-step graph path.
     b = synth.make_batch(2, seed=7, S=96, T=12)
     sim = wsim.Sim(wsim.DeviceBatch(b))
-    info = sim.get_shapes()
+    info = sim.get_tuning()
     sim.close()
     print("buckets", info)
     assert sum(info["bucket_scenes"]) == b.S and min(info["bucket_scenes"][:2]) > 0
     ref = H.run_rollout(b, mode=wsim.MODE_GRAPH)
-    for sh in range(3):
-        g = H.run_rollout(b, mode=wsim.MODE_FUSED, shapes=[sh, sh, sh])
+    configs = [dict(split=False, single_shape=sh) for sh in range(3)]
+    configs += [dict(split=True, bucket_shape=(sh, (sh + 1) % 3, (sh + 2) % 3)) for sh in range(3)]
+    for tun in configs:
+        g = H.run_rollout(b, mode=wsim.MODE_FUSED, tuning=tun)
         for k in ("traj", "final", "ov", "off", "logdiv", "flags", "reward"):
-            assert np.array_equal(g[k].view(np.uint8), ref[k].view(np.uint8)), (sh, k)
+            assert np.array_equal(g[k].view(np.uint8), ref[k].view(np.uint8)), (tun, k)
 
 
 def test_autotune_keeps_results(wsim):
@@ -101,12 +104,13 @@ def test_autotune_keeps_results(wsim):
     res = sim.autotune(st, act, 10, 6)
     print("autotune", res)
     assert torch.equal(st.data, wsim.State.from_batch(b).data)  # input state untouched
-    for bk, sh in enumerate(res["shapes"]):
-        if sh >= 0:
-            assert res["ms"][bk][sh] == min(v for v in res["ms"][bk] if v >= 0)
+    singles = [v for v in res["ms_single"] if v >= 0]
+    chosen = res["ms_split"] if res["split"] else res["ms_single"][res["single_shape"]]
+    assert len(singles) == 3 and chosen <= min(singles + ([res["ms_split"]] if res["ms_split"] >= 0 else []))
+    tun = dict(split=res["split"], single_shape=res["single_shape"], bucket_shape=res["bucket_shape"])
     sim.close()
     g1 = H.run_rollout(b)
-    g2 = H.run_rollout(b, shapes=res["shapes"])
+    g2 = H.run_rollout(b, tuning=tun)
     for k in ("traj", "ov", "off", "flags", "reward"):
         assert np.array_equal(g1[k].view(np.uint8), g2[k].view(np.uint8)), k
 
