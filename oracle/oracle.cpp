@@ -264,14 +264,15 @@ bool boundary_ambiguous(const double* rx, const double* ry, int P, double h, dou
 
 struct IdmOut { St<double> st; double s; int lead; bool band; };
 
+// The agent state arrays of `in` are indexed by (global agent index - base).
 IdmOut idm_agent(const ob_params* p, const ob_batch* b, int a0, int a1, int i,
-                 const ob_state* in) {
+                 const ob_state* in, int base = 0) {
     const double h = p->route_h, eps = p->band;
     const int ro = b->route_off[i], P = b->route_off[i + 1] - ro;
     const double* rx = b->route_x + ro;
     const double* ry = b->route_y + ro;
-    const double xi = in->x[i], yi = in->y[i], si = in->s[i];
-    const double v = std::sqrt(in->vx[i] * in->vx[i] + in->vy[i] * in->vy[i]);
+    const double xi = in->x[i - base], yi = in->y[i - base], si = in->s[i - base];
+    const double v = std::sqrt(in->vx[i - base] * in->vx[i - base] + in->vy[i - base] * in->vy[i - base]);
     const double Li = b->L[i], Wi = b->W[i];
     const int K = p->idm_K;
     bool band = false;
@@ -287,11 +288,11 @@ IdmOut idm_agent(const ob_params* p, const ob_batch* b, int a0, int a1, int i,
     std::vector<double> nonrobust_gaps;
     for (int j = a0; j < a1; ++j) {
         if (j == i || !b->valid[j]) continue;
-        double cj = std::cos(in->th[j]), sj = std::sin(in->th[j]);
+        double cj = std::cos(in->th[j - base]), sj = std::sin(in->th[j - base]);
         int first = -1;
         bool firm = false, maybe = false;
         for (int k = 1; k <= K; ++k) {
-            double rxq = q[k].x - in->x[j], ryq = q[k].y - in->y[j];
+            double rxq = q[k].x - in->x[j - base], ryq = q[k].y - in->y[j - base];
             double pu = std::fabs(rxq * cj + ryq * sj);
             double pn = std::fabs(-rxq * sj + ryq * cj);
             double m = std::min(0.5 * b->L[j] + 0.5 * Wi - pu, 0.5 * b->W[j] + 0.5 * Wi - pn);
@@ -299,7 +300,7 @@ IdmOut idm_agent(const ob_params* p, const ob_batch* b, int a0, int a1, int i,
             if (m >= eps) firm = true;
             if (std::fabs(m) < eps) maybe = true;
         }
-        double dist = std::sqrt((in->x[j] - xi) * (in->x[j] - xi) + (in->y[j] - yi) * (in->y[j] - yi));
+        double dist = std::sqrt((in->x[j - base] - xi) * (in->x[j - base] - xi) + (in->y[j - base] - yi) * (in->y[j - base] - yi));
         double raw = dist - 0.5 * (Li + b->L[j]);
         double g = std::max(p->gap_min, raw);
         if (maybe && !firm) nonrobust_gaps.push_back(g);
@@ -319,16 +320,16 @@ IdmOut idm_agent(const ob_params* p, const ob_batch* b, int a0, int a1, int i,
         band = true;
     double vlead = 0;
     if (lead >= 0) {
-        double cj = std::cos(in->th[lead]), sj = std::sin(in->th[lead]);
+        double cj = std::cos(in->th[lead - base]), sj = std::sin(in->th[lead - base]);
         for (int k = 1; k <= lead_hit; ++k) {
-            double rxq = q[k].x - in->x[lead], ryq = q[k].y - in->y[lead];
+            double rxq = q[k].x - in->x[lead - base], ryq = q[k].y - in->y[lead - base];
             double pu = std::fabs(rxq * cj + ryq * sj);
             double pn = std::fabs(-rxq * sj + ryq * cj);
             double m = std::min(0.5 * b->L[lead] + 0.5 * Wi - pu, 0.5 * b->W[lead] + 0.5 * Wi - pn);
             if (std::fabs(m) < eps) band = true;
         }
         if (boundary_ambiguous(rx, ry, P, h, si + 0.5 * Li + p->idm_dq * lead_hit, eps)) band = true;
-        vlead = in->vx[lead] * q[lead_hit].tx + in->vy[lead] * q[lead_hit].ty;
+        vlead = in->vx[lead - base] * q[lead_hit].tx + in->vy[lead - base] * q[lead_hit].ty;
     }
 
     // Textbook IDM acceleration (delta = 4).
@@ -443,23 +444,45 @@ void metrics_scene(const ob_params* p, const ob_batch* b, int s, const ob_state*
     reward[s] = r;
 }
 
-// The differentiable loss of one scene, generic in the scalar type.
+// The differentiable loss of one scene, generic in the scalar type.  IDM
+// agents move as in oracle_transition but are constants for
+// differentiation (their updates use the values only): the gradient flows
+// through the policy agents' dynamics and every loss term.
 template <class T, class ActFn>
 T scene_loss(const ob_params* p, const ob_batch* b, int s, const ob_state* st0, ActFn act,
              int t0, int nsteps, double lambda, double tau) {
     const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1], n = a1 - a0, N = b->N_tot;
     std::vector<St<T>> cur(n);
-    for (int g = a0; g < a1; ++g)
+    std::vector<double> vals(6 * (size_t)n + 6);
+    ob_state vs = {vals.data(), vals.data() + n, vals.data() + 2 * n, vals.data() + 3 * n,
+                   vals.data() + 4 * n, vals.data() + 5 * n};
+    for (int g = a0; g < a1; ++g) {
         cur[g - a0] = {T(st0->x[g]), T(st0->y[g]), T(st0->th[g]), T(st0->vx[g]), T(st0->vy[g])};
+        vs.s[g - a0] = st0->s[g];
+    }
     T loss = T(0.0);
     std::vector<Box<T>> box(n);
     for (int k = 0; k < nsteps; ++k) {
+        for (int g = a0; g < a1; ++g) {  // values of state t for the IDM agents
+            vs.x[g - a0] = val(cur[g - a0].x); vs.y[g - a0] = val(cur[g - a0].y);
+            vs.th[g - a0] = val(cur[g - a0].th); vs.vx[g - a0] = val(cur[g - a0].vx);
+            vs.vy[g - a0] = val(cur[g - a0].vy);
+        }
+        std::vector<IdmOut> idm;
+        for (int g = a0; g < a1; ++g)
+            if (b->valid[g] && b->kind[g] == 2) idm.push_back(idm_agent(p, b, a0, a1, g, &vs, a0));
+        size_t q = 0;
         for (int g = a0; g < a1; ++g) {
             if (!b->valid[g]) continue;
-            if (b->kind[g] == 0)
+            if (b->kind[g] == 0) {
                 cur[g - a0] = bicycle_forward(cur[g - a0], act(k, 0, g), act(k, 1, g), p->dt);
-            else
+            } else if (b->kind[g] == 1) {
                 cur[g - a0] = delta_forward(cur[g - a0], act(k, 0, g), act(k, 1, g), act(k, 2, g), p->dt);
+            } else {
+                const IdmOut& o = idm[q++];
+                cur[g - a0] = {T(o.st.x), T(o.st.y), T(o.st.th), T(o.st.vx), T(o.st.vy)};
+                vs.s[g - a0] = o.s;
+            }
         }
         const int tl = t0 + k + 1;
         for (int g = a0; g < a1; ++g) {
@@ -483,7 +506,7 @@ T scene_loss(const ob_params* p, const ob_batch* b, int s, const ob_state* st0, 
 
 bool scene_differentiable(const ob_batch* b, int s) {
     for (int g = b->agent_off[s]; g < b->agent_off[s + 1]; ++g)
-        if (b->valid[g] && b->kind[g] != 0 && b->kind[g] != 1) return false;
+        if (b->valid[g] && b->kind[g] == 2 && b->route_off[g + 1] - b->route_off[g] < 2) return false;
     return true;
 }
 

@@ -109,8 +109,10 @@ double oracle_box_depth(const double *box_a, const double *box_b);
 double oracle_point_sd(const ob_params *p, const ob_batch *b, int s,
                        double px, double py, int *ambiguous, int32_t *seg_out);
 
-/* Differentiable loss of one scene over T steps (bicycle / delta agents only):
- * L = sum_t sum_i d_i(t)^2 + lambda * sum_t sum_{i<j} tau*softplus(d_ij/tau). */
+/* Differentiable loss of one scene over T steps:
+ * L = sum_t sum_i d_i(t)^2 + lambda * sum_t sum_{i<j} tau*softplus(d_ij/tau)
+ * over valid agents.  IDM agents move as in oracle_transition but are
+ * constants for differentiation (stop-gradient). */
 double oracle_loss(const ob_params *p, const ob_batch *b, int s,
                    const ob_state *st0, const double *act_seq, int t0, int T,
                    double lambda, double tau);

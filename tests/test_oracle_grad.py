@@ -105,3 +105,36 @@ def test_gradient_of_log_term_closed_form():
     dpos = (dt * dt / 2 + (k - 1) * dt * dt)[:, None] * np.array([np.cos(th), np.sin(th)])
     exp = np.sum(2 * (pos - np.array([50.0, -7.0])) * dpos)
     assert abs(g - exp) < 1e-9
+
+
+def test_loss_with_idm_agents_matches_rollout_log_divergence():
+    # With lambda = 0 the loss is sum_t sum_i d_i(t)^2 of the same closed-loop
+    # rollout (IDM agents included) that oracle_rollout produces.
+    b = synth.make_batch(1, seed=4, S=2, R=3000, T=15)
+    o = oracle.Oracle(b)
+    st = o.initial_state()
+    _, m = o.rollout(st, b.actions, 10, b.T, nthreads=1)
+    for s in range(b.S):
+        a0, a1 = b.agent_off[s], b.agent_off[s + 1]
+        exp = float(np.sum(m["logdiv"][:, a0:a1] ** 2))
+        got = o.loss(s, st, b.actions.astype(np.float64), 10, b.T, lam=0.0)
+        assert abs(got - exp) <= 1e-9 * max(1.0, exp)
+
+
+def test_idm_stop_gradient_equals_fd_when_out_of_reach():
+    # An ego far from every IDM agent: nothing it does changes their motion,
+    # so the stop-gradient derivative equals the finite difference.
+    b = synth.make_batch(1, seed=6, S=1, N=6, R=500, T=12)
+    b.x[0] += 5000.0
+    b.log_x[:, 0] += 5000.0
+    o = oracle.Oracle(b)
+    st = o.initial_state()
+    act = b.actions.astype(np.float64)
+    dirs = [(t, c, 0) for t in (0, 3, 11) for c in (0, 1)]
+    g = o.loss_grad(0, st, act, 10, b.T, dirs)
+    for (t, c, gi), gd in zip(dirs, g):
+        a1, a2 = act.copy(), act.copy()
+        a1[t, c, gi] += H
+        a2[t, c, gi] -= H
+        fd = (o.loss(0, st, a1, 10, b.T) - o.loss(0, st, a2, 10, b.T)) / (2 * H)
+        assert abs(gd - fd) <= 1e-5 * max(1.0, abs(fd))
