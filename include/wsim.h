@@ -203,6 +203,26 @@ int wsim_autotune(wsim_ctx *ctx, const wsim_state *st, const float *act_seq, int
 int wsim_set_tuning(wsim_ctx *ctx, const wsim_tuning *t);
 int wsim_get_tuning(wsim_ctx *ctx, wsim_tuning *out);
 
+/* Backpropagation through a whole rollout (the differentiable simulation of
+ * Sec. 6).  Loss of scene s:
+ *   L_s = sum_{t=t0+1}^{t0+T} sum_i d_i(t)^2
+ *         + loss_lambda * sum_t sum_{i<j} loss_tau * softplus(d_ij(t) / loss_tau)
+ * over valid agents, d_i = distance to the logged position, d_ij = SAT
+ * overlap depth (> 0 when overlapping).  Runs the T-step rollout from st0
+ * (not modified; all policy agents controlled) with the loss, storing the
+ * state every ckpt_every steps, then the reverse sweep, recomputing each
+ * segment from its checkpoint.  loss[S] (device, float64) receives L_s; dact
+ * (device, [T][3][N_tot], may be NULL for the loss only) receives dL/dact
+ * for bicycle (a, kappa, 0) and delta (dx, dy, dtheta) agents and 0 for the
+ * others.  IDM agents move as in wsim_rollout but are constants for the
+ * derivative.  Results do not depend on ckpt_every (bit-identical) and use
+ * no float atomics.  flags: WSIM_GRAD_PLAIN launches one kernel per scene
+ * (baseline) instead of the persistent kernel.  Grows the context's
+ * checkpoint scratch on first use (synchronising `stream` then). */
+#define WSIM_GRAD_PLAIN 1
+int wsim_loss_grad(wsim_ctx *ctx, const wsim_state *st0, const float *act_seq, int t0, int T, int ckpt_every,
+                   int flags, double *loss, float *dact, void *stream);
+
 /* Sticky device status: synchronises `stream`, writes the first device error
  * code recorded since the last call (WSIM_OK if none) to *device_status and
  * clears it. */

@@ -46,6 +46,9 @@ struct wsim_ctx {
     float4* tmeta = nullptr;    // [N_tot] their centre, radius and count
     unsigned long long* counters = nullptr;
     float* tmp = nullptr;  // ping-pong state, 10 x N_tot
+    float* ckpt = nullptr;    // BPTT checkpoints
+    float* segbuf = nullptr;  // BPTT recomputed segment states
+    size_t ckpt_len = 0, seg_len = 0;
     // captured rollout
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -618,6 +621,51 @@ int wsim_get_tuning(wsim_ctx* c, wsim_tuning* out) {
     return WSIM_OK;
 }
 
+int wsim_loss_grad(wsim_ctx* c, const wsim_state* st0, const float* act_seq, int t0, int T, int ckpt_every,
+                   int flags, double* loss, float* dact, void* stream) {
+    if (!c || !state_ok(st0) || !act_seq || !loss) return WSIM_EINVAL;
+    if (T < 1 || t0 < 0 || t0 + T >= c->b.T_log || ckpt_every < 1) return WSIM_ESIZE;
+    if (flags & ~WSIM_GRAD_PLAIN) return WSIM_EINVAL;
+    cudaStream_t s = S_(stream);
+    c->last = s;
+    const int ck = std::min(ckpt_every, T);
+    const size_t per = 10 * static_cast<size_t>(c->N_tot);
+    const size_t nck = static_cast<size_t>((T + ck - 1) / ck + 1) * per, nsg = static_cast<size_t>(ck + 1) * per;
+    if (nck > c->ckpt_len) {
+        CK(cudaStreamSynchronize(s));
+        cudaFree(c->ckpt);
+        c->ckpt = nullptr;
+        c->ckpt_len = 0;
+        int rc = dalloc(&c->ckpt, nck);
+        if (rc) return rc;
+        c->ckpt_len = nck;
+    }
+    if (nsg > c->seg_len) {
+        CK(cudaStreamSynchronize(s));
+        cudaFree(c->segbuf);
+        c->segbuf = nullptr;
+        c->seg_len = 0;
+        int rc = dalloc(&c->segbuf, nsg);
+        if (rc) return rc;
+        c->seg_len = nsg;
+    }
+    StepArgs a = base_args(c);
+    a.in = cstate(st0);
+    a.act = act_seq;
+    a.t_log = t0 + 1;
+    a.T = T;
+    a.queue = c->queue;
+    a.do_transition = 1;
+    const bool plain = (flags & WSIM_GRAD_PLAIN) != 0;
+    if (!plain) CK(cudaMemsetAsync(c->queue, 0, sizeof(int32_t), s));
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    CK(launch_bptt(a, c->ckpt, c->segbuf, ck, loss, dact, c->cfg.loss_lambda, c->cfg.loss_tau,
+                   std::min(c->S, sms * bptt_blocks_per_sm()), plain, s));
+    return WSIM_OK;
+}
+
 int wsim_status(wsim_ctx* c, int* device_status, void* stream) {
     if (!c || !device_status) return WSIM_EINVAL;
     cudaStream_t s = S_(stream);
@@ -670,6 +718,8 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->status);
     cudaFree(c->counters);
     cudaFree(c->tmp);
+    cudaFree(c->ckpt);
+    cudaFree(c->segbuf);
     cudaFree(c->seg_geo);
     cudaFree(c->seg_inv);
     cudaFree(c->seg_flags);

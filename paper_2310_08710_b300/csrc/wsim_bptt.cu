@@ -1,0 +1,344 @@
+// Backpropagation through whole rollouts (sm_103a): the differentiable
+// simulation the paper names as future work (Sec. 6), with the loss
+//     L = sum_t sum_i d_i(t)^2 + lambda sum_t sum_{i<j} tau softplus(d_ij(t)/tau)
+// over valid agents, d_i the log divergence (Sec. 3.4) and d_ij the SAT
+// overlap depth (Sec. 3.4 collision), differentiated with respect to every
+// action of the bicycle and delta agents (App. A.1).  IDM agents (Sec. 3.5)
+// move as in the forward simulation and are constants for differentiation.
+//
+// One CTA owns a scene for the whole computation.  Forward: T steps with the
+// shared step phases, the loss summed in a fixed order, and the state stored
+// every `ck` steps (and at T).  Backward: segments from last to first; each
+// recomputes its inner states from its checkpoint with the same code (so
+// ck = 10 and ck = 1 give bit-identical results), then runs the reverse
+// sweep: the adjoint of the loss at t+1 (every agent sums its own pair terms
+// in a fixed lane order: no float atomics) and the adjoint of the transition
+// t -> t+1, which yields dL/d(actions at t).
+#include "wsim_phases.cuh"
+
+namespace wsim {
+
+constexpr int NTb = 256;
+
+struct BpttArgs {
+    StepArgs A;      // batch, actions (act = [T][3][N_tot]), in = state t0, t_log = t0 + 1, T
+    float* ckpt;     // [n_ckpt][10][N_tot]
+    float* segbuf;   // [ck + 1][10][N_tot]
+    int ck;
+    double* loss;    // [S]
+    float* dact;     // [T][3][N_tot] (may be null: loss only)
+    float lambda, tau;
+    int scene;       // >= 0: this scene only (plain path); -1: persistent over the work list
+};
+
+struct AdjSmem {
+    float x[kMaxN], y[kMaxN], th[kMaxN], vx[kMaxN], vy[kMaxN];
+    float part[kMaxN];
+    double total;
+};
+
+__device__ __forceinline__ StateP slot_state(float* base, int slot, int N_tot) {
+    float* p = base + static_cast<size_t>(slot) * 10 * N_tot;
+    const size_t n = static_cast<size_t>(N_tot);
+    return StateP{p, p + n, p + 2 * n, p + 3 * n, p + 4 * n, p + 5 * n, p + 6 * n, p + 7 * n, p + 8 * n, p + 9 * n};
+}
+__device__ __forceinline__ CStateP cslot(float* base, int slot, int N_tot) {
+    const StateP s = slot_state(base, slot, N_tot);
+    return CStateP{s.x, s.y, s.x_lo, s.y_lo, s.th, s.th_lo, s.vx, s.vy, s.s, s.s_lo};
+}
+
+__device__ __forceinline__ float softplus_f(float x) { return fmaxf(x, 0.f) + log1pf(expf(-fabsf(x))); }
+__device__ __forceinline__ float sigmoid_f(float x) {
+    if (x >= 0.f) return 1.f / (1.f + expf(-x));
+    const float e = expf(x);
+    return e / (1.f + e);
+}
+
+// SAT depth of boxes A, B with the partial derivatives of the active
+// (first minimal) axis term w.r.t. theta_A, theta_B and d = c_B - c_A.
+struct SatGrad {
+    float d, dthA, dthB, ddx, ddy;
+};
+
+__device__ __forceinline__ SatGrad sat_grad(float dx, float dy, float cA, float sA, float hlA, float hwA, float cB,
+                                            float sB, float hlB, float hwB) {
+    const float C = fmaf(cA, cB, sA * sB);
+    const float S = fmaf(cA, sB, -sA * cB);
+    const float aC = fabsf(C), aS = fabsf(S);
+    const float sC = C < 0.f ? -1.f : 1.f, sS = S < 0.f ? -1.f : 1.f;
+    const float pA = fmaf(dx, cA, dy * sA), qA = fmaf(-dx, sA, dy * cA);
+    const float pB = fmaf(dx, cB, dy * sB), qB = fmaf(-dx, sB, dy * cB);
+    const float o0 = hlA + fmaf(hlB, aC, hwB * aS) - fabsf(pA);
+    const float o1 = hwA + fmaf(hlB, aS, hwB * aC) - fabsf(qA);
+    const float o2 = hlB + fmaf(hlA, aC, hwA * aS) - fabsf(pB);
+    const float o3 = hwB + fmaf(hlA, aS, hwA * aC) - fabsf(qB);
+    int k = 0;
+    float m = o0;
+    if (o1 < m) { m = o1; k = 1; }
+    if (o2 < m) { m = o2; k = 2; }
+    if (o3 < m) { m = o3; k = 3; }
+    SatGrad g;
+    g.d = m;
+    if (k == 0) {
+        const float sp = pA < 0.f ? -1.f : 1.f;
+        g.dthA = hlB * sC * S - hwB * sS * C - sp * qA;
+        g.dthB = -hlB * sC * S + hwB * sS * C;
+        g.ddx = -sp * cA;
+        g.ddy = -sp * sA;
+    } else if (k == 1) {
+        const float sq = qA < 0.f ? -1.f : 1.f;
+        g.dthA = -hlB * sS * C + hwB * sC * S + sq * pA;
+        g.dthB = hlB * sS * C - hwB * sC * S;
+        g.ddx = sq * sA;
+        g.ddy = -sq * cA;
+    } else if (k == 2) {
+        const float sp = pB < 0.f ? -1.f : 1.f;
+        g.dthA = hlA * sC * S - hwA * sS * C;
+        g.dthB = -hlA * sC * S + hwA * sS * C - sp * qB;
+        g.ddx = -sp * cB;
+        g.ddy = -sp * sB;
+    } else {
+        const float sq = qB < 0.f ? -1.f : 1.f;
+        g.dthA = -hlA * sS * C + hwA * sC * S;
+        g.dthB = hlA * sS * C - hwA * sC * S + sq * pB;
+        g.ddx = sq * sB;
+        g.ddy = -sq * cB;
+    }
+    return g;
+}
+
+// Loss terms of the current state of agent i (warp): d_i^2 plus the
+// penalty of its pairs with j > i.  Same value in every lane.
+__device__ float loss_agent(const AgentSmem& sm, const StepArgs& A, int a0, int N, int i, int lane, float lambda,
+                            float tau, int t_log) {
+    float acc = 0.f;
+    const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
+    for (int j = i + 1 + lane; j < N; j += 32) {
+        if (!sm.valid[j]) continue;
+        const float dx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
+        const float dy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
+        const float d = sat_depth(dx, dy, sm.c[i], sm.s[i], sm.hl[i], sm.hw[i], sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
+        acc += lambda * tau * softplus_f(d / tau);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    const size_t li = static_cast<size_t>(t_log) * A.N_tot + a0 + i;
+    const float ex = (xih - A.log_x[li]) + xil, ey = (yih - A.log_y[li]) + yil;
+    return acc + fmaf(ex, ex, ey * ey);
+}
+
+// Adds dL/d(x, y, theta) of agent i's loss terms at the current state
+// (warp; all pairs with i, each taken in the canonical order).
+__device__ void loss_adjoint_agent(const AgentSmem& sm, AdjSmem& adj, const StepArgs& A, int a0, int N, int i,
+                                   int lane, float lambda, float tau, int t_log) {
+    float gx = 0.f, gy = 0.f, gth = 0.f;
+    for (int j = lane; j < N; j += 32) {
+        if (j == i || !sm.valid[j]) continue;
+        const int lo = min(i, j), hi = max(i, j);
+        const float dx = comp_diff(sm.xh[hi], sm.xl[hi], sm.xh[lo], sm.xl[lo]);
+        const float dy = comp_diff(sm.yh[hi], sm.yl[hi], sm.yh[lo], sm.yl[lo]);
+        const SatGrad G = sat_grad(dx, dy, sm.c[lo], sm.s[lo], sm.hl[lo], sm.hw[lo], sm.c[hi], sm.s[hi], sm.hl[hi],
+                                   sm.hw[hi]);
+        const float w = lambda * sigmoid_f(G.d / tau);
+        if (i == lo) {
+            gx -= w * G.ddx;
+            gy -= w * G.ddy;
+            gth += w * G.dthA;
+        } else {
+            gx += w * G.ddx;
+            gy += w * G.ddy;
+            gth += w * G.dthB;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        gx += __shfl_xor_sync(kFull, gx, o);
+        gy += __shfl_xor_sync(kFull, gy, o);
+        gth += __shfl_xor_sync(kFull, gth, o);
+    }
+    if (lane == 0) {
+        const size_t li = static_cast<size_t>(t_log) * A.N_tot + a0 + i;
+        const float ex = (sm.xh[i] - A.log_x[li]) + sm.xl[i], ey = (sm.yh[i] - A.log_y[li]) + sm.yl[i];
+        adj.x[i] += gx + 2.f * ex;
+        adj.y[i] += gy + 2.f * ey;
+        adj.th[i] += gth;
+    }
+}
+
+// Load state t into the n* arrays (the transition adjoint reads it there).
+__device__ void load_prev(AgentSmem& sm, const CStateP& st, int a0, int N) {
+    for (int i = threadIdx.x; i < N; i += NTb) {
+        const int g = a0 + i;
+        sm.nth[i] = st.th[g];
+        sm.ntl[i] = st.th_lo[g];
+        sm.nvx[i] = st.vx[g];
+        sm.nvy[i] = st.vy[g];
+    }
+}
+
+// Adjoint of the transition t -> t+1 (thread per agent): state t in the n*
+// arrays, state t+1 in the current arrays, adj = dL/d(state t+1) on entry
+// and dL/d(state t) on exit; writes dL/d(actions at t).
+__device__ void transition_adjoint(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int t, int a0, int N) {
+    const StepArgs& A = B.A;
+    const float dt = A.p.dt, hdt2 = 0.5f * dt * dt;
+    const float* act = A.act + static_cast<size_t>(t) * 3 * A.N_tot;
+    for (int i = threadIdx.x; i < N; i += NTb) {
+        const int g = a0 + i;
+        const int kind = A.kind[g];
+        float ga = 0.f, gk = 0.f, g2 = 0.f;
+        if (!sm.valid[i]) {
+            // held state: the adjoint passes through unchanged
+        } else if (kind == WSIM_KIND_IDM) {
+            adj.x[i] = adj.y[i] = adj.th[i] = adj.vx[i] = adj.vy[i] = 0.f;  // stop-gradient
+        } else if (kind == WSIM_KIND_BICYCLE) {
+            const float a = act[g], kap = act[A.N_tot + g];
+            const float vx = sm.nvx[i], vy = sm.nvy[i];
+            const float v = sqrtf(fmaf(vx, vx, vy * vy));
+            float c, s;
+            comp_sincos(sm.nth[i], sm.ntl[i], c, s);
+            const float cn = sm.c[i], sn = sm.s[i];
+            const float vn = fmaf(a, dt, v);
+            const float X = adj.x[i], Y = adj.y[i], TH = adj.th[i], VX = adj.vx[i], VY = adj.vy[i];
+            const float vbn = fmaf(VX, cn, VY * sn);
+            const float thb = TH + vn * fmaf(-VX, sn, VY * cn);
+            ga = vbn * dt + thb * kap * hdt2 + hdt2 * fmaf(X, c, Y * s);
+            gk = thb * fmaf(v, dt, a * hdt2);
+            const float vb = vbn + thb * kap * dt;
+            adj.th[i] = thb + a * hdt2 * fmaf(-X, s, Y * c);
+            adj.vx[i] = X * dt + (v > 0.f ? vb * vx / v : 0.f);
+            adj.vy[i] = Y * dt + (v > 0.f ? vb * vy / v : 0.f);
+        } else {  // delta
+            const float X = adj.x[i], Y = adj.y[i];
+            ga = X + adj.vx[i] / dt;
+            gk = Y + adj.vy[i] / dt;
+            g2 = adj.th[i];
+            adj.vx[i] = adj.vy[i] = 0.f;
+        }
+        if (B.dact) {
+            float* d = B.dact + static_cast<size_t>(t) * 3 * A.N_tot;
+            d[g] = ga;
+            d[A.N_tot + g] = gk;
+            d[2 * static_cast<size_t>(A.N_tot) + g] = g2;
+        }
+    }
+}
+
+__device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int s) {
+    const StepArgs& A = B.A;
+    const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NTb / 32;
+    Counts cnt;
+    const int T = A.T, ck = B.ck;
+    const int nseg = (T + ck - 1) / ck;
+
+    // Forward.
+    load_state<NTb>(sm, A, A.in, a0, N);
+    __syncthreads();
+    store_state<NTb>(sm, slot_state(B.ckpt, 0, A.N_tot), a0, N);
+    if (threadIdx.x == 0) adj.total = 0.0;
+    for (int k = 0; k < T; ++k) {
+        phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(k) * 3 * A.N_tot, a0, N, cnt);
+        __syncthreads();
+        writeback<NTb>(sm, nullptr, a0, N);
+        __syncthreads();
+        for (int i = warp; i < N; i += NW) {
+            const float v = sm.valid[i] ? loss_agent(sm, A, a0, N, i, lane, B.lambda, B.tau, A.t_log + k) : 0.f;
+            if (lane == 0) adj.part[i] = v;
+        }
+        if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float step = 0.f;
+            for (int i = 0; i < N; ++i) step += adj.part[i];
+            adj.total += static_cast<double>(step);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) B.loss[s] = adj.total;
+    if (!B.dact) return;
+
+    // Backward.
+    for (int i = threadIdx.x; i < N; i += NTb) adj.x[i] = adj.y[i] = adj.th[i] = adj.vx[i] = adj.vy[i] = 0.f;
+    for (int sg = nseg - 1; sg >= 0; --sg) {
+        const int a = sg * ck, b = min(a + ck, T);
+        // Recompute the inner states a+1 .. b-1 of the segment.
+        if (b - a > 1) {
+            __syncthreads();
+            load_state<NTb>(sm, A, cslot(B.ckpt, sg, A.N_tot), a0, N);
+            __syncthreads();
+            for (int t = a; t < b - 1; ++t) {
+                phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(t) * 3 * A.N_tot, a0, N, cnt);
+                __syncthreads();
+                const StateP o = slot_state(B.segbuf, t + 1 - a, A.N_tot);
+                writeback<NTb>(sm, &o, a0, N);
+                __syncthreads();
+            }
+        }
+        for (int t = b - 1; t >= a; --t) {
+            __syncthreads();
+            // state t+1: the next checkpoint or a recomputed state
+            const CStateP nxt = (t + 1 == b) ? cslot(B.ckpt, (b + ck - 1) / ck, A.N_tot)
+                                             : cslot(B.segbuf, t + 1 - a, A.N_tot);
+            load_state<NTb>(sm, A, nxt, a0, N);
+            __syncthreads();
+            for (int i = warp; i < N; i += NW)
+                if (sm.valid[i]) loss_adjoint_agent(sm, adj, A, a0, N, i, lane, B.lambda, B.tau, A.t_log + t);
+            const CStateP cur = (t == a) ? cslot(B.ckpt, sg, A.N_tot) : cslot(B.segbuf, t - a, A.N_tot);
+            load_prev(sm, cur, a0, N);
+            __syncthreads();
+            transition_adjoint(sm, adj, B, t, a0, N);
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(NTb) k_bptt(const BpttArgs B) {
+    __shared__ AgentSmem sm;
+    __shared__ AdjSmem adj;
+    init_cta(sm);
+    if (B.scene >= 0) {
+        bptt_scene(sm, adj, B, B.scene);
+        return;
+    }
+    for (;;) {
+        if (threadIdx.x == 0) sm.scene = atomicAdd(B.A.queue, 1);
+        __syncthreads();
+        const int w = sm.scene;
+        if (w >= B.A.n_work) break;
+        bptt_scene(sm, adj, B, B.A.order[w]);
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_bptt(const StepArgs& a, float* ckpt, float* segbuf, int ck, double* loss, float* dact,
+                        float lambda, float tau, int grid, bool plain, cudaStream_t st) {
+    BpttArgs B;
+    B.A = a;
+    B.ckpt = ckpt;
+    B.segbuf = segbuf;
+    B.ck = ck;
+    B.loss = loss;
+    B.dact = dact;
+    B.lambda = lambda;
+    B.tau = tau;
+    if (plain) {
+        for (int s = 0; s < a.S; ++s) {
+            B.scene = s;
+            k_bptt<<<1, NTb, 0, st>>>(B);
+        }
+    } else {
+        B.scene = -1;
+        k_bptt<<<grid, NTb, 0, st>>>(B);
+    }
+    return cudaGetLastError();
+}
+
+int bptt_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bptt, NTb, 0) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
+}  // namespace wsim

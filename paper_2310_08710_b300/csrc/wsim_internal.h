@@ -102,5 +102,9 @@ int step_blocks_per_sm();
 int shape_max_seg_cap(int shape);
 cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm);
 cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st);
+// Backpropagation through the rollout (wsim_bptt.cu).
+cudaError_t launch_bptt(const StepArgs& a, float* ckpt, float* segbuf, int ck, double* loss, float* dact,
+                        float lambda, float tau, int grid, bool plain, cudaStream_t st);
+int bptt_blocks_per_sm();
 
 }  // namespace wsim

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libwsim.so")
 
 OK, EINVAL, ESIZE, ECUDA, ENONFINITE, ETIMEOUT, ENOMEM, ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
 MODE_GRAPH, MODE_STREAM, MODE_PLAIN, MODE_FUSED = 0, 1, 2, 3
+GRAD_PLAIN = 1
 MAX_AGENTS = 256
 FLAG_COLLISION, FLAG_OFFROAD = 1, 2
 
@@ -94,6 +95,7 @@ def _load():
     lib.wsim_autotune.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, P(WsimTuning), vp]
     lib.wsim_set_tuning.argtypes = [vp, P(WsimTuning)]
     lib.wsim_get_tuning.argtypes = [vp, P(WsimTuning)]
+    lib.wsim_loss_grad.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
     return lib
 
@@ -102,7 +104,7 @@ lib = _load()
 
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
             "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static",
-            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning")
+            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad")
 
 
 class WsimError(RuntimeError):
@@ -252,6 +254,19 @@ class Sim:
         _check(lib.wsim_get_tuning(self._h, C.byref(t)), "wsim_get_tuning")
         return t.as_dict()
 
+    def loss_grad(self, st0: State, act_seq: torch.Tensor, t0: int = 10, T: Optional[int] = None,
+                  ckpt_every: int = 10, grad: bool = True, plain: bool = False, stream=None):
+        """BPTT loss of every scene (float64 [S]) and dL/dact ([T, 3, N_tot], or
+        None when grad is False) of a T-step rollout from st0 (wsim_loss_grad)."""
+        T = act_seq.shape[0] if T is None else T
+        dev = act_seq.device
+        loss = torch.empty(self.batch.S, dtype=torch.float64, device=dev)
+        dact = torch.empty((T, 3, self.batch.N_tot), dtype=torch.float32, device=dev) if grad else None
+        _check(lib.wsim_loss_grad(self._h, C.byref(st0.c()), act_seq.data_ptr(), t0, T, ckpt_every,
+                                  GRAD_PLAIN if plain else 0, loss.data_ptr(), _ptr(dact), _stream(stream)),
+               "wsim_loss_grad")
+        return loss, dact
+
     def status(self, stream=None) -> int:
         v = C.c_int(0)
         _check(lib.wsim_status(self._h, C.byref(v), _stream(stream)), "wsim_status")
@@ -275,3 +290,27 @@ def metrics_static(batch: DeviceBatch, st: State, m: Metrics, t: int, cfg: Optio
     cfg = cfg if cfg is not None else default_config()
     _check(lib.wsim_metrics_static(C.byref(cfg), C.byref(batch.c), C.byref(st.c()), C.byref(m.c()), t,
                                    _stream(stream)), "wsim_metrics_static")
+
+
+class RolloutLoss(torch.autograd.Function):
+    """Differentiable rollout loss: forward returns the per-scene BPTT loss
+    (float64 [S]) of a T-step rollout driven by `actions` ([T, 3, N_tot]);
+    backward returns grad_output[scene] * dL_scene/dactions.  The gradient is
+    computed with the loss (one scene-resident kernel, checkpointed), so the
+    forward costs the whole BPTT pass."""
+
+    @staticmethod
+    def forward(ctx, actions: torch.Tensor, sim: "Sim", st0: State, t0: int = 10, ckpt_every: int = 10):
+        act = actions.detach().contiguous()
+        loss, dact = sim.loss_grad(st0, act, t0, act.shape[0], ckpt_every, grad=True)
+        ctx.save_for_backward(dact)
+        ctx.agent_scene = torch.repeat_interleave(
+            torch.arange(sim.batch.S, device=act.device),
+            (sim.batch.agent_off[1:] - sim.batch.agent_off[:-1]).long())
+        return loss
+
+    @staticmethod
+    def backward(ctx, grad_loss):
+        (dact,) = ctx.saved_tensors
+        w = grad_loss.to(dact.dtype)[ctx.agent_scene]  # per agent, its scene's weight
+        return dact * w[None, None, :], None, None, None, None
