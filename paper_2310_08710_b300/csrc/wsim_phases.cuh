@@ -92,9 +92,12 @@ __device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, 
     if (threadIdx.x == 0) sm.work[0] = sm.work[1] = 0;
 }
 
-// Make the next state current; optionally store it to global memory.
+// Make the next state current; optionally store it to global memory.  Runs
+// between barriers after the transition, so it also rearms the transition's
+// agent counter for the next step.
 template <int NT>
 __device__ void writeback(AgentSmem& sm, const StateP* out, int a0, int N) {
+    if (threadIdx.x == 0) sm.work[0] = 0;
     for (int i = threadIdx.x; i < N; i += NT) {
         if (out) {
             const int g = a0 + i;
@@ -653,7 +656,6 @@ template <int NT>
 __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
                               float4* meta_base, int N, bool do_ov, bool do_off, Counts& cnt) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) sm.work[0] = 0;  // the next transition starts after two barriers
     for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane)) {
         if (!sm.valid[i]) continue;
         if (do_ov) {
