@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--mode", default="fused", choices=["fused", "graph"],
                     help="rollout path timed: scene-resident kernel or graph of per-step launches")
     ap.add_argument("--scenes", type=int, default=None, help="override the scene count (profiling only)")
+    ap.add_argument("--shape", type=int, default=None,
+                    help="pin one launch shape of the scene-resident rollout instead of autotuning (profiling)")
+    ap.add_argument("--bptt-only", action="store_true", help="run only the BPTT leg (profiling)")
     ap.add_argument("--profile", action="store_true",
                     help="time the main path only (no mode comparison, end-to-end or CPU legs)")
     return ap.parse_args()
@@ -186,6 +189,40 @@ def run_reference(args, ws, rank, pg):
     print(json.dumps(line), flush=True)
 
 
+def bptt_leg(wsim, synth, torch, args, rank):
+    """Gradient steps/s of the differentiable rollout (256 scenes x 64 agents x
+    80 steps, bicycle agents): one gradient step = forward rollout with the
+    loss plus the reverse sweep giving dL/d(every action)."""
+    b = synth.make_batch(3, seed=args.seed + 1000 * rank)
+    sim = wsim.Sim(wsim.DeviceBatch(b))
+    st = wsim.State.from_batch(b)
+    act = torch.as_tensor(b.actions).cuda().contiguous()
+    out = {"workload": "config 3: 256 scenes x 64 agents x 80 steps, loss = log divergence^2 + softplus overlap"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, ck, plain, reps in (("ckpt10", 10, False, 5), ("store_all", 1, False, 5), ("plain_per_scene_ckpt10", 10, True, 1)):
+        sim.loss_grad(st, act, synth.T0, b.T, ck, plain=plain)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            sim.loss_grad(st, act, synth.T0, b.T, ck, plain=plain)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"grad_steps_per_s": 1e3 / ms, "ms": ms, "agent_steps_per_s": b.N_tot * b.T / (ms / 1e3)}
+    stc, mf = st.clone(), wsim.Metrics(b.N_tot, b.S, rows=b.T)
+    sim.rollout(stc, act, mf, synth.T0, b.T, mode=wsim.MODE_FUSED)
+    e0.record()
+    for _ in range(5):
+        stc.data.copy_(st.data)
+        sim.rollout(stc, act, mf, synth.T0, b.T, mode=wsim.MODE_FUSED)
+    e1.record()
+    torch.cuda.synchronize()
+    out["forward_rollout_ms"] = e0.elapsed_time(e1) / 5
+    assert sim.status() == 0
+    sim.close()
+    return out
+
+
 def config_dict(args, b):
     wl = workload_desc(args.config)
     return {"workload": f"config {args.config}: {wl.name}", "scenes": int(b.S),
@@ -204,6 +241,11 @@ def main():
     import torch
     from paper_2310_08710_b300 import synth, wsim
     torch.cuda.set_device(local)
+    if args.bptt_only:
+        out = bptt_leg(wsim, synth, torch, args, rank)
+        if rank == 0:
+            print(json.dumps({"profile": True, "bptt": out}), flush=True)
+        return
     b = synth.make_batch(args.config, seed=args.seed + 1000 * rank, S=args.scenes)
     T, N, S = b.T, b.N_tot, b.S
     main_mode = wsim.MODE_FUSED if args.mode == "fused" else wsim.MODE_GRAPH
@@ -220,7 +262,11 @@ def main():
         sim.rollout(st, act, m, synth.T0, T, mode=main_mode)
 
     # Launch shapes per scene-size bucket, tuned on this workload (untimed).
-    tune = sim.autotune(st0, act, synth.T0, 8) if main_mode == wsim.MODE_FUSED else None
+    if args.shape is not None:
+        sim.set_tuning(single_shape=args.shape)
+        tune = sim.get_tuning()
+    else:
+        tune = sim.autotune(st0, act, synth.T0, 8) if main_mode == wsim.MODE_FUSED else None
 
     # Work counters of one rollout (untimed) for the roofline numerator.
     sim.set_counting(True)
@@ -296,6 +342,8 @@ def main():
         modes[name] = {"value": N * T / (mm / 1e3), "unit": UNIT, "ms_per_rollout": mm}
     assert sim.status() == 0
 
+    bptt = bptt_leg(wsim, synth, torch, args, rank)
+
     units = N * T
     if pg:
         t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
@@ -329,6 +377,7 @@ def main():
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": args.steps * launches,
         "modes": modes,
+        "bptt": bptt,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
