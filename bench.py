@@ -355,13 +355,13 @@ def main():
     if rank != 0:
         return
     value = units / (ms / 1e3)
-    flops = (FLOPS_PER_EVAL * cnt[0] + FLOPS_PER_TILE * cnt[1] + FLOPS_PER_PAIR * cnt[2] + FLOPS_PER_TEST * cnt[3]
-             + FLOPS_PER_AGENT * N * T) / launches
     fused = args.mode == "fused"
     # fused: one scene-resident launch per rollout; graph: T step launches
     # (each preceded by a 4-byte memset node, counted in the launch time)
     launch_ms = ms if fused else ms / T
-    launches = 1 if fused else T
+    launches = T if not fused else (sum(1 for n in tune["bucket_scenes"] if n) if tune and tune["split"] else 1)
+    flops = (FLOPS_PER_EVAL * cnt[0] + FLOPS_PER_TILE * cnt[1] + FLOPS_PER_PAIR * cnt[2] + FLOPS_PER_TEST * cnt[3]
+             + FLOPS_PER_AGENT * N * T) / launches
     achieved = flops / (launch_ms / 1e3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
