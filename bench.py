@@ -42,13 +42,40 @@ FLOPS_PER_TEST = 16      # IDM look-ahead sample x box test
 FLOPS_PER_AGENT = 60     # dynamics + log divergence per agent-step
 
 
+def source_hash() -> str:
+    """sha256 (first 16 hex digits) of the CUDA sources and the C ABI header."""
+    import glob
+    import hashlib
+    c = os.path.join(ROOT, "paper_2310_08710_b300", "csrc")
+    files = sorted(glob.glob(os.path.join(c, "*.cu"))) + sorted(glob.glob(os.path.join(c, "*.cuh"))) + \
+        sorted(glob.glob(os.path.join(c, "*.h"))) + [os.path.join(ROOT, "include", "wsim.h")]
+    h = hashlib.sha256()
+    for f in files:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the last ncu capture, if it is of this build."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_sha256_16") != source_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wsim", choices=["wsim", "reference"])
-    ap.add_argument("--config", type=int, default=1)
+    ap.add_argument("--workload", type=int, default=1,
+                    help="synthetic workload id (paper_2310_08710_b300.synth.WORKLOADS); 1 = 1024 scenes x 128 agents, IDM")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
@@ -158,7 +185,7 @@ def run_reference(args, ws, rank, pg):
     from paper_2310_08710_b300 import synth
     if rank != 0:
         return
-    b = synth.make_batch(args.config, seed=args.seed)
+    b = synth.make_batch(args.workload, seed=args.seed)
     import oracle
     cores = os.cpu_count() or 1
     # size each step so that the whole run stays within a few minutes
@@ -191,13 +218,13 @@ def run_reference(args, ws, rank, pg):
 
 def bptt_leg(wsim, synth, torch, args, rank):
     """Gradient steps/s of the differentiable rollout (256 scenes x 64 agents x
-    80 steps, bicycle agents): one gradient step = forward rollout with the
+    80 steps, bicycle agents, synthetic workload 3): one gradient step = forward rollout with the
     loss plus the reverse sweep giving dL/d(every action)."""
     b = synth.make_batch(3, seed=args.seed + 1000 * rank)
     sim = wsim.Sim(wsim.DeviceBatch(b))
     st = wsim.State.from_batch(b)
     act = torch.as_tensor(b.actions).cuda().contiguous()
-    out = {"workload": "config 3: 256 scenes x 64 agents x 80 steps, loss = log divergence^2 + softplus overlap"}
+    out = {"workload": "256 scenes x 64 agents x 80 steps, loss = log divergence^2 + softplus overlap"}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name, ck, plain, reps in (("ckpt10", 10, False, 5), ("store_all", 1, False, 5), ("plain_per_scene_ckpt10", 10, True, 1)):
         sim.loss_grad(st, act, synth.T0, b.T, ck, plain=plain)
@@ -224,8 +251,8 @@ def bptt_leg(wsim, synth, torch, args, rank):
 
 
 def config_dict(args, b):
-    wl = workload_desc(args.config)
-    return {"workload": f"config {args.config}: {wl.name}", "scenes": int(b.S),
+    wl = workload_desc(args.workload)
+    return {"workload": wl.name, "scenes": int(b.S),
             "agents": int(b.N_tot), "rollout_steps": int(b.T), "roadgraph_points": int(b.R_tot),
             "dt_s": 0.1, "rollout_mode": ("scene-resident rollout kernel (one launch per rollout)"
                                           if args.mode == "fused" else "persistent step kernel x80, CUDA graph"),
@@ -246,7 +273,7 @@ def main():
         if rank == 0:
             print(json.dumps({"profile": True, "bptt": out}), flush=True)
         return
-    b = synth.make_batch(args.config, seed=args.seed + 1000 * rank, S=args.scenes)
+    b = synth.make_batch(args.workload, seed=args.seed + 1000 * rank, S=args.scenes)
     T, N, S = b.T, b.N_tot, b.S
     main_mode = wsim.MODE_FUSED if args.mode == "fused" else wsim.MODE_GRAPH
     db = wsim.DeviceBatch(b)
@@ -368,7 +395,8 @@ def main():
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic", "config": {**config_dict(args, b), "rollout_tuning": tune},
         "roofline": {"bound": "alu", "kernel": "k_rollout" if fused else "k_step", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                     "traffic": recorded_traffic("k_rollout") if fused else None,
                      "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
                      "flops_per_launch": flops, "launch_ms": launch_ms,
                      "counts_per_rollout": {"corner_segment_evals": int(cnt[0]), "tile_tests": int(cnt[1]),

@@ -50,7 +50,7 @@ IntSpec = Union[int, Tuple[int, int]]
 
 @dataclass(frozen=True)
 class Workload:
-    """Shape of one workload (the five benchmark configurations below)."""
+    """Shape of one synthetic workload (the five used here are listed below)."""
     name: str
     S: int                      # scenes
     N: IntSpec                  # agents per scene, or inclusive range

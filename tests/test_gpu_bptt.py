@@ -113,7 +113,7 @@ def test_checkpoint_interval_and_launch_path_bit_identical(wsim):
         assert np.array_equal(g.view(np.uint8), ref_g.view(np.uint8)), (ck, plain)
 
 
-def test_config3_full_size_sampled(wsim):
+def test_differentiable_256x64_full_size_sampled(wsim):
     b = synth.make_batch(3, seed=0)
     loss, dact = gpu_grad(wsim, b)
     assert np.isfinite(loss).all() and np.isfinite(dact).all()

@@ -25,16 +25,16 @@ def wsim():
     return w
 
 
-def test_config0_every_step(wsim):
+def test_single_scene_32_agents_every_step(wsim):
     b = synth.make_batch(0, seed=1)
     g = H.run_rollout(b)
     assert g["status"] == 0
     c = H.teacher_forced(b, g, [0], range(b.T))
     assert c["steps"] == 80
-    print("config0", c)
+    print("single scene", c)
 
 
-def test_config0_modes_bit_identical_and_deterministic(wsim):
+def test_single_scene_modes_bit_identical_and_deterministic(wsim):
     b = synth.make_batch(0, seed=2)
     ref = H.run_rollout(b, mode=wsim.MODE_FUSED)
     for mode in (wsim.MODE_FUSED, wsim.MODE_GRAPH, wsim.MODE_STREAM, wsim.MODE_PLAIN):
@@ -43,7 +43,7 @@ def test_config0_modes_bit_identical_and_deterministic(wsim):
             assert np.array_equal(g[k].view(np.uint8), ref[k].view(np.uint8)), (mode, k)
 
 
-def test_config1_sampled_scenes_full_size(wsim):
+def test_batch_1024x128_idm_full_size_sampled_scenes(wsim):
     # Full 1024-scene batch in the benchmark's launch configuration (the
     # scene-resident rollout); the oracle checks a spread of scenes at every
     # step, and the per-step graph path must agree bit for bit.
@@ -55,11 +55,11 @@ def test_config1_sampled_scenes_full_size(wsim):
     assert g["status"] == 0
     scenes = [0, 333, 700, 1023]
     c = H.teacher_forced(b, g, scenes, range(b.T))
-    print("config1", c)
+    print("1024x128 IDM batch", c)
     assert c["band_idm"] <= 0.02 * c["agent_steps"]
 
 
-def test_config2_uneven_against_plain_and_oracle(wsim):
+def test_uneven_batch_against_plain_and_oracle(wsim):
     # Scenes of 1k-30k roadgraph points: the largest do not fit the
     # shared-memory stage and read their segments from global memory.
     b = synth.make_batch(2, seed=0, S=512)
@@ -72,7 +72,7 @@ def test_config2_uneven_against_plain_and_oracle(wsim):
     scenes = sorted(rng.choice(b.S, 8, replace=False).tolist())
     big = int(np.argmax(np.diff(b.rg_off)))
     c = H.teacher_forced(b, g, sorted(set(scenes + [big])), [0, 1, 2, 17, 40, 79])
-    print("config2", c)
+    print("uneven batch", c)
 
 
 def test_every_launch_configuration_bit_identical(wsim):
