@@ -136,6 +136,20 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
 
 
+def combine_ranks(pg, times_ms, units, device):
+    """Whole-job view of per-rank measurements: the slowest rank's times and
+    the total units of all ranks (weak scaling: every rank simulates its own
+    scenes, nothing else is exchanged)."""
+    if pg is None:
+        return (*times_ms, units)
+    import torch
+    t = torch.tensor(list(times_ms), dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    pg.all_reduce(u)
+    return (*t.tolist(), u.item())
+
+
 def dist_setup(args):
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -185,7 +199,7 @@ def run_reference(args, ws, rank, pg):
     from paper_2310_08710_b300 import synth
     if rank != 0:
         return
-    b = synth.make_batch(args.workload, seed=args.seed)
+    b = synth.make_batch(args.workload, seed=args.seed, S=args.scenes)
     import oracle
     cores = os.cpu_count() or 1
     # size each step so that the whole run stays within a few minutes
@@ -371,14 +385,7 @@ def main():
 
     bptt = bptt_leg(wsim, synth, torch, args, rank)
 
-    units = N * T
-    if pg:
-        t = torch.tensor([ms, ms_e2e], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms, ms_e2e = t.tolist()
-        u = torch.tensor([units], dtype=torch.float64, device="cuda")
-        pg.all_reduce(u)
-        units = u.item()
+    ms, ms_e2e, units = combine_ranks(pg, [ms, ms_e2e], N * T, "cuda")
     if rank != 0:
         return
     value = units / (ms / 1e3)

@@ -115,6 +115,19 @@ def test_autotune_keeps_results(wsim):
         assert np.array_equal(g1[k].view(np.uint8), g2[k].view(np.uint8)), k
 
 
+def test_large_scene_workload_delta_and_bicycle_egos_with_idm(wsim):
+    # Scenes of the 16384 x 128 sweep workload (30k-point roadgraphs, delta
+    # ego in the first half, bicycle ego in the second, 127 IDM agents); many
+    # exceed the shared-memory stage and read their segments from L2.
+    b = synth.make_batch(4, seed=0, S=256)
+    g = H.run_rollout(b)
+    assert g["status"] == 0
+    big = int(np.argmax(np.diff(b.rg_off)))
+    c = H.teacher_forced(b, g, sorted({0, 127, 128, 255, big}), [0, 1, 2, 39, 79])
+    print("large-scene workload", c)
+    assert c["band_idm"] <= 0.02 * c["agent_steps"]
+
+
 def test_edge_cases_tiny_scenes(wsim):
     # scenes with 1 agent, 2 agents, no road edges, all agents invalid, an
     # empty scene, and a box touching an edge
