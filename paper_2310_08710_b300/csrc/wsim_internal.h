@@ -14,7 +14,8 @@ constexpr int kTile = 16;               // road-edge segments per culling tile (
 constexpr int kSegAlign = kTile;        // per-scene segment arrays start on a tile boundary
 constexpr int kSuper = 8;               // tiles per super-tile (first culling level)
 constexpr int kList = 32;               // tiles in an agent's cached candidate list (one per lane)
-constexpr float kSkin = 4.0f;           // extra radius of a candidate list beyond the current need (m)
+constexpr float kSkin = 8.0f;           // extra radius of a candidate list beyond the current need (m)
+constexpr float kSkinSmall = 2.0f;      // fallback when the kSkin list would not fit in kList tiles
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
 
 // Packed road-edge segments of the whole batch (built by wsim_init).  Scene s

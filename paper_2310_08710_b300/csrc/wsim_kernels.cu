@@ -175,7 +175,10 @@ __global__ void __launch_bounds__(256) k_seg_pack(const int32_t* rg_off, RgView 
     }
 }
 
-// Per tile: bounding box of its segments and two of their start points.
+// Per tile: a capsule around its segments: the chord from the first
+// segment's start to the last segment's end, and the largest distance of any
+// segment end point from that chord (rounded up).  Record 0: (start, chord);
+// record 1: (radius, 1/|chord|^2, 0, 0).  Both chord ends lie on segments.
 __global__ void __launch_bounds__(256) k_tile_build(const int32_t* seg_off, const int32_t* seg_cnt,
                                                     const float4* geo, float4* tiles) {
     const int s = blockIdx.x;
@@ -184,23 +187,28 @@ __global__ void __launch_bounds__(256) k_tile_build(const int32_t* seg_off, cons
     for (int t = threadIdx.x; t < nt; t += 256) {
         const int b = e0 + t * kTile;
         const int n = min(kTile, E - t * kTile);
-        float x0 = WSIM_INF, y0 = WSIM_INF, x1 = -WSIM_INF, y1 = -WSIM_INF;
+        const float4 A = geo[b], Z = geo[b + n - 1];
+        const float sx = A.x, sy = A.y;
+        const float dx = (Z.x + Z.z) - sx, dy = (Z.y + Z.w) - sy;
+        const float dd = fmaf(dx, dx, dy * dy);
+        const float inv = dd > 0.f ? 1.0f / dd : 0.f;
+        float r2 = 0.f;
         for (int j = 0; j < n; ++j) {
             const float4 G = geo[b + j];
-            const float ex = G.x + G.z, ey = G.y + G.w;
-            x0 = fminf(x0, fminf(G.x, ex));
-            y0 = fminf(y0, fminf(G.y, ey));
-            x1 = fmaxf(x1, fmaxf(G.x, ex));
-            y1 = fmaxf(y1, fmaxf(G.y, ey));
+            for (int end = 0; end < 2; ++end) {
+                const float wx = (end ? G.x + G.z : G.x) - sx, wy = (end ? G.y + G.w : G.y) - sy;
+                const float u = __saturatef(fmaf(wx, dx, wy * dy) * inv);
+                const float ex = fmaf(-u, dx, wx), ey = fmaf(-u, dy, wy);
+                r2 = fmaxf(r2, fmaf(ex, ex, ey * ey));
+            }
         }
-        const float4 A = geo[b], M = geo[b + min(kTile / 2, n - 1)];
         const size_t ti = static_cast<size_t>(e0 / kTile + t);
-        tiles[2 * ti] = make_float4(x0, y0, x1, y1);
-        tiles[2 * ti + 1] = make_float4(A.x, A.y, M.x, M.y);
+        tiles[2 * ti] = make_float4(sx, sy, dx, dy);
+        tiles[2 * ti + 1] = make_float4(sqrtf(r2) * 1.00001f + 1e-4f, inv, 0.f, 0.f);
     }
 }
 
-// Per super-tile: bounding box of its kSuper tiles.
+// Per super-tile: bounding box of its kSuper tiles' capsules.
 __global__ void __launch_bounds__(256) k_super_build(const int32_t* seg_off, const int32_t* seg_cnt,
                                                      const int32_t* soff, const float4* tiles, float4* sup) {
     const int s = blockIdx.x;
@@ -210,11 +218,13 @@ __global__ void __launch_bounds__(256) k_super_build(const int32_t* seg_off, con
     for (int j = threadIdx.x; j < ns; j += 256) {
         float x0 = WSIM_INF, y0 = WSIM_INF, x1 = -WSIM_INF, y1 = -WSIM_INF;
         for (int t = j * kSuper; t < min(nt, (j + 1) * kSuper); ++t) {
-            const float4 B = tiles[2 * (static_cast<size_t>(e0 / kTile) + t)];
-            x0 = fminf(x0, B.x);
-            y0 = fminf(y0, B.y);
-            x1 = fmaxf(x1, B.z);
-            y1 = fmaxf(y1, B.w);
+            const size_t ti = static_cast<size_t>(e0 / kTile) + t;
+            const float4 C = tiles[2 * ti];
+            const float r = tiles[2 * ti + 1].x;
+            x0 = fminf(x0, fminf(C.x, C.x + C.z) - r);
+            y0 = fminf(y0, fminf(C.y, C.y + C.w) - r);
+            x1 = fmaxf(x1, fmaxf(C.x, C.x + C.z) + r);
+            y1 = fmaxf(y1, fmaxf(C.y, C.y + C.w) + r);
         }
         sup[soff[s] + j] = make_float4(x0, y0, x1, y1);
     }

@@ -26,7 +26,7 @@ struct __align__(16) AgentSmem {
     uint8_t valid[kMaxN];
     int scene;
     int reward;
-    int work[2];              // agent counters of the warp phases (transition, metrics)
+    int work[3];              // counters of the warp phases (transition, overlap rows, off-road groups)
 };
 
 // Work counters of one thread (flushed into the CTA's AgentSmem::cnt).
@@ -39,7 +39,7 @@ struct SegView {
     const float4* geo;
     const float* inv;
     const uint8_t* flags;
-    const float4* tiles;  // 2 per tile: bounding box, two points on segments
+    const float4* tiles;  // 2 per tile: capsule (start, chord), (radius, 1/|chord|^2)
     const float4* sup;    // bounding box per super-tile of kSuper tiles
     int E, nt, ns;
 };
@@ -57,6 +57,9 @@ __device__ __forceinline__ int next_agent(AgentSmem& sm, int slot, int lane) {
     if (lane == 0) i = atomicAdd(&sm.work[slot], 1);
     return __shfl_sync(0xffffffffu, i, 0);
 }
+
+// sqrt within a few float32 ulps (bounds and margins only; not for results).
+__device__ __forceinline__ float sqrt_approx(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 
 template <class T> __device__ __forceinline__ T pick4(const T (&a)[4], int k) {
     return k == 0 ? a[0] : (k == 1 ? a[1] : (k == 2 ? a[2] : a[3]));
@@ -89,7 +92,7 @@ __device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, 
         sm.valid[i] = A.valid[g];
         sm.ovk[i] = fkey(-WSIM_INF);
     }
-    if (threadIdx.x == 0) sm.work[0] = sm.work[1] = 0;
+    if (threadIdx.x == 0) sm.work[0] = sm.work[1] = sm.work[2] = 0;
 }
 
 // Make the next state current; optionally store it to global memory.  Runs
@@ -301,7 +304,7 @@ static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N
 template <int NT>
 __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* act, int a0, int N, Counts& cnt) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) sm.work[1] = 0;  // the metrics phase starts after two barriers
+    if (threadIdx.x == 0) sm.work[1] = sm.work[2] = 0;  // the metrics phase starts after two barriers
     for (int i = next_agent(sm, 0, lane); i < N; i = next_agent(sm, 0, lane)) {
         if (A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i]) idm_agent(sm, A, a0, N, i, lane, cnt);
     }
@@ -376,6 +379,14 @@ static __device__ float overlap_row(AgentSmem& sm, int N, int i, int lane, Count
     return best;
 }
 
+// Squared distance of point p to the chord of capsule record C (1/|chord|^2 = inv).
+__device__ __forceinline__ float cap_d2(float4 C, float inv, float px, float py) {
+    const float wx = px - C.x, wy = py - C.y;
+    const float t = __saturatef(fmaf(wx, C.z, wy * C.w) * inv);
+    const float ex = fmaf(-t, C.z, wx), ey = fmaf(-t, C.w, wy);
+    return fmaf(ex, ex, ey * ey);
+}
+
 // Squared distance from corner (ch + cl) to segment G; raw projection in *traw.
 __device__ __forceinline__ float seg_dist2(float4 G, float iv, float cxh, float cxl, float cyh, float cyl,
                                            float* traw = nullptr) {
@@ -446,9 +457,40 @@ __device__ __forceinline__ void scan_next_two(const SegView& V, int lane, unsign
 // skipped; the rest are scanned with one segment per lane, so the result
 // equals the exhaustive scan.  hint (may be null) is read and updated.
 // ---------------------------------------------------------------------------
+// Signed distance of a corner (xh + cl, yh + dl) whose nearest segment is e
+// at squared distance d2: side of the nearest feature, with the vertex rule
+// where that feature is a vertex shared by two segments.
+__device__ __forceinline__ float corner_side(const SegView& V, int e, float d2, float xh, float cl, float yh,
+                                             float dl) {
+    const float4 G = V.geo[e];
+    const uint8_t fl = V.flags[e];
+    float traw;
+    seg_dist2(G, V.inv[e], xh, cl, yh, dl, &traw);
+    const float wx = (xh - G.x) + cl, wy = (yh - G.y) + dl;
+    bool on;
+    if (traw <= 0.f && (fl & 1)) {
+        const float4 Gp = V.geo[e - 1];
+        const bool l1 = fmaf(Gp.z, wy, -Gp.w * wx) > 0.f;
+        const bool l2 = fmaf(G.z, wy, -G.w * wx) > 0.f;
+        const float turn = fmaf(Gp.z, G.w, -Gp.w * G.z);
+        on = turn > 0.f ? (l1 && l2) : (turn < 0.f ? (l1 || l2) : l1);
+    } else if (traw >= 1.f && (fl & 2)) {
+        const float4 Gn = V.geo[e + 1];
+        const float qx = wx - G.z, qy = wy - G.w;
+        const bool l1 = fmaf(G.z, qy, -G.w * qx) > 0.f;
+        const bool l2 = fmaf(Gn.z, qy, -Gn.w * qx) > 0.f;
+        const float turn = fmaf(G.z, Gn.w, -G.w * Gn.z);
+        on = turn > 0.f ? (l1 && l2) : (turn < 0.f ? (l1 || l2) : l1);
+    } else {
+        on = fmaf(G.z, wy, -G.w * wx) > 0.f;
+    }
+    const float d = sqrtf(d2);
+    return on ? -d : d;
+}
+
 static __device__ float offroad_agent(const SegView& V, int lane, float xh, float xl, float yh, float yl, float c,
                                       float s, float hl, float hw, int32_t* hint, uint16_t* tl, float4* meta,
-                                      Counts& cnt) {
+                                      Counts& cnt, bool force_scan = false) {
     if (V.E == 0) {
         if (hint && lane < 4) hint[lane] = -1;
         return -WSIM_INF;
@@ -476,10 +518,11 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
         // Bounds from points on segments (two per tile).
         float m[4] = {WSIM_INF, WSIM_INF, WSIM_INF, WSIM_INF};
         for (int t = lane; t < V.nt; t += 32) {
-            const float4 P = V.tiles[2 * t + 1];
+            const float4 P = V.tiles[2 * t];  // both chord ends lie on segments
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const float ax = P.x - px[k], ay = P.y - py[k], bx = P.z - px[k], by = P.w - py[k];
+                const float ax = P.x - px[k], ay = P.y - py[k];
+                const float bx = (P.x + P.z) - px[k], by = (P.y + P.w) - py[k];
                 m[k] = fminf(m[k], fminf(fmaf(ax, ax, ay * ay), fmaf(bx, bx, by * by)));
             }
         }
@@ -494,20 +537,23 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
     float lim2[4], ucap = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const float u = sqrtf(u2[k]) + 2e-3f;
+        const float u = sqrt_approx(u2[k]) * 1.000001f + 2e-3f;
         lim2[k] = u * u;
         ucap = fmaxf(ucap, u);
     }
-    // Agent-level test: the centre's distance to a box minus the half
-    // diagonal bounds every corner's distance to it from below.
+    // Agent-level test: the centre's distance to a box or capsule minus the
+    // half diagonal bounds every corner's distance to it from below.
     const float ccx = xh + xl, ccy = yh + yl;
-    const float rad = sqrtf(fmaf(hl, hl, hw * hw)) + 1e-3f;
+    const float rad = sqrt_approx(fmaf(hl, hl, hw * hw)) * 1.000001f + 1e-3f;
     const float clim = (ucap + rad) * (ucap + rad);
+    float lim[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) lim[k] = sqrt_approx(lim2[k]) * 1.000001f;
 
     float bd[4] = {WSIM_INF, WSIM_INF, WSIM_INF, WSIM_INF};
     int bi[4] = {-1, -1, -1, -1};
     bool done = false;
-    if (tl) {
+    if (tl && !force_scan) {
         // Cached candidate tiles: every tile whose box lies within radius r0
         // of centre c0.  A segment outside them is farther than
         // r0 - |p - c0| from corner p, so a best distance below that bound
@@ -519,24 +565,25 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
             int t = 0;
             if (lane < n) {
                 t = tl[lane];
-                const float4 B = V.tiles[2 * t];
+                const float4 C = V.tiles[2 * t];
+                const float4 Q = V.tiles[2 * t + 1];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    const float dx = fmaxf(fmaxf(B.x - px[k], px[k] - B.z), 0.f);
-                    const float dy = fmaxf(fmaxf(B.y - py[k], py[k] - B.w), 0.f);
-                    if (fmaf(dx, dx, dy * dy) <= lim2[k]) cm |= 1u << k;
+                    const float l = lim[k] + Q.x;
+                    if (cap_d2(C, Q.y, px[k], py[k]) <= l * l) cm |= 1u << k;
                 }
             }
             if (lane == 0) cnt.tiles += n;
             unsigned want = __ballot_sync(kFull, cm != 0);
             while (want) scan_next_two(V, lane, want, t, cm, xh, yh, cxl, cyl, bd, bi, cnt);
-            // The check is on per-lane values; all lanes agree after the vote.
+            // best + |p - c0| <= r0 - 1 mm for every corner (approximate roots
+            // rounded up); the reduced minima agree in all lanes.
             bool ok = true;
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 const float b = __uint_as_float(__reduce_min_sync(kFull, __float_as_uint(bd[k])));
                 const float dx = px[k] - M.x, dy = py[k] - M.y;
-                ok = ok && sqrtf(b) + sqrtf(fmaf(dx, dx, dy * dy)) <= M.z - 1e-3f;
+                ok = ok && (sqrt_approx(b) + sqrt_approx(fmaf(dx, dx, dy * dy))) * 1.000001f <= M.z - 1e-3f;
             }
             done = ok;
             if (!done) {
@@ -551,10 +598,12 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
     if (!done) {
         // Full search over the super-tiles; on the way, collect the tiles
         // within R of the centre as the next candidate list.
-        const float R = ucap + rad + kSkin;
+        // Two list radii are collected in one scan; the wider is kept when it fits.
+        const float R = ucap + rad + kSkin, Rs = ucap + rad + kSkinSmall;
         const float R2 = (R + 1e-3f) * (R + 1e-3f);
         const float slim = fmaxf(clim, R2);
-        int nl = 0;
+        int nl = 0, nls = 0;
+        int small_t = -1;  // the narrow list, entry n kept by lane n
         for (int sb = 0; sb < V.ns; sb += 32) {
             bool pass = false;
             if (sb + lane < V.ns) {
@@ -570,20 +619,20 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
                 sup &= sup - 1;
                 // Lanes 0..kSuper-1 test the super-tile's tiles corner by corner.
                 unsigned cm = 0;
-                bool inl = false;
+                bool inl = false, inls = false;
                 const int t = t0 + lane;
                 if (lane < kSuper && t < V.nt) {
-                    const float4 B = V.tiles[2 * t];
-                    float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
-                    float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
-                    const float dc = fmaf(dx, dx, dy * dy);
-                    inl = dc <= R2;
-                    if (dc <= clim) {
+                    const float4 C = V.tiles[2 * t];
+                    const float4 Q = V.tiles[2 * t + 1];
+                    const float dc = cap_d2(C, Q.y, ccx, ccy);
+                    const float rl = R + Q.x + 1e-3f, rs = Rs + Q.x + 1e-3f, rc = ucap + rad + Q.x;
+                    inl = dc <= rl * rl;
+                    inls = dc <= rs * rs;
+                    if (dc <= rc * rc) {
 #pragma unroll
                         for (int k = 0; k < 4; ++k) {
-                            dx = fmaxf(fmaxf(B.x - px[k], px[k] - B.z), 0.f);
-                            dy = fmaxf(fmaxf(B.y - py[k], py[k] - B.w), 0.f);
-                            if (fmaf(dx, dx, dy * dy) <= lim2[k]) cm |= 1u << k;
+                            const float l = lim[k] + Q.x;
+                            if (cap_d2(C, Q.y, px[k], py[k]) <= l * l) cm |= 1u << k;
                         }
                     }
                 }
@@ -593,12 +642,30 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
                     const int pos = nl + __popc(lb & ((1u << lane) - 1u));
                     if (inl && pos < kList) tl[pos] = static_cast<uint16_t>(t);
                     nl += __popc(lb);
+                    // narrow list: entry n is kept by lane n
+                    unsigned sb2 = __ballot_sync(kFull, inls);
+                    while (sb2) {
+                        const int l = __ffs(sb2) - 1;
+                        sb2 &= sb2 - 1;
+                        if (lane == nls) small_t = t0 + l;
+                        ++nls;
+                    }
                 }
                 unsigned want = __ballot_sync(kFull, cm != 0);
                 while (want) scan_next_two(V, lane, want, t, cm, xh, yh, cxl, cyl, bd, bi, cnt);
             }
         }
-        if (tl && lane == 0) *meta = make_float4(ccx, ccy, R, __int_as_float(nl <= kList ? nl : -1));
+        if (tl) {
+            if (nl <= kList) {
+                if (lane == 0) *meta = make_float4(ccx, ccy, R, __int_as_float(nl));
+            } else if (nls <= kList) {
+                __syncwarp();
+                if (lane < nls) tl[lane] = static_cast<uint16_t>(small_t);
+                if (lane == 0) *meta = make_float4(ccx, ccy, Rs, __int_as_float(nls));
+            } else if (lane == 0) {
+                *meta = make_float4(ccx, ccy, R, __int_as_float(-1));
+            }
+        }
     }
     // Nearest segment per corner: the lexicographic (distance, index)
     // minimum over lanes (distances >= 0 order like their bit patterns).
@@ -614,33 +681,7 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
     float sd = -WSIM_INF;
     if (lane < 4) {
         const int e = pick4(bi, lane);
-        if (e >= 0) {
-            const float4 G = V.geo[e];
-            const uint8_t fl = V.flags[e];
-            float traw;
-            const float cl = pick4(cxl, lane), dl = pick4(cyl, lane);
-            seg_dist2(G, V.inv[e], xh, cl, yh, dl, &traw);
-            const float wx = (xh - G.x) + cl, wy = (yh - G.y) + dl;
-            bool on;
-            if (traw <= 0.f && (fl & 1)) {
-                const float4 Gp = V.geo[e - 1];
-                const bool l1 = fmaf(Gp.z, wy, -Gp.w * wx) > 0.f;
-                const bool l2 = fmaf(G.z, wy, -G.w * wx) > 0.f;
-                const float turn = fmaf(Gp.z, G.w, -Gp.w * G.z);
-                on = turn > 0.f ? (l1 && l2) : (turn < 0.f ? (l1 || l2) : l1);
-            } else if (traw >= 1.f && (fl & 2)) {
-                const float4 Gn = V.geo[e + 1];
-                const float qx = wx - G.z, qy = wy - G.w;
-                const bool l1 = fmaf(G.z, qy, -G.w * qx) > 0.f;
-                const bool l2 = fmaf(Gn.z, qy, -Gn.w * qx) > 0.f;
-                const float turn = fmaf(G.z, Gn.w, -G.w * Gn.z);
-                on = turn > 0.f ? (l1 && l2) : (turn < 0.f ? (l1 || l2) : l1);
-            } else {
-                on = fmaf(G.z, wy, -G.w * wx) > 0.f;
-            }
-            const float d = sqrtf(pick4(bd, lane));
-            sd = on ? -d : d;
-        }
+        if (e >= 0) sd = corner_side(V, e, pick4(bd, lane), xh, pick4(cxl, lane), yh, pick4(cyl, lane));
         if (hint) hint[lane] = e;
     }
     sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 1));
@@ -649,26 +690,120 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
 }
 
 // ---------------------------------------------------------------------------
-// Overlap rows and off-road of every agent, one warp per agent taken from a
-// shared counter.  sm.ov receives the row maxima; finish merges the columns.
+// Off-road of eight agents (warp; lane 4a+k = corner k of agent a).  Fast
+// path, lane by lane: the bound U from the corner's previous nearest
+// segment, the agent's cached candidate tiles whose capsule lies within U,
+// a scan of those tiles, and the cache condition best + |p - c0| <= r0 - 1 mm
+// (then the result is the exact nearest segment).  Agents whose cache or
+// hints fail any corner take the warp-cooperative search (offroad_agent),
+// which also rebuilds the cache.
+// ---------------------------------------------------------------------------
+static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
+                                     float4* meta_base, int N, int g0, int lane, Counts& cnt) {
+    const int a = g0 + (lane >> 2), k = lane & 3;
+    const bool act = a < N && sm.valid[a];
+    bool fast = false;
+    float best = WSIM_INF;
+    int bi = -1;
+    float xh = 0.f, yh = 0.f, cl = 0.f, dl = 0.f, px = 0.f, py = 0.f;
+    float4 M = make_float4(0.f, 0.f, 0.f, 0.f);
+    unsigned mask = 0;
+    const uint16_t* L = nullptr;
+    if (act && V.E > 0 && hint_base && tl_base) {
+        const float hl = (k < 2 ? 1.f : -1.f) * sm.hl[a], hw = (k == 0 || k == 3 ? 1.f : -1.f) * sm.hw[a];
+        const float c = sm.c[a], s = sm.s[a];
+        xh = sm.xh[a];
+        yh = sm.yh[a];
+        cl = sm.xl[a] + fmaf(hl, c, -hw * s);
+        dl = sm.yl[a] + fmaf(hl, s, hw * c);
+        px = xh + cl;
+        py = yh + dl;
+        M = meta_base[a];
+        const int n = __float_as_int(M.w);
+        const int eh = hint_base[4 * a + k];
+        if (n >= 0 && eh >= 0 && eh < V.E) {
+            fast = true;
+            const float U = sqrt_approx(seg_dist2(V.geo[eh], V.inv[eh], xh, cl, yh, dl)) * 1.000001f + 2e-3f;
+            L = tl_base + kList * a;
+            for (int j = 0; j < n; ++j) {
+                const int t = L[j];
+                const float4 C = V.tiles[2 * t];
+                const float4 Q = V.tiles[2 * t + 1];
+                const float l = U + Q.x;
+                if (cap_d2(C, Q.y, px, py) <= l * l) mask |= 1u << j;
+            }
+            cnt.tiles += n;
+        }
+    }
+    // Scan each lane's passing tiles (lanes with fewer tiles idle).
+    while (__any_sync(kFull, mask != 0)) {
+        if (mask) {
+            const int j = __ffs(mask) - 1;
+            mask &= mask - 1;
+            const int e0 = static_cast<int>(L[j]) * kTile;
+            cnt.evals += kTile;
+#pragma unroll 4
+            for (int q = 0; q < kTile; ++q) {
+                const int e = e0 + q;
+                if (e < V.E) {
+                    const float d2 = seg_dist2(V.geo[e], V.inv[e], xh, cl, yh, dl);
+                    if (d2 < best) {
+                        best = d2;
+                        bi = e;
+                    }
+                }
+            }
+        }
+    }
+    bool ok = fast;
+    if (fast) {
+        const float dx = px - M.x, dy = py - M.y;
+        ok = (sqrt_approx(best) + sqrt_approx(fmaf(dx, dx, dy * dy))) * 1.000001f <= M.z - 1e-3f;
+    }
+    // all four corners of the agent must pass
+    unsigned okv = __ballot_sync(kFull, ok);
+    const unsigned quad = 0xfu << (lane & ~3);
+    ok = (okv & quad) == quad;
+    float sd = -WSIM_INF;
+    if (ok) {
+        sd = corner_side(V, bi, best, xh, cl, yh, dl);
+        hint_base[4 * a + k] = bi;
+    }
+    sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 1));
+    sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 2));
+    if (ok && k == 0) sm.off[a] = sd;
+    // The others: warp-cooperative search (no usable cache or hint).
+    unsigned need = __ballot_sync(kFull, act && !ok && k == 0);
+    while (need) {
+        const int ai = g0 + ((__ffs(need) - 1) >> 2);
+        need &= need - 1;
+        const float f = offroad_agent(V, lane, sm.xh[ai], sm.xl[ai], sm.yh[ai], sm.yl[ai], sm.c[ai], sm.s[ai],
+                                      sm.hl[ai], sm.hw[ai], hint_base ? hint_base + 4 * ai : nullptr,
+                                      tl_base ? tl_base + kList * ai : nullptr, tl_base ? meta_base + ai : nullptr,
+                                      cnt, true);
+        if (lane == 0) sm.off[ai] = f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Overlap rows (one warp per agent) and off-road (one warp per eight
+// agents), both taken from shared counters.  sm.ov receives the row maxima;
+// finish merges the columns.
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
                               float4* meta_base, int N, bool do_ov, bool do_off, Counts& cnt) {
     const int lane = threadIdx.x & 31;
-    for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane)) {
-        if (!sm.valid[i]) continue;
-        if (do_ov) {
+    if (do_ov) {
+        for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane)) {
+            if (!sm.valid[i]) continue;
             const float o = overlap_row(sm, N, i, lane, cnt);
             if (lane == 0) sm.ov[i] = o;
         }
-        if (do_off) {
-            const float f = offroad_agent(V, lane, sm.xh[i], sm.xl[i], sm.yh[i], sm.yl[i], sm.c[i], sm.s[i], sm.hl[i],
-                                          sm.hw[i], hint_base ? hint_base + 4 * i : nullptr,
-                                          tl_base ? tl_base + kList * i : nullptr, tl_base ? meta_base + i : nullptr,
-                                          cnt);
-            if (lane == 0) sm.off[i] = f;
-        }
+    }
+    if (do_off) {
+        for (int g = next_agent(sm, 2, lane); 8 * g < N; g = next_agent(sm, 2, lane))
+            offroad_group(sm, V, hint_base, tl_base, meta_base, N, 8 * g, lane, cnt);
     }
 }
 
