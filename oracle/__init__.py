@@ -38,7 +38,9 @@ class ObParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("idm_amax", C.c_double), ("idm_b", C.c_double),
                 ("idm_T", C.c_double), ("idm_s0", C.c_double), ("idm_dq", C.c_double),
                 ("route_h", C.c_double), ("gap_min", C.c_double), ("band", C.c_double),
-                ("idm_K", C.c_int32), ("pad_", C.c_int32)]
+                ("idm_K", C.c_int32), ("pad_", C.c_int32),
+                ("kin_amax", C.c_double), ("kin_kmax", C.c_double), ("kin_band_a", C.c_double),
+                ("kin_band_th", C.c_double)]
 
 
 class ObBatch(C.Structure):
@@ -48,7 +50,7 @@ class ObBatch(C.Structure):
                 ("valid", _u8p), ("kind", _u8p),
                 ("route_off", _i32p), ("route_x", _dp), ("route_y", _dp),
                 ("rg_x", _dp), ("rg_y", _dp), ("rg_poly", _i32p), ("rg_type", _u8p), ("rg_valid", _u8p),
-                ("log_x", _dp), ("log_y", _dp)]
+                ("log_x", _dp), ("log_y", _dp), ("log_th", _dp), ("log_vx", _dp), ("log_vy", _dp)]
 
 
 class ObState(C.Structure):
@@ -68,11 +70,14 @@ def lib():
         _lib = C.CDLL(build())
         P = C.POINTER
         _lib.oracle_transition.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp,
-                                           _u8p, P(ObState), _u8p, _i32p]
-        _lib.oracle_metrics.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), C.c_int,
-                                        P(ObMetrics)]
-        _lib.oracle_rollout.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp,
+                                           _u8p, C.c_int, P(ObState), _u8p, _i32p]
+        _lib.oracle_metrics.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), P(ObState),
+                                        C.c_int, P(ObMetrics)]
+        _lib.oracle_rollout.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp, _u8p,
                                         C.c_int, C.c_int, P(ObMetrics), C.c_int]
+        _lib.oracle_inverse.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), P(ObState), _dp]
+        _lib.oracle_expert_actions.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, C.c_int, C.c_int,
+                                               _dp]
         _lib.oracle_box_depth.argtypes = [_dp, _dp]
         _lib.oracle_box_depth.restype = C.c_double
         _lib.oracle_point_sd.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_double, C.c_double,
@@ -99,10 +104,15 @@ class Params:
     gap_min: float = 0.1
     band: float = 1e-4
     idm_K: int = 32
+    kin_amax: float = 6.0
+    kin_kmax: float = 0.3
+    kin_band_a: float = 1e-3
+    kin_band_th: float = 1e-5
 
     def c(self) -> ObParams:
         return ObParams(self.dt, self.idm_amax, self.idm_b, self.idm_T, self.idm_s0, self.idm_dq,
-                        self.route_h, self.gap_min, self.band, self.idm_K, 0)
+                        self.route_h, self.gap_min, self.band, self.idm_K, 0, self.kin_amax, self.kin_kmax,
+                        self.kin_band_a, self.kin_band_th)
 
 
 def _ptr(a: np.ndarray, t):
@@ -114,6 +124,7 @@ def _f64(a) -> np.ndarray:
 
 
 STATE_KEYS = ("x", "y", "th", "vx", "vy", "s")
+CTRL_HOLD, CTRL_ACTION, CTRL_EXPERT, CTRL_LOG = 0, 1, 2, 3
 
 
 class Oracle:
@@ -144,6 +155,8 @@ class Oracle:
             _ptr(k("gt", np.ascontiguousarray(batch.rg_type, np.uint8)), _u8p),
             _ptr(k("gv", np.ascontiguousarray(batch.rg_valid, np.uint8)), _u8p),
             _ptr(k("lx", _f64(batch.log_x)), _dp), _ptr(k("ly", _f64(batch.log_y)), _dp),
+            _ptr(k("lth", _f64(batch.log_th)), _dp), _ptr(k("lvx", _f64(batch.log_vx)), _dp),
+            _ptr(k("lvy", _f64(batch.log_vy)), _dp),
         )
         self._keep = keep
 
@@ -164,24 +177,31 @@ class Oracle:
         return (0, self.b.S) if scenes is None else scenes
 
     # -- calls ---------------------------------------------------------------
-    def transition(self, st: dict, act: np.ndarray, ctrl=None, scenes=None):
-        """State t -> t+1; act is [3][N_tot].  Returns (state, band_idm, lead)."""
+    def transition(self, st: dict, act: Optional[np.ndarray], ctrl=None, scenes=None, t_next: int = -1):
+        """State t -> t+1 = t_next; act is [3][N_tot] (None: no agent takes
+        CTRL_ACTION).  Returns (state, band_idm, lead)."""
         N = self.b.N_tot
         s0, s1 = self._scenes(scenes)
         st = {k: _f64(st[k]) for k in STATE_KEYS}
         out = {k: st[k].copy() for k in STATE_KEYS}
-        act = _f64(act).reshape(3, N)
+        act_p = None
+        if act is not None:
+            act = _f64(act).reshape(3, N)
+            act_p = _ptr(act, _dp)
         band = np.zeros(N, np.uint8)
         lead = np.full(N, -1, np.int32)
-        ctrl_p = None if ctrl is None else _ptr(np.ascontiguousarray(ctrl, np.uint8), _u8p)
+        ctrl_a = None if ctrl is None else np.ascontiguousarray(ctrl, np.uint8)
+        ctrl_p = None if ctrl_a is None else _ptr(ctrl_a, _u8p)
         rc = lib().oracle_transition(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(st)),
-                                     _ptr(act, _dp), ctrl_p, C.byref(self._cstate(out)),
+                                     act_p, ctrl_p, t_next, C.byref(self._cstate(out)),
                                      _ptr(band, _u8p), _ptr(lead, _i32p))
         if rc:
             raise RuntimeError("oracle_transition failed")
         return out, band, lead
 
-    def metrics(self, st: dict, t: int, scenes=None) -> dict:
+    def metrics(self, st: dict, t: int, scenes=None, prev: Optional[dict] = None) -> dict:
+        """Metrics of state st against log row t; with prev (the state
+        before) also the kinematic-infeasibility bits."""
         N, S = self.b.N_tot, self.b.S
         s0, s1 = self._scenes(scenes)
         st = {k: _f64(st[k]) for k in STATE_KEYS}
@@ -189,27 +209,60 @@ class Oracle:
                  reward=np.zeros(S, np.int32))
         cm = ObMetrics(_ptr(m["ov"], _dp), _ptr(m["off"], _dp), _ptr(m["logdiv"], _dp),
                        _ptr(m["flags"], _u8p), _ptr(m["reward"], _i32p))
+        pv = None
+        if prev is not None:
+            prev = {k: _f64(prev[k]) for k in STATE_KEYS}
+            pv = C.byref(self._cstate(prev))
         rc = lib().oracle_metrics(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(st)),
-                                  t, C.byref(cm))
+                                  pv, t, C.byref(cm))
         if rc:
             raise RuntimeError("oracle_metrics failed")
         return m
 
-    def rollout(self, st: dict, act_seq: np.ndarray, t0: int, T: int, scenes=None, nthreads: int = 0):
+    def rollout(self, st: dict, act_seq: Optional[np.ndarray], t0: int, T: int, scenes=None, nthreads: int = 0,
+                ctrl=None):
         """Free-running FP64 rollout; returns (final state, metrics [T][...])."""
         N, S = self.b.N_tot, self.b.S
         s0, s1 = self._scenes(scenes)
         st = {k: _f64(st[k]).copy() for k in STATE_KEYS}
-        act = _f64(act_seq).reshape(-1, 3, N)
+        act_p = None
+        if act_seq is not None:
+            act = _f64(act_seq).reshape(-1, 3, N)
+            act_p = _ptr(act, _dp)
+        ctrl_a = None if ctrl is None else np.ascontiguousarray(ctrl, np.uint8)
+        ctrl_p = None if ctrl_a is None else _ptr(ctrl_a, _u8p)
         m = dict(ov=np.zeros((T, N)), off=np.zeros((T, N)), logdiv=np.zeros((T, N)),
                  flags=np.zeros((T, N), np.uint8), reward=np.zeros((T, S), np.int32))
         cm = ObMetrics(_ptr(m["ov"], _dp), _ptr(m["off"], _dp), _ptr(m["logdiv"], _dp),
                        _ptr(m["flags"], _u8p), _ptr(m["reward"], _i32p))
         rc = lib().oracle_rollout(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(st)),
-                                  _ptr(act, _dp), t0, T, C.byref(cm), nthreads)
+                                  act_p, ctrl_p, t0, T, C.byref(cm), nthreads)
         if rc:
             raise RuntimeError("oracle_rollout failed")
         return st, m
+
+    def inverse(self, prev: dict, nxt: dict, scenes=None) -> np.ndarray:
+        """The action [3][N_tot] taking prev to nxt in each agent's action space."""
+        N = self.b.N_tot
+        s0, s1 = self._scenes(scenes)
+        a = {k: _f64(prev[k]) for k in STATE_KEYS}
+        c = {k: _f64(nxt[k]) for k in STATE_KEYS}
+        out = np.zeros((3, N))
+        rc = lib().oracle_inverse(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(a)),
+                                  C.byref(self._cstate(c)), _ptr(out, _dp))
+        if rc:
+            raise RuntimeError("oracle_inverse failed")
+        return out
+
+    def expert_actions(self, t0: int, T: int, scenes=None) -> np.ndarray:
+        """Open-loop expert actions [T][3][N_tot] fitted to the log."""
+        N = self.b.N_tot
+        s0, s1 = self._scenes(scenes)
+        out = np.zeros((T, 3, N))
+        rc = lib().oracle_expert_actions(C.byref(self._cp), C.byref(self._batch), s0, s1, t0, T, _ptr(out, _dp))
+        if rc:
+            raise RuntimeError("oracle_expert_actions failed")
+        return out
 
     def point_sd(self, scene: int, px: float, py: float) -> Tuple[float, int, int]:
         amb = C.c_int(0)

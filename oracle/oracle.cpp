@@ -19,6 +19,7 @@
 namespace {
 
 const double kInf = std::numeric_limits<double>::infinity();
+const double kTwoPi = 2.0 * std::acos(-1.0);
 
 // ---------------------------------------------------------------------------
 // Forward-mode dual numbers (value, one tangent) for the loss gradient.
@@ -91,6 +92,65 @@ St<T> delta_forward(const St<T>& s, T dx, T dy, T dth, double dt) {
     o.vx = (o.x - s.x) / dt;
     o.vy = (o.y - s.y) / dt;
     return o;
+}
+
+// App. A.1, inverse kinematics of the bicycle action space, from two
+// consecutive states: the acceleration is the change of speed over one step;
+// the curvature is the turn of the direction of travel divided by the
+// distance travelled, v dt + a dt^2 / 2.  Readings: the direction of the new
+// state is the heading of its velocity, atan2(vy', vx') (the paper prints
+// arctan(vx'/vy'), which swaps the components and loses the quadrant); the
+// turn away from the old heading is reduced modulo 2 pi into [-pi, pi]; a
+// state with zero velocity has no direction, so the turn is 0; with no
+// distance travelled the curvature is 0.
+struct BicycleInverse { double a, kappa, turn, dist; };
+
+BicycleInverse bicycle_inverse(const St<double>& s, const St<double>& n, double dt) {
+    BicycleInverse r;
+    const double v = std::sqrt(s.vx * s.vx + s.vy * s.vy);
+    const double vn = std::sqrt(n.vx * n.vx + n.vy * n.vy);
+    r.a = (vn - v) / dt;
+    const bool has_dir = n.vx != 0.0 || n.vy != 0.0;
+    r.turn = has_dir ? std::remainder(std::atan2(n.vy, n.vx) - s.th, kTwoPi) : 0.0;
+    r.dist = v * dt + 0.5 * r.a * dt * dt;
+    r.kappa = r.dist > 0 ? r.turn / r.dist : 0.0;
+    return r;
+}
+
+// Sec. 3.4, kinematic infeasibility of the transition s -> n: the inverse
+// kinematics estimate breaks |a| <= kin_amax or |kappa| <= kin_kmax.  *band
+// is set when either comparison lies inside its band: |a| against the limit,
+// or the turn against kin_kmax times the distance (the curvature test with
+// the distance multiplied out, which stays defined for short steps).
+void kin_check(const ob_params* p, const St<double>& s, const St<double>& n, bool* flag, bool* band) {
+    const BicycleInverse r = bicycle_inverse(s, n, p->dt);
+    *flag = std::fabs(r.a) > p->kin_amax || std::fabs(r.kappa) > p->kin_kmax;
+    *band = std::fabs(std::fabs(r.a) - p->kin_amax) <= p->kin_band_a ||
+            std::fabs(std::fabs(r.turn) - p->kin_kmax * r.dist) <= p->kin_band_th;
+}
+
+bool has_full_log(const ob_batch* b) { return b->log_th && b->log_vx && b->log_vy; }
+
+St<double> log_state(const ob_batch* b, int t, int g) {
+    const size_t i = (size_t)t * b->N_tot + g;
+    return {b->log_x[i], b->log_y[i], b->log_th[i], b->log_vx[i], b->log_vy[i]};
+}
+
+St<double> get_state(const ob_state* st, int g) { return {st->x[g], st->y[g], st->th[g], st->vx[g], st->vy[g]}; }
+
+// The action of agent g's action space that takes state s to state n (App.
+// A.1 inverses): bicycle (a, kappa, 0), delta (x'-x, y'-y, theta'-theta).
+void inverse_action(const ob_params* p, int kind, const St<double>& s, const St<double>& n, double out[3]) {
+    out[0] = out[1] = out[2] = 0.0;
+    if (kind == 0) {
+        const BicycleInverse r = bicycle_inverse(s, n, p->dt);
+        out[0] = r.a;
+        out[1] = r.kappa;
+    } else if (kind == 1) {
+        out[0] = n.x - s.x;
+        out[1] = n.y - s.y;
+        out[2] = n.th - s.th;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -364,24 +424,40 @@ void copy_agent(const ob_state* in, ob_state* out, int g) {
     out->vx[g] = in->vx[g]; out->vy[g] = in->vy[g]; out->s[g] = in->s[g];
 }
 
+void put_state(ob_state* out, int g, const St<double>& n) {
+    out->x[g] = n.x; out->y[g] = n.y; out->th[g] = n.th; out->vx[g] = n.vx; out->vy[g] = n.vy;
+}
+
 int transition_scene(const ob_params* p, const ob_batch* b, int s, const ob_state* in,
-                     const double* act, const uint8_t* ctrl, ob_state* out,
+                     const double* act, const uint8_t* ctrl, int t_next, ob_state* out,
                      uint8_t* band_idm, int32_t* lead_out) {
     const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1], N = b->N_tot;
     for (int g = a0; g < a1; ++g) {
         if (band_idm) band_idm[g] = 0;
         if (lead_out) lead_out[g] = -1;
         const int kind = b->kind[g];
-        bool moves = b->valid[g] && (kind == 2 || !ctrl || ctrl[g]);
-        if (!moves) { copy_agent(in, out, g); continue; }
-        St<double> cur = {in->x[g], in->y[g], in->th[g], in->vx[g], in->vy[g]};
-        if (kind == 0) {
-            St<double> n = bicycle_forward(cur, act[g], act[N + g], p->dt);
-            out->x[g] = n.x; out->y[g] = n.y; out->th[g] = n.th; out->vx[g] = n.vx; out->vy[g] = n.vy;
+        const int cm = ctrl ? ctrl[g] : OB_CTRL_ACTION;
+        if (cm > OB_CTRL_LOG) return -1;
+        if (!b->valid[g] || (kind != 2 && cm == OB_CTRL_HOLD)) { copy_agent(in, out, g); continue; }
+        const bool needs_log = cm == OB_CTRL_LOG || (cm == OB_CTRL_EXPERT && kind != 2);
+        if (needs_log && (!has_full_log(b) || t_next < 0 || t_next >= b->T_log)) return -1;
+        if (cm == OB_CTRL_LOG) {  // log playback (Sec. 3.5): the logged state of t+1
+            put_state(out, g, log_state(b, t_next, g));
             out->s[g] = in->s[g];
-        } else if (kind == 1) {
-            St<double> n = delta_forward(cur, act[g], act[N + g], act[2 * N + g], p->dt);
-            out->x[g] = n.x; out->y[g] = n.y; out->th[g] = n.th; out->vx[g] = n.vx; out->vy[g] = n.vy;
+            continue;
+        }
+        if (kind != 2 && cm == OB_CTRL_ACTION && !act) return -1;
+        St<double> cur = get_state(in, g);
+        if (kind == 0 || kind == 1) {
+            double u[3];
+            if (cm == OB_CTRL_EXPERT) {  // Sec. 5.2 expert: the action fitted to the log
+                inverse_action(p, kind, cur, log_state(b, t_next, g), u);
+            } else {
+                u[0] = act[g]; u[1] = act[N + g]; u[2] = act[2 * N + g];
+            }
+            St<double> n = kind == 0 ? bicycle_forward(cur, u[0], u[1], p->dt)
+                                     : delta_forward(cur, u[0], u[1], u[2], p->dt);
+            put_state(out, g, n);
             out->s[g] = in->s[g];
         } else if (kind == 2) {
             if (b->route_off[g + 1] - b->route_off[g] < 2) return -1;
@@ -397,9 +473,10 @@ int transition_scene(const ob_params* p, const ob_batch* b, int s, const ob_stat
     return 0;
 }
 
-// Metrics of one scene (Sec. 3.4) on state st, log row t.
-void metrics_scene(const ob_params* p, const ob_batch* b, int s, const ob_state* st, int t,
-                   double* ov, double* off, double* logdiv, uint8_t* flags, int32_t* reward) {
+// Metrics of one scene (Sec. 3.4) on state st, log row t; prev (may be NULL)
+// is the state before, for kinematic infeasibility.
+void metrics_scene(const ob_params* p, const ob_batch* b, int s, const ob_state* st, const ob_state* prev,
+                   int t, double* ov, double* off, double* logdiv, uint8_t* flags, int32_t* reward) {
     const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1], N = b->N_tot;
     const double eps = p->band;
     std::vector<Box<double>> box(a1 - a0);
@@ -438,6 +515,12 @@ void metrics_scene(const ob_params* p, const ob_batch* b, int s, const ob_state*
         if (f > 0) fl |= 2;
         if (std::fabs(o) < eps) fl |= 4;
         if (std::fabs(f) < eps || amb_any) fl |= 8;
+        if (prev) {
+            bool kf = false, kb = false;
+            kin_check(p, get_state(prev, g), get_state(st, g), &kf, &kb);
+            if (kf) fl |= 16;
+            if (kb) fl |= 32;
+        }
         flags[g] = fl;
         r -= (o > 0) + (f > 0);
     }
@@ -515,25 +598,53 @@ bool scene_differentiable(const ob_batch* b, int s) {
 extern "C" {
 
 int oracle_transition(const ob_params* p, const ob_batch* b, int s0, int s1,
-                      const ob_state* in, const double* act, const uint8_t* ctrl,
+                      const ob_state* in, const double* act, const uint8_t* ctrl, int t_next,
                       ob_state* out, uint8_t* band_idm, int32_t* lead) {
     if (!p || !b || !in || !out || s0 < 0 || s1 > b->S || s0 > s1) return -1;
     for (int s = s0; s < s1; ++s)
-        if (transition_scene(p, b, s, in, act, ctrl, out, band_idm, lead)) return -1;
+        if (transition_scene(p, b, s, in, act, ctrl, t_next, out, band_idm, lead)) return -1;
     return 0;
 }
 
 int oracle_metrics(const ob_params* p, const ob_batch* b, int s0, int s1,
-                   const ob_state* st, int t, ob_metrics* m) {
+                   const ob_state* st, const ob_state* prev, int t, ob_metrics* m) {
     if (!p || !b || !st || !m || s0 < 0 || s1 > b->S || s0 > s1 || t < 0 || t >= b->T_log) return -1;
     for (int s = s0; s < s1; ++s)
-        metrics_scene(p, b, s, st, t, m->ov, m->off, m->logdiv, m->flags, m->reward);
+        metrics_scene(p, b, s, st, prev, t, m->ov, m->off, m->logdiv, m->flags, m->reward);
+    return 0;
+}
+
+int oracle_inverse(const ob_params* p, const ob_batch* b, int s0, int s1,
+                   const ob_state* prev, const ob_state* next, double* act) {
+    if (!p || !b || !prev || !next || !act || s0 < 0 || s1 > b->S || s0 > s1) return -1;
+    const int N = b->N_tot;
+    for (int g = b->agent_off[s0]; g < b->agent_off[s1]; ++g) {
+        double u[3] = {0.0, 0.0, 0.0};
+        if (b->valid[g]) inverse_action(p, b->kind[g], get_state(prev, g), get_state(next, g), u);
+        for (int c = 0; c < 3; ++c) act[(size_t)c * N + g] = u[c];
+    }
+    return 0;
+}
+
+int oracle_expert_actions(const ob_params* p, const ob_batch* b, int s0, int s1, int t0, int T,
+                          double* act_seq) {
+    if (!p || !b || !act_seq || !has_full_log(b) || s0 < 0 || s1 > b->S || s0 > s1) return -1;
+    if (t0 < 0 || T < 0 || t0 + T > b->T_log - 1) return -1;
+    const int N = b->N_tot;
+    for (int k = 0; k < T; ++k)
+        for (int g = b->agent_off[s0]; g < b->agent_off[s1]; ++g) {
+            double u[3] = {0.0, 0.0, 0.0};
+            if (b->valid[g]) inverse_action(p, b->kind[g], log_state(b, t0 + k, g), log_state(b, t0 + k + 1, g), u);
+            for (int c = 0; c < 3; ++c) act_seq[((size_t)k * 3 + c) * N + g] = u[c];
+        }
     return 0;
 }
 
 int oracle_rollout(const ob_params* p, const ob_batch* b, int s0, int s1, ob_state* st,
-                   const double* act_seq, int t0, int T, ob_metrics* mseq, int nthreads) {
-    if (!p || !b || !st || !act_seq || !mseq || s0 < 0 || s1 > b->S || s0 > s1) return -1;
+                   const double* act_seq, const uint8_t* ctrl, int t0, int T, ob_metrics* mseq,
+                   int nthreads) {
+    if (!p || !b || !st || !mseq || s0 < 0 || s1 > b->S || s0 > s1) return -1;
+    if (!act_seq && !ctrl) return -1;
     if (t0 < 0 || t0 + T > b->T_log - 1) return -1;
     const int N = b->N_tot, S = b->S;
     int status = 0;
@@ -548,17 +659,18 @@ int oracle_rollout(const ob_params* p, const ob_batch* b, int s0, int s1, ob_sta
         ob_state nxt = {buf.data(), buf.data() + N, buf.data() + 2 * N, buf.data() + 3 * N,
                         buf.data() + 4 * N, buf.data() + 5 * N};
         for (int k = 0; k < T; ++k) {
-            if (transition_scene(p, b, s, st, act_seq + (size_t)k * 3 * N, nullptr, &nxt, nullptr, nullptr)) {
+            const double* act = act_seq ? act_seq + (size_t)k * 3 * N : nullptr;
+            if (transition_scene(p, b, s, st, act, ctrl, t0 + k + 1, &nxt, nullptr, nullptr)) {
 #ifdef _OPENMP
 #pragma omp atomic write
 #endif
                 status = -1;
                 break;
             }
-            for (int g = a0; g < a1; ++g) copy_agent(&nxt, st, g);
             size_t o = (size_t)k * N;
-            metrics_scene(p, b, s, st, t0 + k + 1, mseq->ov + o, mseq->off + o, mseq->logdiv + o,
+            metrics_scene(p, b, s, &nxt, st, t0 + k + 1, mseq->ov + o, mseq->off + o, mseq->logdiv + o,
                           mseq->flags + o, mseq->reward + (size_t)k * S);
+            for (int g = a0; g < a1; ++g) copy_agent(&nxt, st, g);
         }
     }
     return status;

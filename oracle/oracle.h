@@ -40,6 +40,10 @@ typedef struct {
     double band;        /* ambiguity band for discrete decisions (m)            */
     int32_t idm_K;      /* number of lead-search samples                        */
     int32_t pad_;
+    double kin_amax;    /* kinematic infeasibility: |a| limit, 6 m/s^2 (Sec. 3.4) */
+    double kin_kmax;    /* ... |kappa| limit, 0.3 1/m (Sec. 3.4)                 */
+    double kin_band_a;  /* band around the |a| limit (m/s^2)                     */
+    double kin_band_th; /* band around the turn limit kin_kmax * distance (rad)  */
 } ob_params;
 
 /* A batch of scenes in CSR form.  Scene s owns agents [agent_off[s],
@@ -58,6 +62,8 @@ typedef struct {
     const int32_t *rg_poly;            /* [R_tot] polyline id */
     const uint8_t *rg_type, *rg_valid; /* [R_tot] type 1 = road edge */
     const double  *log_x, *log_y;      /* [T_log][N_tot] */
+    const double  *log_th, *log_vx, *log_vy; /* [T_log][N_tot]; may be NULL (no expert
+                                                or log playback then) */
 } ob_batch;
 
 /* Dynamic state per agent, [N_tot] each.  s is the IDM route cursor. */
@@ -65,37 +71,60 @@ typedef struct { double *x, *y, *th, *vx, *vy, *s; } ob_state;
 
 /* Per-step metrics, [N_tot] each (reward [S]).
  * flags: bit0 collision, bit1 off-road, bit2 overlap band, bit3 off-road
- * band (boolean not gated in parity), bits 4.. reserved. */
+ * band, bit4 kinematically infeasible transition, bit5 kinematic band (a
+ * band bit means the boolean is not gated in parity), bits 6.. reserved. */
 typedef struct {
     double  *ov, *off, *logdiv;
     uint8_t *flags;
     int32_t *reward;
 } ob_metrics;
 
+/* Who drives an agent (ctrl[g]).  NULL ctrl means OB_CTRL_ACTION for all. */
+#define OB_CTRL_HOLD 0    /* keep the state                                       */
+#define OB_CTRL_ACTION 1  /* policy agent: the given action                        */
+#define OB_CTRL_EXPERT 2  /* policy agent: the expert action fitted to log row t+1 */
+#define OB_CTRL_LOG 3     /* any agent: log playback (state := log row t+1)         */
+
 /* One transition t -> t+1 for scenes [s0, s1) (Sec. 4 step(): all actions are
- * resolved from state t, then every agent moves).  act is [3][N_tot]:
+ * resolved from state t, then every agent moves) into log time index t+1 =
+ * t_next (used by the expert and log playback only).  act is [3][N_tot]:
  * (a, kappa, -) for bicycle agents, (dx, dy, dtheta) for delta agents;
- * IDM agents ignore it.  ctrl may be NULL (all controlled); an uncontrolled
- * or invalid agent keeps its state.  band_idm[g] (may be NULL) is set to 1
+ * IDM agents ignore it and follow their route unless ctrl = OB_CTRL_LOG.
+ * Invalid agents keep their state.  band_idm[g] (may be NULL) is set to 1
  * when an IDM decision of agent g lies inside the ambiguity band; lead[g]
  * (may be NULL) receives the chosen lead agent (global index) or -1. */
 int oracle_transition(const ob_params *p, const ob_batch *b, int s0, int s1,
-                      const ob_state *in, const double *act, const uint8_t *ctrl,
+                      const ob_state *in, const double *act, const uint8_t *ctrl, int t_next,
                       ob_state *out, uint8_t *band_idm, int32_t *lead);
 
 /* Metrics of state st at time index t (log row t) for scenes [s0, s1):
  * overlap (Sec. 3.4 collision), off-road (Sec. 3.4), log divergence
- * (Sec. 3.4 displacement error) and the sparse reward (Sec. 5.2). */
+ * (Sec. 3.4 displacement error), the sparse reward (Sec. 5.2) and, when prev
+ * (the state at t-1) is given, kinematic infeasibility of the transition
+ * prev -> st (Sec. 3.4). */
 int oracle_metrics(const ob_params *p, const ob_batch *b, int s0, int s1,
-                   const ob_state *st, int t, ob_metrics *m);
+                   const ob_state *st, const ob_state *prev, int t, ob_metrics *m);
 
 /* Free-running rollout of T steps from time index t0 for scenes [s0, s1):
  * st holds state t0 on entry and state t0+T on exit; act_seq is
- * [T][3][N_tot]; metric arrays are [T][N_tot] (reward [T][S]).  Scenes are
- * split over nthreads OpenMP threads (<= 0: all cores). */
+ * [T][3][N_tot] (may be NULL when no agent takes OB_CTRL_ACTION); ctrl as in
+ * oracle_transition (may be NULL); metric arrays are [T][N_tot] (reward
+ * [T][S]).  Scenes are split over nthreads OpenMP threads (<= 0: all cores). */
 int oracle_rollout(const ob_params *p, const ob_batch *b, int s0, int s1,
-                   ob_state *st, const double *act_seq, int t0, int T,
+                   ob_state *st, const double *act_seq, const uint8_t *ctrl, int t0, int T,
                    ob_metrics *mseq, int nthreads);
+
+/* Inverse of the action spaces (App. A.1) for every agent of scenes [s0, s1):
+ * the action that takes state prev to state next, written to act [3][N_tot]:
+ * bicycle agents (a, kappa, 0) by the inverse kinematics, delta agents
+ * (x'-x, y'-y, theta'-theta); IDM and invalid agents 0. */
+int oracle_inverse(const ob_params *p, const ob_batch *b, int s0, int s1,
+                   const ob_state *prev, const ob_state *next, double *act);
+
+/* Expert actions (Sec. 5.2, open loop): act_seq[k] = the inverse of log row
+ * t0+k -> log row t0+k+1 for k < T, [T][3][N_tot], as oracle_inverse. */
+int oracle_expert_actions(const ob_params *p, const ob_batch *b, int s0, int s1,
+                          int t0, int T, double *act_seq);
 
 /* Signed SAT depth of two boxes (centre, heading, length, width):
  * > 0 iff the boxes overlap (then it is the minimum translation distance). */

@@ -133,19 +133,26 @@ def _log_controls(rng, n):
 
 
 def _integrate_logs(ctl, x0, y0, th0, v0, T_log=T_LOG, t0=T0, sub=10):
-    """Logged x, y from a continuous unicycle with smooth seeded controls.
+    """Logged x, y, heading, vx, vy from a continuous unicycle with smooth
+    seeded controls.
 
     speed' = A sin(2 pi f t + phi) (speed kept >= 0), heading' = K sin(2 pi fk
-    t + phik) * speed, integrated with `sub` midpoint substeps per 0.1 s.
-    History steps before t0 hold the t0 pose.
+    t + phik) * speed, integrated with `sub` midpoint substeps per 0.1 s.  The
+    logged velocity is the speed along the heading.  History steps before t0
+    hold the t0 state.  This is the generator's own integrator, not either
+    action space's dynamics, so fitted actions only approximate the log.
     """
     A, f, ph, K, fk, phk = ctl
     n = len(x0)
-    lx = np.empty((T_log, n), dtype=np.float32)
-    ly = np.empty((T_log, n), dtype=np.float32)
+    lx, ly, lth, lvx, lvy = (np.empty((T_log, n), dtype=np.float32) for _ in range(5))
     x, y, th, v = (np.asarray(a, dtype=np.float64).copy() for a in (x0, y0, th0, v0))
-    lx[: t0 + 1] = x
-    ly[: t0 + 1] = y
+
+    def record(t):
+        lx[t], ly[t], lth[t] = x, y, th
+        lvx[t], lvy[t] = v * np.cos(th), v * np.sin(th)
+
+    for t in range(t0 + 1):
+        record(t)
     h = DT / sub
     for t in range(t0 + 1, T_log):
         for j in range(sub):
@@ -158,9 +165,8 @@ def _integrate_logs(ctl, x0, y0, th0, v0, T_log=T_LOG, t0=T0, sub=10):
             y += h * vm * np.sin(thm)
             th += h * kap * vm
             v = np.maximum(0.0, v + h * acc)
-        lx[t] = x
-        ly[t] = y
-    return lx, ly
+        record(t)
+    return lx, ly, lth, lvx, lvy
 
 
 def _scene(rng, wl: Workload, s: int, N: Optional[int], R: Optional[int]):
@@ -255,7 +261,15 @@ class SceneBatch:
     vx: np.ndarray
     vy: np.ndarray
     actions: np.ndarray           # float32 [T][3][N_tot]
+    log_th: Optional[np.ndarray] = None   # float32 [T_LOG][N_tot] logged heading (zeros if not given)
+    log_vx: Optional[np.ndarray] = None   # logged velocity
+    log_vy: Optional[np.ndarray] = None
     extra: dict = field(default_factory=dict)
+
+    def __post_init__(self):
+        for k in ("log_th", "log_vx", "log_vy"):
+            if getattr(self, k) is None:
+                setattr(self, k, np.zeros_like(self.log_x))
 
     @property
     def T_log(self) -> int:
@@ -286,6 +300,8 @@ class SceneBatch:
             rg_x=self.rg_x[rg], rg_y=self.rg_y[rg], rg_poly=self.rg_poly[rg], rg_type=self.rg_type[rg],
             rg_valid=self.rg_valid[rg],
             log_x=np.ascontiguousarray(self.log_x[:, ag]), log_y=np.ascontiguousarray(self.log_y[:, ag]),
+            log_th=np.ascontiguousarray(self.log_th[:, ag]), log_vx=np.ascontiguousarray(self.log_vx[:, ag]),
+            log_vy=np.ascontiguousarray(self.log_vy[:, ag]),
             x=self.x[ag], y=self.y[ag], th=self.th[ag], vx=self.vx[ag], vy=self.vy[ag],
             actions=np.ascontiguousarray(self.actions[:, :, ag]),
         )
@@ -318,7 +334,9 @@ def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
     x, y, th = cat("x", np.float32), cat("y", np.float32), cat("th", np.float32)
     vx, vy = cat("vx", np.float32), cat("vy", np.float32)
     ctl = np.concatenate([p["ctl"] for p in parts], axis=1)
-    log_x, log_y = _integrate_logs(ctl, x, y, th, np.hypot(vx.astype(np.float64), vy.astype(np.float64)))
+    log_x, log_y, log_th, log_vx, log_vy = _integrate_logs(ctl, x, y, th,
+                                                           np.hypot(vx.astype(np.float64), vy.astype(np.float64)))
+    log_vx[: T0 + 1], log_vy[: T0 + 1] = vx, vy  # the history rows hold the start state exactly
     return SceneBatch(
         cfg=cfg, seed=seed, scenes=ids, S=len(ids), N_tot=int(Ns.sum()), T=wl.T,
         agent_off=agent_off, rg_off=rg_off,
@@ -332,6 +350,6 @@ def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
         rg_poly=np.concatenate([p["rg"][2] for p in parts]),
         rg_type=np.concatenate([p["rg"][3] for p in parts]),
         rg_valid=np.concatenate([p["rg"][4] for p in parts]),
-        log_x=log_x, log_y=log_y, x=x, y=y, th=th, vx=vx, vy=vy,
+        log_x=log_x, log_y=log_y, log_th=log_th, log_vx=log_vx, log_vy=log_vy, x=x, y=y, th=th, vx=vx, vy=vy,
         actions=np.ascontiguousarray(np.concatenate([p["act"] for p in parts], axis=2)),
     )
