@@ -103,15 +103,15 @@ St<T> delta_forward(const St<T>& s, T dx, T dy, T dth, double dt) {
 // turn away from the old heading is reduced modulo 2 pi into [-pi, pi]; a
 // state with zero velocity has no direction, so the turn is 0; with no
 // distance travelled the curvature is 0.
-struct BicycleInverse { double a, kappa, turn, dist; };
+struct BicycleInverse { double a, kappa, turn, dist; bool has_dir; };
 
 BicycleInverse bicycle_inverse(const St<double>& s, const St<double>& n, double dt) {
     BicycleInverse r;
     const double v = std::sqrt(s.vx * s.vx + s.vy * s.vy);
     const double vn = std::sqrt(n.vx * n.vx + n.vy * n.vy);
     r.a = (vn - v) / dt;
-    const bool has_dir = n.vx != 0.0 || n.vy != 0.0;
-    r.turn = has_dir ? std::remainder(std::atan2(n.vy, n.vx) - s.th, kTwoPi) : 0.0;
+    r.has_dir = n.vx != 0.0 || n.vy != 0.0;
+    r.turn = r.has_dir ? std::remainder(std::atan2(n.vy, n.vx) - s.th, kTwoPi) : 0.0;
     r.dist = v * dt + 0.5 * r.a * dt * dt;
     r.kappa = r.dist > 0 ? r.turn / r.dist : 0.0;
     return r;
@@ -121,12 +121,14 @@ BicycleInverse bicycle_inverse(const St<double>& s, const St<double>& n, double 
 // kinematics estimate breaks |a| <= kin_amax or |kappa| <= kin_kmax.  *band
 // is set when either comparison lies inside its band: |a| against the limit,
 // or the turn against kin_kmax times the distance (the curvature test with
-// the distance multiplied out, which stays defined for short steps).
+// the distance multiplied out, which stays defined for short steps).  A new
+// state without velocity has no direction and a turn of exactly 0, so its
+// curvature decision is exact and never in the band.
 void kin_check(const ob_params* p, const St<double>& s, const St<double>& n, bool* flag, bool* band) {
     const BicycleInverse r = bicycle_inverse(s, n, p->dt);
     *flag = std::fabs(r.a) > p->kin_amax || std::fabs(r.kappa) > p->kin_kmax;
     *band = std::fabs(std::fabs(r.a) - p->kin_amax) <= p->kin_band_a ||
-            std::fabs(std::fabs(r.turn) - p->kin_kmax * r.dist) <= p->kin_band_th;
+            (r.has_dir && std::fabs(std::fabs(r.turn) - p->kin_kmax * r.dist) <= p->kin_band_th);
 }
 
 bool has_full_log(const ob_batch* b) { return b->log_th && b->log_vx && b->log_vy; }

@@ -240,6 +240,9 @@ def test_kinematic_infeasibility_limits():
     tl = th + 0.3 * v * DT  # turn at the curvature limit over the distance v dt
     s1c = _st(np.zeros(n), np.zeros(n), np.full(n, tl), np.full(n, v * np.cos(tl)), np.full(n, v * np.sin(tl)))
     assert (_kin_flags(o, s0, s1c) & 32).all()
+    # a stopped agent that stays stopped: no direction, exactly feasible, no band
+    z = _st(np.zeros(n), np.zeros(n), np.full(n, th), np.zeros(n), np.zeros(n))
+    assert (_kin_flags(o, z, z) & 48 == 0).all()
 
 
 def test_reverse_motion_reads_as_infeasible():
