@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "agent-steps/s (step+overlap+offroad) on 1 B300; BPTT grad steps/s vs plain"
 UNIT = "agent-steps/s"
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12  # SMs x FP32 lanes x FMA x max clock
-# FP32 operations per unit of counted work (roofline section).
+# FP32 operations per unit of counted work (counted from the kernels' inner loops).
 FLOPS_PER_EVAL = 15      # corner x road-edge segment distance
 FLOPS_PER_TILE = 10      # culling-tile bound test
 FLOPS_PER_PAIR = 44      # ordered SAT pair
@@ -264,6 +264,76 @@ def bptt_leg(wsim, synth, torch, args, rank):
     return out
 
 
+def hbm_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6400.0, "fallback"
+
+
+def expert_leg(wsim, synth, torch, args, rank, b, reps):
+    """The paper's expert actor (Sec. 5.2) on the bench's scenes with every
+    valid agent a bicycle policy agent: (1) the open-loop expert actions of
+    all 80 steps (one HBM-bound launch), (2) the closed-loop expert rollout
+    (RolloutExpert of the Sec. 5.1 runtime table: every agent's action fitted
+    to the log each step, all metrics incl. kinematic infeasibility), (3)
+    log playback of every agent with all metrics."""
+    import copy
+    eb = copy.copy(b)
+    eb.kind = np.full_like(b.kind, synth.KIND_BICYCLE)
+    sim = wsim.Sim(wsim.DeviceBatch(eb))
+    N, S, T = eb.N_tot, eb.S, eb.T
+    st0 = wsim.State.from_batch(eb)
+    st = st0.clone()
+    m = wsim.Metrics(N, S, rows=T)
+    act = torch.empty((T, 3, N), dtype=torch.float32, device="cuda")
+    sim.autotune(st0, torch.as_tensor(eb.actions).cuda().contiguous(), synth.T0, 8)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{S} scenes x up to {int(np.diff(eb.agent_off).max())} agents x {T} steps, "
+                       "every valid agent a bicycle expert"}
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms = timed(lambda: sim.expert_actions(synth.T0, T, act))
+    valid = eb.valid.astype(bool)
+    # algorithmic bytes: every action row written (12 B per agent-step); for a
+    # valid policy agent its log rows t0 .. t0+T read once (heading, velocity:
+    # 12 B per row); kind and valid (2 B per agent)
+    nbytes = N * T * 12 + int(valid.sum()) * (T + 1) * 12 + N * 2
+    peak, src = hbm_peak_gbs()
+    gbs = nbytes / (ms / 1e3) / 1e9
+    out["expert_actions"] = {"ms": ms, "agent_steps_per_s": N * T / (ms / 1e3),
+                             "roofline": {"bound": "hbm", "kernel": "k_expert_actions", "achieved": gbs,
+                                          "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                          "bytes_per_launch": nbytes, "peak_source": src, "traffic": None}}
+    for name, ctrl_v in (("rollout_expert", wsim.CTRL_EXPERT), ("log_playback", wsim.CTRL_LOG)):
+        ctrl = torch.full((N,), ctrl_v, dtype=torch.uint8, device="cuda")
+
+        def run():
+            st.data.copy_(st0.data)
+            sim.rollout(st, None, m, synth.T0, T, mode=wsim.MODE_FUSED, ctrl=ctrl)
+        ms = timed(run)
+        out[name] = {"value": N * T / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms}
+        if name == "rollout_expert":
+            lg = m.logdiv.cpu().numpy()[:, valid]
+            out[name]["ade_m"] = float(lg.mean())
+            out[name]["kin_infeasible_frac"] = float(((m.flags.cpu().numpy()[:, valid] & 4) != 0).mean())
+    assert sim.status() == 0
+    sim.close()
+    return out
+
+
 def config_dict(args, b):
     wl = workload_desc(args.workload)
     return {"workload": wl.name, "scenes": int(b.S),
@@ -384,6 +454,7 @@ def main():
     assert sim.status() == 0
 
     bptt = bptt_leg(wsim, synth, torch, args, rank)
+    expert = expert_leg(wsim, synth, torch, args, rank, b, args.steps)
 
     ms, ms_e2e, units = combine_ranks(pg, [ms, ms_e2e], N * T, "cuda")
     if rank != 0:
@@ -413,6 +484,7 @@ def main():
         "gpu_launches": args.steps * launches,
         "modes": modes,
         "bptt": bptt,
+        "expert": expert,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

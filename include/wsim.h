@@ -61,6 +61,14 @@ extern "C" {
 /* Metric flag bits (wsim_metric_buf.flags). */
 #define WSIM_FLAG_COLLISION 1
 #define WSIM_FLAG_OFFROAD 2
+#define WSIM_FLAG_KININF 4    /* kinematically infeasible transition (Sec. 3.4)  */
+
+/* Who drives an agent in a step (the per-agent ctrl array; NULL ctrl means
+ * WSIM_CTRL_ACTION for every agent). */
+#define WSIM_CTRL_HOLD 0      /* policy agent keeps its state                    */
+#define WSIM_CTRL_ACTION 1    /* policy agent takes the given action             */
+#define WSIM_CTRL_EXPERT 2    /* policy agent takes the expert action (Sec. 5.2) */
+#define WSIM_CTRL_LOG 3       /* any agent replays the log (Sec. 3.5)            */
 
 /* Rollout modes. */
 #define WSIM_MODE_GRAPH 0      /* persistent step kernel per step, CUDA graph   */
@@ -82,6 +90,8 @@ typedef struct {
     float loss_tau;    /* softplus temperature of the overlap penalty [m]: 0.25  */
     int32_t ckpt_every;/* BPTT checkpoint interval in steps (1 = store all): 10  */
     int32_t tile_segs; /* road-edge segments per culling tile (0 = default)      */
+    float kin_amax;    /* kinematic infeasibility: |a| limit [m/s^2]: 6 (Sec. 3.4) */
+    float kin_kmax;    /* ... |kappa| limit [1/m]: 0.3 (Sec. 3.4)                 */
 } wsim_config;
 
 /* A batch of S scenes (all device pointers; sizes on the host).
@@ -105,6 +115,10 @@ typedef struct {
     const int32_t *rg_poly;            /* [R_tot] polyline id                 */
     const uint8_t *rg_type, *rg_valid; /* [R_tot]                             */
     const float *log_x, *log_y;        /* [T_log][N_tot] logged positions     */
+    const float *log_th;               /* [T_log][N_tot] logged heading; with */
+    const float *log_vx, *log_vy;      /* the logged velocity it may be NULL, */
+                                       /* which disables the expert and log   */
+                                       /* playback (WSIM_EINVAL if asked for) */
 } wsim_batch;
 
 /* Agent state, [N_tot] each.  Positions, heading and route cursor are
@@ -119,7 +133,12 @@ typedef struct {
  * agent (> 0 = collision; -inf if none).  off: largest signed distance of a
  * box corner to the nearest road edge (> 0 = off road; -inf if the scene has
  * no edge).  logdiv: distance to the logged position.  flags: bit0 collision,
- * bit1 off road.  reward[s] = -(collisions + off-road agents) of scene s.
+ * bit1 off road, bit2 kinematically infeasible transition into this state
+ * (Sec. 3.4: the App. A.1 bicycle inverse kinematics of the two consecutive
+ * states, direction atan2(vy', vx') against the old heading, breaks |a| <=
+ * kin_amax or |kappa| <= kin_kmax; set by wsim_step and wsim_rollout, 0 from
+ * wsim_metrics, which sees one state).  reward[s] = -(collisions + off-road
+ * agents) of scene s.
  * Invalid agents report 0 everywhere.  In wsim_rollout each pointer is the
  * base of a [T][N_tot] (reward [T][S]) array. */
 typedef struct {
@@ -143,10 +162,16 @@ int wsim_init(wsim_ctx **out, const wsim_config *cfg, const wsim_batch *b, void 
 /* step() of Sec. 4: state t -> t+1 for every scene, then the metrics of t+1
  * against log row t+1.  act is [3][N_tot]: (a, kappa, unused) for bicycle
  * agents, (dx, dy, dtheta) for delta agents; IDM agents ignore it.
- * ctrl [N_tot] may be NULL (all policy agents controlled); a policy agent
- * with ctrl = 0, and every invalid agent, keeps its state.  `in` and `out`
- * must not alias.  m may be NULL (transition only).  Requires 0 <= t and
- * t+1 < T_log. */
+ * ctrl [N_tot] (device, may be NULL = all WSIM_CTRL_ACTION) picks the driver
+ * of each agent: a policy agent holds its state (WSIM_CTRL_HOLD), takes its
+ * action (WSIM_CTRL_ACTION), or takes the expert action (WSIM_CTRL_EXPERT:
+ * the App. A.1 inverse of its action space from its state t to log row t+1,
+ * then its forward dynamics); any agent with WSIM_CTRL_LOG takes log row t+1
+ * as its state; IDM agents follow their route for every other value.
+ * Invalid agents keep their state.  A value above WSIM_CTRL_LOG, or the
+ * expert or log playback without log_th/log_vx/log_vy, holds the agent and
+ * sets the device status to WSIM_EINVAL.  `in` and `out` must not alias.
+ * m may be NULL (transition only).  Requires 0 <= t and t+1 < T_log. */
 int wsim_step(wsim_ctx *ctx, const wsim_state *in, const float *act, const uint8_t *ctrl,
               wsim_state *out, const wsim_metric_buf *m, int t, void *stream);
 
@@ -154,7 +179,9 @@ int wsim_step(wsim_ctx *ctx, const wsim_state *in, const float *act, const uint8
 int wsim_metrics(wsim_ctx *ctx, const wsim_state *st, const wsim_metric_buf *m, int t, void *stream);
 
 /* Rollout (Sec. 5.1): T steps from time index t0.  st holds state t0 on
- * entry and state t0+T on return (device order); act_seq is [T][3][N_tot];
+ * entry and state t0+T on return (device order); act_seq is [T][3][N_tot]
+ * (may be NULL only with a ctrl array in which no agent takes
+ * WSIM_CTRL_ACTION); ctrl as in wsim_step, for every step;
  * mseq arrays are [T][N_tot] ([T][S] for reward), row k holding the metrics
  * of time t0+k+1.  mode: WSIM_MODE_FUSED (fastest) runs one persistent
  * launch in which each CTA carries whole scenes through all T steps with
@@ -168,6 +195,15 @@ int wsim_metrics(wsim_ctx *ctx, const wsim_state *st, const wsim_metric_buf *m, 
  * are the base pointers advanced by k*N_tot. */
 int wsim_rollout(wsim_ctx *ctx, wsim_state *st, const float *act_seq, const uint8_t *ctrl, int t0,
                  int T, int mode, const wsim_metric_buf *mseq, const wsim_state *traj, void *stream);
+
+/* Expert actions, open loop (Sec. 5.2: the inverse of each agent's action
+ * space fitted to the logged trajectory, App. A.1): act_out [T][3][N_tot]
+ * (device, caller-owned) row k receives the action that takes log row
+ * t0+k to log row t0+k+1: (a, kappa, 0) for bicycle agents by the inverse
+ * kinematics, (dx, dy, dtheta) for delta agents, 0 for IDM and invalid
+ * agents.  Requires log_th/log_vx/log_vy (else WSIM_EINVAL), 0 <= t0,
+ * T >= 0 and t0+T < T_log (else WSIM_ESIZE).  Asynchronous on `stream`. */
+int wsim_expert_actions(wsim_ctx *ctx, int t0, int T, float *act_out, void *stream);
 
 /* Launch configuration of the scene-resident rollout (WSIM_MODE_FUSED).
  * Three launch shapes exist: 0 = 512 threads, one CTA per SM, large

@@ -117,6 +117,9 @@ StepArgs base_args(const wsim_ctx* c) {
     a.route_y = b.route_y;
     a.log_x = b.log_x;
     a.log_y = b.log_y;
+    a.log_th = b.log_th;
+    a.log_vx = b.log_vx;
+    a.log_vy = b.log_vy;
     a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags, c->seg_tiles, c->seg_soff, c->seg_sup};
     a.n_work = b.S;
     a.hint = c->hint;
@@ -185,8 +188,8 @@ int enqueue_rollout(wsim_ctx* c, const RolloutKey& k, bool plain, cudaStream_t s
         m.flags += static_cast<size_t>(i) * N;
         m.reward += static_cast<size_t>(i) * c->S;
         StateP o = mstate(&out);
-        int rc = enqueue_step(c, cstate(&prev), &o, k.act + static_cast<size_t>(i) * 3 * N, k.ctrl, &m, k.t0 + i + 1,
-                              c->queue + i, plain, st);
+        const float* act = k.act ? k.act + static_cast<size_t>(i) * 3 * N : nullptr;
+        int rc = enqueue_step(c, cstate(&prev), &o, act, k.ctrl, &m, k.t0 + i + 1, c->queue + i, plain, st);
         if (rc) return rc;
         prev = out;
     }
@@ -266,6 +269,8 @@ void wsim_default_config(wsim_config* cfg) {
     cfg->loss_tau = 0.25f;
     cfg->ckpt_every = 10;
     cfg->tile_segs = 0;
+    cfg->kin_amax = 6.0f;
+    cfg->kin_kmax = 0.3f;
 }
 
 const char* wsim_strerror(int code) {
@@ -328,7 +333,7 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     c->h_agent_off = ao;
     c->p = Params{cfg->dt,     cfg->idm_amax,         cfg->idm_b,  cfg->idm_T,
                   cfg->idm_s0, cfg->idm_dq,           cfg->route_h, 1.0f / cfg->route_h,
-                  cfg->gap_min, 2.0f * sqrtf(cfg->idm_amax * cfg->idm_b)};
+                  cfg->gap_min, 2.0f * sqrtf(cfg->idm_amax * cfg->idm_b), cfg->kin_amax, cfg->kin_kmax};
     int rc = WSIM_OK;
     auto fail = [&](int code) {
         wsim_destroy(c);
@@ -439,7 +444,7 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
 
 int wsim_step(wsim_ctx* c, const wsim_state* in, const float* act, const uint8_t* ctrl, wsim_state* out,
               const wsim_metric_buf* m, int t, void* stream) {
-    if (!c || !state_ok(in) || !state_ok(out) || !act || (m && !metrics_ok(m))) return WSIM_EINVAL;
+    if (!c || !state_ok(in) || !state_ok(out) || (!act && !ctrl) || (m && !metrics_ok(m))) return WSIM_EINVAL;
     if (in->x == out->x) return WSIM_EINVAL;
     if (t < 0 || t + 1 >= c->b.T_log) return WSIM_ESIZE;
     c->last = S_(stream);
@@ -456,7 +461,8 @@ int wsim_metrics(wsim_ctx* c, const wsim_state* st, const wsim_metric_buf* m, in
 
 int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_t* ctrl, int t0, int T, int mode,
                  const wsim_metric_buf* mseq, const wsim_state* traj, void* stream) {
-    if (!c || !state_ok(st) || !act_seq || !metrics_ok(mseq) || (traj && !state_ok(traj))) return WSIM_EINVAL;
+    if (!c || !state_ok(st) || (!act_seq && !ctrl) || !metrics_ok(mseq) || (traj && !state_ok(traj)))
+        return WSIM_EINVAL;
     if (mode < WSIM_MODE_GRAPH || mode > WSIM_MODE_FUSED) return WSIM_EINVAL;
     if (T < 1 || t0 < 0 || t0 + T >= c->b.T_log) return WSIM_ESIZE;
     cudaStream_t s = S_(stream);
@@ -502,6 +508,15 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
         c->have_key = true;
     }
     CK(cudaGraphLaunch(c->exec, s));
+    return WSIM_OK;
+}
+
+int wsim_expert_actions(wsim_ctx* c, int t0, int T, float* act_out, void* stream) {
+    if (!c || !act_out) return WSIM_EINVAL;
+    if (!c->b.log_th || !c->b.log_vx || !c->b.log_vy) return WSIM_EINVAL;
+    if (t0 < 0 || T < 0 || t0 + T >= c->b.T_log) return WSIM_ESIZE;
+    c->last = S_(stream);
+    CK(launch_expert_actions(base_args(c), t0, T, act_out, S_(stream)));
     return WSIM_OK;
 }
 

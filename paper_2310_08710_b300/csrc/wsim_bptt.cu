@@ -239,9 +239,9 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int s
     store_state<NTb>(sm, slot_state(B.ckpt, 0, A.N_tot), a0, N);
     if (threadIdx.x == 0) adj.total = 0.0;
     for (int k = 0; k < T; ++k) {
-        phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(k) * 3 * A.N_tot, a0, N, cnt);
+        phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(k) * 3 * A.N_tot, A.t_log + k, a0, N, cnt);
         __syncthreads();
-        writeback<NTb>(sm, nullptr, a0, N);
+        writeback<NTb>(sm, A.p, nullptr, a0, N);
         __syncthreads();
         for (int i = warp; i < N; i += NW) {
             const float v = sm.valid[i] ? loss_agent(sm, A, a0, N, i, lane, B.lambda, B.tau, A.t_log + k) : 0.f;
@@ -269,10 +269,10 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int s
             load_state<NTb>(sm, A, cslot(B.ckpt, sg, A.N_tot), a0, N);
             __syncthreads();
             for (int t = a; t < b - 1; ++t) {
-                phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(t) * 3 * A.N_tot, a0, N, cnt);
+                phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(t) * 3 * A.N_tot, A.t_log + t, a0, N, cnt);
                 __syncthreads();
                 const StateP o = slot_state(B.segbuf, t + 1 - a, A.N_tot);
-                writeback<NTb>(sm, &o, a0, N);
+                writeback<NTb>(sm, A.p, &o, a0, N);
                 __syncthreads();
             }
         }

@@ -49,6 +49,7 @@ struct MetricsP {
 
 struct Params {
     float dt, amax, b, T, s0, dq, h, inv_h, gap_min, idm_sqrt_ab2;  // 2 sqrt(a b)
+    float kin_amax, kin_kmax;  // kinematic infeasibility limits
 };
 
 // Everything a step or rollout kernel needs.
@@ -61,6 +62,7 @@ struct StepArgs {
     const int32_t* route_off;
     const float *route_x, *route_y;
     const float *log_x, *log_y;
+    const float *log_th, *log_vx, *log_vy;  // may be null (no expert, no log playback)
     Segs segs;
     int32_t* hint;    // [N_tot][4] nearest-segment cache of the per-step kernels (may be null)
     uint16_t* tlist;  // [N_tot][kList] candidate-tile cache of the per-step kernels (may be null)
@@ -95,6 +97,8 @@ cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_
 cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const int32_t* soff,
                                const float4* tiles, float4* sup, cudaStream_t st);
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);
+// Open-loop expert actions over log rows [t0, t0+T] into act [T][3][N_tot].
+cudaError_t launch_expert_actions(const StepArgs& a, int t0, int T, float* act, cudaStream_t st);
 cudaError_t launch_plain_scene(const StepArgs& a, int scene, cudaStream_t st);
 int step_blocks_per_sm();
 // Scene-resident rollout, launch shape 0 (512 threads, 1 CTA/SM, large stage),

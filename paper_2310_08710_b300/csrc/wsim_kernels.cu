@@ -35,9 +35,9 @@ __global__ void __launch_bounds__(NTs) k_step(const StepArgs A) {
         load_state<NTs>(sm, A, A.in, a0, N);
         __syncthreads();
         if (A.do_transition) {
-            phase_transition<NTs>(sm, A, A.act, a0, N, cnt);
+            phase_transition<NTs>(sm, A, A.act, A.t_log, a0, N, cnt);
             __syncthreads();
-            writeback<NTs>(sm, &A.out, a0, N);
+            writeback<NTs>(sm, A.p, &A.out, a0, N);
             __syncthreads();
         }
         if (A.do_metrics) {
@@ -66,9 +66,9 @@ __global__ void __launch_bounds__(NTs) k_plain_transition(const StepArgs A, int 
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
     load_state<NTs>(sm, A, A.in, a0, N);
     __syncthreads();
-    phase_transition<NTs>(sm, A, A.act, a0, N, cnt);
+    phase_transition<NTs>(sm, A, A.act, A.t_log, a0, N, cnt);
     __syncthreads();
-    writeback<NTs>(sm, &A.out, a0, N);
+    writeback<NTs>(sm, A.p, &A.out, a0, N);
     publish_counts(sm, A, cnt);
 }
 
@@ -107,11 +107,62 @@ __global__ void __launch_bounds__(NTs) k_plain_finish(const StepArgs A, int s) {
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
     load_state<NTs>(sm, A, A.do_transition ? as_const(A.out) : A.in, a0, N);
     for (int i = threadIdx.x; i < N; i += NTs) {
-        sm.ov[i] = A.m.ov[a0 + i];
-        sm.off[i] = A.m.off[a0 + i];
+        const int g = a0 + i;
+        sm.ov[i] = A.m.ov[g];
+        sm.off[i] = A.m.off[g];
+        if (A.do_transition && sm.valid[i])  // transition A.in -> A.out
+            sm.kin[i] = kin_infeasible(A.p, A.in.vx[g], A.in.vy[g], A.in.th[g], A.in.th_lo[g], sm.vx[i], sm.vy[i]);
     }
     __syncthreads();
     phase_finish<NTs>(sm, A, A.m, A.m.reward + s, A.t_log, a0, N);
+}
+
+// ---------------------------------------------------------------------------
+// Expert actions, open loop (Sec. 5.2): element (k, g) is the inverse of
+// agent g's action space (App. A.1) from log row t0+k to row t0+k+1.  One
+// thread per agent-step, agents fastest, so every load and store of a warp
+// is one coalesced row segment; row t0+k+1 is read again as the next step's
+// row t0+k from L2.  HBM-bound: per policy agent-step 12 B of log read, 12 B
+// of action written.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_expert_actions(const StepArgs A, int t0, int T, float* act) {
+    const size_t n_tot = static_cast<size_t>(A.N_tot);
+    const size_t n = static_cast<size_t>(T) * n_tot;
+    for (size_t idx = static_cast<size_t>(blockIdx.x) * 256 + threadIdx.x; idx < n;
+         idx += static_cast<size_t>(gridDim.x) * 256) {
+        const size_t k = idx / n_tot, g = idx - k * n_tot;
+        const size_t i0 = (static_cast<size_t>(t0) + k) * n_tot + g, i1 = i0 + n_tot;
+        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+        if (A.valid[g]) {
+            const int kind = A.kind[g];
+            if (kind == WSIM_KIND_BICYCLE) {
+                const BicycleInv r =
+                    bicycle_inverse(A.p, A.log_vx[i0], A.log_vy[i0], A.log_th[i0], 0.f, A.log_vx[i1], A.log_vy[i1]);
+                u0 = r.a;
+                u1 = r.kappa;
+            } else if (kind == WSIM_KIND_DELTA) {
+                u0 = A.log_x[i1] - A.log_x[i0];
+                u1 = A.log_y[i1] - A.log_y[i0];
+                u2 = A.log_th[i1] - A.log_th[i0];
+            }
+        }
+        float* row = act + k * 3 * n_tot + g;
+        row[0] = u0;
+        row[n_tot] = u1;
+        row[2 * n_tot] = u2;
+    }
+}
+
+cudaError_t launch_expert_actions(const StepArgs& a, int t0, int T, float* act, cudaStream_t st) {
+    const size_t n = static_cast<size_t>(T) * static_cast<size_t>(a.N_tot);
+    if (n == 0) return cudaSuccess;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t blocks = (n + 255) / 256;
+    const int grid = static_cast<int>(blocks < static_cast<size_t>(sms) * 8 ? blocks : static_cast<size_t>(sms) * 8);
+    k_expert_actions<<<grid, 256, 0, st>>>(a, t0, T, act);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

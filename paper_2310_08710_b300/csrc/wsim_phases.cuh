@@ -24,6 +24,7 @@ struct __align__(16) AgentSmem {
     int32_t ovk[kMaxN];       // column maxima of the pair depths, as ordered keys
     int32_t hint[4 * kMaxN];  // scene-resident nearest-segment cache
     uint8_t valid[kMaxN];
+    uint8_t kin[kMaxN];       // kinematically infeasible transition into the current state
     int scene;
     int reward;
     int work[3];              // counters of the warp phases (transition, overlap rows, off-road groups)
@@ -66,6 +67,54 @@ template <class T> __device__ __forceinline__ T pick4(const T (&a)[4], int k) {
 }
 
 // ---------------------------------------------------------------------------
+// Inverse kinematics of the bicycle action space (App. A.1) from two
+// consecutive states: a = (|v'| - |v|) / dt; the direction of travel turns
+// from the old heading to atan2(vy', vx') (the paper prints arctan(vx'/vy'):
+// components swapped, quadrant lost), reduced modulo 2 pi; a state with zero
+// velocity has no direction (turn 0); kappa = turn / (v dt + a dt^2 / 2),
+// 0 when no distance is travelled.  dist is formed exactly as the forward
+// model forms it, so an expert action turns the heading by `turn`.
+// ---------------------------------------------------------------------------
+constexpr float kTwoPiHi = 6.28318548202514648f;      // float nearest 2 pi
+constexpr float kTwoPiLo = -1.74845553146951715e-7f;  // 2 pi - kTwoPiHi
+constexpr float kInvTwoPi = 0.159154943091895336f;
+
+// phi - (thh + thl) reduced modulo 2 pi (about [-pi, pi]); thh may be large.
+__device__ __forceinline__ float turn_from(float phi, float thh, float thl) {
+    float dh, dl;
+    two_sum(phi, -thh, dh, dl);
+    dl = __fsub_rn(dl, thl);
+    const float k = rintf(dh * kInvTwoPi);
+    const float r = fmaf(-k, kTwoPiHi, dh);  // one rounding of an almost exact difference
+    return fmaf(-k, kTwoPiLo, r) + dl;
+}
+
+struct BicycleInv {
+    float a, kappa, turn, dist;
+};
+
+__device__ __forceinline__ BicycleInv bicycle_inverse(const Params& p, float vx, float vy, float thh, float thl,
+                                                      float nvx, float nvy) {
+    BicycleInv r;
+    const float v = sqrtf(fmaf(vx, vx, vy * vy));
+    const float vn = sqrtf(fmaf(nvx, nvx, nvy * nvy));
+    r.a = (vn - v) / p.dt;
+    r.turn = (nvx != 0.f || nvy != 0.f) ? turn_from(atan2f(nvy, nvx), thh, thl) : 0.f;
+    r.dist = fmaf(v, p.dt, r.a * (0.5f * p.dt * p.dt));
+    r.kappa = r.dist > 0.f ? r.turn / r.dist : 0.f;
+    return r;
+}
+
+// Sec. 3.4 kinematic infeasibility of a transition: the inverse kinematics
+// break |a| <= kin_amax or |kappa| <= kin_kmax (the curvature test with the
+// distance multiplied out, defined for any step length).
+__device__ __forceinline__ uint8_t kin_infeasible(const Params& p, float vx, float vy, float thh, float thl,
+                                                  float nvx, float nvy) {
+    const BicycleInv r = bicycle_inverse(p, vx, vy, thh, thl, nvx, nvy);
+    return fabsf(r.a) > p.kin_amax || fabsf(r.turn) > p.kin_kmax * r.dist;
+}
+
+// ---------------------------------------------------------------------------
 // Loading and storing agent state.
 // ---------------------------------------------------------------------------
 template <int NT>
@@ -90,18 +139,22 @@ __device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, 
         sm.sh[i] = st.s[g];
         sm.sl[i] = st.s_lo[g];
         sm.valid[i] = A.valid[g];
+        sm.kin[i] = 0;
         sm.ovk[i] = fkey(-WSIM_INF);
     }
     if (threadIdx.x == 0) sm.work[0] = sm.work[1] = sm.work[2] = 0;
 }
 
-// Make the next state current; optionally store it to global memory.  Runs
-// between barriers after the transition, so it also rearms the transition's
-// agent counter for the next step.
+// Make the next state current (after flagging a kinematically infeasible
+// transition); optionally store it to global memory.  Runs between barriers
+// after the transition, so it also rearms the transition's agent counter for
+// the next step.
 template <int NT>
-__device__ void writeback(AgentSmem& sm, const StateP* out, int a0, int N) {
+__device__ void writeback(AgentSmem& sm, const Params& p, const StateP* out, int a0, int N) {
     if (threadIdx.x == 0) sm.work[0] = 0;
     for (int i = threadIdx.x; i < N; i += NT) {
+        sm.kin[i] = sm.valid[i] ? kin_infeasible(p, sm.vx[i], sm.vy[i], sm.thh[i], sm.thl[i], sm.nvx[i], sm.nvy[i])
+                                : uint8_t(0);
         if (out) {
             const int g = a0 + i;
             out->x[g] = sm.nxh[i];
@@ -299,27 +352,60 @@ static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N
 }
 
 // ---------------------------------------------------------------------------
-// Transition t -> t+1 of one scene into the n* arrays.  act is [3][N_tot].
+// Transition t -> t+1 of one scene into the n* arrays.  act is [3][N_tot]
+// (null when no agent takes WSIM_CTRL_ACTION); t_next = t+1 is the log row
+// read by the expert and by log playback.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ int ctrl_of(const StepArgs& A, int g) {
+    return A.ctrl ? A.ctrl[g] : WSIM_CTRL_ACTION;
+}
+
 template <int NT>
-__device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* act, int a0, int N, Counts& cnt) {
+__device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* act, int t_next, int a0, int N,
+                                 Counts& cnt) {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) sm.work[1] = sm.work[2] = 0;  // the metrics phase starts after two barriers
     for (int i = next_agent(sm, 0, lane); i < N; i = next_agent(sm, 0, lane)) {
-        if (A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i]) idm_agent(sm, A, a0, N, i, lane, cnt);
+        if (A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i] && ctrl_of(A, a0 + i) != WSIM_CTRL_LOG)
+            idm_agent(sm, A, a0, N, i, lane, cnt);
     }
     const Params& p = A.p;
+    const bool full_log = A.log_th && A.log_vx && A.log_vy;
+    const size_t row = static_cast<size_t>(t_next) * A.N_tot;
     for (int i = threadIdx.x; i < N; i += NT) {
         const int g = a0 + i;
         const int kind = A.kind[g];
-        if (kind == WSIM_KIND_IDM && sm.valid[i]) continue;
+        const int cm = ctrl_of(A, g);
+        if (kind == WSIM_KIND_IDM && sm.valid[i] && cm != WSIM_CTRL_LOG) continue;
         float xh = sm.xh[i], xl = sm.xl[i], yh = sm.yh[i], yl = sm.yl[i];
         float thh = sm.thh[i], thl = sm.thl[i];
         float vx = sm.vx[i], vy = sm.vy[i];
-        const bool moves = sm.valid[i] && kind != WSIM_KIND_IDM && (A.ctrl == nullptr || A.ctrl[g]);
-        if (moves && kind == WSIM_KIND_BICYCLE) {
-            // App. A.1 bicycle forward dynamics.
-            const float a = act[g], k = act[A.N_tot + g];
+        bool moves = sm.valid[i] && (cm == WSIM_CTRL_LOG || (kind != WSIM_KIND_IDM && cm != WSIM_CTRL_HOLD));
+        if (moves && (cm > WSIM_CTRL_LOG || (cm == WSIM_CTRL_ACTION && !act) ||
+                      ((cm == WSIM_CTRL_EXPERT || cm == WSIM_CTRL_LOG) && !full_log))) {
+            set_status(A.status, WSIM_EINVAL);
+            moves = false;
+        }
+        if (moves && cm == WSIM_CTRL_LOG) {
+            // Log playback (Sec. 3.5): the logged state of t+1.
+            xh = A.log_x[row + g];
+            yh = A.log_y[row + g];
+            thh = A.log_th[row + g];
+            xl = yl = thl = 0.f;
+            vx = A.log_vx[row + g];
+            vy = A.log_vy[row + g];
+        } else if (moves && kind == WSIM_KIND_BICYCLE) {
+            // App. A.1 bicycle forward dynamics; the expert (Sec. 5.2) first
+            // fits (a, kappa) to the logged velocity of t+1.
+            float a, k;
+            if (cm == WSIM_CTRL_EXPERT) {
+                const BicycleInv r = bicycle_inverse(p, vx, vy, thh, thl, A.log_vx[row + g], A.log_vy[row + g]);
+                a = r.a;
+                k = r.kappa;
+            } else {
+                a = act[g];
+                k = act[A.N_tot + g];
+            }
             if (!isfinite(a) || !isfinite(k)) set_status(A.status, WSIM_ENONFINITE);
             const float v = sqrtf(fmaf(vx, vx, vy * vy));
             const float ah = a * (0.5f * p.dt * p.dt);
@@ -332,8 +418,18 @@ __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* 
             vx = vn * cn;
             vy = vn * sn;
         } else if (moves && kind == WSIM_KIND_DELTA) {
-            // App. A.1 delta dynamics.
-            const float ddx = act[g], ddy = act[A.N_tot + g], dth = act[2 * A.N_tot + g];
+            // App. A.1 delta dynamics; the expert's displacement (Sec. 5.2)
+            // is the delta inverse, log row t+1 minus the state.
+            float ddx, ddy, dth;
+            if (cm == WSIM_CTRL_EXPERT) {
+                ddx = __fsub_rn(A.log_x[row + g] - xh, xl);
+                ddy = __fsub_rn(A.log_y[row + g] - yh, yl);
+                dth = __fsub_rn(A.log_th[row + g] - thh, thl);
+            } else {
+                ddx = act[g];
+                ddy = act[A.N_tot + g];
+                dth = act[2 * A.N_tot + g];
+            }
             if (!isfinite(ddx) || !isfinite(ddy) || !isfinite(dth)) set_status(A.status, WSIM_ENONFINITE);
             comp_add(xh, xl, ddx);
             comp_add(yh, yl, ddy);
@@ -830,7 +926,8 @@ __device__ void phase_finish(AgentSmem& sm, const StepArgs& A, const MetricsP& m
             ld = sqrtf(fmaf(dx, dx, dy * dy));
             ov = merged_ov(sm, i);
             off = sm.off[i];
-            fl = (ov > 0.f ? WSIM_FLAG_COLLISION : 0) | (off > 0.f ? WSIM_FLAG_OFFROAD : 0);
+            fl = (ov > 0.f ? WSIM_FLAG_COLLISION : 0) | (off > 0.f ? WSIM_FLAG_OFFROAD : 0) |
+                 (sm.kin[i] ? WSIM_FLAG_KININF : 0);
             r -= (ov > 0.f) + (off > 0.f);
         }
         m.ov[g] = ov;

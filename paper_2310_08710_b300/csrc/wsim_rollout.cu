@@ -90,13 +90,14 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
         }
         __syncthreads();
         for (int k = 0; k < A.T; ++k) {
-            phase_transition<NT>(sm, A, A.act + static_cast<size_t>(k) * 3 * N_tot, a0, N, cnt);
+            phase_transition<NT>(sm, A, A.act ? A.act + static_cast<size_t>(k) * 3 * N_tot : nullptr, A.t_log + k,
+                                 a0, N, cnt);
             __syncthreads();
             if (A.traj.x) {
                 const StateP tr = offset_state(A.traj, static_cast<size_t>(k) * N_tot);
-                writeback<NT>(sm, &tr, a0, N);
+                writeback<NT>(sm, A.p, &tr, a0, N);
             } else {
-                writeback<NT>(sm, nullptr, a0, N);
+                writeback<NT>(sm, A.p, nullptr, a0, N);
             }
             __syncthreads();
             phase_metrics<NT>(sm, V, sm.hint, tlist, tmeta, N, true, true, cnt);

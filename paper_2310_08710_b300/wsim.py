@@ -22,7 +22,8 @@ OK, EINVAL, ESIZE, ECUDA, ENONFINITE, ETIMEOUT, ENOMEM, ESTATE = 0, -1, -2, -3, 
 MODE_GRAPH, MODE_STREAM, MODE_PLAIN, MODE_FUSED = 0, 1, 2, 3
 GRAD_PLAIN = 1
 MAX_AGENTS = 256
-FLAG_COLLISION, FLAG_OFFROAD = 1, 2
+FLAG_COLLISION, FLAG_OFFROAD, FLAG_KININF = 1, 2, 4
+CTRL_HOLD, CTRL_ACTION, CTRL_EXPERT, CTRL_LOG = 0, 1, 2, 3
 
 _fp = C.POINTER(C.c_float)
 _u8p = C.POINTER(C.c_uint8)
@@ -33,7 +34,7 @@ class WsimConfig(C.Structure):
     _fields_ = [("dt", C.c_float), ("idm_amax", C.c_float), ("idm_b", C.c_float), ("idm_T", C.c_float),
                 ("idm_s0", C.c_float), ("idm_dq", C.c_float), ("route_h", C.c_float), ("gap_min", C.c_float),
                 ("loss_lambda", C.c_float), ("loss_tau", C.c_float), ("ckpt_every", C.c_int32),
-                ("tile_segs", C.c_int32)]
+                ("tile_segs", C.c_int32), ("kin_amax", C.c_float), ("kin_kmax", C.c_float)]
 
 
 class WsimBatch(C.Structure):
@@ -44,7 +45,8 @@ class WsimBatch(C.Structure):
                 ("valid", C.c_void_p), ("kind", C.c_void_p), ("route_off", C.c_void_p),
                 ("route_x", C.c_void_p), ("route_y", C.c_void_p), ("rg_x", C.c_void_p), ("rg_y", C.c_void_p),
                 ("rg_poly", C.c_void_p), ("rg_type", C.c_void_p), ("rg_valid", C.c_void_p),
-                ("log_x", C.c_void_p), ("log_y", C.c_void_p)]
+                ("log_x", C.c_void_p), ("log_y", C.c_void_p),
+                ("log_th", C.c_void_p), ("log_vx", C.c_void_p), ("log_vy", C.c_void_p)]
 
 
 STATE_FIELDS = ("x", "y", "x_lo", "y_lo", "th", "th_lo", "vx", "vy", "s", "s_lo")
@@ -97,6 +99,7 @@ def _load():
     lib.wsim_get_tuning.argtypes = [vp, P(WsimTuning)]
     lib.wsim_loss_grad.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
+    lib.wsim_expert_actions.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     return lib
 
 
@@ -104,7 +107,7 @@ lib = _load()
 
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
             "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static",
-            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad")
+            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad", "wsim_expert_actions")
 
 
 class WsimError(RuntimeError):
@@ -152,11 +155,15 @@ class DeviceBatch:
         self.rg_poly = t(b.rg_poly, torch.int32)
         self.rg_type, self.rg_valid = t(b.rg_type, torch.uint8), t(b.rg_valid, torch.uint8)
         self.log_x, self.log_y = t(b.log_x, torch.float32), t(b.log_y, torch.float32)
+        full = getattr(b, "log_th", None) is not None
+        self.log_th = t(b.log_th, torch.float32) if full else None
+        self.log_vx = t(b.log_vx, torch.float32) if full else None
+        self.log_vy = t(b.log_vy, torch.float32) if full else None
         self.c = WsimBatch(self.S, self.N_tot, self.T_log, 0, int(b.rg_off[-1]), int(b.route_off[-1]),
                            *[_ptr(getattr(self, k)) for k in (
                                "agent_off", "rg_off", "L", "W", "idm_v0", "valid", "kind", "route_off",
                                "route_x", "route_y", "rg_x", "rg_y", "rg_poly", "rg_type", "rg_valid",
-                               "log_x", "log_y")])
+                               "log_x", "log_y", "log_th", "log_vx", "log_vy")])
 
 
 class State:
@@ -218,19 +225,20 @@ class Sim:
         except Exception:
             pass
 
-    def step(self, st_in: State, act: torch.Tensor, st_out: State, m: Optional[Metrics], t: int,
+    def step(self, st_in: State, act: Optional[torch.Tensor], st_out: State, m: Optional[Metrics], t: int,
              ctrl: Optional[torch.Tensor] = None, stream=None):
         mc = m.c() if m is not None else None
-        _check(lib.wsim_step(self._h, C.byref(st_in.c()), act.data_ptr(), _ptr(ctrl), C.byref(st_out.c()),
+        _check(lib.wsim_step(self._h, C.byref(st_in.c()), _ptr(act), _ptr(ctrl), C.byref(st_out.c()),
                              C.byref(mc) if mc is not None else None, t, _stream(stream)), "wsim_step")
 
     def metrics(self, st: State, m: Metrics, t: int, stream=None):
         _check(lib.wsim_metrics(self._h, C.byref(st.c()), C.byref(m.c()), t, _stream(stream)), "wsim_metrics")
 
-    def rollout(self, st: State, act_seq: torch.Tensor, mseq: Metrics, t0: int, T: int, mode: int = MODE_GRAPH,
-                ctrl: Optional[torch.Tensor] = None, traj: Optional[State] = None, stream=None):
+    def rollout(self, st: State, act_seq: Optional[torch.Tensor], mseq: Metrics, t0: int, T: int,
+                mode: int = MODE_GRAPH, ctrl: Optional[torch.Tensor] = None, traj: Optional[State] = None,
+                stream=None):
         tc = traj.c() if traj is not None else None
-        _check(lib.wsim_rollout(self._h, C.byref(st.c()), act_seq.data_ptr(), _ptr(ctrl), t0, T, mode,
+        _check(lib.wsim_rollout(self._h, C.byref(st.c()), _ptr(act_seq), _ptr(ctrl), t0, T, mode,
                                 C.byref(mseq.c()), C.byref(tc) if tc is not None else None, _stream(stream)),
                "wsim_rollout")
 
@@ -266,6 +274,14 @@ class Sim:
                                   GRAD_PLAIN if plain else 0, loss.data_ptr(), _ptr(dact), _stream(stream)),
                "wsim_loss_grad")
         return loss, dact
+
+    def expert_actions(self, t0: int, T: int, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Open-loop expert actions [T, 3, N_tot] fitted to log rows t0 .. t0+T
+        (wsim_expert_actions)."""
+        if out is None:
+            out = torch.empty((T, 3, self.batch.N_tot), dtype=torch.float32, device=self.batch.log_x.device)
+        _check(lib.wsim_expert_actions(self._h, t0, T, out.data_ptr(), _stream(stream)), "wsim_expert_actions")
+        return out
 
     def status(self, stream=None) -> int:
         v = C.c_int(0)

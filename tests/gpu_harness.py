@@ -23,7 +23,7 @@ TOL_DEPTH = 2e-5    # m, overlap depth and off-road distance
 ULP_SLACK = 4       # float32 ulps of the value for large magnitudes
 
 
-def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None, tuning=None):
+def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None, tuning=None, no_actions=False):
     from paper_2310_08710_b300 import wsim
     mode = wsim.MODE_FUSED if mode is None else mode
     T = b.T if T is None else T
@@ -32,7 +32,7 @@ def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None, tuning=None):
     if tuning is not None:
         sim.set_tuning(**tuning)
     st = wsim.State.from_batch(b)
-    act = torch.as_tensor(b.actions[:T]).cuda().contiguous()
+    act = None if no_actions else torch.as_tensor(b.actions[:T]).cuda().contiguous()
     traj = wsim.State(b.N_tot, rows=T)
     m = wsim.Metrics(b.N_tot, b.S, rows=T)
     ct = None if ctrl is None else torch.as_tensor(ctrl, dtype=torch.uint8).cuda()
@@ -66,19 +66,21 @@ def _ulp_tol(base, v):
     return np.maximum(base, ULP_SLACK * np.spacing(v.astype(np.float32)).astype(np.float64))
 
 
-def teacher_forced(b, gpu, scene_idx, steps, report=None):
-    """Checks the given steps of the given scenes; returns counters."""
+def teacher_forced(b, gpu, scene_idx, steps, report=None, ctrl=None):
+    """Checks the given steps of the given scenes; returns counters.  ctrl:
+    the per-agent driver array the GPU rollout ran with (None: all actions)."""
     sub = b.subset(scene_idx)
     o = oracle.Oracle(sub)
     ag = np.concatenate([np.arange(b.agent_off[s], b.agent_off[s + 1]) for s in scene_idx]).astype(np.int64)
     valid = sub.valid.astype(bool)
-    c = dict(steps=0, agent_steps=0, band_idm=0, band_ov=0, band_off=0, max_pos=0.0, max_th=0.0, max_v=0.0,
-             max_s=0.0, max_ov=0.0, max_off=0.0, max_logdiv=0.0, reward_checked=0)
+    sub_ctrl = None if ctrl is None else np.ascontiguousarray(np.asarray(ctrl, np.uint8)[ag])
+    c = dict(steps=0, agent_steps=0, band_idm=0, band_ov=0, band_off=0, band_kin=0, kin_flagged=0, max_pos=0.0,
+             max_th=0.0, max_v=0.0, max_s=0.0, max_ov=0.0, max_off=0.0, max_logdiv=0.0, reward_checked=0)
     traj = gpu["traj"]
     for k in steps:
         prev = initial_rows(b) if k == 0 else traj[:, k - 1, :]
         st_t = state64(prev, ag)
-        exp, band, _ = o.transition(st_t, sub.actions[k])
+        exp, band, _ = o.transition(st_t, sub.actions[k], ctrl=sub_ctrl, t_next=synth.T0 + k + 1)
         got = state64(traj[:, k, :], ag)
         keep = ~band.astype(bool)
         c["band_idm"] += int(band.sum())
@@ -96,7 +98,7 @@ def teacher_forced(b, gpu, scene_idx, steps, report=None):
         c["max_s"] = max(c["max_s"], float(ds.max(initial=0)))
         # Metrics of the GPU's own t+1 state.
         t = synth.T0 + k + 1
-        me = o.metrics(got, t)
+        me = o.metrics(got, t, prev=st_t)
         for key, tol, mk in (("ov", TOL_DEPTH, "max_ov"), ("off", TOL_DEPTH, "max_off"),
                              ("logdiv", TOL_LOGDIV, "max_logdiv")):
             gv = gpu[key][k][ag].astype(np.float64)
@@ -114,8 +116,12 @@ def teacher_forced(b, gpu, scene_idx, steps, report=None):
         b_off = (ef & 8) != 0
         assert np.array_equal((gf & 1)[~b_ov], (ef & 1)[~b_ov]), ("collision flag", k)
         assert np.array_equal((gf & 2)[~b_off], (ef & 2)[~b_off]), ("offroad flag", k)
+        b_kin = (ef & 32) != 0
+        assert np.array_equal(((gf & 4) != 0)[~b_kin], ((ef & 16) != 0)[~b_kin]), ("kinematic flag", k)
         c["band_ov"] += int((b_ov & valid).sum())
         c["band_off"] += int((b_off & valid).sum())
+        c["band_kin"] += int((b_kin & valid).sum())
+        c["kin_flagged"] += int(((gf & 4) != 0).sum())
         for j, s in enumerate(scene_idx):
             a0, a1 = sub.agent_off[j], sub.agent_off[j + 1]
             if not (ef[a0:a1] & 12).any():

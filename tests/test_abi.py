@@ -41,6 +41,7 @@ def test_host_side_argument_checks_without_gpu():
     h = C.c_void_p()
     cfg = wsim.default_config()
     assert abs(cfg.dt - 0.1) < 1e-7 and cfg.ckpt_every == 10
+    assert cfg.kin_amax == 6.0 and abs(cfg.kin_kmax - 0.3) < 1e-7  # Sec. 3.4 limits
     b = wsim.WsimBatch()
     b.S = 0
     assert lib.wsim_init(C.byref(h), C.byref(cfg), C.byref(b), None) == wsim.ESIZE
@@ -48,6 +49,7 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.wsim_init(C.byref(h), C.byref(cfg), C.byref(b), None) == wsim.EINVAL  # null arrays
     assert lib.wsim_step(None, None, None, None, None, None, 0, None) == wsim.EINVAL
     assert lib.wsim_rollout(None, None, None, None, 10, 80, 0, None, None, None) == wsim.EINVAL
+    assert lib.wsim_expert_actions(None, 10, 80, None, None) == wsim.EINVAL
     assert lib.wsim_strerror(wsim.ETIMEOUT).decode().startswith("a bounded")
 
 
