@@ -284,8 +284,10 @@ void wsim_destroy(wsim_ctx *ctx);
  * must not allocate).  The scratch wsim_init would allocate lives instead in
  * one file-scope device array of about 6.2 MB that every GPU loading the
  * library holds until the process exits.  Limits: at most 4096 scenes, and
- * R_tot + 15 * S <= 262144 (the packed road-edge segments must fit); larger
- * batches return WSIM_ESIZE before any work.  The first call on a device
+ * at most 262144 packed road-edge positions (segments, with each run of
+ * consecutive segments padded to a multiple of 16 and each scene to a
+ * multiple of 16; R_tot + 15 * S > 262144 is rejected at once); larger
+ * batches return WSIM_ESIZE before any metric work.  The first call on a device
  * looks up the array's device address (once per device, with that device
  * current); make that first call before any stream capture.  All calls share
  * the array and it keeps the previous call's contents, so calls that overlap

@@ -383,7 +383,7 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
         return fail(WSIM_ECUDA);
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, S, c->seg_off, c->seg_geo,
                         c->seg_inv, c->seg_flags, st) != cudaSuccess ||
-        launch_tile_build(S, c->seg_off, c->seg_cnt, c->seg_geo, c->seg_tiles, st) != cudaSuccess ||
+        launch_tile_build(S, c->seg_off, c->seg_cnt, c->seg_geo, c->seg_flags, c->seg_tiles, st) != cudaSuccess ||
         launch_super_build(S, c->seg_off, c->seg_cnt, c->seg_soff, c->seg_tiles, c->seg_sup, st) != cudaSuccess)
         return fail(WSIM_ECUDA);
 

@@ -19,16 +19,20 @@ constexpr float kSkinSmall = 2.0f;      // fallback when the kSkin list would no
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
 
 // Packed road-edge segments of the whole batch (built by wsim_init).  Scene s
-// owns segments [off[s], off[s] + cnt[s]); off[s] is a multiple of kTile and
-// the region is zero-padded to the next multiple.  Tile t of the batch covers
-// segments [t kTile, (t+1) kTile) and has two float4 records: its bounding box
-// (xmin, ymin, xmax, ymax) and two points that lie on its segments.
+// owns positions [off[s], off[s] + cnt[s]); off[s] is a multiple of kTile.
+// Inside a scene, segments keep roadgraph order and every run of consecutive
+// segments (one polyline without a gap) starts on a multiple of kTile; the
+// positions between runs and up to the next multiple of kTile hold padding
+// (far away, flags 0).  Tile t of the batch covers positions
+// [t kTile, (t+1) kTile), i.e. part of one run, and has two float4 records:
+// its capsule (chord start, chord) and (radius, 1/|chord|^2, 0, 0).
 struct Segs {
     const int32_t* off;    // [S+1]
     const int32_t* cnt;    // [S]
     const float4* geo;     // (ax, ay, ux, uy): start point and k -> k+1 vector
     const float* inv;      // 1 / |u|^2
-    const uint8_t* flags;  // bit0: a segment ends where this one starts; bit1: one starts where it ends
+    const uint8_t* flags;  // bit0: a segment ends where this one starts; bit1: one starts where it ends;
+                           // bit2: a segment (0: padding between runs, far away, never nearest)
     const float4* tiles;   // [2 * tiles]
     const int32_t* soff;   // [S+1] first super-tile of each scene
     const float4* sup;     // super-tile bounding boxes: super-tile j of scene s covers its tiles 8j .. 8j+7
@@ -93,7 +97,7 @@ cudaError_t launch_seg_pack(const int32_t* rg_off, const float* rg_x, const floa
                             const uint8_t* rg_type, const uint8_t* rg_valid, int S, const int32_t* seg_off,
                             float4* geo, float* inv, uint8_t* flags, cudaStream_t st);
 cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const float4* geo,
-                              float4* tiles, cudaStream_t st);
+                              const uint8_t* flags, float4* tiles, cudaStream_t st);
 cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const int32_t* soff,
                                const float4* tiles, float4* sup, cudaStream_t st);
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NTs) k_plain_finish(const StepArgs A, int s) {
     load_state<NTs>(sm, A, A.do_transition ? as_const(A.out) : A.in, a0, N);
     for (int i = threadIdx.x; i < N; i += NTs) {
         const int g = a0 + i;
-        sm.ov[i] = A.m.ov[g];
+        sm.ovk[i] = ukey(A.m.ov[g]);
         sm.off[i] = A.m.off[g];
         if (A.do_transition && sm.valid[i])  // transition A.in -> A.out
             sm.kin[i] = kin_infeasible(A.p, A.in.vx[g], A.in.vy[g], A.in.th[g], A.in.th_lo[g], sm.vx[i], sm.vy[i]);
@@ -119,48 +119,66 @@ __global__ void __launch_bounds__(NTs) k_plain_finish(const StepArgs A, int s) {
 
 // ---------------------------------------------------------------------------
 // Expert actions, open loop (Sec. 5.2): element (k, g) is the inverse of
-// agent g's action space (App. A.1) from log row t0+k to row t0+k+1.  One
-// thread per agent-step, agents fastest, so every load and store of a warp
-// is one coalesced row segment; row t0+k+1 is read again as the next step's
-// row t0+k from L2.  HBM-bound: per policy agent-step 12 B of log read, 12 B
-// of action written.
+// agent g's action space (App. A.1) from log row t0+k to row t0+k+1.  A
+// thread takes one agent and a chunk of kExpertChunk steps: it loads the
+// chunk's kExpertChunk+1 log rows of that agent first (all loads in flight
+// together), then writes the chunk's actions.  Consecutive threads take
+// consecutive agents, so every load and store of a warp is one coalesced row
+// segment.  HBM-bound: per policy agent-step 12 B of log read (heading and
+// velocity for bicycle agents, position and heading for delta agents), per
+// agent-step 12 B of action written; the first row of a chunk is read twice.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_expert_actions(const StepArgs A, int t0, int T, float* act) {
-    const size_t n_tot = static_cast<size_t>(A.N_tot);
-    const size_t n = static_cast<size_t>(T) * n_tot;
-    for (size_t idx = static_cast<size_t>(blockIdx.x) * 256 + threadIdx.x; idx < n;
-         idx += static_cast<size_t>(gridDim.x) * 256) {
-        const size_t k = idx / n_tot, g = idx - k * n_tot;
-        const size_t i0 = (static_cast<size_t>(t0) + k) * n_tot + g, i1 = i0 + n_tot;
-        float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-        if (A.valid[g]) {
-            const int kind = A.kind[g];
-            if (kind == WSIM_KIND_BICYCLE) {
-                const BicycleInv r =
-                    bicycle_inverse(A.p, A.log_vx[i0], A.log_vy[i0], A.log_th[i0], 0.f, A.log_vx[i1], A.log_vy[i1]);
-                u0 = r.a;
-                u1 = r.kappa;
-            } else if (kind == WSIM_KIND_DELTA) {
-                u0 = A.log_x[i1] - A.log_x[i0];
-                u1 = A.log_y[i1] - A.log_y[i0];
-                u2 = A.log_th[i1] - A.log_th[i0];
+constexpr int kExpertChunk = 8;
+
+__global__ void __launch_bounds__(256) k_expert_actions(const StepArgs A, int t0, int T, float* __restrict__ act) {
+    const int g = blockIdx.x * 256 + threadIdx.x;
+    if (g >= A.N_tot) return;
+    const size_t n = static_cast<size_t>(A.N_tot);
+    const int k0 = blockIdx.y * kExpertChunk;
+    const int m = min(kExpertChunk, T - k0);  // steps of this chunk
+    const int kind = A.valid[g] ? A.kind[g] : -1;
+    const bool bic = kind == WSIM_KIND_BICYCLE, del = kind == WSIM_KIND_DELTA;
+    // Three logged quantities per row: bicycle (vx, vy, heading), delta (x, y, heading).
+    const float* __restrict__ q0 = bic ? A.log_vx : A.log_x;
+    const float* __restrict__ q1 = bic ? A.log_vy : A.log_y;
+    const float* __restrict__ q2 = A.log_th;
+    float r0[kExpertChunk + 1], r1[kExpertChunk + 1], r2[kExpertChunk + 1];
+    if (bic || del) {
+        const size_t base = (static_cast<size_t>(t0) + k0) * n + g;
+#pragma unroll
+        for (int j = 0; j <= kExpertChunk; ++j) {
+            if (j <= m) {
+                r0[j] = q0[base + j * n];
+                r1[j] = q1[base + j * n];
+                r2[j] = q2[base + j * n];
             }
         }
-        float* row = act + k * 3 * n_tot + g;
-        row[0] = u0;
-        row[n_tot] = u1;
-        row[2 * n_tot] = u2;
+    }
+    float* out = act + static_cast<size_t>(k0) * 3 * n + g;
+#pragma unroll
+    for (int j = 0; j < kExpertChunk; ++j) {
+        if (j < m) {
+            float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+            if (bic) {
+                const BicycleInv r = bicycle_inverse(A.p, r0[j], r1[j], r2[j], 0.f, r0[j + 1], r1[j + 1]);
+                u0 = r.a;
+                u1 = r.kappa;
+            } else if (del) {
+                u0 = r0[j + 1] - r0[j];
+                u1 = r1[j + 1] - r1[j];
+                u2 = r2[j + 1] - r2[j];
+            }
+            out[0] = u0;
+            out[n] = u1;
+            out[2 * n] = u2;
+            out += 3 * n;
+        }
     }
 }
 
 cudaError_t launch_expert_actions(const StepArgs& a, int t0, int T, float* act, cudaStream_t st) {
-    const size_t n = static_cast<size_t>(T) * static_cast<size_t>(a.N_tot);
-    if (n == 0) return cudaSuccess;
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t blocks = (n + 255) / 256;
-    const int grid = static_cast<int>(blocks < static_cast<size_t>(sms) * 8 ? blocks : static_cast<size_t>(sms) * 8);
+    if (T == 0 || a.N_tot == 0) return cudaSuccess;
+    const dim3 grid((a.N_tot + 255) / 256, (T + kExpertChunk - 1) / kExpertChunk);
     k_expert_actions<<<grid, 256, 0, st>>>(a, t0, T, act);
     return cudaGetLastError();
 }
@@ -180,49 +198,83 @@ __device__ __forceinline__ bool is_seg(const RgView& r, int r0, int r1, int k) {
            r.poly[k] == r.poly[k + 1];
 }
 
-__global__ void __launch_bounds__(256) k_seg_count(const int32_t* rg_off, RgView rg, int32_t* cnt) {
-    const int s = blockIdx.x;
-    const int r0 = rg_off[s], r1 = rg_off[s + 1];
-    int c = 0;
-    for (int k = r0 + threadIdx.x; k < r1; k += 256) c += is_seg(rg, r0, r1, k);
-    __shared__ int tot;
-    if (threadIdx.x == 0) tot = 0;
-    __syncthreads();
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&tot, c);
-    __syncthreads();
-    if (threadIdx.x == 0) cnt[s] = tot;
+// Packing order of one scene's road-edge segments: roadgraph order, with
+// every run of consecutive segments (one polyline without a gap) starting on
+// a kTile boundary, so that no culling tile holds two runs (a tile across two
+// polylines would have a capsule as long as the distance between them).
+// One warp per scene, 32 points per iteration; emit(k, p) receives segment
+// k's scene-relative position p, pad(p) each padding position.  Returns the
+// number of positions used (padding between runs included).
+__device__ __forceinline__ unsigned lanes_between(int a, int b) {  // bits [a, b)
+    const unsigned hi = b >= 32 ? 0xffffffffu : ((1u << b) - 1u);
+    return hi & ~((1u << a) - 1u);
 }
 
-__global__ void __launch_bounds__(256) k_seg_pack(const int32_t* rg_off, RgView rg, const int32_t* seg_off,
-                                                  float4* geo, float* inv, uint8_t* flags) {
+template <class Emit, class Pad>
+__device__ int pack_runs(const RgView& rg, int r0, int r1, int lane, Emit emit, Pad pad) {
+    int pos = 0;  // next free position
+    for (int c0 = r0; c0 < r1; c0 += 32) {
+        const int k = c0 + lane;
+        const bool f = is_seg(rg, r0, r1, k);
+        const bool st = f && !is_seg(rg, r0, r1, k - 1);
+        const unsigned fm = __ballot_sync(kFull, f);
+        unsigned starts = __ballot_sync(kFull, st);
+        int cur = pos, prev = 0, base = pos, first = 0;  // lanes before the first start continue a run
+        while (starts) {
+            const int s = __ffs(starts) - 1;
+            starts &= starts - 1;
+            cur += __popc(fm & lanes_between(prev, s));
+            const int aligned = (cur + kTile - 1) / kTile * kTile;
+            if (lane < aligned - cur) pad(cur + lane);
+            cur = aligned;
+            if (lane >= s) {
+                base = cur;
+                first = s;
+            }
+            prev = s;
+        }
+        cur += __popc(fm & lanes_between(prev, 32));
+        if (f) emit(k, base + (lane - first));
+        pos = cur;
+    }
+    return pos;
+}
+
+__global__ void __launch_bounds__(32) k_seg_count(const int32_t* rg_off, RgView rg, int32_t* cnt) {
+    const int s = blockIdx.x;
+    const int n = pack_runs(rg, rg_off[s], rg_off[s + 1], threadIdx.x, [](int, int) {}, [](int) {});
+    if (threadIdx.x == 0) cnt[s] = n;
+}
+
+// Far-away padding segment: its squared distance overflows to +inf, so it
+// never wins a nearest-segment search; flags 0 (not a segment).
+constexpr float kFarAway = 1e30f;
+
+__global__ void __launch_bounds__(32) k_seg_pack(const int32_t* rg_off, RgView rg, const int32_t* seg_off,
+                                                 float4* geo, float* inv, uint8_t* flags) {
     const int s = blockIdx.x;
     const int r0 = rg_off[s], r1 = rg_off[s + 1];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ int wsum[8];
-    int running = seg_off[s];
-    for (int c0 = r0; c0 < r1; c0 += 256) {
-        const int k = c0 + threadIdx.x;
-        const bool f = is_seg(rg, r0, r1, k);
-        const unsigned bal = __ballot_sync(kFull, f);
-        if (lane == 0) wsum[warp] = __popc(bal);
-        __syncthreads();
-        int before = 0, total = 0;
-        for (int w = 0; w < 8; ++w) {
-            before += w < warp ? wsum[w] : 0;
-            total += wsum[w];
-        }
-        if (f) {
-            const int pos = running + before + __popc(bal & ((1u << lane) - 1u));
+    const int e0 = seg_off[s];
+    const int n = pack_runs(
+        rg, r0, r1, threadIdx.x,
+        [&](int k, int p) {
             const float ax = rg.x[k], ay = rg.y[k];
             const float ux = rg.x[k + 1] - ax, uy = rg.y[k + 1] - ay;
-            geo[pos] = make_float4(ax, ay, ux, uy);
-            inv[pos] = 1.0f / fmaf(ux, ux, uy * uy);
-            flags[pos] = (is_seg(rg, r0, r1, k - 1) ? 1 : 0) | (is_seg(rg, r0, r1, k + 1) ? 2 : 0);
-        }
-        running += total;
-        __syncthreads();
+            geo[e0 + p] = make_float4(ax, ay, ux, uy);
+            inv[e0 + p] = 1.0f / fmaf(ux, ux, uy * uy);
+            flags[e0 + p] = (is_seg(rg, r0, r1, k - 1) ? 1 : 0) | (is_seg(rg, r0, r1, k + 1) ? 2 : 0) | 4;
+        },
+        [&](int p) {
+            geo[e0 + p] = make_float4(kFarAway, kFarAway, 0.f, 0.f);
+            inv[e0 + p] = 0.f;
+            flags[e0 + p] = 0;
+        });
+    // the scene's tail up to its aligned end
+    const int end = (n + kSegAlign - 1) / kSegAlign * kSegAlign;
+    for (int p = n + static_cast<int>(threadIdx.x); p < end; p += 32) {
+        geo[e0 + p] = make_float4(kFarAway, kFarAway, 0.f, 0.f);
+        inv[e0 + p] = 0.f;
+        flags[e0 + p] = 0;
     }
 }
 
@@ -230,14 +282,16 @@ __global__ void __launch_bounds__(256) k_seg_pack(const int32_t* rg_off, RgView 
 // segment's start to the last segment's end, and the largest distance of any
 // segment end point from that chord (rounded up).  Record 0: (start, chord);
 // record 1: (radius, 1/|chord|^2, 0, 0).  Both chord ends lie on segments.
+// A tile holds one run: segments first, then padding (flags 0).
 __global__ void __launch_bounds__(256) k_tile_build(const int32_t* seg_off, const int32_t* seg_cnt,
-                                                    const float4* geo, float4* tiles) {
+                                                    const float4* geo, const uint8_t* flags, float4* tiles) {
     const int s = blockIdx.x;
     const int e0 = seg_off[s], E = seg_cnt[s];
     const int nt = (E + kTile - 1) / kTile;
     for (int t = threadIdx.x; t < nt; t += 256) {
         const int b = e0 + t * kTile;
-        const int n = min(kTile, E - t * kTile);
+        int n = min(kTile, E - t * kTile);
+        while (n > 1 && !(flags[b + n - 1] & 4)) --n;
         const float4 A = geo[b], Z = geo[b + n - 1];
         const float sx = A.x, sy = A.y;
         const float dx = (Z.x + Z.z) - sx, dy = (Z.y + Z.w) - sy;
@@ -288,7 +342,7 @@ cudaError_t launch_seg_count(const int32_t* rg_off, const float* rg_x, const flo
                              const uint8_t* rg_type, const uint8_t* rg_valid, int S, int32_t* cnt,
                              cudaStream_t st) {
     RgView rg{rg_x, rg_y, rg_poly, rg_type, rg_valid};
-    k_seg_count<<<S, 256, 0, st>>>(rg_off, rg, cnt);
+    k_seg_count<<<S, 32, 0, st>>>(rg_off, rg, cnt);
     return cudaGetLastError();
 }
 
@@ -296,13 +350,13 @@ cudaError_t launch_seg_pack(const int32_t* rg_off, const float* rg_x, const floa
                             const uint8_t* rg_type, const uint8_t* rg_valid, int S, const int32_t* seg_off,
                             float4* geo, float* inv, uint8_t* flags, cudaStream_t st) {
     RgView rg{rg_x, rg_y, rg_poly, rg_type, rg_valid};
-    k_seg_pack<<<S, 256, 0, st>>>(rg_off, rg, seg_off, geo, inv, flags);
+    k_seg_pack<<<S, 32, 0, st>>>(rg_off, rg, seg_off, geo, inv, flags);
     return cudaGetLastError();
 }
 
 cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const float4* geo,
-                              float4* tiles, cudaStream_t st) {
-    k_tile_build<<<S, 256, 0, st>>>(seg_off, seg_cnt, geo, tiles);
+                              const uint8_t* flags, float4* tiles, cudaStream_t st) {
+    k_tile_build<<<S, 256, 0, st>>>(seg_off, seg_cnt, geo, flags, tiles);
     return cudaGetLastError();
 }
 

@@ -20,8 +20,10 @@ struct __align__(16) AgentSmem {
     // next state
     float nxh[kMaxN], nxl[kMaxN], nyh[kMaxN], nyl[kMaxN], nth[kMaxN], ntl[kMaxN];
     float nvx[kMaxN], nvy[kMaxN], nsh[kMaxN], nsl[kMaxN];
-    float ov[kMaxN], off[kMaxN];
-    int32_t ovk[kMaxN];       // column maxima of the pair depths, as ordered keys
+    float off[kMaxN];
+    uint32_t ovk[kMaxN];      // ov as an ordered key (max over the pair depths, atomicMax)
+    uint32_t pk[kMaxN];       // the same with its low 8 bits replaced by the pair's other agent
+    float4 obox[kMaxN];       // overlap culling record: (x, y, R, R - lower bound of ov)
     int32_t hint[4 * kMaxN];  // scene-resident nearest-segment cache
     uint8_t valid[kMaxN];
     uint8_t kin[kMaxN];       // kinematically infeasible transition into the current state
@@ -45,12 +47,18 @@ struct SegView {
     int E, nt, ns;
 };
 
-// Order-preserving int key of a float (for atomicMax on shared memory).
-__device__ __forceinline__ int32_t fkey(float f) {
-    const int32_t b = __float_as_int(f);
-    return b >= 0 ? b : b ^ 0x7fffffff;
+
+// Order-preserving unsigned key of a float (atomicMax in shared memory).
+// A pair depth and the pair's other agent share one key in pk: the depth's
+// key with its low 8 bits replaced by the agent (the deepest partner to
+// within 2^-16 relative, good enough to seed the next step's bound).
+__device__ __forceinline__ uint32_t ukey(float f) {
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
-__device__ __forceinline__ float funkey(int32_t k) { return __int_as_float(k >= 0 ? k : k ^ 0x7fffffff); }
+__device__ __forceinline__ float unukey(uint32_t k) { return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k); }
+__device__ __forceinline__ uint32_t partner_key(float d, int j) { return (ukey(d) & 0xffffff00u) | static_cast<uint32_t>(j); }
+constexpr uint32_t kNoDepth = 0x007fffffu;  // ukey(-inf)
 
 // Next agent of a warp phase (dynamic assignment balances uneven agents).
 __device__ __forceinline__ int next_agent(AgentSmem& sm, int slot, int lane) {
@@ -140,7 +148,8 @@ __device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, 
         sm.sl[i] = st.s_lo[g];
         sm.valid[i] = A.valid[g];
         sm.kin[i] = 0;
-        sm.ovk[i] = fkey(-WSIM_INF);
+        sm.ovk[i] = kNoDepth;
+        sm.pk[i] = kNoDepth;
     }
     if (threadIdx.x == 0) sm.work[0] = sm.work[1] = sm.work[2] = 0;
 }
@@ -182,7 +191,6 @@ __device__ void writeback(AgentSmem& sm, const Params& p, const StateP* out, int
         sm.vy[i] = sm.nvy[i];
         sm.sh[i] = sm.nsh[i];
         sm.sl[i] = sm.nsl[i];
-        sm.ovk[i] = fkey(-WSIM_INF);
     }
 }
 
@@ -259,53 +267,86 @@ static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N
     int seg;
     float tau;
     route_locate(bh, bl, p, P, seg, tau);
+    // Route points near the cursor, loaded with the samples: the advance
+    // below moves the cursor by (v + v') dt / 2, a few segments at most, so
+    // its segment is almost always among them (lane k < kNear: point seg0 + k).
+    constexpr int kNear = 8;
+    int seg0;
+    float tau0;
+    route_locate(s_hi, s_lo, p, P, seg0, tau0);
+    const int kn = min(seg0 + lane, P - 1);
+    const float nxp = lane < kNear ? rx[kn] : 0.f, nyp = lane < kNear ? ry[kn] : 0.f;
     const float Px = rx[seg], Py = ry[seg];
     const float dx = rx[seg + 1] - Px, dy = ry[seg + 1] - Py;
     const float qox = tau * dx, qoy = tau * dy;
     const float rn = rsqrtf(fmaf(dx, dx, dy * dy));
     const float tx = dx * rn, ty = dy * rn;
 
-    // Bounding circle of the samples.
+    // Bounding circles of the four groups of 8 consecutive samples: a box
+    // (widened by wi) that holds a sample of group G has its centre within
+    // r_G + hl + hw + 2 wi of the circle's centre (5 cm of slack for the
+    // float32 positions).
     const float qx = Px + qox, qy = Py + qoy;
-    const float cx = __shfl_sync(kFull, qx, 15), cy = __shfl_sync(kFull, qy, 15);
-    float rq = sqrtf((qx - cx) * (qx - cx) + (qy - cy) * (qy - cy));
+    const int gl = lane & ~7;
+    const float gcx = __shfl_sync(kFull, qx, gl + 4), gcy = __shfl_sync(kFull, qy, gl + 4);
+    float gr = sqrtf((qx - gcx) * (qx - gcx) + (qy - gcy) * (qy - gcy));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rq = fmaxf(rq, __shfl_xor_sync(kFull, rq, o));
+    for (int o = 4; o > 0; o >>= 1) gr = fmaxf(gr, __shfl_xor_sync(kFull, gr, o));
+    gr += 2.f * wi + 0.05f;  // lanes 8G .. 8G+7 hold circle G
 
     const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
     int lead = -1, lead_hit = 0;
     float gbest = WSIM_INF;
+    // Samples in the widened box of agent j (one ballot bit per sample).
+    auto box_hits = [&](int j) {
+        const float rxq = (Px - sm.xh[j]) + (qox - sm.xl[j]);
+        const float ryq = (Py - sm.yh[j]) + (qoy - sm.yl[j]);
+        const float cj = sm.c[j], sj = sm.s[j];
+        const float pu = fabsf(fmaf(rxq, cj, ryq * sj));
+        const float pn = fabsf(fmaf(-rxq, sj, ryq * cj));
+        return fminf(sm.hl[j] + wi - pu, sm.hw[j] + wi - pn) >= 0.f;
+    };
+    auto take = [&](int j, unsigned hits) {
+        const float ddx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
+        const float ddy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
+        const float gap = fmaxf(p.gap_min, sqrtf(fmaf(ddx, ddx, ddy * ddy)) - (hli + sm.hl[j]));
+        if (gap < gbest) {
+            gbest = gap;
+            lead = j;
+            lead_hit = __ffs(hits) - 1;
+        }
+    };
     for (int jb = 0; jb < N; jb += 32) {
         const int jl = jb + lane;
         bool cand = false;
+        // non-candidates test a point that no circle reaches
+        float xj = WSIM_INF, yj = WSIM_INF, reach = 0.f;
         if (jl < N && jl != i && sm.valid[jl]) {
-            const float ex = sm.xh[jl] - cx, ey = sm.yh[jl] - cy;
-            const float reach = rq + sm.hl[jl] + sm.hw[jl] + 2.f * wi + 0.05f;
-            cand = ex * ex + ey * ey <= reach * reach;
+            xj = sm.xh[jl];
+            yj = sm.yh[jl];
+            reach = sm.hl[jl] + sm.hw[jl];
+        }
+#pragma unroll
+        for (int G = 0; G < 4; ++G) {
+            const float ex = xj - __shfl_sync(kFull, gcx, 8 * G), ey = yj - __shfl_sync(kFull, gcy, 8 * G);
+            const float rr = __shfl_sync(kFull, gr, 8 * G) + reach;
+            cand = cand || fmaf(ex, ex, ey * ey) <= rr * rr;
         }
         unsigned cm = __ballot_sync(kFull, cand);
+        // Two candidates per iteration (independent tests), taken in index
+        // order so that ties go to the lower index.
         while (cm) {
-            const int j = jb + __ffs(cm) - 1;
+            const int j1 = jb + __ffs(cm) - 1;
             cm &= cm - 1;
-            if (lane == 0) cnt.tests += 32;
-            const float xjh = sm.xh[j], yjh = sm.yh[j];
-            const float hlj = sm.hl[j], hwj = sm.hw[j];
-            const float rxq = (Px - xjh) + (qox - sm.xl[j]);
-            const float ryq = (Py - yjh) + (qoy - sm.yl[j]);
-            const float cj = sm.c[j], sj = sm.s[j];
-            const float pu = fabsf(fmaf(rxq, cj, ryq * sj));
-            const float pn = fabsf(fmaf(-rxq, sj, ryq * cj));
-            const float m = fminf(hlj + wi - pu, hwj + wi - pn);
-            const unsigned hits = __ballot_sync(kFull, m >= 0.f);
-            if (!hits) continue;
-            const float ddx = comp_diff(xjh, sm.xl[j], xih, xil);
-            const float ddy = comp_diff(yjh, sm.yl[j], yih, yil);
-            const float gap = fmaxf(p.gap_min, sqrtf(fmaf(ddx, ddx, ddy * ddy)) - (hli + hlj));
-            if (gap < gbest) {
-                gbest = gap;
-                lead = j;
-                lead_hit = __ffs(hits) - 1;
-            }
+            const bool two = cm != 0;
+            const int j2 = two ? jb + __ffs(cm) - 1 : j1;
+            if (two) cm &= cm - 1;
+            if (lane == 0) cnt.tests += two ? 64 : 32;
+            const bool in1 = box_hits(j1), in2 = box_hits(j2);
+            const unsigned h1 = __ballot_sync(kFull, in1);
+            const unsigned h2 = __ballot_sync(kFull, in2 && two);
+            if (h1) take(j1, h1);
+            if (h2) take(j2, h2);
         }
     }
 
@@ -331,8 +372,20 @@ static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N
     int sg;
     float ta;
     route_locate(sh, sl, p, P, sg, ta);
-    const float Qx = rx[sg], Qy = ry[sg];
-    const float ux = rx[sg + 1] - Qx, uy = ry[sg + 1] - Qy;
+    const int d = sg - seg0;  // the same in every lane
+    float Qx, Qy, Q1x, Q1y;
+    if (d >= 0 && d + 1 < kNear) {
+        Qx = __shfl_sync(kFull, nxp, d);
+        Qy = __shfl_sync(kFull, nyp, d);
+        Q1x = __shfl_sync(kFull, nxp, d + 1);
+        Q1y = __shfl_sync(kFull, nyp, d + 1);
+    } else {
+        Qx = rx[sg];
+        Qy = ry[sg];
+        Q1x = rx[sg + 1];
+        Q1y = ry[sg + 1];
+    }
+    const float ux = Q1x - Qx, uy = Q1y - Qy;
     if (lane == 0) {
         float xh, xe, yh, ye;
         two_sum(Qx, ta * ux, xh, xe);
@@ -453,26 +506,73 @@ __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* 
 // ---------------------------------------------------------------------------
 // Overlap, row i (warp): the SAT depth d_ij of every valid j > i, computed once
 // per unordered pair with i as the first box (the canonical order, so that
-// d_ij is one value for both agents).  Returns max_j d_ij of the row in every
-// lane and folds each d_ij into agent j's column maximum (ovk).  ov_i is
-// then max(row i, column i) = max over all valid j != i.
+// d_ij is one value for both agents), folded into both agents' maxima (ovk)
+// and partner keys (pk) by atomicMax.  ov_i = max over all valid j != i.
+//
+// Culling (exact): d_ij <= R_i + R_j - |c_j - c_i| / sqrt(2), where R = half
+// length + half width bounds the half diagonal (one of box i's two axes takes
+// at least |dc| / sqrt(2) of the centre distance).  lb_i <= ov_i is the depth
+// against last step's deepest partner, so a pair whose bound lies below both
+// lb_i and lb_j changes neither maximum and is skipped (1.5 mm of slack for
+// the float32 bound and the hi words used).
 // ---------------------------------------------------------------------------
-static __device__ float overlap_row(AgentSmem& sm, int N, int i, int lane, Counts& cnt) {
-    float best = -WSIM_INF;
+static __device__ void overlap_row(AgentSmem& sm, int N, int i, int lane, Counts& cnt) {
+    const float4 Pi = sm.obox[i];
     const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
     const float ci = sm.c[i], si = sm.s[i], hli = sm.hl[i], hwi = sm.hw[i];
+    float best = -WSIM_INF;
+    int bj = -1;
     for (int j = i + 1 + lane; j < N; j += 32) {
-        if (!sm.valid[j]) continue;
-        const float dx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
-        const float dy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
-        const float d = sat_depth(dx, dy, ci, si, hli, hwi, sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
-        best = fmaxf(best, d);
-        atomicMax(&sm.ovk[j], fkey(d));
+        const float4 Pj = sm.obox[j];  // invalid agents: R = -inf, always skipped
+        const float dx = Pj.x - Pi.x, dy = Pj.y - Pi.y;
+        const float t = fmaxf(Pi.w + Pj.z, Pi.z + Pj.w);  // |dc| / sqrt(2) above this: skip
+        if (!(t >= 0.f) || fmaf(dx, dx, dy * dy) > 2.f * t * t) continue;
+        const float ddx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
+        const float ddy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
+        const float d = sat_depth(ddx, ddy, ci, si, hli, hwi, sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
+        if (d > best) {
+            best = d;
+            bj = j;
+        }
+        atomicMax(&sm.ovk[j], ukey(d));
+        atomicMax(&sm.pk[j], partner_key(d, i));
         cnt.pairs += 2;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
-    return best;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(kFull, best, o);
+        const int oj = __shfl_xor_sync(kFull, bj, o);
+        if (ob > best || (ob == best && oj > bj)) {
+            best = ob;
+            bj = oj;
+        }
+    }
+    if (lane == 0 && bj >= 0) {
+        atomicMax(&sm.ovk[i], ukey(best));
+        atomicMax(&sm.pk[i], partner_key(best, bj));
+    }
+}
+
+// The culling records (thread per agent, before the rows): lb_i is the depth
+// of agent i against the partner its key names (the pair's canonical
+// evaluation), -inf without one; then the maxima are reset for this step.
+template <int NT>
+__device__ void overlap_bounds(AgentSmem& sm, int N) {
+    for (int i = threadIdx.x; i < N; i += NT) {
+        float lb = -WSIM_INF;
+        const int p = (sm.pk[i] >> 8) > (kNoDepth >> 8) ? static_cast<int>(sm.pk[i] & 0xffu) : -1;
+        if (sm.valid[i] && p >= 0 && p < N && p != i && sm.valid[p]) {
+            const int a = min(i, p), b = max(i, p);
+            const float dx = comp_diff(sm.xh[b], sm.xl[b], sm.xh[a], sm.xl[a]);
+            const float dy = comp_diff(sm.yh[b], sm.yl[b], sm.yh[a], sm.yl[a]);
+            lb = sat_depth(dx, dy, sm.c[a], sm.s[a], sm.hl[a], sm.hw[a], sm.c[b], sm.s[b], sm.hl[b], sm.hw[b]);
+        }
+        const float R = (sm.hl[i] + sm.hw[i]) * 1.000001f + 5e-4f;
+        sm.obox[i] = sm.valid[i] ? make_float4(sm.xh[i], sm.yh[i], R, R - lb + 5e-4f)
+                                 : make_float4(sm.xh[i], sm.yh[i], -WSIM_INF, -WSIM_INF);
+        sm.ovk[i] = kNoDepth;
+        sm.pk[i] = kNoDepth;
+    }
 }
 
 // Squared distance of point p to the chord of capsule record C (1/|chord|^2 = inv).
@@ -538,6 +638,7 @@ __device__ __forceinline__ void scan_next_two(const SegView& V, int lane, unsign
     const int t2 = __shfl_sync(kFull, tl_lane, l2);
     scan_pair(V, lane, t1, m1, t2, two ? m2 : 0u, xh, yh, cxl, cyl, bd, bi, cnt);
 }
+
 
 // ---------------------------------------------------------------------------
 // Off-road of agent i (warp; Sec. 3.4: the road lies left of an oriented road
@@ -891,11 +992,10 @@ __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_bas
                               float4* meta_base, int N, bool do_ov, bool do_off, Counts& cnt) {
     const int lane = threadIdx.x & 31;
     if (do_ov) {
-        for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane)) {
-            if (!sm.valid[i]) continue;
-            const float o = overlap_row(sm, N, i, lane, cnt);
-            if (lane == 0) sm.ov[i] = o;
-        }
+        overlap_bounds<NT>(sm, N);
+        __syncthreads();
+        for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane))
+            if (sm.valid[i]) overlap_row(sm, N, i, lane, cnt);
     }
     if (do_off) {
         for (int g = next_agent(sm, 2, lane); 8 * g < N; g = next_agent(sm, 2, lane))
@@ -903,8 +1003,8 @@ __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_bas
     }
 }
 
-// ov_i of a valid agent after phase_metrics: max(row i, column i).
-__device__ __forceinline__ float merged_ov(const AgentSmem& sm, int i) { return fmaxf(sm.ov[i], funkey(sm.ovk[i])); }
+// ov_i of a valid agent after phase_metrics.
+__device__ __forceinline__ float merged_ov(const AgentSmem& sm, int i) { return unukey(sm.ovk[i]); }
 
 // ---------------------------------------------------------------------------
 // Log divergence, flags, metric stores and the scene reward.

@@ -124,6 +124,8 @@ __global__ void __launch_bounds__(1024) k_static_offsets(const int32_t* agent_of
             if (s == S - 1) {
                 sc->seg_off[S] = e + padded;
                 sc->soff[S] = u + nsup;
+                // packed segments (runs padded to tiles) beyond the fixed arrays
+                if (static_cast<int64_t>(e) + padded > kStaticMaxSegs) atomicCAS(&sc->status, 0, WSIM_ESIZE);
             }
         }
     }
@@ -178,7 +180,7 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
     if (rc) return rc;
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, b->S, sc->seg_off,
                         sc->geo, sc->inv, sc->flags, s) != cudaSuccess ||
-        launch_tile_build(b->S, sc->seg_off, sc->seg_cnt, sc->geo, sc->tiles, s) != cudaSuccess ||
+        launch_tile_build(b->S, sc->seg_off, sc->seg_cnt, sc->geo, sc->flags, sc->tiles, s) != cudaSuccess ||
         launch_super_build(b->S, sc->seg_off, sc->seg_cnt, sc->soff, sc->tiles, sc->sup, s) != cudaSuccess)
         return WSIM_ECUDA;
 

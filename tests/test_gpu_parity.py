@@ -75,6 +75,27 @@ def test_uneven_batch_against_plain_and_oracle(wsim):
     print("uneven batch", c)
 
 
+def test_roadgraph_gaps_and_short_runs(wsim):
+    # Invalid points and type changes inside polylines split the road edges
+    # into many runs of 1 to a few segments; every run starts its own culling
+    # tile, with padding in between.  All launch shapes and the oracle agree.
+    b = synth.make_batch(0, seed=5, S=1, R=4000)
+    rng = np.random.default_rng(5)
+    b.rg_valid = (rng.random(b.R_tot) > 0.12).astype(np.uint8)
+    flip = rng.random(b.R_tot) < 0.05
+    b.rg_type = np.where(flip, 1 - b.rg_type, b.rg_type).astype(np.uint8)
+    g = H.run_rollout(b)
+    assert g["status"] == 0
+    for shape in range(3):
+        p = H.run_rollout(b, tuning=dict(single_shape=shape))
+        for k in ("traj", "off", "flags", "reward"):
+            assert np.array_equal(g[k].view(np.uint8), p[k].view(np.uint8)), (shape, k)
+    p = H.run_rollout(b, mode=wsim.MODE_PLAIN)
+    assert np.array_equal(g["off"].view(np.uint8), p["off"].view(np.uint8))
+    c = H.teacher_forced(b, g, [0], range(b.T))
+    print("gaps and short runs", c)
+
+
 def test_every_launch_configuration_bit_identical(wsim):
     # Uneven scenes span the three size buckets; every single launch shape
     # and every split configuration of the scene-resident rollout must give
