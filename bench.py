@@ -40,6 +40,9 @@ FLOPS_PER_TILE = 10      # culling-tile bound test
 FLOPS_PER_PAIR = 44      # ordered SAT pair
 FLOPS_PER_TEST = 16      # IDM look-ahead sample x box test
 FLOPS_PER_AGENT = 60     # dynamics + log divergence per agent-step
+FLOPS_PER_BOUND = 11     # overlap pair bound test (culling)
+FLOPS_PER_FILTER = 9     # IDM lead-candidate circle test
+FLOPS_PER_IDM_STEP = 800 # IDM agent-step: 32 look-ahead samples on the route, acceleration, advance
 
 
 def source_hash() -> str:
@@ -465,7 +468,9 @@ def main():
     # (each preceded by a 4-byte memset node, counted in the launch time)
     launch_ms = ms if fused else ms / T
     launches = T if not fused else (sum(1 for n in tune["bucket_scenes"] if n) if tune and tune["split"] else 1)
+    idm_steps = int(((b.kind == synth.KIND_IDM) & (b.valid != 0)).sum()) * T
     flops = (FLOPS_PER_EVAL * cnt[0] + FLOPS_PER_TILE * cnt[1] + FLOPS_PER_PAIR * cnt[2] + FLOPS_PER_TEST * cnt[3]
+             + FLOPS_PER_BOUND * cnt[4] + FLOPS_PER_FILTER * cnt[5] + FLOPS_PER_IDM_STEP * idm_steps
              + FLOPS_PER_AGENT * N * T) / launches
     achieved = flops / (launch_ms / 1e3) / 1e12
     line = {
@@ -478,7 +483,9 @@ def main():
                      "peak_source": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz",
                      "flops_per_launch": flops, "launch_ms": launch_ms,
                      "counts_per_rollout": {"corner_segment_evals": int(cnt[0]), "tile_tests": int(cnt[1]),
-                                            "sat_pairs": int(cnt[2]), "idm_sample_tests": int(cnt[3])}},
+                                            "sat_pairs": int(cnt[2]), "idm_sample_tests": int(cnt[3]),
+                                            "pair_bound_tests": int(cnt[4]), "idm_circle_tests": int(cnt[5]),
+                                            "idm_agent_steps": idm_steps}},
         "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": args.steps * launches,

@@ -206,22 +206,25 @@ int wsim_rollout(wsim_ctx *ctx, wsim_state *st, const float *act_seq, const uint
 int wsim_expert_actions(wsim_ctx *ctx, int t0, int T, float *act_out, void *stream);
 
 /* Launch configuration of the scene-resident rollout (WSIM_MODE_FUSED).
- * Three launch shapes exist: 0 = 512 threads, one CTA per SM, large
- * shared-memory stage for the scene's road-edge segments; 1 = 256 threads,
- * two CTAs per SM, small stage; 2 = 256 threads, four CTAs per SM, segments
- * read from global memory (L2).  Scenes are grouped at wsim_init into size
- * buckets by road-edge segment count: bucket 0 fits the small stage, bucket
- * 1 the large one, bucket 2 neither.  Either one shape runs the whole
- * cost-ordered batch (split = 0, single_shape) or each bucket runs its own
- * shape on its own stream, concurrently (split = 1, bucket_shape).  Every
- * configuration gives bit-identical results. */
+ * Five launch shapes exist (threads per CTA x CTAs per SM, where the
+ * scene's road-edge segments are read from): 0 = 512 x 1, large
+ * shared-memory stage; 1 = 256 x 2, small stage; 2 = 256 x 4, global memory
+ * (L2); 3 = 512 x 2, global memory; 4 = 512 x 2, small stage.  Scenes are
+ * grouped at wsim_init into size buckets by road-edge segment count: bucket
+ * 0 fits the small stage, bucket 1 the large one, bucket 2 neither.  Either
+ * one shape runs the whole cost-ordered batch (split = 0, single_shape) or
+ * each bucket runs its own shape on its own stream, concurrently (split = 1,
+ * bucket_shape).  A staged shape reads a scene that does not fit its stage
+ * from global memory.  Every configuration gives bit-identical results. */
+#define WSIM_ROLL_SHAPES 5
+#define WSIM_BUCKETS 3
 typedef struct {
     int32_t split;            /* 0: one launch of single_shape; 1: per bucket   */
     int32_t single_shape;
-    int32_t bucket_shape[3];
-    int32_t bucket_scenes[3]; /* filled by wsim_get_tuning / wsim_autotune      */
-    float ms_single[3];       /* wsim_autotune: T-step time of each shape       */
-    float ms_bucket[3][3];    /* ... of each shape on each bucket alone (-1: n/a) */
+    int32_t bucket_shape[WSIM_BUCKETS];
+    int32_t bucket_scenes[WSIM_BUCKETS]; /* filled by wsim_get_tuning / wsim_autotune */
+    float ms_single[WSIM_ROLL_SHAPES];   /* wsim_autotune: T-step time of each shape */
+    float ms_bucket[WSIM_BUCKETS][WSIM_ROLL_SHAPES]; /* ... of each shape on each bucket alone (-1: n/a) */
     float ms_split;           /* ... of the split configuration (-1: n/a)       */
 } wsim_tuning;
 
@@ -267,9 +270,12 @@ int wsim_status(wsim_ctx *ctx, int *device_status, void *stream);
 /* Work counters of the last rollout (for roofline accounting; 0 unless
  * wsim_set_counting(ctx, 1) was called before it): [0] corner-segment
  * distance evaluations, [1] culling-tile bound tests, [2] SAT pair
- * evaluations, [3] IDM look-ahead sample-box tests.  Synchronises. */
+ * evaluations (each unordered pair counts 2), [3] IDM look-ahead sample-box
+ * tests, [4] overlap pair bound tests, [5] IDM lead-candidate circle tests.
+ * Synchronises. */
+#define WSIM_COUNTERS 6
 int wsim_set_counting(wsim_ctx *ctx, int on);
-int wsim_counters(wsim_ctx *ctx, int64_t out[4], void *stream);
+int wsim_counters(wsim_ctx *ctx, int64_t out[WSIM_COUNTERS], void *stream);
 
 /* Message for a WSIM_E* code. */
 const char *wsim_strerror(int code);

@@ -22,15 +22,15 @@ struct wsim_ctx {
     Params p;
     int S = 0, N_tot = 0, grid = 1, count = 0;
     // scene-resident rollout: scenes in size buckets, each with a launch shape
-    int shape_cap[kRollShapes] = {0, 0, 0};   // staged segments per shape
-    int shape_grid[kRollShapes] = {1, 1, 1};  // persistent grid per shape
-    int bucket_n[kRollShapes] = {0, 0, 0};    // scenes per bucket
-    int bucket_at[kRollShapes] = {0, 0, 0};   // first entry of the bucket in border
-    int bucket_shape[kRollShapes] = {1, 0, 2};
-    int split = 0, single_shape = 0;          // one launch of single_shape, or one per bucket
-    int32_t* border = nullptr;                // cost-ordered scene ids, grouped by bucket
-    cudaStream_t side[kRollShapes] = {nullptr, nullptr, nullptr};
-    cudaEvent_t fork = nullptr, join[kRollShapes] = {nullptr, nullptr, nullptr};
+    int shape_cap[kRollShapes] = {};   // staged segments per shape
+    int shape_grid[kRollShapes] = {};  // persistent grid per shape
+    int bucket_n[kBuckets] = {};       // scenes per bucket
+    int bucket_at[kBuckets] = {};      // first entry of the bucket in border
+    int bucket_shape[kBuckets] = {4, 0, 3};
+    int split = 0, single_shape = 0;   // one launch of single_shape, or one per bucket
+    int32_t* border = nullptr;         // cost-ordered scene ids, grouped by bucket
+    cudaStream_t side[kBuckets] = {};
+    cudaEvent_t fork = nullptr, join[kBuckets] = {};
     std::vector<int32_t> h_agent_off;
     // device scratch owned by the context
     int32_t *seg_off = nullptr, *seg_cnt = nullptr, *order = nullptr, *queue = nullptr, *status = nullptr;
@@ -201,9 +201,12 @@ int enqueue_rollout(wsim_ctx* c, const RolloutKey& k, bool plain, cudaStream_t s
     return WSIM_OK;
 }
 
-// Scene-resident rollout.  how: -1 = the context's configuration; 0..2 =
-// whole batch with that shape; 3 = split with the context's bucket shapes;
-// 10 + 3*b + shape = bucket b alone with that shape.
+// Scene-resident rollout.  how: -1 = the context's configuration; a shape =
+// whole batch with that shape; kHowSplit = one launch per bucket with the
+// context's bucket shapes, concurrently; kHowBucket + kRollShapes*b + shape
+// = bucket b alone with that shape.
+constexpr int kHowSplit = 100, kHowBucket = 1000;
+
 int enqueue_fused(wsim_ctx* c, const wsim_state* st, const float* act_seq, const uint8_t* ctrl, int t0, int T,
                   const wsim_metric_buf* mseq, const wsim_state* traj, int how, cudaStream_t s) {
     StepArgs a = base_args(c);
@@ -217,8 +220,8 @@ int enqueue_fused(wsim_ctx* c, const wsim_state* st, const float* act_seq, const
     if (traj) a.traj = mstate(traj);
     a.do_transition = 1;
     a.do_metrics = 1;
-    if (how < 0) how = c->split ? 3 : c->single_shape;
-    CK(cudaMemsetAsync(c->queue, 0, kRollShapes * sizeof(int32_t), s));
+    if (how < 0) how = c->split ? kHowSplit : c->single_shape;
+    CK(cudaMemsetAsync(c->queue, 0, kBuckets * sizeof(int32_t), s));
     if (how < kRollShapes) {  // whole batch, one shape
         a.order = c->order;
         a.n_work = c->S;
@@ -227,14 +230,14 @@ int enqueue_fused(wsim_ctx* c, const wsim_state* st, const float* act_seq, const
         CK(launch_rollout(how, a, std::min(c->S, c->shape_grid[how]), s));
         return WSIM_OK;
     }
-    const bool split = how == 3;
+    const bool split = how == kHowSplit;
     if (split) CK(cudaEventRecord(c->fork, s));
-    for (int bk = 0; bk < kRollShapes; ++bk) {
+    for (int bk = 0; bk < kBuckets; ++bk) {
         if (c->bucket_n[bk] == 0) continue;
         int sh = c->bucket_shape[bk];
         if (!split) {
-            if ((how - 10) / kRollShapes != bk) continue;
-            sh = (how - 10) % kRollShapes;
+            if ((how - kHowBucket) / kRollShapes != bk) continue;
+            sh = (how - kHowBucket) % kRollShapes;
         }
         a.order = c->border + c->bucket_at[bk];
         a.n_work = c->bucket_n[bk];
@@ -341,7 +344,7 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     };
     if ((rc = dalloc(&c->seg_off, S + 1)) || (rc = dalloc(&c->seg_cnt, S)) || (rc = dalloc(&c->order, S)) ||
         (rc = dalloc(&c->border, S)) ||
-        (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->counters, 4)) ||
+        (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->counters, kCounters)) ||
         (rc = dalloc(&c->tmp, static_cast<size_t>(N) * 10)) || (rc = ensure_queue(c, 128)) ||
         (rc = dalloc(&c->hint, static_cast<size_t>(N) * 4)) ||
         (rc = dalloc(&c->tlist, static_cast<size_t>(N) * kList)) || (rc = dalloc(&c->tmeta, static_cast<size_t>(N))))
@@ -351,7 +354,7 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
         cudaMemsetAsync(c->tmeta, 0xff, std::max<size_t>(N, 1) * sizeof(float4), st) != cudaSuccess)
         return fail(WSIM_ECUDA);
     if (cudaMemsetAsync(c->status, 0, sizeof(int32_t), st) != cudaSuccess ||
-        cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), st) != cudaSuccess)
+        cudaMemsetAsync(c->counters, 0, kCounters * sizeof(unsigned long long), st) != cudaSuccess)
         return fail(WSIM_ECUDA);
 
     // Road-edge segments: count, pad each scene to kSegAlign, pack.
@@ -405,12 +408,12 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     c->grid = std::min(S, sms * step_blocks_per_sm());
     // Scene-resident rollout.  Buckets by staged size: 0 = fits the small
-    // stage (shape 1), 1 = fits the large stage (shape 0), 2 = neither.
+    // stage (shapes 1 and 4), 1 = fits the large stage (shape 0), 2 = neither.
     int need = 0;
     for (int s = 0; s < S; ++s) need = std::max(need, off[s + 1] - off[s]);
     for (int sh = 0; sh < kRollShapes; ++sh) c->shape_cap[sh] = std::min(need, shape_max_seg_cap(sh));
     std::vector<int32_t> border;
-    for (int bk = 0; bk < kRollShapes; ++bk) {
+    for (int bk = 0; bk < kBuckets; ++bk) {
         c->bucket_at[bk] = static_cast<int>(border.size());
         for (int w = 0; w < S; ++w) {
             const int s = order[w], segs = off[s + 1] - off[s];
@@ -430,13 +433,13 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess)
         return fail(WSIM_ECUDA);
-    for (int b = 0; b < kRollShapes; ++b)
+    for (int b = 0; b < kBuckets; ++b)
         if (cudaStreamCreateWithFlags(&c->side[b], cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->join[b], cudaEventDisableTiming) != cudaSuccess)
             return fail(WSIM_ECUDA);
-    // Default until tuned: one launch with the large stage if any scene uses
-    // it, else the small-stage shape.
-    c->single_shape = c->bucket_n[1] + c->bucket_n[2] > 0 ? 0 : 1;
+    // Default until tuned: one launch of 512 x 2 CTAs per SM, with the scenes'
+    // segments staged in shared memory if every scene fits the stage.
+    c->single_shape = c->bucket_n[1] + c->bucket_n[2] > 0 ? 3 : 4;
     c->last = st;
     *out = c;
     return WSIM_OK;
@@ -573,13 +576,13 @@ int wsim_autotune(wsim_ctx* c, const wsim_state* st, const float* act_seq, int t
         }
     }
     int used = 0;
-    for (int bk = 0; bk < kRollShapes; ++bk) {
+    for (int bk = 0; bk < kBuckets; ++bk) {
         out->bucket_scenes[bk] = c->bucket_n[bk];
         float bb = 1e30f;
         for (int sh = 0; sh < kRollShapes; ++sh) {
             out->ms_bucket[bk][sh] = -1.f;
             if (!c->bucket_n[bk] || rc) continue;
-            timeit(10 + kRollShapes * bk + sh, &out->ms_bucket[bk][sh]);
+            timeit(kHowBucket + kRollShapes * bk + sh, &out->ms_bucket[bk][sh]);
             if (!rc && out->ms_bucket[bk][sh] < bb) {
                 bb = out->ms_bucket[bk][sh];
                 c->bucket_shape[bk] = sh;
@@ -589,19 +592,19 @@ int wsim_autotune(wsim_ctx* c, const wsim_state* st, const float* act_seq, int t
     }
     out->ms_split = -1.f;
     if (used > 1 && !rc) {
-        timeit(3, &out->ms_split);
+        timeit(kHowSplit, &out->ms_split);
         if (!rc && out->ms_split < best) {
             best = out->ms_split;
-            best_how = 3;
+            best_how = kHowSplit;
         }
     }
     if (!rc) {
-        c->split = best_how == 3;
+        c->split = best_how == kHowSplit;
         if (!c->split) c->single_shape = best_how;
     }
     out->split = c->split;
     out->single_shape = c->single_shape;
-    for (int bk = 0; bk < kRollShapes; ++bk) out->bucket_shape[bk] = c->bucket_shape[bk];
+    for (int bk = 0; bk < kBuckets; ++bk) out->bucket_shape[bk] = c->bucket_shape[bk];
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
     cudaStreamSynchronize(s);
@@ -613,11 +616,11 @@ int wsim_autotune(wsim_ctx* c, const wsim_state* st, const float* act_seq, int t
 int wsim_set_tuning(wsim_ctx* c, const wsim_tuning* t) {
     if (!c || !t) return WSIM_EINVAL;
     if (t->single_shape < 0 || t->single_shape >= kRollShapes) return WSIM_EINVAL;
-    for (int b = 0; b < kRollShapes; ++b)
+    for (int b = 0; b < kBuckets; ++b)
         if (t->bucket_shape[b] < 0 || t->bucket_shape[b] >= kRollShapes) return WSIM_EINVAL;
     c->split = t->split ? 1 : 0;
     c->single_shape = t->single_shape;
-    for (int b = 0; b < kRollShapes; ++b) c->bucket_shape[b] = t->bucket_shape[b];
+    for (int b = 0; b < kBuckets; ++b) c->bucket_shape[b] = t->bucket_shape[b];
     return WSIM_OK;
 }
 
@@ -626,10 +629,10 @@ int wsim_get_tuning(wsim_ctx* c, wsim_tuning* out) {
     std::memset(out, 0, sizeof(*out));
     out->split = c->split;
     out->single_shape = c->single_shape;
-    for (int b = 0; b < kRollShapes; ++b) {
+    for (int k = 0; k < kRollShapes; ++k) out->ms_single[k] = -1.f;
+    for (int b = 0; b < kBuckets; ++b) {
         out->bucket_shape[b] = c->bucket_shape[b];
         out->bucket_scenes[b] = c->bucket_n[b];
-        out->ms_single[b] = -1.f;
         for (int k = 0; k < kRollShapes; ++k) out->ms_bucket[b][k] = -1.f;
     }
     out->ms_split = -1.f;
@@ -701,17 +704,17 @@ int wsim_set_counting(wsim_ctx* c, int on) {
         c->exec = nullptr;
         c->have_key = false;
     }
-    CK(cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), c->last));
+    CK(cudaMemsetAsync(c->counters, 0, kCounters * sizeof(unsigned long long), c->last));
     return WSIM_OK;
 }
 
-int wsim_counters(wsim_ctx* c, int64_t out[4], void* stream) {
+int wsim_counters(wsim_ctx* c, int64_t out[WSIM_COUNTERS], void* stream) {
     if (!c || !out) return WSIM_EINVAL;
-    unsigned long long v[4];
+    unsigned long long v[kCounters];
     cudaStream_t s = S_(stream);
     CK(cudaMemcpyAsync(v, c->counters, sizeof(v), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    for (int k = 0; k < 4; ++k) out[k] = static_cast<int64_t>(v[k]);
+    for (int k = 0; k < kCounters; ++k) out[k] = static_cast<int64_t>(v[k]);
     return WSIM_OK;
 }
 
@@ -721,7 +724,7 @@ void wsim_destroy(wsim_ctx* c) {
     if (c->exec) cudaGraphExecDestroy(c->exec);
     if (c->cap) cudaStreamDestroy(c->cap);
     if (c->fork) cudaEventDestroy(c->fork);
-    for (int b = 0; b < kRollShapes; ++b) {
+    for (int b = 0; b < kBuckets; ++b) {
         if (c->side[b]) cudaStreamDestroy(c->side[b]);
         if (c->join[b]) cudaEventDestroy(c->join[b]);
     }

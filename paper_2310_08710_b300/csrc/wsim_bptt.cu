@@ -294,7 +294,7 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int s
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NTb) k_bptt(const BpttArgs B) {
+__global__ void __launch_bounds__(NTb, 2) k_bptt(const BpttArgs B) {
     __shared__ AgentSmem sm;
     __shared__ AdjSmem adj;
     init_cta(sm);

@@ -9,7 +9,8 @@ namespace wsim {
 
 constexpr int kMaxN = WSIM_MAX_AGENTS;  // agents per scene
 constexpr int kStepThreads = 256;       // threads per CTA of the per-step kernels
-constexpr int kRollShapes = 3;          // launch shapes of the scene-resident rollout kernel
+constexpr int kRollShapes = WSIM_ROLL_SHAPES;  // launch shapes of the scene-resident rollout kernel
+constexpr int kBuckets = WSIM_BUCKETS;          // scene-size buckets of the rollout work list
 constexpr int kTile = 16;               // road-edge segments per culling tile (half a warp)
 constexpr int kSegAlign = kTile;        // per-scene segment arrays start on a tile boundary
 constexpr int kSuper = 8;               // tiles per super-tile (first culling level)
@@ -17,6 +18,7 @@ constexpr int kList = 32;               // tiles in an agent's cached candidate 
 constexpr float kSkin = 8.0f;           // extra radius of a candidate list beyond the current need (m)
 constexpr float kSkinSmall = 2.0f;      // fallback when the kSkin list would not fit in kList tiles
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
+constexpr int kCounters = WSIM_COUNTERS;         // work counters (wsim_counters)
 
 // Packed road-edge segments of the whole batch (built by wsim_init).  Scene s
 // owns positions [off[s], off[s] + cnt[s]); off[s] is a multiple of kTile.
@@ -83,7 +85,7 @@ struct StepArgs {
     const int32_t* order;  // cost-ordered scene ids
     int32_t* queue;        // scene work counter (zeroed before each launch)
     int32_t* status;       // sticky device status
-    unsigned long long* counters;  // [4] work counters (when count != 0)
+    unsigned long long* counters;  // [kCounters] work counters (when count != 0)
     int count;
     int seg_cap;           // rollout: segments that fit in the shared-memory stage
     Params p;
@@ -105,9 +107,10 @@ cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_expert_actions(const StepArgs& a, int t0, int T, float* act, cudaStream_t st);
 cudaError_t launch_plain_scene(const StepArgs& a, int scene, cudaStream_t st);
 int step_blocks_per_sm();
-// Scene-resident rollout, launch shape 0 (512 threads, 1 CTA/SM, large stage),
-// 1 (256 threads, 2 CTAs/SM, small stage) or 2 (256 threads, 4 CTAs/SM, no
-// stage).  seg_cap: staged segments (a.seg_cap at launch).
+// Scene-resident rollout, launch shapes (threads x CTAs per SM, stage): 0
+// 512 x 1 large stage, 1 256 x 2 small stage, 2 256 x 4 no stage, 3 512 x 2
+// no stage, 4 512 x 2 small stage.  seg_cap: staged segments (a.seg_cap at
+// launch).
 int shape_max_seg_cap(int shape);
 cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm);
 cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st);

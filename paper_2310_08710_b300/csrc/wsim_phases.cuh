@@ -13,7 +13,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 struct __align__(16) AgentSmem {
     uint64_t bar[2];
-    unsigned long long cnt[4];
+    unsigned long long cnt[kCounters];
     // current state (t during the transition, t+1 after the writeback)
     float xh[kMaxN], xl[kMaxN], yh[kMaxN], yl[kMaxN], c[kMaxN], s[kMaxN], hl[kMaxN], hw[kMaxN];
     float vx[kMaxN], vy[kMaxN], thh[kMaxN], thl[kMaxN], sh[kMaxN], sl[kMaxN];
@@ -34,7 +34,8 @@ struct __align__(16) AgentSmem {
 
 // Work counters of one thread (flushed into the CTA's AgentSmem::cnt).
 struct Counts {
-    unsigned long long evals = 0, tiles = 0, pairs = 0, tests = 0;
+    // 32 bits per thread: a thread's share of one launch stays far below 2^32
+    uint32_t evals = 0, tiles = 0, pairs = 0, tests = 0, bounds = 0, filters = 0;
 };
 
 // One scene's packed road-edge segments, in global or shared memory.
@@ -326,6 +327,7 @@ static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N
             yj = sm.yh[jl];
             reach = sm.hl[jl] + sm.hw[jl];
         }
+        cnt.filters += 4;
 #pragma unroll
         for (int G = 0; G < 4; ++G) {
             const float ex = xj - __shfl_sync(kFull, gcx, 8 * G), ey = yj - __shfl_sync(kFull, gcy, 8 * G);
@@ -524,6 +526,7 @@ static __device__ void overlap_row(AgentSmem& sm, int N, int i, int lane, Counts
     int bj = -1;
     for (int j = i + 1 + lane; j < N; j += 32) {
         const float4 Pj = sm.obox[j];  // invalid agents: R = -inf, always skipped
+        cnt.bounds += 1;
         const float dx = Pj.x - Pi.x, dy = Pj.y - Pi.y;
         const float t = fmaxf(Pi.w + Pj.z, Pi.z + Pj.w);  // |dc| / sqrt(2) above this: skip
         if (!(t >= 0.f) || fmaf(dx, dx, dy * dy) > 2.f * t * t) continue;
@@ -1048,21 +1051,21 @@ __device__ __forceinline__ void init_cta(AgentSmem& sm) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
         fence_mbar_init();
-        for (int k = 0; k < 4; ++k) sm.cnt[k] = 0;
+        for (int k = 0; k < kCounters; ++k) sm.cnt[k] = 0;
     }
     __syncthreads();
 }
 
 __device__ __forceinline__ void publish_counts(AgentSmem& sm, const StepArgs& A, const Counts& c) {
     if (A.count) {
-        if (c.evals) atomicAdd(&sm.cnt[0], c.evals);
-        if (c.tiles) atomicAdd(&sm.cnt[1], c.tiles);
-        if (c.pairs) atomicAdd(&sm.cnt[2], c.pairs);
-        if (c.tests) atomicAdd(&sm.cnt[3], c.tests);
+        const uint32_t v[kCounters] = {c.evals, c.tiles, c.pairs, c.tests, c.bounds, c.filters};
+#pragma unroll
+        for (int k = 0; k < kCounters; ++k)
+            if (v[k]) atomicAdd(&sm.cnt[k], static_cast<unsigned long long>(v[k]));
     }
     __syncthreads();
     if (A.count && threadIdx.x == 0)
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < kCounters; ++k)
             if (sm.cnt[k]) atomicAdd(&A.counters[k], sm.cnt[k]);
 }
 

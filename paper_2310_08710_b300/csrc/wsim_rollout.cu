@@ -15,6 +15,8 @@
 //
 // Launch shapes (threads per CTA x resident CTAs per SM, staged or not) are
 // picked per scene-size bucket; wsim_autotune times them on the workload.
+// Fewer, larger CTAs keep the same warps per SM with fewer resident scenes,
+// whose route and segment data then stay in L2 between steps.
 #include "wsim_phases.cuh"
 
 namespace wsim {
@@ -28,7 +30,8 @@ struct ShapeDesc {
     int threads, min_blocks;
     bool stage;
 };
-constexpr ShapeDesc kShapes[kRollShapes] = {{512, 1, true}, {256, 2, true}, {256, 4, false}};
+constexpr ShapeDesc kShapes[kRollShapes] = {
+    {512, 1, true}, {256, 2, true}, {256, 4, false}, {512, 2, false}, {512, 2, true}};
 
 __device__ __forceinline__ StateP offset_state(const StateP& s, size_t k) {
     return StateP{s.x + k, s.y + k, s.x_lo + k, s.y_lo + k, s.th + k,
@@ -115,7 +118,8 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
 
 using KernelFn = void (*)(StepArgs);
 constexpr KernelFn kKernels[kRollShapes] = {k_rollout<512, 1, true>, k_rollout<256, 2, true>,
-                                            k_rollout<256, 4, false>};
+                                            k_rollout<256, 4, false>, k_rollout<512, 2, false>,
+                                            k_rollout<512, 2, true>};
 
 static size_t stage_bytes(int seg_cap) {
     const size_t nt = static_cast<size_t>(seg_cap / kTile);

@@ -22,6 +22,7 @@ OK, EINVAL, ESIZE, ECUDA, ENONFINITE, ETIMEOUT, ENOMEM, ESTATE = 0, -1, -2, -3, 
 MODE_GRAPH, MODE_STREAM, MODE_PLAIN, MODE_FUSED = 0, 1, 2, 3
 GRAD_PLAIN = 1
 MAX_AGENTS = 256
+COUNTERS = 6  # wsim_counters: evals, tile tests, SAT pairs, IDM sample tests, pair bound tests, IDM circle tests
 FLAG_COLLISION, FLAG_OFFROAD, FLAG_KININF = 1, 2, 4
 CTRL_HOLD, CTRL_ACTION, CTRL_EXPERT, CTRL_LOG = 0, 1, 2, 3
 
@@ -56,10 +57,13 @@ class WsimState(C.Structure):
     _fields_ = [(k, C.c_void_p) for k in STATE_FIELDS]
 
 
+ROLL_SHAPES, BUCKETS = 5, 3
+
+
 class WsimTuning(C.Structure):
-    _fields_ = [("split", C.c_int32), ("single_shape", C.c_int32), ("bucket_shape", C.c_int32 * 3),
-                ("bucket_scenes", C.c_int32 * 3), ("ms_single", C.c_float * 3), ("ms_bucket", (C.c_float * 3) * 3),
-                ("ms_split", C.c_float)]
+    _fields_ = [("split", C.c_int32), ("single_shape", C.c_int32), ("bucket_shape", C.c_int32 * BUCKETS),
+                ("bucket_scenes", C.c_int32 * BUCKETS), ("ms_single", C.c_float * ROLL_SHAPES),
+                ("ms_bucket", (C.c_float * ROLL_SHAPES) * BUCKETS), ("ms_split", C.c_float)]
 
     def as_dict(self) -> dict:
         return {"split": bool(self.split), "single_shape": self.single_shape,
@@ -250,7 +254,7 @@ class Sim:
                "wsim_autotune")
         return t.as_dict()
 
-    def set_tuning(self, split: bool = False, single_shape: int = 0, bucket_shape=(1, 0, 2)):
+    def set_tuning(self, split: bool = False, single_shape: int = 3, bucket_shape=(4, 0, 3)):
         t = WsimTuning()
         t.split, t.single_shape = int(split), single_shape
         for i, v in enumerate(bucket_shape):
@@ -292,7 +296,7 @@ class Sim:
         _check(lib.wsim_set_counting(self._h, int(on)), "wsim_set_counting")
 
     def counters(self, stream=None) -> np.ndarray:
-        out = (C.c_int64 * 4)()
+        out = (C.c_int64 * COUNTERS)()
         _check(lib.wsim_counters(self._h, out, _stream(stream)), "wsim_counters")
         return np.array(out[:], dtype=np.int64)
 

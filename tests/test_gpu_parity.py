@@ -15,6 +15,7 @@ from tests import gpu_harness as H
 from tests.scenes import straight_route, tiny_batch
 
 pytestmark = pytest.mark.gpu
+SHAPES = 5  # launch shapes of the scene-resident rollout
 
 
 @pytest.fixture(scope="module")
@@ -86,7 +87,7 @@ def test_roadgraph_gaps_and_short_runs(wsim):
     b.rg_type = np.where(flip, 1 - b.rg_type, b.rg_type).astype(np.uint8)
     g = H.run_rollout(b)
     assert g["status"] == 0
-    for shape in range(3):
+    for shape in range(SHAPES):
         p = H.run_rollout(b, tuning=dict(single_shape=shape))
         for k in ("traj", "off", "flags", "reward"):
             assert np.array_equal(g[k].view(np.uint8), p[k].view(np.uint8)), (shape, k)
@@ -107,8 +108,8 @@ def test_every_launch_configuration_bit_identical(wsim):
     print("buckets", info)
     assert sum(info["bucket_scenes"]) == b.S and min(info["bucket_scenes"][:2]) > 0
     ref = H.run_rollout(b, mode=wsim.MODE_GRAPH)
-    configs = [dict(split=False, single_shape=sh) for sh in range(3)]
-    configs += [dict(split=True, bucket_shape=(sh, (sh + 1) % 3, (sh + 2) % 3)) for sh in range(3)]
+    configs = [dict(split=False, single_shape=sh) for sh in range(SHAPES)]
+    configs += [dict(split=True, bucket_shape=(sh, (sh + 1) % SHAPES, (sh + 2) % SHAPES)) for sh in range(SHAPES)]
     for tun in configs:
         g = H.run_rollout(b, mode=wsim.MODE_FUSED, tuning=tun)
         for k in ("traj", "final", "ov", "off", "logdiv", "flags", "reward"):
@@ -127,7 +128,7 @@ def test_autotune_keeps_results(wsim):
     assert torch.equal(st.data, wsim.State.from_batch(b).data)  # input state untouched
     singles = [v for v in res["ms_single"] if v >= 0]
     chosen = res["ms_split"] if res["split"] else res["ms_single"][res["single_shape"]]
-    assert len(singles) == 3 and chosen <= min(singles + ([res["ms_split"]] if res["ms_split"] >= 0 else []))
+    assert len(singles) == SHAPES and chosen <= min(singles + ([res["ms_split"]] if res["ms_split"] >= 0 else []))
     tun = dict(split=res["split"], single_shape=res["single_shape"], bucket_shape=res["bucket_shape"])
     sim.close()
     g1 = H.run_rollout(b)
