@@ -29,7 +29,7 @@ def build(force: bool = False) -> str:
     stale = not os.path.exists(_SO) or os.path.getmtime(_SO) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "oracle.h")))
     if force or stale:
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", _SO, _SRC])
     return _SO
 
@@ -76,6 +76,8 @@ def lib():
         _lib.oracle_rollout.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp, _u8p,
                                         C.c_int, C.c_int, P(ObMetrics), C.c_int]
         _lib.oracle_inverse.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), P(ObState), _dp]
+        _lib.oracle_observe.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _u8p, C.c_int,
+                                        C.c_int, _dp, _u8p, _dp, _i32p]
         _lib.oracle_expert_actions.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, C.c_int, C.c_int,
                                                _dp]
         _lib.oracle_box_depth.argtypes = [_dp, _dp]
@@ -252,6 +254,23 @@ class Oracle:
                                   C.byref(self._cstate(c)), _ptr(out, _dp))
         if rc:
             raise RuntimeError("oracle_inverse failed")
+        return out
+
+    def observe(self, st: dict, M: int, K: int, observers=None, scenes=None) -> dict:
+        """Observation of state st (Sec. 3.2): agents [N_tot, M, 5] and
+        agents_valid [N_tot, M]; rg [N_tot, K, 2] and rg_idx [N_tot, K]
+        (rows of non-observers zero / -1)."""
+        N = self.b.N_tot
+        s0, s1 = self._scenes(scenes)
+        st = {k: _f64(st[k]) for k in STATE_KEYS}
+        out = dict(agents=np.zeros((N, M, 5)), agents_valid=np.zeros((N, M), np.uint8),
+                   rg=np.zeros((N, K, 2)), rg_idx=np.full((N, K), -1, np.int32))
+        obs = None if observers is None else np.ascontiguousarray(observers, np.uint8)
+        rc = lib().oracle_observe(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(st)),
+                                  None if obs is None else _ptr(obs, _u8p), M, K, _ptr(out["agents"], _dp),
+                                  _ptr(out["agents_valid"], _u8p), _ptr(out["rg"], _dp), _ptr(out["rg_idx"], _i32p))
+        if rc:
+            raise RuntimeError("oracle_observe failed")
         return out
 
     def expert_actions(self, t0: int, T: int, scenes=None) -> np.ndarray:

@@ -678,6 +678,63 @@ int oracle_rollout(const ob_params* p, const ob_batch* b, int s0, int s1, ob_sta
     return status;
 }
 
+int oracle_observe(const ob_params* p, const ob_batch* b, int s0, int s1, const ob_state* st,
+                   const uint8_t* observers, int M, int K, double* agents, uint8_t* agents_valid,
+                   double* rg, int32_t* rg_idx) {
+    (void)p;
+    if (!b || !st || !agents || !agents_valid || !rg || !rg_idx || K < 1 || s0 < 0 || s1 > b->S || s0 > s1)
+        return -1;
+    for (int s = s0; s < s1; ++s) {
+        const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1];
+        const int r0 = b->rg_off[s], r1 = b->rg_off[s + 1];
+        if (a1 - a0 > M) return -1;
+        for (int g = a0; g < a1; ++g) {
+            if (observers ? !observers[g] : !b->valid[g]) continue;
+            const double cx = st->x[g], cy = st->y[g], th = st->th[g];
+            const double c = std::cos(th), sn = std::sin(th);
+            // Other agents in g's frame: rotate (p - c) by -theta_g.
+            for (int j = 0; j < M; ++j) {
+                double* o = agents + ((size_t)g * M + j) * 5;
+                const int q = a0 + j;
+                const bool ok = q < a1 && q != g && b->valid[q];
+                agents_valid[(size_t)g * M + j] = ok;
+                for (int k = 0; k < 5; ++k) o[k] = 0.0;
+                if (!ok) continue;
+                const double dx = st->x[q] - cx, dy = st->y[q] - cy;
+                o[0] = c * dx + sn * dy;
+                o[1] = -sn * dx + c * dy;
+                o[2] = std::remainder(st->th[q] - th, kTwoPi);
+                o[3] = c * st->vx[q] + sn * st->vy[q];
+                o[4] = -sn * st->vx[q] + c * st->vy[q];
+            }
+            // The K nearest valid roadgraph points by the float32 key.
+            const float fx = (float)cx, fy = (float)cy;
+            std::vector<std::pair<float, int>> cand;
+            for (int r = r0; r < r1; ++r) {
+                if (!b->rg_valid[r]) continue;
+                const float dxf = (float)b->rg_x[r] - fx, dyf = (float)b->rg_y[r] - fy;
+                const float dyy = dyf * dyf;
+                cand.push_back({std::fmaf(dxf, dxf, dyy), r});
+            }
+            std::sort(cand.begin(), cand.end());  // key, then index
+            for (int k = 0; k < K; ++k) {
+                double* o = rg + ((size_t)g * K + k) * 2;
+                if (k < (int)cand.size()) {
+                    const int r = cand[k].second;
+                    const double dx = b->rg_x[r] - cx, dy = b->rg_y[r] - cy;
+                    o[0] = c * dx + sn * dy;
+                    o[1] = -sn * dx + c * dy;
+                    rg_idx[(size_t)g * K + k] = r;
+                } else {
+                    o[0] = o[1] = 0.0;
+                    rg_idx[(size_t)g * K + k] = -1;
+                }
+            }
+        }
+    }
+    return 0;
+}
+
 double oracle_box_depth(const double* A, const double* B) {
     Box<double> a = make_box(A[0], A[1], A[2], A[3], A[4]);
     Box<double> c = make_box(B[0], B[1], B[2], B[3], B[4]);

@@ -126,6 +126,24 @@ int oracle_inverse(const ob_params *p, const ob_batch *b, int s0, int s1,
 int oracle_expert_actions(const ob_params *p, const ob_batch *b, int s0, int s1,
                           int t0, int T, double *act_seq);
 
+/* Observation (Sec. 3.2: other agents in the agent's own frame, the
+ * roadgraph subsampled by distance) of state st for every agent g of scenes
+ * [s0, s1) with observers[g] != 0 (observers NULL: every valid agent).  The
+ * frame of g: origin at g's centre, x axis along its heading.
+ * agents[(g*M + j)*5 + c], c = x, y, yaw, vx, vy: agent j (index within g's
+ * scene) in g's frame, yaw reduced to [-pi, pi]; agents_valid[g*M + j] = 1
+ * iff agent j is valid and j != g (other entries 0).  rg[(g*K + k)*2 + c]
+ * and rg_idx[g*K + k]: the K valid roadgraph points (any type) of g's scene
+ * nearest to g's centre, ascending, ties to the lower global point index,
+ * in g's frame; -1 and 0 past the scene's valid points.  Reading: the
+ * ranking key is float32 (the precision of the GPU kernel, which makes the
+ * same integer decision): c = float(centre), d = float(p - c), key =
+ * fmaf(dx, dx, dy*dy).  Rows of non-observers are not written.  Requires
+ * M >= agents of every scene in range, K >= 1. */
+int oracle_observe(const ob_params *p, const ob_batch *b, int s0, int s1, const ob_state *st,
+                   const uint8_t *observers, int M, int K, double *agents, uint8_t *agents_valid,
+                   double *rg, int32_t *rg_idx);
+
 /* Signed SAT depth of two boxes (centre, heading, length, width):
  * > 0 iff the boxes overlap (then it is the minimum translation distance). */
 double oracle_box_depth(const double *box_a, const double *box_b);
