@@ -337,6 +337,34 @@ def expert_leg(wsim, synth, torch, args, rank, b, reps):
     return out
 
 
+def observe_leg(wsim, synth, torch, b, sim, st, reps):
+    """Observation (Sec. 3.2) of the bench's state: (1) the ego of every scene
+    with the 256 nearest roadgraph points, (2) every valid agent with the 64
+    nearest; both with all other agents of the scene in the observer's frame."""
+    N = b.N_tot
+    M = int(np.diff(b.agent_off).max())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"workload": f"{b.S} scenes x up to {M} agents, {int(np.diff(b.rg_off).max())}-point roadgraphs"}
+    ego = torch.zeros(N, dtype=torch.uint8, device="cuda")
+    ego[torch.as_tensor(b.agent_off[:-1].astype(np.int64), device="cuda")] = 1
+    for name, obs, K in (("ego_k256", ego, 256), ("all_agents_k64", None, 64)):
+        res = sim.observe(st, M, K, observers=obs)
+        for _ in range(2):
+            sim.observe(st, M, K, observers=obs, out=res)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            sim.observe(st, M, K, observers=obs, out=res)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        n_obs = int(obs.sum().item()) if obs is not None else int(b.valid.sum())
+        out[name] = {"ms": ms, "observers": n_obs, "observations_per_s": n_obs / (ms / 1e3), "K": K, "M": M}
+        del res
+    assert sim.status() == 0
+    return out
+
+
 def config_dict(args, b):
     wl = workload_desc(args.workload)
     return {"workload": wl.name, "scenes": int(b.S),
@@ -456,6 +484,7 @@ def main():
         modes[name] = {"value": N * T / (mm / 1e3), "unit": UNIT, "ms_per_rollout": mm}
     assert sim.status() == 0
 
+    observe = observe_leg(wsim, synth, torch, b, sim, st0, args.steps)
     bptt = bptt_leg(wsim, synth, torch, args, rank)
     expert = expert_leg(wsim, synth, torch, args, rank, b, args.steps)
 
@@ -492,6 +521,7 @@ def main():
         "modes": modes,
         "bptt": bptt,
         "expert": expert,
+        "observe": observe,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

@@ -205,6 +205,28 @@ int wsim_rollout(wsim_ctx *ctx, wsim_state *st, const float *act_seq, const uint
  * T >= 0 and t0+T < T_log (else WSIM_ESIZE).  Asynchronous on `stream`. */
 int wsim_expert_actions(wsim_ctx *ctx, int t0, int T, float *act_out, void *stream);
 
+/* Observation (Sec. 3.2: each agent sees the other agents in its own frame
+ * and the roadgraph subsampled by distance) of state st, for every agent g
+ * with observers[g] != 0 (device [N_tot]; NULL: every valid agent).  The
+ * frame of g has its origin at g's centre and its x axis along g's heading.
+ * agents [N_tot][M][5] (device, caller-owned): agent j of g's scene (index
+ * within the scene) as (x, y, yaw, vx, vy) in g's frame, yaw reduced to
+ * [-pi, pi]; agents_valid [N_tot][M]: 1 iff agent j is valid and not g.
+ * rg [N_tot][K][2] and rg_idx [N_tot][K]: the K valid roadgraph points
+ * (any type) of g's scene nearest to g's centre, ascending, ties to the
+ * lower global point index, as (x, y) in g's frame and their global index;
+ * -1 and 0 past the scene's valid points.  Ranking key (float32, exact
+ * integer decisions): c = fl(x + x_lo), d = fl(p - c), key =
+ * fmaf(dx, dx, dy*dy).  Rows of other agents are not written.  Requires
+ * M >= the largest scene's agent count and 1 <= K <= WSIM_OBS_MAX_K (else
+ * WSIM_ESIZE); more than WSIM_OBS_MAX_K points at the K-th key set
+ * WSIM_ESIZE in the device status and leave that observer's points at -1.
+ * The first call builds the context's roadgraph point tiles (allocation,
+ * synchronises `stream`); later calls are asynchronous. */
+#define WSIM_OBS_MAX_K 4096
+int wsim_observe(wsim_ctx *ctx, const wsim_state *st, const uint8_t *observers, int M, int K, float *agents,
+                 uint8_t *agents_valid, float *rg, int32_t *rg_idx, void *stream);
+
 /* Launch configuration of the scene-resident rollout (WSIM_MODE_FUSED).
  * Five launch shapes exist (threads per CTA x CTAs per SM, where the
  * scene's road-edge segments are read from): 0 = 512 x 1, large

@@ -45,6 +45,10 @@ struct wsim_ctx {
     uint16_t* tlist = nullptr;  // [N_tot][kList] candidate-tile lists of the per-step kernels
     float4* tmeta = nullptr;    // [N_tot] their centre, radius and count
     unsigned long long* counters = nullptr;
+    // observation: roadgraph point tiles, observer list, agent -> scene (built on first use)
+    int32_t *pt_tile_off = nullptr, *pt_cnt = nullptr, *obs_list = nullptr, *obs_count = nullptr,
+            *scene_of = nullptr;
+    float4* pt_box = nullptr;
     float* tmp = nullptr;  // ping-pong state, 10 x N_tot
     float* ckpt = nullptr;    // BPTT checkpoints
     float* segbuf = nullptr;  // BPTT recomputed segment states
@@ -514,6 +518,49 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
     return WSIM_OK;
 }
 
+int wsim_observe(wsim_ctx* c, const wsim_state* st, const uint8_t* observers, int M, int K, float* agents,
+                 uint8_t* agents_valid, float* rg, int32_t* rg_idx, void* stream) {
+    if (!c || !state_ok(st) || !agents || !agents_valid || !rg || !rg_idx) return WSIM_EINVAL;
+    int nmax = 0;
+    for (int s = 0; s < c->S; ++s) nmax = std::max(nmax, c->h_agent_off[s + 1] - c->h_agent_off[s]);
+    if (M < nmax || M < 1 || K < 1 || K > WSIM_OBS_MAX_K) return WSIM_ESIZE;
+    cudaStream_t s = S_(stream);
+    c->last = s;
+    if (!c->pt_box) {  // first call: point tiles and the agent -> scene map
+        const int S = c->S, N = c->N_tot;
+        std::vector<int32_t> ro(S + 1), toff(S + 1, 0), sc(std::max(N, 1));
+        CK(cudaMemcpyAsync(ro.data(), c->b.rg_off, sizeof(int32_t) * (S + 1), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int i = 0; i < S; ++i) toff[i + 1] = toff[i] + (ro[i + 1] - ro[i] + kPtTile - 1) / kPtTile;
+        for (int i = 0; i < S; ++i)
+            for (int g = c->h_agent_off[i]; g < c->h_agent_off[i + 1]; ++g) sc[g] = i;
+        int rc = WSIM_OK;
+        if ((rc = dalloc(&c->pt_tile_off, S + 1)) || (rc = dalloc(&c->pt_cnt, toff[S])) ||
+            (rc = dalloc(&c->pt_box, toff[S])) || (rc = dalloc(&c->obs_list, N)) || (rc = dalloc(&c->obs_count, 1)) ||
+            (rc = dalloc(&c->scene_of, N))) {
+            cudaFree(c->pt_tile_off);
+            cudaFree(c->pt_cnt);
+            cudaFree(c->pt_box);
+            cudaFree(c->obs_list);
+            cudaFree(c->obs_count);
+            cudaFree(c->scene_of);
+            c->pt_tile_off = c->pt_cnt = c->obs_list = c->obs_count = c->scene_of = nullptr;
+            c->pt_box = nullptr;
+            return rc;
+        }
+        CK(cudaMemcpyAsync(c->pt_tile_off, toff.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c->scene_of, sc.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
+        CK(launch_pt_tiles(c->b.rg_off, c->pt_tile_off, c->b.rg_x, c->b.rg_y, c->b.rg_valid, S, c->pt_box, c->pt_cnt,
+                           s));
+        CK(cudaStreamSynchronize(s));
+    }
+    StepArgs a = base_args(c);
+    a.in = cstate(st);
+    CK(launch_observe(a, observers, c->obs_list, c->obs_count, c->b.rg_off, c->b.rg_x, c->b.rg_y, c->b.rg_valid,
+                      c->pt_tile_off, c->pt_box, c->pt_cnt, c->scene_of, M, K, agents, agents_valid, rg, rg_idx, s));
+    return WSIM_OK;
+}
+
 int wsim_expert_actions(wsim_ctx* c, int t0, int T, float* act_out, void* stream) {
     if (!c || !act_out) return WSIM_EINVAL;
     if (!c->b.log_th || !c->b.log_vx || !c->b.log_vy) return WSIM_EINVAL;
@@ -735,6 +782,12 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->queue);
     cudaFree(c->status);
     cudaFree(c->counters);
+    cudaFree(c->pt_tile_off);
+    cudaFree(c->pt_cnt);
+    cudaFree(c->pt_box);
+    cudaFree(c->obs_list);
+    cudaFree(c->obs_count);
+    cudaFree(c->scene_of);
     cudaFree(c->tmp);
     cudaFree(c->ckpt);
     cudaFree(c->segbuf);

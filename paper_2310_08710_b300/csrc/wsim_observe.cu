@@ -1,0 +1,396 @@
+// Observation (Sec. 3.2): for each observing agent, the other agents in its
+// own frame (origin at its centre, x axis along its heading) and the K valid
+// roadgraph points nearest to it (the roadgraph subsampled by distance),
+// ascending, ties to the lower point index, in its frame.
+//
+// The ranking key of a point p is float32: c = fl(x_hi + x_lo) (the centre
+// rounded once), d = fl(p - c), key = fmaf(dx, dx, dy * dy).  Rounding is
+// monotone, so the same expression on a tile's bounding box clamped towards
+// (or away from) c gives an exact lower (upper) bound of every key in the
+// tile, with no slack.
+//
+// Roadgraph points are grouped in tiles of kPtTile consecutive points of a
+// scene (the roadgraph's own order, invalid points skipped in the box and
+// the count), built once per context.  Per observer one CTA:
+//   1. writes the other agents in the observer's frame;
+//   2. bounds the K-th key from above: a histogram of the tiles' upper bounds
+//      gives a key below which whole tiles already hold K points, and a
+//      histogram of the keys of the points below it tightens the bound to the
+//      bucket of the K-th key;
+//   3. gathers every point with key <= that bound from the tiles whose lower
+//      bound is <= it (at least K points; if more than fit the shared-memory
+//      list, the bound is lowered by bisection over the gathered tiles);
+//   4. sorts the (key, index) pairs (bitonic, shared memory) and writes the
+//      first K in the observer's frame.
+#include "wsim_phases.cuh"
+
+namespace wsim {
+
+constexpr int kObsThreads = 256;
+constexpr int kObsCap = WSIM_OBS_MAX_K;  // candidate points sorted in shared memory
+
+__device__ __forceinline__ float obs_key(float px, float py, float cx, float cy) {
+    const float dx = px - cx, dy = py - cy;
+    return fmaf(dx, dx, dy * dy);
+}
+
+// Tile boxes: (xmin, ymin, xmax, ymax) of the valid points and their count.
+__global__ void __launch_bounds__(256) k_pt_tiles(const int32_t* rg_off, const int32_t* tile_off, const float* rg_x,
+                                                  const float* rg_y, const uint8_t* rg_valid, int S, float4* box,
+                                                  int32_t* cnt) {
+    const int s = blockIdx.x;
+    const int r0 = rg_off[s], r1 = rg_off[s + 1];
+    const int t0 = tile_off[s], nt = tile_off[s + 1] - t0;
+    for (int t = threadIdx.x; t < nt; t += 256) {
+        float x0 = WSIM_INF, y0 = WSIM_INF, x1 = -WSIM_INF, y1 = -WSIM_INF;
+        int n = 0;
+        const int a = r0 + t * kPtTile, b = min(r1, a + kPtTile);
+        for (int r = a; r < b; ++r) {
+            if (!rg_valid[r]) continue;
+            const float x = rg_x[r], y = rg_y[r];
+            x0 = fminf(x0, x);
+            x1 = fmaxf(x1, x);
+            y0 = fminf(y0, y);
+            y1 = fmaxf(y1, y);
+            ++n;
+        }
+        box[t0 + t] = make_float4(x0, y0, x1, y1);
+        cnt[t0 + t] = n;
+    }
+}
+
+// Observers in a list (any order: every observer's output is its own).
+__global__ void k_obs_list(const uint8_t* observers, const uint8_t* valid, int N_tot, int32_t* list, int32_t* count) {
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N_tot; g += gridDim.x * blockDim.x) {
+        const bool obs = observers ? observers[g] != 0 : valid[g] != 0;
+        if (obs) list[atomicAdd(count, 1)] = g;
+    }
+}
+
+constexpr int kHistBits = 12;  // key histogram: top 12 bits of the float (an eighth of an octave)
+constexpr int kObsTiles = 1500;  // tiles whose upper bound and count are cached per observer
+constexpr int kObsList = 1000;   // tiles that can hold a point below the bound (48 KB static in all)
+
+struct ObsSmem {
+    unsigned long long item[kObsCap];  // (key bits << 32) | point index
+    float tmax[kObsTiles];             // per tile: upper bound of its keys (+inf: empty)
+    int tcnt[kObsTiles];
+    int list[kObsList];                // tiles whose lower bound is <= the tile bound
+    int red[kObsThreads / 32];
+    int n, nlist;
+};
+
+__device__ __forceinline__ int block_sum(int v, ObsSmem& sm) {
+    v = __reduce_add_sync(kFull, v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) sm.red[w] = v;
+    __syncthreads();
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < kObsThreads / 32; ++k) t += sm.red[k];
+    return t;
+}
+
+// Upper bound of the keys of tile B (the box corner farthest from c).
+__device__ __forceinline__ float tile_upper(const float4 B, float cx, float cy) {
+    const float fx = fmaxf(fabsf(B.x - cx), fabsf(B.z - cx)), fy = fmaxf(fabsf(B.y - cy), fabsf(B.w - cy));
+    return fmaf(fx, fx, fy * fy);
+}
+
+// Lower bound of the keys of tile B (the box clamped towards c).
+__device__ __forceinline__ float tile_lower(const float4 B, float cx, float cy) {
+    const float nx = fminf(fmaxf(cx, B.x), B.z), ny = fminf(fmaxf(cy, B.y), B.w);
+    return obs_key(nx, ny, cx, cy);
+}
+
+// The first bucket of hist (1 << kHistBits counts) at which the running
+// total reaches `want` (-1 if it never does); *upto = the total up to and
+// including that bucket.  Block-wide, ends with a barrier.
+__device__ int hist_crossing(const int* hist, int want, ObsSmem& sm, int* upto) {
+    constexpr int H = 1 << kHistBits, per = H / kObsThreads;
+    int local = 0;
+    for (int k = 0; k < per; ++k) local += hist[threadIdx.x * per + k];
+    int incl = local;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) sm.red[warp] = incl;
+    __syncthreads();
+    int before = 0;
+    for (int w = 0; w < warp; ++w) before += sm.red[w];
+    incl += before;
+    const int excl = incl - local;
+    __shared__ int found[2];
+    if (threadIdx.x == 0) found[0] = -1;
+    __syncthreads();
+    if (excl < want && incl >= want) {  // the crossing bucket is in this thread's range
+        int run = excl, b = threadIdx.x * per;
+        while (run + hist[b] < want) run += hist[b++];
+        found[0] = b;
+        found[1] = run + hist[b];
+    }
+    __syncthreads();
+    const int b = found[0];
+    *upto = b >= 0 ? found[1] : 0;
+    __syncthreads();
+    return b;
+}
+
+// A tighter bound from the points themselves: a histogram of the keys of
+// every point in the tiles that can hold one below tau gives the top of the
+// bucket holding the want-th key; *n = the points at or below it.
+__device__ float point_bound(const float4* box, const int32_t* cnt, int t0, int nt, int r0, int r1, const float* rg_x,
+                             const float* rg_y, const uint8_t* rg_valid, float cx, float cy, float tau, int want,
+                             ObsSmem& sm, int* n) {
+    int* hist = reinterpret_cast<int*>(sm.item);
+    constexpr int H = 1 << kHistBits;
+    for (int i = threadIdx.x; i < H; i += kObsThreads) hist[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nl = sm.nlist, m = nl >= 0 ? nl : nt;
+    for (int q = warp; q < m; q += kObsThreads / 32) {
+        const int t = nl >= 0 ? sm.list[q] : q;
+        if (nl < 0 && (cnt[t0 + t] == 0 || tile_lower(box[t0 + t], cx, cy) > tau)) continue;
+        const int r = r0 + t * kPtTile + lane;
+        if (r < r1 && rg_valid[r]) {
+            const float key = obs_key(rg_x[r], rg_y[r], cx, cy);
+            if (key <= tau && key < WSIM_INF) atomicAdd(&hist[__float_as_uint(key) >> (32 - kHistBits)], 1);
+        }
+    }
+    __syncthreads();
+    const int b = hist_crossing(hist, want, sm, n);
+    if (b < 0) {  // fewer finite keys than wanted below tau: keep tau
+        *n = -1;
+        return tau;
+    }
+    return fminf(tau, __uint_as_float(((static_cast<uint32_t>(b) + 1u) << (32 - kHistBits)) - 1u));
+}
+
+// An upper bound tau of the want-th smallest key: the tiles' upper bounds
+// are counted in a histogram of their float bits' top 12 bits (keys are >= 0,
+// so bits order like values; a bucket spans an eighth of an octave), and tau
+// is the top of the first bucket at which the counts reach `want`: every tile
+// up to that bucket lies entirely within tau.  Tiles whose bounds overflow
+// (+inf) never count; if they would be needed, tau = +inf.
+
+__device__ float tile_bound(const float4* box, const int32_t* cnt, int t0, int nt, float cx, float cy, int want,
+                            ObsSmem& sm) {
+    int* hist = reinterpret_cast<int*>(sm.item);  // the item list is free until the gather
+    constexpr int H = 1 << kHistBits;
+    for (int i = threadIdx.x; i < H; i += kObsThreads) hist[i] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < nt; t += kObsThreads) {
+        float u;
+        int n;
+        if (t < kObsTiles) {
+            u = sm.tmax[t];
+            n = sm.tcnt[t];
+        } else {
+            n = cnt[t0 + t];
+            u = n > 0 ? tile_upper(box[t0 + t], cx, cy) : WSIM_INF;
+        }
+        if (n > 0 && u < WSIM_INF) atomicAdd(&hist[__float_as_uint(u) >> (32 - kHistBits)], n);
+    }
+    __syncthreads();
+    int total;
+    const int b = hist_crossing(hist, want, sm, &total);
+    if (b < 0) return WSIM_INF;
+    return __uint_as_float(((static_cast<uint32_t>(b) + 1u) << (32 - kHistBits)) - 1u);
+}
+
+
+// Points with key <= tau in the tiles that can hold one.
+__device__ int count_points_within(const float4* box, const int32_t* cnt, int t0, int nt, int r0, int r1,
+                                   const float* rg_x, const float* rg_y, const uint8_t* rg_valid, float cx, float cy,
+                                   float tau, ObsSmem& sm) {
+    int c = 0;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nl = sm.nlist, m = nl >= 0 ? nl : nt;
+    for (int q = warp; q < m; q += kObsThreads / 32) {
+        const int t = nl >= 0 ? sm.list[q] : q;
+        if (nl < 0 && (cnt[t0 + t] == 0 || tile_lower(box[t0 + t], cx, cy) > tau)) continue;
+        const int r = r0 + t * kPtTile + lane;
+        if (r < r1 && rg_valid[r] && obs_key(rg_x[r], rg_y[r], cx, cy) <= tau) ++c;
+    }
+    return block_sum(c, sm);
+}
+
+__global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const int32_t* list, const int32_t* count,
+                                                         const int32_t* rg_off, const float* rg_x, const float* rg_y,
+                                                         const uint8_t* rg_valid, const int32_t* tile_off,
+                                                         const float4* box, const int32_t* cnt, int M, int K,
+                                                         float* agents, uint8_t* agents_valid, float* rg_out,
+                                                         int32_t* rg_idx, const int32_t* scene_of) {
+    __shared__ ObsSmem sm;
+    const int n_obs = *count;
+    for (int q = blockIdx.x; q < n_obs; q += gridDim.x) {
+        const int g = list[q];
+        const int s = scene_of[g];
+        const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
+        const float xh = A.in.x[g], xl = A.in.x_lo[g], yh = A.in.y[g], yl = A.in.y_lo[g];
+        const float th = A.in.th[g], tl = A.in.th_lo[g];
+        float c, sn;
+        comp_sincos(th, tl, c, sn);
+        // 1. Other agents in the observer's frame.
+        for (int j = threadIdx.x; j < M; j += kObsThreads) {
+            const int gj = a0 + j;
+            const bool ok = j < N && gj != g && A.valid[gj];
+            const size_t o = static_cast<size_t>(g) * M + j;
+            float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+            if (ok) {
+                const float dx = comp_diff(A.in.x[gj], A.in.x_lo[gj], xh, xl);
+                const float dy = comp_diff(A.in.y[gj], A.in.y_lo[gj], yh, yl);
+                v[0] = fmaf(c, dx, sn * dy);
+                v[1] = fmaf(-sn, dx, c * dy);
+                v[2] = turn_from(A.in.th[gj], th, tl - A.in.th_lo[gj]);  // heading difference mod 2 pi
+                const float vx = A.in.vx[gj], vy = A.in.vy[gj];
+                v[3] = fmaf(c, vx, sn * vy);
+                v[4] = fmaf(-sn, vx, c * vy);
+            }
+            agents_valid[o] = ok;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) agents[o * 5 + k] = v[k];
+        }
+        // 2. Upper bound of the K-th key from the tiles.
+        const int r0 = rg_off[s], r1 = rg_off[s + 1];
+        const int t0 = tile_off[s], nt = tile_off[s + 1] - t0;
+        const float cx = __fadd_rn(xh, xl), cy = __fadd_rn(yh, yl);
+        int total = 0;
+        for (int t = threadIdx.x; t < nt; t += kObsThreads) {
+            const int n = cnt[t0 + t];
+            total += n;
+            if (t < kObsTiles) {
+                sm.tcnt[t] = n;
+                sm.tmax[t] = n > 0 ? tile_upper(box[t0 + t], cx, cy) : WSIM_INF;
+            }
+        }
+        total = block_sum(total, sm);  // its barriers also publish the cache
+        const int want = min(K, total);
+        float tau = WSIM_INF;
+        if (want > 0) tau = tile_bound(box, cnt, t0, nt, cx, cy, want, sm);
+        // the tiles that can hold a point below tau (-1: more than fit, scan all)
+        if (threadIdx.x == 0) sm.nlist = 0;
+        __syncthreads();
+        for (int t = threadIdx.x; t < nt; t += kObsThreads) {
+            const bool in = cnt[t0 + t] > 0 && tile_lower(box[t0 + t], cx, cy) <= tau;
+            if (in) {
+                const int q = atomicAdd(&sm.nlist, 1);
+                if (q < kObsList) sm.list[q] = t;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && sm.nlist > kObsList) sm.nlist = -1;
+        __syncthreads();
+        // 3. Gather (lowering tau while the list would overflow).
+        int n = 0;
+        if (want > 0) {
+            tau = point_bound(box, cnt, t0, nt, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, want, sm, &n);
+            if (n < 0) n = count_points_within(box, cnt, t0, nt, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, sm);
+        }
+        if (n > kObsCap) {
+            uint32_t lo = 0, hi = __float_as_uint(tau);
+            while (lo < hi) {  // smallest tau' with at least `want` points
+                const uint32_t mid = lo + (hi - lo) / 2;
+                if (count_points_within(box, cnt, t0, nt, r0, r1, rg_x, rg_y, rg_valid, cx, cy, __uint_as_float(mid),
+                                        sm) >= want)
+                    hi = mid;
+                else
+                    lo = mid + 1;
+            }
+            tau = __uint_as_float(lo);
+            n = count_points_within(box, cnt, t0, nt, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, sm);
+            if (n > kObsCap) {  // more than kObsCap points share the K-th key
+                if (threadIdx.x == 0) set_status(A.status, WSIM_ESIZE);
+                n = 0;
+            }
+        }
+        if (threadIdx.x == 0) sm.n = 0;
+        __syncthreads();
+        if (n > 0) {
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            const int nl = sm.nlist, m = nl >= 0 ? nl : nt;
+            for (int qq = warp; qq < m; qq += kObsThreads / 32) {
+                const int t = nl >= 0 ? sm.list[qq] : qq;
+                if (nl < 0 && (cnt[t0 + t] == 0 || tile_lower(box[t0 + t], cx, cy) > tau)) continue;
+                const int r = r0 + t * kPtTile + lane;
+                float key = 0.f;
+                const bool in = r < r1 && rg_valid[r] && (key = obs_key(rg_x[r], rg_y[r], cx, cy)) <= tau;
+                const unsigned bal = __ballot_sync(kFull, in);
+                int base = 0;
+                if (lane == 0 && bal) base = atomicAdd(&sm.n, __popc(bal));
+                base = __shfl_sync(kFull, base, 0);
+                if (in)
+                    sm.item[base + __popc(bal & ((1u << lane) - 1u))] =
+                        (static_cast<unsigned long long>(__float_as_uint(key)) << 32) | static_cast<uint32_t>(r);
+            }
+        }
+        __syncthreads();
+        // 4. Bitonic sort of the gathered items (padded to a power of two).
+        int p2 = 1;
+        while (p2 < n) p2 <<= 1;
+        for (int i = n + threadIdx.x; i < p2; i += kObsThreads) sm.item[i] = ~0ull;
+        __syncthreads();
+        for (int size = 2; size <= p2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < p2 / 2; i += kObsThreads) {
+                    const int lo = 2 * i - (i & (stride - 1));
+                    const int hi = lo + stride;
+                    const bool up = (lo & size) == 0;
+                    const unsigned long long a = sm.item[lo], b = sm.item[hi];
+                    if ((a > b) == up) {
+                        sm.item[lo] = b;
+                        sm.item[hi] = a;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int k = threadIdx.x; k < K; k += kObsThreads) {
+            const size_t o = static_cast<size_t>(g) * K + k;
+            float ox = 0.f, oy = 0.f;
+            int idx = -1;
+            if (k < want && k < n) {
+                idx = static_cast<int>(sm.item[k] & 0xffffffffull);
+                const float dx = comp_diff(rg_x[idx], 0.f, xh, xl);
+                const float dy = comp_diff(rg_y[idx], 0.f, yh, yl);
+                ox = fmaf(c, dx, sn * dy);
+                oy = fmaf(-sn, dx, c * dy);
+            }
+            rg_out[2 * o] = ox;
+            rg_out[2 * o + 1] = oy;
+            rg_idx[o] = idx;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_pt_tiles(const int32_t* rg_off, const int32_t* tile_off, const float* rg_x, const float* rg_y,
+                            const uint8_t* rg_valid, int S, float4* box, int32_t* cnt, cudaStream_t st) {
+    k_pt_tiles<<<S, 256, 0, st>>>(rg_off, tile_off, rg_x, rg_y, rg_valid, S, box, cnt);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_observe(const StepArgs& a, const uint8_t* observers, int32_t* list, int32_t* count,
+                           const int32_t* rg_off, const float* rg_x, const float* rg_y, const uint8_t* rg_valid,
+                           const int32_t* tile_off, const float4* box, const int32_t* cnt, const int32_t* scene_of,
+                           int M, int K, float* agents, uint8_t* agents_valid, float* rg, int32_t* rg_idx,
+                           cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), st);
+    if (e != cudaSuccess) return e;
+    const int nb = std::min((a.N_tot + 255) / 256, 4096);
+    if (a.N_tot > 0) k_obs_list<<<std::max(nb, 1), 256, 0, st>>>(observers, a.valid, a.N_tot, list, count);
+    int dev = 0, sms = 148, per = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_observe, kObsThreads, 0);
+    const int grid = sms * std::max(per, 1);
+    k_observe<<<grid, kObsThreads, 0, st>>>(a, list, count, rg_off, rg_x, rg_y, rg_valid, tile_off, box, cnt, M, K,
+                                             agents, agents_valid, rg, rg_idx, scene_of);
+    return cudaGetLastError();
+}
+
+}  // namespace wsim

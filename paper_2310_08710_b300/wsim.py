@@ -104,6 +104,7 @@ def _load():
     lib.wsim_loss_grad.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
     lib.wsim_expert_actions.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    lib.wsim_observe.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
     return lib
 
 
@@ -111,7 +112,7 @@ lib = _load()
 
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
             "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static",
-            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad", "wsim_expert_actions")
+            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad", "wsim_expert_actions", "wsim_observe")
 
 
 class WsimError(RuntimeError):
@@ -278,6 +279,22 @@ class Sim:
                                   GRAD_PLAIN if plain else 0, loss.data_ptr(), _ptr(dact), _stream(stream)),
                "wsim_loss_grad")
         return loss, dact
+
+    def observe(self, st: State, M: int, K: int, observers: Optional[torch.Tensor] = None, out: Optional[dict] = None,
+                stream=None) -> dict:
+        """Observation (wsim_observe): agents [N_tot, M, 5], agents_valid
+        [N_tot, M], rg [N_tot, K, 2], rg_idx [N_tot, K]; rows of agents that
+        do not observe are left as they were in `out` (zeros / -1 when new)."""
+        N, dev = self.batch.N_tot, self.batch.log_x.device
+        if out is None:
+            out = dict(agents=torch.zeros((N, M, 5), dtype=torch.float32, device=dev),
+                       agents_valid=torch.zeros((N, M), dtype=torch.uint8, device=dev),
+                       rg=torch.zeros((N, K, 2), dtype=torch.float32, device=dev),
+                       rg_idx=torch.full((N, K), -1, dtype=torch.int32, device=dev))
+        _check(lib.wsim_observe(self._h, C.byref(st.c()), _ptr(observers), M, K, out["agents"].data_ptr(),
+                                out["agents_valid"].data_ptr(), out["rg"].data_ptr(), out["rg_idx"].data_ptr(),
+                                _stream(stream)), "wsim_observe")
+        return out
 
     def expert_actions(self, t0: int, T: int, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         """Open-loop expert actions [T, 3, N_tot] fitted to log rows t0 .. t0+T

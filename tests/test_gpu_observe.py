@@ -1,0 +1,127 @@
+"""Observation function on the GPU against the FP64 oracle (needs a B300).
+
+Agents in the observer's frame within float32 tolerances; the K nearest
+roadgraph point indices bit-exact (both sides rank by the same float32 key,
+ties to the lower index) and their coordinates in the observer's frame
+within tolerance; every agent observing and an observer subset; K above a
+scene's point count; the 1024-scene batch sampled.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2310_08710_b300 import synth
+from tests.gpu_harness import run_rollout, state64
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5       # m, m/s absolute ...
+REL = 3e-7       # ... plus this fraction of the vector's length: a float32
+                 # rotation (cos, sin within 1 ulp, two rounded products) of a
+                 # vector of length r errs by up to ~2.4e-7 r
+TOL_YAW = 1e-6   # rad
+
+
+@pytest.fixture(scope="module")
+def wsim():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_08710_b300 import wsim as w
+    return w
+
+
+def _tol(r):
+    """Tolerance of a rotated vector's components, r its length."""
+    return TOL + REL * r
+
+
+def _check(g, o, obs_rows, M, K):
+    av, ov = g["agents_valid"][obs_rows], o["agents_valid"][obs_rows]
+    assert np.array_equal(av, ov)
+    ga, oa = g["agents"][obs_rows].astype(np.float64), o["agents"][obs_rows]
+    m = ov.astype(bool)
+    for c0 in (0, 3):  # position, velocity
+        r = np.hypot(oa[..., c0], oa[..., c0 + 1])[m]
+        for c in (c0, c0 + 1):
+            d = np.abs(ga[..., c] - oa[..., c])[m]
+            assert (d <= _tol(r)).all(), (c, d.max())
+    dyaw = np.abs(np.angle(np.exp(1j * (ga[..., 2] - oa[..., 2]))))[m]
+    assert dyaw.max(initial=0) <= TOL_YAW
+    assert np.array_equal(g["rg_idx"][obs_rows], o["rg_idx"][obs_rows])
+    ok = o["rg_idx"][obs_rows] >= 0
+    orr = o["rg"][obs_rows]
+    d = np.abs(g["rg"][obs_rows].astype(np.float64) - orr)[ok]
+    r = np.hypot(orr[..., 0], orr[..., 1])[ok][:, None]
+    assert (d <= _tol(r)).all(), d.max()
+    return float(d.max(initial=0))
+
+
+def _gpu_observe(wsim, b, rows, M, K, observers=None):
+    sim = wsim.Sim(wsim.DeviceBatch(b))
+    st = wsim.State(b.N_tot, data=torch.as_tensor(rows).cuda().contiguous())
+    ob = None if observers is None else torch.as_tensor(observers, dtype=torch.uint8).cuda()
+    out = sim.observe(st, M, K, observers=ob)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    sim.close()
+    return {k: v.cpu().numpy() for k, v in out.items()}
+
+
+def test_every_agent_observes_after_a_rollout(wsim):
+    # state after 40 steps of a rollout (compensated positions, unwrapped headings)
+    b = synth.make_batch(0, seed=3, T=40)
+    g = run_rollout(b, T=40)
+    rows = g["final"]
+    ag = np.arange(b.N_tot)
+    st = state64(rows, ag)
+    for K in (16, 500, 2500):  # 2500 > the scene's 2000 points: padding
+        go = _gpu_observe(wsim, b, rows, 32, K)
+        oo = oracle.Oracle(b).observe(st, 32, K)
+        obs = np.nonzero(b.valid)[0]
+        err = _check(go, oo, obs, 32, K)
+        print("K", K, "max point error", err)
+        assert (go["rg_idx"][b.valid == 0] == -1).all()  # invalid agents do not observe
+
+
+def test_observer_subset_and_untouched_rows(wsim):
+    b = synth.make_batch(3, seed=2, S=6, N=20, R=3000)
+    rows = np.zeros((10, b.N_tot), np.float32)
+    rows[0], rows[1], rows[4], rows[6], rows[7] = b.x, b.y, b.th, b.vx, b.vy
+    observers = np.zeros(b.N_tot, np.uint8)
+    observers[b.agent_off[:-1]] = 1  # the first agent of every scene
+    go = _gpu_observe(wsim, b, rows, 24, 64, observers)
+    oo = oracle.Oracle(b).observe(state64(rows, np.arange(b.N_tot)), 24, 64, observers)
+    _check(go, oo, np.nonzero(observers)[0], 24, 64)
+    others = observers == 0
+    assert (go["rg_idx"][others] == -1).all() and (go["agents_valid"][others] == 0).all()
+
+
+def test_batch_1024x128_sampled_observers(wsim):
+    # the ego of every scene observes; 16 scenes checked against the oracle
+    b = synth.make_batch(1, seed=0)
+    rows = np.zeros((10, b.N_tot), np.float32)
+    rows[0], rows[1], rows[4], rows[6], rows[7] = b.x, b.y, b.th, b.vx, b.vy
+    observers = np.zeros(b.N_tot, np.uint8)
+    observers[b.agent_off[:-1]] = 1
+    go = _gpu_observe(wsim, b, rows, 128, 256, observers)
+    scenes = list(range(0, b.S, b.S // 16))
+    sub = b.subset(scenes)
+    ag = np.concatenate([np.arange(b.agent_off[s], b.agent_off[s + 1]) for s in scenes])
+    sub_obs = observers[ag]
+    oo = oracle.Oracle(sub).observe(state64(rows, ag), 128, 256, sub_obs)
+    # global roadgraph indices of the subset are renumbered: map back
+    rg_map = np.concatenate([np.arange(b.rg_off[s], b.rg_off[s + 1]) for s in scenes])
+    oo["rg_idx"] = np.where(oo["rg_idx"] >= 0, rg_map[np.maximum(oo["rg_idx"], 0)], -1)
+    go_sub = {k: v[ag] for k, v in go.items()}
+    _check(go_sub, oo, np.nonzero(sub_obs)[0], 128, 256)
+
+
+def test_observe_argument_limits(wsim):
+    b = synth.make_batch(0, seed=1)
+    sim = wsim.Sim(wsim.DeviceBatch(b))
+    st = wsim.State.from_batch(b)
+    with pytest.raises(wsim.WsimError):
+        sim.observe(st, 16, 8)  # M below the scene's 32 agents
+    with pytest.raises(wsim.WsimError):
+        sim.observe(st, 32, 5000)  # K above the limit
+    sim.close()
