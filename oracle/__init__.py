@@ -40,7 +40,7 @@ class ObParams(C.Structure):
                 ("route_h", C.c_double), ("gap_min", C.c_double), ("band", C.c_double),
                 ("idm_K", C.c_int32), ("pad_", C.c_int32),
                 ("kin_amax", C.c_double), ("kin_kmax", C.c_double), ("kin_band_a", C.c_double),
-                ("kin_band_th", C.c_double)]
+                ("kin_band_th", C.c_double), ("route_max_dist", C.c_double), ("route_max_rel", C.c_double)]
 
 
 class ObBatch(C.Structure):
@@ -50,7 +50,8 @@ class ObBatch(C.Structure):
                 ("valid", _u8p), ("kind", _u8p),
                 ("route_off", _i32p), ("route_x", _dp), ("route_y", _dp),
                 ("rg_x", _dp), ("rg_y", _dp), ("rg_poly", _i32p), ("rg_type", _u8p), ("rg_valid", _u8p),
-                ("log_x", _dp), ("log_y", _dp), ("log_th", _dp), ("log_vx", _dp), ("log_vy", _dp)]
+                ("log_x", _dp), ("log_y", _dp), ("log_th", _dp), ("log_vx", _dp), ("log_vy", _dp),
+                ("path_off", _i32p), ("path_pt_off", _i32p), ("path_x", _dp), ("path_y", _dp), ("path_on", _u8p)]
 
 
 class ObState(C.Structure):
@@ -76,6 +77,7 @@ def lib():
         _lib.oracle_rollout.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp, _u8p,
                                         C.c_int, C.c_int, P(ObMetrics), C.c_int]
         _lib.oracle_inverse.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), P(ObState), _dp]
+        _lib.oracle_route.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp, _u8p]
         _lib.oracle_observe.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _u8p, C.c_int,
                                         C.c_int, _dp, _u8p, _dp, _i32p]
         _lib.oracle_expert_actions.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, C.c_int, C.c_int,
@@ -110,11 +112,13 @@ class Params:
     kin_kmax: float = 0.3
     kin_band_a: float = 1e-3
     kin_band_th: float = 1e-5
+    route_max_dist: float = 5.0
+    route_max_rel: float = 2.0
 
     def c(self) -> ObParams:
         return ObParams(self.dt, self.idm_amax, self.idm_b, self.idm_T, self.idm_s0, self.idm_dq,
                         self.route_h, self.gap_min, self.band, self.idm_K, 0, self.kin_amax, self.kin_kmax,
-                        self.kin_band_a, self.kin_band_th)
+                        self.kin_band_a, self.kin_band_th, self.route_max_dist, self.route_max_rel)
 
 
 def _ptr(a: np.ndarray, t):
@@ -159,6 +163,10 @@ class Oracle:
             _ptr(k("lx", _f64(batch.log_x)), _dp), _ptr(k("ly", _f64(batch.log_y)), _dp),
             _ptr(k("lth", _f64(batch.log_th)), _dp), _ptr(k("lvx", _f64(batch.log_vx)), _dp),
             _ptr(k("lvy", _f64(batch.log_vy)), _dp),
+            _ptr(k("po", np.ascontiguousarray(batch.path_off, np.int32)), _i32p),
+            _ptr(k("ppo", np.ascontiguousarray(batch.path_pt_off, np.int32)), _i32p),
+            _ptr(k("px", _f64(batch.path_x)), _dp), _ptr(k("py", _f64(batch.path_y)), _dp),
+            _ptr(k("pon", np.ascontiguousarray(batch.path_on, np.uint8)), _u8p),
         )
         self._keep = keep
 
@@ -272,6 +280,21 @@ class Oracle:
         if rc:
             raise RuntimeError("oracle_observe failed")
         return out
+
+    def route(self, st: dict, scenes=None):
+        """Route progress ratio [S] (NaN when undefined) and flags [S] (bit0
+        off-route, bit1 band, bit2 progress ambiguous) of each scene's
+        first agent."""
+        S = self.b.S
+        s0, s1 = self._scenes(scenes)
+        st = {k: _f64(st[k]) for k in STATE_KEYS}
+        prog = np.full(S, np.nan)
+        flags = np.zeros(S, np.uint8)
+        rc = lib().oracle_route(C.byref(self._cp), C.byref(self._batch), s0, s1, C.byref(self._cstate(st)),
+                                _ptr(prog, _dp), _ptr(flags, _u8p))
+        if rc:
+            raise RuntimeError("oracle_route failed")
+        return prog, flags
 
     def expert_actions(self, t0: int, T: int, scenes=None) -> np.ndarray:
         """Open-loop expert actions [T][3][N_tot] fitted to the log."""

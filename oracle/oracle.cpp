@@ -678,6 +678,80 @@ int oracle_rollout(const ob_params* p, const ob_batch* b, int s0, int s1, ob_sta
     return status;
 }
 
+namespace {
+// Nearest point of path q (points [k0, k1)) to (px, py): distance, arc length
+// from the path's start, segment (ties: lower), and whether a non-adjacent
+// segment lies within `band` of the nearest distance.
+struct PathHit { double dist, arc; int seg; bool amb; };
+
+PathHit path_nearest(const ob_batch* b, int k0, int k1, double px, double py, double band) {
+    PathHit h{kInf, 0.0, -1, false};
+    std::vector<double> d(std::max(k1 - k0 - 1, 0));
+    double arc = 0.0;
+    for (int k = k0; k + 1 < k1; ++k) {
+        const double ax = b->path_x[k], ay = b->path_y[k];
+        const double ux = b->path_x[k + 1] - ax, uy = b->path_y[k + 1] - ay;
+        const double uu = ux * ux + uy * uy;
+        const double t = uu > 0 ? std::min(1.0, std::max(0.0, ((px - ax) * ux + (py - ay) * uy) / uu)) : 0.0;
+        const double ex = px - ax - t * ux, ey = py - ay - t * uy;
+        const double dist = std::sqrt(ex * ex + ey * ey);
+        d[k - k0] = dist;
+        if (dist < h.dist) {
+            h.dist = dist;
+            h.arc = arc + t * std::sqrt(uu);
+            h.seg = k - k0;
+        }
+        arc += std::sqrt(uu);
+    }
+    for (int j = 0; j < (int)d.size(); ++j)
+        if (std::abs(j - h.seg) > 1 && d[j] - h.dist < band) h.amb = true;
+    return h;
+}
+}  // namespace
+
+int oracle_route(const ob_params* p, const ob_batch* b, int s0, int s1, const ob_state* st, double* progress,
+                 uint8_t* flags) {
+    if (!p || !b || !st || !progress || !flags || !b->path_off || s0 < 0 || s1 > b->S || s0 > s1) return -1;
+    const int N = b->N_tot, TL = b->T_log;
+    for (int s = s0; s < s1; ++s) {
+        progress[s] = std::nan("");
+        flags[s] = 0;
+        const int g = b->agent_off[s];
+        if (g >= b->agent_off[s + 1]) continue;
+        int best = -1;
+        PathHit on{kInf, 0, -1, false};
+        double off = kInf, second_on = kInf;
+        for (int q = b->path_off[s]; q < b->path_off[s + 1]; ++q) {
+            const PathHit h = path_nearest(b, b->path_pt_off[q], b->path_pt_off[q + 1], st->x[g], st->y[g], p->band);
+            if (b->path_on[q]) {
+                if (h.dist < on.dist) {
+                    second_on = on.dist;
+                    on = h;
+                    best = q;
+                } else {
+                    second_on = std::min(second_on, h.dist);
+                }
+            } else {
+                off = std::min(off, h.dist);
+            }
+        }
+        if (best < 0) continue;
+        uint8_t fl = 0;
+        if (on.dist > p->route_max_dist || on.dist - off > p->route_max_rel) fl |= 1;
+        if (std::fabs(on.dist - p->route_max_dist) < p->band || std::fabs(on.dist - off - p->route_max_rel) < p->band)
+            fl |= 2;
+        if (on.amb || second_on - on.dist < p->band) fl |= 4;
+        const int k0 = b->path_pt_off[best], k1 = b->path_pt_off[best + 1];
+        const PathHit hp = path_nearest(b, k0, k1, b->log_x[g], b->log_y[g], p->band);
+        const PathHit hq = path_nearest(b, k0, k1, b->log_x[(size_t)(TL - 1) * N + g], b->log_y[(size_t)(TL - 1) * N + g],
+                                        p->band);
+        if (hp.amb || hq.amb) fl |= 4;
+        if (hq.arc - hp.arc > 1e-3) progress[s] = (on.arc - hp.arc) / (hq.arc - hp.arc);
+        flags[s] = fl;
+    }
+    return 0;
+}
+
 int oracle_observe(const ob_params* p, const ob_batch* b, int s0, int s1, const ob_state* st,
                    const uint8_t* observers, int M, int K, double* agents, uint8_t* agents_valid,
                    double* rg, int32_t* rg_idx) {

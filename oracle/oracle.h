@@ -44,6 +44,8 @@ typedef struct {
     double kin_kmax;    /* ... |kappa| limit, 0.3 1/m (Sec. 3.4)                 */
     double kin_band_a;  /* band around the |a| limit (m/s^2)                     */
     double kin_band_th; /* band around the turn limit kin_kmax * distance (rad)  */
+    double route_max_dist; /* off-route: farther than this from every on-route path (m) */
+    double route_max_rel;  /* off-route: an off-route path closer by more than this (m)  */
 } ob_params;
 
 /* A batch of scenes in CSR form.  Scene s owns agents [agent_off[s],
@@ -64,6 +66,13 @@ typedef struct {
     const double  *log_x, *log_y;      /* [T_log][N_tot] */
     const double  *log_th, *log_vx, *log_vy; /* [T_log][N_tot]; may be NULL (no expert
                                                 or log playback then) */
+    /* Route paths of each scene's first agent (may be NULL: no paths): scene
+     * s owns paths [path_off[s], path_off[s+1]), path p owns points
+     * [path_pt_off[p], path_pt_off[p+1]) in order; path_on[p] = 1 marks an
+     * on-route path. */
+    const int32_t *path_off, *path_pt_off;
+    const double  *path_x, *path_y;
+    const uint8_t *path_on;
 } ob_batch;
 
 /* Dynamic state per agent, [N_tot] each.  s is the IDM route cursor. */
@@ -143,6 +152,20 @@ int oracle_expert_actions(const ob_params *p, const ob_batch *b, int s0, int s1,
 int oracle_observe(const ob_params *p, const ob_batch *b, int s0, int s1, const ob_state *st,
                    const uint8_t *observers, int M, int K, double *agents, uint8_t *agents_valid,
                    double *rg, int32_t *rg_idx);
+
+/* Route metrics (Sec. 3.4) of the first agent of each scene in [s0, s1) at
+ * state st: progress[s] = (d_x - d_p) / (d_q - d_p), where d_x is the arc
+ * length along the on-route path nearest to the agent (ties: lower path) of
+ * the agent's nearest point on it (ties: lower segment), and d_p, d_q those
+ * of the first and last logged positions (log rows 0 and T_log-1) on the
+ * same path; NaN when d_q - d_p <= 1e-3 m or the scene has no on-route
+ * path.  flags[s]: bit0 off-route (distance to the nearest on-route path >
+ * route_max_dist, or an off-route path nearer by more than route_max_rel),
+ * bit1 band (a deciding distance within p->band of its threshold), bit2
+ * progress ambiguous (two on-route paths, or two non-adjacent segments of
+ * the chosen path, within p->band of the nearest). */
+int oracle_route(const ob_params *p, const ob_batch *b, int s0, int s1, const ob_state *st,
+                 double *progress, uint8_t *flags);
 
 /* Signed SAT depth of two boxes (centre, heading, length, width):
  * > 0 iff the boxes overlap (then it is the minimum translation distance). */

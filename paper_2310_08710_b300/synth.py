@@ -223,10 +223,40 @@ def _scene(rng, wl: Workload, s: int, N: Optional[int], R: Optional[int]):
         act[:, 0, dl] = spd * DT * np.cos(psi)
         act[:, 1, dl] = spd * DT * np.sin(psi)
         act[:, 2, dl] = rng.uniform(-0.05, 0.05, (T, len(dl)))
+    # Route paths of the ego (built from its log in make_batch): where the two
+    # off-route branches leave the on-route path, their turn and curvature.
+    branch = np.stack([rng.uniform(0.05, 0.6, 2), rng.uniform(0.4, 1.0, 2) * np.where(rng.random(2) < 0.5, -1, 1),
+                       rng.uniform(-0.02, 0.02, 2)])
     return dict(
         N=N, R=R, x=x, y=y, th=th, vx=vx, vy=vy, L=L, W=W, valid=valid, kind=kind, v0=v0,
-        rg=rg, n_route=n_route, rx=rx, ry=ry, ctl=ctl, act=act,
+        rg=rg, n_route=n_route, rx=rx, ry=ry, ctl=ctl, act=act, branch=branch,
     )
+
+
+def _route_paths(lx, ly, th0, branch):
+    """The ego's route paths (Sec. 3.2 on-/off-route paths, synthetic): one
+    on-route polyline through its logged positions (t0 onwards, points closer
+    than 0.25 m to the previous one dropped) extended 20 m before the start
+    and 30 m past the end, and two off-route branches leaving it at the
+    fractions branch[0] of its points, turning by branch[1] rad and then
+    following curvature branch[2] for 60 m at 1 m spacing."""
+    pts = [(lx[0], ly[0])]
+    for x, y in zip(lx[1:], ly[1:]):
+        if np.hypot(x - pts[-1][0], y - pts[-1][1]) >= 0.25:
+            pts.append((x, y))
+    pts = np.array(pts, dtype=np.float64)
+    d0 = pts[1] - pts[0] if len(pts) > 1 else np.array([np.cos(th0), np.sin(th0)])
+    d1 = pts[-1] - pts[-2] if len(pts) > 1 else d0
+    d0, d1 = d0 / np.linalg.norm(d0), d1 / np.linalg.norm(d1)
+    on = np.concatenate([[pts[0] - 20.0 * d0], pts, [pts[-1] + 30.0 * d1]])
+    paths = [on]
+    for frac, turn, kap in branch.T:
+        k = min(len(on) - 2, max(1, int(frac * (len(on) - 1))))
+        u = on[k + 1] - on[k]
+        h = np.arctan2(u[1], u[0]) + turn + np.cumsum(np.full(60, kap))
+        off = on[k] + np.concatenate([[[0.0, 0.0]], np.cumsum(np.stack([np.cos(h), np.sin(h)], 1), 0)])
+        paths.append(off)
+    return paths, np.array([1, 0, 0], np.uint8)
 
 
 @dataclass
@@ -264,12 +294,26 @@ class SceneBatch:
     log_th: Optional[np.ndarray] = None   # float32 [T_LOG][N_tot] logged heading (zeros if not given)
     log_vx: Optional[np.ndarray] = None   # logged velocity
     log_vy: Optional[np.ndarray] = None
+    # Route paths of each scene's first agent: scene s owns paths
+    # [path_off[s], path_off[s+1]); path p owns points [path_pt_off[p],
+    # path_pt_off[p+1]); path_on[p] = 1 for an on-route path.
+    path_off: Optional[np.ndarray] = None     # int32 [S+1] (no paths if not given)
+    path_pt_off: Optional[np.ndarray] = None  # int32 [P+1]
+    path_x: Optional[np.ndarray] = None       # float32 [path points]
+    path_y: Optional[np.ndarray] = None
+    path_on: Optional[np.ndarray] = None      # uint8 [P]
     extra: dict = field(default_factory=dict)
 
     def __post_init__(self):
         for k in ("log_th", "log_vx", "log_vy"):
             if getattr(self, k) is None:
                 setattr(self, k, np.zeros_like(self.log_x))
+        if self.path_off is None:
+            self.path_off = np.zeros(self.S + 1, np.int32)
+            self.path_pt_off = np.zeros(1, np.int32)
+            self.path_x = np.zeros(0, np.float32)
+            self.path_y = np.zeros(0, np.float32)
+            self.path_on = np.zeros(0, np.uint8)
 
     @property
     def T_log(self) -> int:
@@ -304,7 +348,17 @@ class SceneBatch:
             log_vy=np.ascontiguousarray(self.log_vy[:, ag]),
             x=self.x[ag], y=self.y[ag], th=self.th[ag], vx=self.vx[ag], vy=self.vy[ag],
             actions=np.ascontiguousarray(self.actions[:, :, ag]),
+            **self._path_subset(idx),
         )
+
+    def _path_subset(self, idx) -> dict:
+        p0, p1 = self.path_off[idx], self.path_off[idx + 1]
+        pp = np.concatenate([np.arange(a, b) for a, b in zip(p0, p1)] + [np.zeros(0, np.int64)]).astype(np.int64)
+        q0, q1 = self.path_pt_off[pp], self.path_pt_off[pp + 1]
+        pts = np.concatenate([np.arange(a, b) for a, b in zip(q0, q1)] + [np.zeros(0, np.int64)]).astype(np.int64)
+        off = lambda n: np.concatenate([[0], np.cumsum(n)]).astype(np.int32)
+        return dict(path_off=off(p1 - p0), path_pt_off=off(q1 - q0), path_x=self.path_x[pts],
+                    path_y=self.path_y[pts], path_on=self.path_on[pp])
 
 
 def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
@@ -337,6 +391,21 @@ def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
     log_x, log_y, log_th, log_vx, log_vy = _integrate_logs(ctl, x, y, th,
                                                            np.hypot(vx.astype(np.float64), vy.astype(np.float64)))
     log_vx[: T0 + 1], log_vy[: T0 + 1] = vx, vy  # the history rows hold the start state exactly
+    # route paths of each scene's ego (its first agent)
+    px, py, pon, ppt, poff = [], [], [], [0], [0]
+    for j, part in enumerate(parts):
+        a = int(agent_off[j])
+        if part["N"] == 0:
+            poff.append(poff[-1])
+            continue
+        paths, on = _route_paths(log_x[T0:, a].astype(np.float64), log_y[T0:, a].astype(np.float64),
+                                 float(th[a]), part["branch"])
+        for q in paths:
+            px.append(q[:, 0])
+            py.append(q[:, 1])
+            ppt.append(ppt[-1] + len(q))
+        pon.append(on)
+        poff.append(poff[-1] + len(paths))
     return SceneBatch(
         cfg=cfg, seed=seed, scenes=ids, S=len(ids), N_tot=int(Ns.sum()), T=wl.T,
         agent_off=agent_off, rg_off=rg_off,
@@ -352,4 +421,8 @@ def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
         rg_valid=np.concatenate([p["rg"][4] for p in parts]),
         log_x=log_x, log_y=log_y, log_th=log_th, log_vx=log_vx, log_vy=log_vy, x=x, y=y, th=th, vx=vx, vy=vy,
         actions=np.ascontiguousarray(np.concatenate([p["act"] for p in parts], axis=2)),
+        path_off=np.array(poff, np.int32), path_pt_off=np.array(ppt, np.int32),
+        path_x=(np.concatenate(px) if px else np.zeros(0)).astype(np.float32),
+        path_y=(np.concatenate(py) if py else np.zeros(0)).astype(np.float32),
+        path_on=(np.concatenate(pon) if pon else np.zeros(0)).astype(np.uint8),
     )
