@@ -361,6 +361,16 @@ def observe_leg(wsim, synth, torch, b, sim, st, reps):
         n_obs = int(obs.sum().item()) if obs is not None else int(b.valid.sum())
         out[name] = {"ms": ms, "observers": n_obs, "observations_per_s": n_obs / (ms / 1e3), "K": K, "M": M}
         del res
+    prog, offr = sim.route_metrics(st)
+    for _ in range(2):
+        sim.route_metrics(st)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        sim.route_metrics(st)
+    e1.record()
+    torch.cuda.synchronize()
+    out["route_metrics"] = {"ms": e0.elapsed_time(e1) / reps, "scenes": b.S}
     assert sim.status() == 0
     return out
 

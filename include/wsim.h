@@ -92,6 +92,8 @@ typedef struct {
     int32_t tile_segs; /* road-edge segments per culling tile (0 = default)      */
     float kin_amax;    /* kinematic infeasibility: |a| limit [m/s^2]: 6 (Sec. 3.4) */
     float kin_kmax;    /* ... |kappa| limit [1/m]: 0.3 (Sec. 3.4)                 */
+    float route_max_dist; /* off-route: farther than this from every on-route path [m]: 5 */
+    float route_max_rel;  /* off-route: an off-route path nearer by more than this [m]: 2 */
 } wsim_config;
 
 /* A batch of S scenes (all device pointers; sizes on the host).
@@ -119,6 +121,14 @@ typedef struct {
     const float *log_vx, *log_vy;      /* the logged velocity it may be NULL, */
                                        /* which disables the expert and log   */
                                        /* playback (WSIM_EINVAL if asked for) */
+    /* Route paths of each scene's first agent (Sec. 3.2 on-/off-route paths;
+     * may be NULL: no route metrics): scene s owns paths [path_off[s],
+     * path_off[s+1]), path p owns points [path_pt_off[p], path_pt_off[p+1]),
+     * path_on[p] = 1 marks an on-route path. */
+    const int32_t *path_off;           /* [S+1]                               */
+    const int32_t *path_pt_off;        /* [paths+1]                           */
+    const float *path_x, *path_y;      /* [path points]                       */
+    const uint8_t *path_on;            /* [paths]                             */
 } wsim_batch;
 
 /* Agent state, [N_tot] each.  Positions, heading and route cursor are
@@ -195,6 +205,18 @@ int wsim_metrics(wsim_ctx *ctx, const wsim_state *st, const wsim_metric_buf *m, 
  * are the base pointers advanced by k*N_tot. */
 int wsim_rollout(wsim_ctx *ctx, wsim_state *st, const float *act_seq, const uint8_t *ctrl, int t0,
                  int T, int mode, const wsim_metric_buf *mseq, const wsim_state *traj, void *stream);
+
+/* Route metrics (Sec. 3.4) of each scene's first agent at state st:
+ * progress[s] (device, [S]) = (d_x - d_p) / (d_q - d_p), where d_x is the
+ * arc length along the on-route path nearest to the agent (ties: the lower
+ * path) of the agent's nearest point on it (ties: the lower segment), and
+ * d_p, d_q those of the first and last logged positions (log rows 0 and
+ * T_log-1) on the same path; NaN when d_q - d_p <= 1 mm or the scene has no
+ * on-route path.  off_route[s] (device, [S]) = 1 when the agent is farther
+ * than route_max_dist from every on-route path or nearer to an off-route
+ * path by more than route_max_rel.  Requires the batch's route paths
+ * (WSIM_EINVAL without).  Asynchronous on `stream`. */
+int wsim_route_metrics(wsim_ctx *ctx, const wsim_state *st, float *progress, uint8_t *off_route, void *stream);
 
 /* Expert actions, open loop (Sec. 5.2: the inverse of each agent's action
  * space fitted to the logged trajectory, App. A.1): act_out [T][3][N_tot]

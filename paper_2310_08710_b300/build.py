@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SO = os.path.join(HERE, "libwsim.so")
-SOURCES = ["wsim_kernels.cu", "wsim_rollout.cu", "wsim_bptt.cu", "wsim_observe.cu", "wsim_api.cu", "wsim_static.cu"]
+SOURCES = ["wsim_kernels.cu", "wsim_rollout.cu", "wsim_bptt.cu", "wsim_observe.cu", "wsim_route.cu", "wsim_api.cu", "wsim_static.cu"]
 HEADERS = ["wsim_device.cuh", "wsim_internal.h", "wsim_phases.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-shared"]

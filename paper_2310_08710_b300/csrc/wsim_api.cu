@@ -278,6 +278,8 @@ void wsim_default_config(wsim_config* cfg) {
     cfg->tile_segs = 0;
     cfg->kin_amax = 6.0f;
     cfg->kin_kmax = 0.3f;
+    cfg->route_max_dist = 5.0f;
+    cfg->route_max_rel = 2.0f;
 }
 
 const char* wsim_strerror(int code) {
@@ -515,6 +517,18 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
         c->have_key = true;
     }
     CK(cudaGraphLaunch(c->exec, s));
+    return WSIM_OK;
+}
+
+int wsim_route_metrics(wsim_ctx* c, const wsim_state* st, float* progress, uint8_t* off_route, void* stream) {
+    if (!c || !state_ok(st) || !progress || !off_route) return WSIM_EINVAL;
+    const wsim_batch& b = c->b;
+    if (!b.path_off || !b.path_pt_off || !b.path_x || !b.path_y || !b.path_on) return WSIM_EINVAL;
+    c->last = S_(stream);
+    StepArgs a = base_args(c);
+    a.in = cstate(st);
+    CK(launch_route(a, b.path_off, b.path_pt_off, b.path_x, b.path_y, b.path_on, c->cfg.route_max_dist,
+                    c->cfg.route_max_rel, progress, off_route, S_(stream)));
     return WSIM_OK;
 }
 

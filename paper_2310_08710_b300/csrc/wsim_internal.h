@@ -124,6 +124,10 @@ cudaError_t launch_observe(const StepArgs& a, const uint8_t* observers, int32_t*
                            const int32_t* tile_off, const float4* box, const int32_t* cnt, const int32_t* scene_of,
                            int M, int K, float* agents, uint8_t* agents_valid, float* rg, int32_t* rg_idx,
                            cudaStream_t st);
+// Route metrics (wsim_route.cu).
+cudaError_t launch_route(const StepArgs& a, const int32_t* path_off, const int32_t* path_pt_off, const float* path_x,
+                         const float* path_y, const uint8_t* path_on, float max_dist, float max_rel, float* progress,
+                         uint8_t* off_route, cudaStream_t st);
 // Backpropagation through the rollout (wsim_bptt.cu).
 cudaError_t launch_bptt(const StepArgs& a, float* ckpt, float* segbuf, int ck, double* loss, float* dact,
                         float lambda, float tau, int grid, bool plain, cudaStream_t st);

@@ -35,7 +35,8 @@ class WsimConfig(C.Structure):
     _fields_ = [("dt", C.c_float), ("idm_amax", C.c_float), ("idm_b", C.c_float), ("idm_T", C.c_float),
                 ("idm_s0", C.c_float), ("idm_dq", C.c_float), ("route_h", C.c_float), ("gap_min", C.c_float),
                 ("loss_lambda", C.c_float), ("loss_tau", C.c_float), ("ckpt_every", C.c_int32),
-                ("tile_segs", C.c_int32), ("kin_amax", C.c_float), ("kin_kmax", C.c_float)]
+                ("tile_segs", C.c_int32), ("kin_amax", C.c_float), ("kin_kmax", C.c_float),
+                ("route_max_dist", C.c_float), ("route_max_rel", C.c_float)]
 
 
 class WsimBatch(C.Structure):
@@ -47,7 +48,9 @@ class WsimBatch(C.Structure):
                 ("route_x", C.c_void_p), ("route_y", C.c_void_p), ("rg_x", C.c_void_p), ("rg_y", C.c_void_p),
                 ("rg_poly", C.c_void_p), ("rg_type", C.c_void_p), ("rg_valid", C.c_void_p),
                 ("log_x", C.c_void_p), ("log_y", C.c_void_p),
-                ("log_th", C.c_void_p), ("log_vx", C.c_void_p), ("log_vy", C.c_void_p)]
+                ("log_th", C.c_void_p), ("log_vx", C.c_void_p), ("log_vy", C.c_void_p),
+                ("path_off", C.c_void_p), ("path_pt_off", C.c_void_p), ("path_x", C.c_void_p),
+                ("path_y", C.c_void_p), ("path_on", C.c_void_p)]
 
 
 STATE_FIELDS = ("x", "y", "x_lo", "y_lo", "th", "th_lo", "vx", "vy", "s", "s_lo")
@@ -104,6 +107,7 @@ def _load():
     lib.wsim_loss_grad.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
     lib.wsim_expert_actions.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    lib.wsim_route_metrics.argtypes = [vp, P(WsimState), vp, vp, vp]
     lib.wsim_observe.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
     return lib
 
@@ -112,7 +116,8 @@ lib = _load()
 
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
             "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static",
-            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad", "wsim_expert_actions", "wsim_observe")
+            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad", "wsim_expert_actions", "wsim_observe",
+            "wsim_route_metrics")
 
 
 class WsimError(RuntimeError):
@@ -164,11 +169,18 @@ class DeviceBatch:
         self.log_th = t(b.log_th, torch.float32) if full else None
         self.log_vx = t(b.log_vx, torch.float32) if full else None
         self.log_vy = t(b.log_vy, torch.float32) if full else None
+        paths = getattr(b, "path_off", None) is not None and int(b.path_off[-1]) > 0
+        self.path_off = t(b.path_off, torch.int32) if paths else None
+        self.path_pt_off = t(b.path_pt_off, torch.int32) if paths else None
+        self.path_x = t(b.path_x, torch.float32) if paths else None
+        self.path_y = t(b.path_y, torch.float32) if paths else None
+        self.path_on = t(b.path_on, torch.uint8) if paths else None
         self.c = WsimBatch(self.S, self.N_tot, self.T_log, 0, int(b.rg_off[-1]), int(b.route_off[-1]),
                            *[_ptr(getattr(self, k)) for k in (
                                "agent_off", "rg_off", "L", "W", "idm_v0", "valid", "kind", "route_off",
                                "route_x", "route_y", "rg_x", "rg_y", "rg_poly", "rg_type", "rg_valid",
-                               "log_x", "log_y", "log_th", "log_vx", "log_vy")])
+                               "log_x", "log_y", "log_th", "log_vx", "log_vy",
+                               "path_off", "path_pt_off", "path_x", "path_y", "path_on")])
 
 
 class State:
@@ -295,6 +307,17 @@ class Sim:
                                 out["agents_valid"].data_ptr(), out["rg"].data_ptr(), out["rg_idx"].data_ptr(),
                                 _stream(stream)), "wsim_observe")
         return out
+
+    def route_metrics(self, st: State, stream=None):
+        """Route progress ratio (float32 [S], NaN when undefined) and
+        off-route flag (uint8 [S]) of each scene's first agent
+        (wsim_route_metrics)."""
+        S, dev = self.batch.S, self.batch.log_x.device
+        prog = torch.empty(S, dtype=torch.float32, device=dev)
+        off = torch.empty(S, dtype=torch.uint8, device=dev)
+        _check(lib.wsim_route_metrics(self._h, C.byref(st.c()), prog.data_ptr(), off.data_ptr(), _stream(stream)),
+               "wsim_route_metrics")
+        return prog, off
 
     def expert_actions(self, t0: int, T: int, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
         """Open-loop expert actions [T, 3, N_tot] fitted to log rows t0 .. t0+T

@@ -51,6 +51,8 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.wsim_rollout(None, None, None, None, 10, 80, 0, None, None, None) == wsim.EINVAL
     assert lib.wsim_expert_actions(None, 10, 80, None, None) == wsim.EINVAL
     assert lib.wsim_observe(None, None, None, 128, 64, None, None, None, None, None) == wsim.EINVAL
+    assert lib.wsim_route_metrics(None, None, None, None, None) == wsim.EINVAL
+    assert cfg.route_max_dist == 5.0 and cfg.route_max_rel == 2.0
     assert lib.wsim_strerror(wsim.ETIMEOUT).decode().startswith("a bounded")
 
 
