@@ -40,7 +40,10 @@ class ObParams(C.Structure):
                 ("route_h", C.c_double), ("gap_min", C.c_double), ("band", C.c_double),
                 ("idm_K", C.c_int32), ("pad_", C.c_int32),
                 ("kin_amax", C.c_double), ("kin_kmax", C.c_double), ("kin_band_a", C.c_double),
-                ("kin_band_th", C.c_double), ("route_max_dist", C.c_double), ("route_max_rel", C.c_double)]
+                ("kin_band_th", C.c_double), ("route_max_dist", C.c_double), ("route_max_rel", C.c_double),
+                ("disc_a_max", C.c_double), ("disc_k_max", C.c_double), ("disc_d_max", C.c_double),
+                ("disc_t_max", C.c_double), ("disc_na", C.c_int32), ("disc_nk", C.c_int32), ("disc_nd", C.c_int32),
+                ("disc_nt", C.c_int32)]
 
 
 class ObBatch(C.Structure):
@@ -77,6 +80,8 @@ def lib():
         _lib.oracle_rollout.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp, _u8p,
                                         C.c_int, C.c_int, P(ObMetrics), C.c_int]
         _lib.oracle_inverse.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), P(ObState), _dp]
+        _lib.oracle_discretize.argtypes = [P(ObParams), P(ObBatch), _dp, C.c_int, _i32p, _u8p]
+        _lib.oracle_decode_actions.argtypes = [P(ObParams), P(ObBatch), _i32p, C.c_int, _dp]
         _lib.oracle_route.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _dp, _u8p]
         _lib.oracle_observe.argtypes = [P(ObParams), P(ObBatch), C.c_int, C.c_int, P(ObState), _u8p, C.c_int,
                                         C.c_int, _dp, _u8p, _dp, _i32p]
@@ -114,11 +119,21 @@ class Params:
     kin_band_th: float = 1e-5
     route_max_dist: float = 5.0
     route_max_rel: float = 2.0
+    disc_a_max: float = 6.0
+    disc_k_max: float = 0.3
+    disc_d_max: float = 6.0
+    disc_t_max: float = 0.3
+    disc_na: int = 13
+    disc_nk: int = 31
+    disc_nd: int = 25
+    disc_nt: int = 13
 
     def c(self) -> ObParams:
         return ObParams(self.dt, self.idm_amax, self.idm_b, self.idm_T, self.idm_s0, self.idm_dq,
                         self.route_h, self.gap_min, self.band, self.idm_K, 0, self.kin_amax, self.kin_kmax,
-                        self.kin_band_a, self.kin_band_th, self.route_max_dist, self.route_max_rel)
+                        self.kin_band_a, self.kin_band_th, self.route_max_dist, self.route_max_rel,
+                        self.disc_a_max, self.disc_k_max, self.disc_d_max, self.disc_t_max, self.disc_na,
+                        self.disc_nk, self.disc_nd, self.disc_nt)
 
 
 def _ptr(a: np.ndarray, t):
@@ -130,7 +145,7 @@ def _f64(a) -> np.ndarray:
 
 
 STATE_KEYS = ("x", "y", "th", "vx", "vy", "s")
-CTRL_HOLD, CTRL_ACTION, CTRL_EXPERT, CTRL_LOG = 0, 1, 2, 3
+CTRL_HOLD, CTRL_ACTION, CTRL_EXPERT, CTRL_LOG, CTRL_EXPERT_DISCRETE = 0, 1, 2, 3, 4
 
 
 class Oracle:
@@ -280,6 +295,26 @@ class Oracle:
         if rc:
             raise RuntimeError("oracle_observe failed")
         return out
+
+    def discretize(self, act_seq: np.ndarray):
+        """Discrete action indices [T][N_tot] of act_seq [T][3][N_tot] and
+        the band flags (a component near a rounding boundary)."""
+        act = _f64(act_seq).reshape(-1, 3, self.b.N_tot)
+        T = act.shape[0]
+        idx = np.zeros((T, self.b.N_tot), np.int32)
+        band = np.zeros((T, self.b.N_tot), np.uint8)
+        if lib().oracle_discretize(C.byref(self._cp), C.byref(self._batch), _ptr(act, _dp), T, _ptr(idx, _i32p),
+                                   _ptr(band, _u8p)):
+            raise RuntimeError("oracle_discretize failed")
+        return idx, band
+
+    def decode_actions(self, idx: np.ndarray) -> np.ndarray:
+        idx = np.ascontiguousarray(idx, np.int32).reshape(-1, self.b.N_tot)
+        act = np.zeros((idx.shape[0], 3, self.b.N_tot))
+        if lib().oracle_decode_actions(C.byref(self._cp), C.byref(self._batch), _ptr(idx, _i32p), idx.shape[0],
+                                       _ptr(act, _dp)):
+            raise RuntimeError("oracle_decode_actions failed")
+        return act
 
     def route(self, st: dict, scenes=None):
         """Route progress ratio [S] (NaN when undefined) and flags [S] (bit0

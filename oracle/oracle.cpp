@@ -133,6 +133,47 @@ void kin_check(const ob_params* p, const St<double>& s, const St<double>& n, boo
 
 bool has_full_log(const ob_batch* b) { return b->log_th && b->log_vx && b->log_vy; }
 
+// Grid index of v on n values over [-max, max] (float32, see oracle.h);
+// *near = the scaled value lies within 1e-3 of a rounding boundary.
+int disc_index(double v, double max, int n, bool* near) {
+    const float step = 2.0f * (float)max / (float)(n - 1);
+    const float c = 0.5f * (float)(n - 1);
+    const float q = (float)v / step + c;
+    const float r = std::rint(q);
+    if (near && std::fabs(std::fabs(q - std::floor(q)) - 0.5f) < 1e-3f && q > -0.5f && q < n - 0.5f) *near = true;
+    return (int)std::min((float)(n - 1), std::max(0.0f, r));
+}
+float disc_value(int i, double max, int n) {
+    const float step = 2.0f * (float)max / (float)(n - 1);
+    const float c = 0.5f * (float)(n - 1);
+    return ((float)i - c) * step;
+}
+
+// Flat discrete index of an action of agent kind `kind` (-1 for IDM).
+int disc_encode(const ob_params* p, int kind, const double u[3], bool* near) {
+    if (kind == 0)
+        return disc_index(u[0], p->disc_a_max, p->disc_na, near) * p->disc_nk +
+               disc_index(u[1], p->disc_k_max, p->disc_nk, near);
+    if (kind == 1)
+        return (disc_index(u[0], p->disc_d_max, p->disc_nd, near) * p->disc_nd +
+                disc_index(u[1], p->disc_d_max, p->disc_nd, near)) * p->disc_nt +
+               disc_index(u[2], p->disc_t_max, p->disc_nt, near);
+    return -1;
+}
+void disc_decode(const ob_params* p, int kind, int idx, double u[3]) {
+    u[0] = u[1] = u[2] = 0.0;
+    if (idx < 0) return;
+    if (kind == 0) {
+        u[0] = disc_value(idx / p->disc_nk, p->disc_a_max, p->disc_na);
+        u[1] = disc_value(idx % p->disc_nk, p->disc_k_max, p->disc_nk);
+    } else if (kind == 1) {
+        const int it = idx % p->disc_nt, ixy = idx / p->disc_nt;
+        u[0] = disc_value(ixy / p->disc_nd, p->disc_d_max, p->disc_nd);
+        u[1] = disc_value(ixy % p->disc_nd, p->disc_d_max, p->disc_nd);
+        u[2] = disc_value(it, p->disc_t_max, p->disc_nt);
+    }
+}
+
 St<double> log_state(const ob_batch* b, int t, int g) {
     const size_t i = (size_t)t * b->N_tot + g;
     return {b->log_x[i], b->log_y[i], b->log_th[i], b->log_vx[i], b->log_vy[i]};
@@ -439,9 +480,10 @@ int transition_scene(const ob_params* p, const ob_batch* b, int s, const ob_stat
         if (lead_out) lead_out[g] = -1;
         const int kind = b->kind[g];
         const int cm = ctrl ? ctrl[g] : OB_CTRL_ACTION;
-        if (cm > OB_CTRL_LOG) return -1;
+        if (cm > OB_CTRL_EXPERT_DISCRETE) return -1;
         if (!b->valid[g] || (kind != 2 && cm == OB_CTRL_HOLD)) { copy_agent(in, out, g); continue; }
-        const bool needs_log = cm == OB_CTRL_LOG || (cm == OB_CTRL_EXPERT && kind != 2);
+        const bool expert = cm == OB_CTRL_EXPERT || cm == OB_CTRL_EXPERT_DISCRETE;
+        const bool needs_log = cm == OB_CTRL_LOG || (expert && kind != 2);
         if (needs_log && (!has_full_log(b) || t_next < 0 || t_next >= b->T_log)) return -1;
         if (cm == OB_CTRL_LOG) {  // log playback (Sec. 3.5): the logged state of t+1
             put_state(out, g, log_state(b, t_next, g));
@@ -452,8 +494,14 @@ int transition_scene(const ob_params* p, const ob_batch* b, int s, const ob_stat
         St<double> cur = get_state(in, g);
         if (kind == 0 || kind == 1) {
             double u[3];
-            if (cm == OB_CTRL_EXPERT) {  // Sec. 5.2 expert: the action fitted to the log
+            if (expert) {  // Sec. 5.2 expert: the action fitted to the log
                 inverse_action(p, kind, cur, log_state(b, t_next, g), u);
+                if (cm == OB_CTRL_EXPERT_DISCRETE) {  // ... snapped to the discrete grid
+                    bool near = false;
+                    const int idx = disc_encode(p, kind, u, &near);
+                    disc_decode(p, kind, idx, u);
+                    if (band_idm && near) band_idm[g] = 1;
+                }
             } else {
                 u[0] = act[g]; u[1] = act[N + g]; u[2] = act[2 * N + g];
             }
@@ -613,6 +661,34 @@ int oracle_metrics(const ob_params* p, const ob_batch* b, int s0, int s1,
     if (!p || !b || !st || !m || s0 < 0 || s1 > b->S || s0 > s1 || t < 0 || t >= b->T_log) return -1;
     for (int s = s0; s < s1; ++s)
         metrics_scene(p, b, s, st, prev, t, m->ov, m->off, m->logdiv, m->flags, m->reward);
+    return 0;
+}
+
+int oracle_discretize(const ob_params* p, const ob_batch* b, const double* act, int T, int32_t* idx,
+                      uint8_t* band) {
+    if (!p || !b || !act || !idx || T < 0) return -1;
+    const int N = b->N_tot;
+    for (int k = 0; k < T; ++k)
+        for (int g = 0; g < N; ++g) {
+            const size_t o = (size_t)k * N + g;
+            bool near = false;
+            const double u[3] = {act[(k * 3 + 0) * (size_t)N + g], act[(k * 3 + 1) * (size_t)N + g],
+                                 act[(k * 3 + 2) * (size_t)N + g]};
+            idx[o] = b->valid[g] ? disc_encode(p, b->kind[g], u, &near) : -1;
+            if (band) band[o] = near;
+        }
+    return 0;
+}
+
+int oracle_decode_actions(const ob_params* p, const ob_batch* b, const int32_t* idx, int T, double* act) {
+    if (!p || !b || !act || !idx || T < 0) return -1;
+    const int N = b->N_tot;
+    for (int k = 0; k < T; ++k)
+        for (int g = 0; g < N; ++g) {
+            double u[3];
+            disc_decode(p, b->kind[g], idx[(size_t)k * N + g], u);
+            for (int c = 0; c < 3; ++c) act[(k * 3 + c) * (size_t)N + g] = u[c];
+        }
     return 0;
 }
 

@@ -46,6 +46,10 @@ typedef struct {
     double kin_band_th; /* band around the turn limit kin_kmax * distance (rad)  */
     double route_max_dist; /* off-route: farther than this from every on-route path (m) */
     double route_max_rel;  /* off-route: an off-route path closer by more than this (m)  */
+    /* Discrete action spaces (Sec. 5.2): uniform grids [-max, max] of n values
+     * per component.  Bicycle (a, kappa); delta (dx, dy share max/n, dtheta). */
+    double disc_a_max, disc_k_max, disc_d_max, disc_t_max;
+    int32_t disc_na, disc_nk, disc_nd, disc_nt;
 } ob_params;
 
 /* A batch of scenes in CSR form.  Scene s owns agents [agent_off[s],
@@ -93,6 +97,8 @@ typedef struct {
 #define OB_CTRL_ACTION 1  /* policy agent: the given action                        */
 #define OB_CTRL_EXPERT 2  /* policy agent: the expert action fitted to log row t+1 */
 #define OB_CTRL_LOG 3     /* any agent: log playback (state := log row t+1)         */
+#define OB_CTRL_EXPERT_DISCRETE 4 /* policy agent: the expert action snapped to the
+                                     discrete grid (Sec. 5.2)                    */
 
 /* One transition t -> t+1 for scenes [s0, s1) (Sec. 4 step(): all actions are
  * resolved from state t, then every agent moves) into log time index t+1 =
@@ -122,6 +128,21 @@ int oracle_metrics(const ob_params *p, const ob_batch *b, int s0, int s1,
 int oracle_rollout(const ob_params *p, const ob_batch *b, int s0, int s1,
                    ob_state *st, const double *act_seq, const uint8_t *ctrl, int t0, int T,
                    ob_metrics *mseq, int nthreads);
+
+/* Discrete actions (Sec. 5.2: a discrete action space's inverse is the
+ * continuous inverse, discretised).  The index of a value v on a grid of n
+ * values over [-max, max] is rint(fl(fl(v) / step) + c) clamped to [0, n-1],
+ * with step = fl(2 max / (n-1)) and c = (n-1)/2, in float32 (an integer
+ * decision taken in the kernel's precision); the grid value of index i is
+ * fl(fl(i - c) * step), so an odd n puts 0 on the grid.  Flat index:
+ * bicycle i_a * n_k + i_k; delta (i_x * n_d + i_y) * n_t + i_t.
+ * oracle_discretize: act [T][3][N_tot] -> idx [T][N_tot] (-1 for IDM and
+ * invalid agents); band[T][N_tot] (may be NULL) = 1 when some component's
+ * scaled value lies within 1e-3 of a rounding boundary.
+ * oracle_decode_actions: idx -> act (grid values; 0 for idx < 0). */
+int oracle_discretize(const ob_params *p, const ob_batch *b, const double *act, int T, int32_t *idx,
+                      uint8_t *band);
+int oracle_decode_actions(const ob_params *p, const ob_batch *b, const int32_t *idx, int T, double *act);
 
 /* Inverse of the action spaces (App. A.1) for every agent of scenes [s0, s1):
  * the action that takes state prev to state next, written to act [3][N_tot]:

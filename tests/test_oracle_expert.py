@@ -204,8 +204,8 @@ def test_log_playback_and_ctrl_values():
     assert (m["logdiv"][[0, 1, 4]] == 0).all()
     with pytest.raises(RuntimeError):  # expert and playback need the log row
         o.transition(st, act, ctrl=ctrl)
-    with pytest.raises(RuntimeError):  # ctrl values above 3 are rejected
-        o.transition(st, act, ctrl=np.full(b.N_tot, 4, np.uint8), t_next=t1)
+    with pytest.raises(RuntimeError):  # ctrl values above 4 are rejected
+        o.transition(st, act, ctrl=np.full(b.N_tot, 5, np.uint8), t_next=t1)
 
 
 def _kin_flags(o, s0, s1):
