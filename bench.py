@@ -320,7 +320,8 @@ def expert_leg(wsim, synth, torch, args, rank, b, reps):
                              "roofline": {"bound": "hbm", "kernel": "k_expert_actions", "achieved": gbs,
                                           "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                                           "bytes_per_launch": nbytes, "peak_source": src, "traffic": None}}
-    for name, ctrl_v in (("rollout_expert", wsim.CTRL_EXPERT), ("log_playback", wsim.CTRL_LOG)):
+    for name, ctrl_v in (("rollout_expert", wsim.CTRL_EXPERT), ("rollout_expert_discrete", wsim.CTRL_EXPERT_DISCRETE),
+                         ("log_playback", wsim.CTRL_LOG)):
         ctrl = torch.full((N,), ctrl_v, dtype=torch.uint8, device="cuda")
 
         def run():
@@ -328,7 +329,7 @@ def expert_leg(wsim, synth, torch, args, rank, b, reps):
             sim.rollout(st, None, m, synth.T0, T, mode=wsim.MODE_FUSED, ctrl=ctrl)
         ms = timed(run)
         out[name] = {"value": N * T / (ms / 1e3), "unit": UNIT, "ms_per_rollout": ms}
-        if name == "rollout_expert":
+        if name.startswith("rollout_expert"):
             lg = m.logdiv.cpu().numpy()[:, valid]
             out[name]["ade_m"] = float(lg.mean())
             out[name]["kin_infeasible_frac"] = float(((m.flags.cpu().numpy()[:, valid] & 4) != 0).mean())

@@ -69,6 +69,8 @@ extern "C" {
 #define WSIM_CTRL_ACTION 1    /* policy agent takes the given action             */
 #define WSIM_CTRL_EXPERT 2    /* policy agent takes the expert action (Sec. 5.2) */
 #define WSIM_CTRL_LOG 3       /* any agent replays the log (Sec. 3.5)            */
+#define WSIM_CTRL_EXPERT_DISCRETE 4 /* policy agent: the expert action snapped to
+                                       the discrete grid (Sec. 5.2)              */
 
 /* Rollout modes. */
 #define WSIM_MODE_GRAPH 0      /* persistent step kernel per step, CUDA graph   */
@@ -94,6 +96,11 @@ typedef struct {
     float kin_kmax;    /* ... |kappa| limit [1/m]: 0.3 (Sec. 3.4)                 */
     float route_max_dist; /* off-route: farther than this from every on-route path [m]: 5 */
     float route_max_rel;  /* off-route: an off-route path nearer by more than this [m]: 2 */
+    /* Discrete action spaces (Sec. 5.2): n uniform values over [-max, max]
+     * per component.  Bicycle: a 13 over 6 m/s^2, kappa 31 over 0.3 1/m;
+     * delta: dx and dy 25 over 6 m, dtheta 13 over 0.3 rad. */
+    float disc_a_max, disc_k_max, disc_d_max, disc_t_max;
+    int32_t disc_na, disc_nk, disc_nd, disc_nt;
 } wsim_config;
 
 /* A batch of S scenes (all device pointers; sizes on the host).
@@ -177,8 +184,10 @@ int wsim_init(wsim_ctx **out, const wsim_config *cfg, const wsim_batch *b, void 
  * action (WSIM_CTRL_ACTION), or takes the expert action (WSIM_CTRL_EXPERT:
  * the App. A.1 inverse of its action space from its state t to log row t+1,
  * then its forward dynamics); any agent with WSIM_CTRL_LOG takes log row t+1
- * as its state; IDM agents follow their route for every other value.
- * Invalid agents keep their state.  A value above WSIM_CTRL_LOG, or the
+ * as its state; WSIM_CTRL_EXPERT_DISCRETE snaps the expert action to the
+ * discrete grid (see wsim_discretize) before applying it; IDM agents follow
+ * their route for every value but WSIM_CTRL_LOG.
+ * Invalid agents keep their state.  A value above WSIM_CTRL_EXPERT_DISCRETE, or the
  * expert or log playback without log_th/log_vx/log_vy, holds the agent and
  * sets the device status to WSIM_EINVAL.  `in` and `out` must not alias.
  * m may be NULL (transition only).  Requires 0 <= t and t+1 < T_log. */
@@ -217,6 +226,20 @@ int wsim_rollout(wsim_ctx *ctx, wsim_state *st, const float *act_seq, const uint
  * path by more than route_max_rel.  Requires the batch's route paths
  * (WSIM_EINVAL without).  Asynchronous on `stream`. */
 int wsim_route_metrics(wsim_ctx *ctx, const wsim_state *st, float *progress, uint8_t *off_route, void *stream);
+
+/* Discrete action spaces (Sec. 5.2: the expert of a discrete action space
+ * discretises the continuous inverse).  A component value v on a grid of n
+ * values over [-max, max] has index rint(fl(v / step) + c) clamped to
+ * [0, n-1], step = fl(2 max / (n-1)), c = (n-1)/2 (float32), and the grid
+ * value of index i is fl((i - c) * step).  Flat indices: bicycle
+ * i_a * disc_nk + i_k; delta (i_x * disc_nd + i_y) * disc_nt + i_t.
+ * wsim_discretize: act [T][3][N_tot] -> idx [T][N_tot] (-1 for IDM and
+ * invalid agents).  wsim_decode_actions: idx -> act [T][3][N_tot] (grid
+ * values; zeros for idx < 0; an index past the grid also gives zeros and
+ * sets WSIM_EINVAL in the device status).  Device arrays, caller-owned;
+ * asynchronous on `stream`. */
+int wsim_discretize(wsim_ctx *ctx, const float *act, int T, int32_t *idx, void *stream);
+int wsim_decode_actions(wsim_ctx *ctx, const int32_t *idx, int T, float *act, void *stream);
 
 /* Expert actions, open loop (Sec. 5.2: the inverse of each agent's action
  * space fitted to the logged trajectory, App. A.1): act_out [T][3][N_tot]

@@ -280,6 +280,14 @@ void wsim_default_config(wsim_config* cfg) {
     cfg->kin_kmax = 0.3f;
     cfg->route_max_dist = 5.0f;
     cfg->route_max_rel = 2.0f;
+    cfg->disc_a_max = 6.0f;
+    cfg->disc_k_max = 0.3f;
+    cfg->disc_d_max = 6.0f;
+    cfg->disc_t_max = 0.3f;
+    cfg->disc_na = 13;
+    cfg->disc_nk = 31;
+    cfg->disc_nd = 25;
+    cfg->disc_nt = 13;
 }
 
 const char* wsim_strerror(int code) {
@@ -306,6 +314,11 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     if (b->R_tot > 0 && (!b->rg_x || !b->rg_y || !b->rg_poly || !b->rg_type || !b->rg_valid)) return WSIM_EINVAL;
     if (b->route_tot > 0 && (!b->route_x || !b->route_y)) return WSIM_EINVAL;
     if (!(cfg->dt > 0.f) || !(cfg->route_h > 0.f) || !(cfg->idm_amax > 0.f) || !(cfg->idm_b > 0.f))
+        return WSIM_EINVAL;
+    if (cfg->disc_na < 2 || cfg->disc_nk < 2 || cfg->disc_nd < 2 || cfg->disc_nt < 2 ||
+        static_cast<int64_t>(cfg->disc_nd) * cfg->disc_nd * cfg->disc_nt > (1ll << 30) ||
+        static_cast<int64_t>(cfg->disc_na) * cfg->disc_nk > (1ll << 30) || !(cfg->disc_a_max > 0.f) ||
+        !(cfg->disc_k_max > 0.f) || !(cfg->disc_d_max > 0.f) || !(cfg->disc_t_max > 0.f))
         return WSIM_EINVAL;
     cudaStream_t st = S_(stream);
     const int S = b->S, N = b->N_tot;
@@ -342,7 +355,9 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     c->h_agent_off = ao;
     c->p = Params{cfg->dt,     cfg->idm_amax,         cfg->idm_b,  cfg->idm_T,
                   cfg->idm_s0, cfg->idm_dq,           cfg->route_h, 1.0f / cfg->route_h,
-                  cfg->gap_min, 2.0f * sqrtf(cfg->idm_amax * cfg->idm_b), cfg->kin_amax, cfg->kin_kmax};
+                  cfg->gap_min, 2.0f * sqrtf(cfg->idm_amax * cfg->idm_b), cfg->kin_amax, cfg->kin_kmax,
+                  cfg->disc_a_max, cfg->disc_k_max, cfg->disc_d_max, cfg->disc_t_max,
+                  cfg->disc_na, cfg->disc_nk, cfg->disc_nd, cfg->disc_nt};
     int rc = WSIM_OK;
     auto fail = [&](int code) {
         wsim_destroy(c);
@@ -517,6 +532,22 @@ int wsim_rollout(wsim_ctx* c, wsim_state* st, const float* act_seq, const uint8_
         c->have_key = true;
     }
     CK(cudaGraphLaunch(c->exec, s));
+    return WSIM_OK;
+}
+
+int wsim_discretize(wsim_ctx* c, const float* act, int T, int32_t* idx, void* stream) {
+    if (!c || !act || !idx) return WSIM_EINVAL;
+    if (T < 0) return WSIM_ESIZE;
+    c->last = S_(stream);
+    CK(launch_discretize(base_args(c), act, T, idx, S_(stream)));
+    return WSIM_OK;
+}
+
+int wsim_decode_actions(wsim_ctx* c, const int32_t* idx, int T, float* act, void* stream) {
+    if (!c || !act || !idx) return WSIM_EINVAL;
+    if (T < 0) return WSIM_ESIZE;
+    c->last = S_(stream);
+    CK(launch_decode_actions(base_args(c), idx, T, act, S_(stream)));
     return WSIM_OK;
 }
 

@@ -56,6 +56,8 @@ struct MetricsP {
 struct Params {
     float dt, amax, b, T, s0, dq, h, inv_h, gap_min, idm_sqrt_ab2;  // 2 sqrt(a b)
     float kin_amax, kin_kmax;  // kinematic infeasibility limits
+    float da_max, dk_max, dd_max, dt_max;  // discrete action grids (ranges)
+    int na, nk, nd, nt;                    // ... and values per component
 };
 
 // Everything a step or rollout kernel needs.
@@ -103,6 +105,9 @@ cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_
 cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const int32_t* soff,
                                const float4* tiles, float4* sup, cudaStream_t st);
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);
+// Discrete actions: continuous [T][3][N_tot] <-> flat grid indices [T][N_tot].
+cudaError_t launch_discretize(const StepArgs& a, const float* act, int T, int32_t* idx, cudaStream_t st);
+cudaError_t launch_decode_actions(const StepArgs& a, const int32_t* idx, int T, float* act, cudaStream_t st);
 // Open-loop expert actions over log rows [t0, t0+T] into act [T][3][N_tot].
 cudaError_t launch_expert_actions(const StepArgs& a, int t0, int T, float* act, cudaStream_t st);
 cudaError_t launch_plain_scene(const StepArgs& a, int scene, cudaStream_t st);

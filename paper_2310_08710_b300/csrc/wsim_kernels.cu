@@ -184,6 +184,53 @@ cudaError_t launch_expert_actions(const StepArgs& a, int t0, int T, float* act, 
 }
 
 // ---------------------------------------------------------------------------
+// Discrete actions (Sec. 5.2): one thread per agent-step, agents fastest.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_discretize(const StepArgs A, const float* act, int T, int32_t* idx) {
+    const size_t n_tot = static_cast<size_t>(A.N_tot), n = static_cast<size_t>(T) * n_tot;
+    for (size_t q = static_cast<size_t>(blockIdx.x) * 256 + threadIdx.x; q < n; q += static_cast<size_t>(gridDim.x) * 256) {
+        const size_t k = q / n_tot, g = q - k * n_tot;
+        const float* u = act + k * 3 * n_tot + g;
+        idx[q] = A.valid[g] ? disc_encode(A.p, A.kind[g], u[0], u[n_tot], u[2 * n_tot]) : -1;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_decode_actions(const StepArgs A, const int32_t* idx, int T, float* act) {
+    const size_t n_tot = static_cast<size_t>(A.N_tot), n = static_cast<size_t>(T) * n_tot;
+    for (size_t q = static_cast<size_t>(blockIdx.x) * 256 + threadIdx.x; q < n; q += static_cast<size_t>(gridDim.x) * 256) {
+        const size_t k = q / n_tot, g = q - k * n_tot;
+        float u0, u1, u2;
+        if (!disc_decode(A.p, A.kind[g], idx[q], u0, u1, u2)) set_status(A.status, WSIM_EINVAL);
+        float* o = act + k * 3 * n_tot + g;
+        o[0] = u0;
+        o[n_tot] = u1;
+        o[2 * n_tot] = u2;
+    }
+}
+
+static int grid_for(size_t n) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t blocks = (n + 255) / 256;
+    return static_cast<int>(blocks < static_cast<size_t>(sms) * 8 ? blocks : static_cast<size_t>(sms) * 8);
+}
+
+cudaError_t launch_discretize(const StepArgs& a, const float* act, int T, int32_t* idx, cudaStream_t st) {
+    const size_t n = static_cast<size_t>(T) * static_cast<size_t>(a.N_tot);
+    if (n == 0) return cudaSuccess;
+    k_discretize<<<grid_for(n), 256, 0, st>>>(a, act, T, idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_actions(const StepArgs& a, const int32_t* idx, int T, float* act, cudaStream_t st) {
+    const size_t n = static_cast<size_t>(T) * static_cast<size_t>(a.N_tot);
+    if (n == 0) return cudaSuccess;
+    k_decode_actions<<<grid_for(n), 256, 0, st>>>(a, idx, T, act);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
 // Road-edge segment packing (wsim_init).
 // ---------------------------------------------------------------------------
 struct RgView {

@@ -114,6 +114,46 @@ __device__ __forceinline__ BicycleInv bicycle_inverse(const Params& p, float vx,
     return r;
 }
 
+// Discrete action grids (Sec. 5.2): n values over [-max, max], centred on 0
+// for odd n.  Index rint(fl(v / step) + c) clamped to [0, n-1]; value
+// fl((i - c) * step); step = fl(2 max / (n-1)), c = (n-1)/2.
+__device__ __forceinline__ int disc_index(float v, float max, int n) {
+    const float step = __fdiv_rn(2.0f * max, static_cast<float>(n - 1));
+    const float c = 0.5f * static_cast<float>(n - 1);
+    const float q = __fadd_rn(__fdiv_rn(v, step), c);
+    return static_cast<int>(fminf(static_cast<float>(n - 1), fmaxf(0.f, rintf(q))));
+}
+__device__ __forceinline__ float disc_value(int i, float max, int n) {
+    const float step = __fdiv_rn(2.0f * max, static_cast<float>(n - 1));
+    const float c = 0.5f * static_cast<float>(n - 1);
+    return __fmul_rn(__fsub_rn(static_cast<float>(i), c), step);
+}
+// Flat index of an action (u0, u1, u2) of agent kind `kind` (-1 for IDM).
+__device__ __forceinline__ int disc_encode(const Params& p, int kind, float u0, float u1, float u2) {
+    if (kind == WSIM_KIND_BICYCLE) return disc_index(u0, p.da_max, p.na) * p.nk + disc_index(u1, p.dk_max, p.nk);
+    if (kind == WSIM_KIND_DELTA)
+        return (disc_index(u0, p.dd_max, p.nd) * p.nd + disc_index(u1, p.dd_max, p.nd)) * p.nt +
+               disc_index(u2, p.dt_max, p.nt);
+    return -1;
+}
+// The grid action of flat index idx (false when idx lies past the grid).
+__device__ __forceinline__ bool disc_decode(const Params& p, int kind, int idx, float& u0, float& u1, float& u2) {
+    u0 = u1 = u2 = 0.f;
+    if (idx < 0) return true;
+    if (kind == WSIM_KIND_BICYCLE) {
+        if (idx >= p.na * p.nk) return false;
+        u0 = disc_value(idx / p.nk, p.da_max, p.na);
+        u1 = disc_value(idx % p.nk, p.dk_max, p.nk);
+    } else if (kind == WSIM_KIND_DELTA) {
+        if (idx >= p.nd * p.nd * p.nt) return false;
+        const int it = idx % p.nt, ixy = idx / p.nt;
+        u0 = disc_value(ixy / p.nd, p.dd_max, p.nd);
+        u1 = disc_value(ixy % p.nd, p.dd_max, p.nd);
+        u2 = disc_value(it, p.dt_max, p.nt);
+    }
+    return true;
+}
+
 // Sec. 3.4 kinematic infeasibility of a transition: the inverse kinematics
 // break |a| <= kin_amax or |kappa| <= kin_kmax (the curvature test with the
 // distance multiplied out, defined for any step length).
@@ -435,9 +475,10 @@ __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* 
         float xh = sm.xh[i], xl = sm.xl[i], yh = sm.yh[i], yl = sm.yl[i];
         float thh = sm.thh[i], thl = sm.thl[i];
         float vx = sm.vx[i], vy = sm.vy[i];
+        const bool expert = cm == WSIM_CTRL_EXPERT || cm == WSIM_CTRL_EXPERT_DISCRETE;
         bool moves = sm.valid[i] && (cm == WSIM_CTRL_LOG || (kind != WSIM_KIND_IDM && cm != WSIM_CTRL_HOLD));
-        if (moves && (cm > WSIM_CTRL_LOG || (cm == WSIM_CTRL_ACTION && !act) ||
-                      ((cm == WSIM_CTRL_EXPERT || cm == WSIM_CTRL_LOG) && !full_log))) {
+        if (moves && (cm > WSIM_CTRL_EXPERT_DISCRETE || (cm == WSIM_CTRL_ACTION && !act) ||
+                      ((expert || cm == WSIM_CTRL_LOG) && !full_log))) {
             set_status(A.status, WSIM_EINVAL);
             moves = false;
         }
@@ -453,10 +494,14 @@ __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* 
             // App. A.1 bicycle forward dynamics; the expert (Sec. 5.2) first
             // fits (a, kappa) to the logged velocity of t+1.
             float a, k;
-            if (cm == WSIM_CTRL_EXPERT) {
+            if (expert) {
                 const BicycleInv r = bicycle_inverse(p, vx, vy, thh, thl, A.log_vx[row + g], A.log_vy[row + g]);
                 a = r.a;
                 k = r.kappa;
+                if (cm == WSIM_CTRL_EXPERT_DISCRETE) {  // snapped to the discrete grid
+                    float unused;
+                    disc_decode(p, kind, disc_encode(p, kind, a, k, 0.f), a, k, unused);
+                }
             } else {
                 a = act[g];
                 k = act[A.N_tot + g];
@@ -476,10 +521,12 @@ __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* 
             // App. A.1 delta dynamics; the expert's displacement (Sec. 5.2)
             // is the delta inverse, log row t+1 minus the state.
             float ddx, ddy, dth;
-            if (cm == WSIM_CTRL_EXPERT) {
+            if (expert) {
                 ddx = __fsub_rn(A.log_x[row + g] - xh, xl);
                 ddy = __fsub_rn(A.log_y[row + g] - yh, yl);
                 dth = __fsub_rn(A.log_th[row + g] - thh, thl);
+                if (cm == WSIM_CTRL_EXPERT_DISCRETE)  // snapped to the discrete grid
+                    disc_decode(p, kind, disc_encode(p, kind, ddx, ddy, dth), ddx, ddy, dth);
             } else {
                 ddx = act[g];
                 ddy = act[A.N_tot + g];

@@ -24,7 +24,7 @@ GRAD_PLAIN = 1
 MAX_AGENTS = 256
 COUNTERS = 6  # wsim_counters: evals, tile tests, SAT pairs, IDM sample tests, pair bound tests, IDM circle tests
 FLAG_COLLISION, FLAG_OFFROAD, FLAG_KININF = 1, 2, 4
-CTRL_HOLD, CTRL_ACTION, CTRL_EXPERT, CTRL_LOG = 0, 1, 2, 3
+CTRL_HOLD, CTRL_ACTION, CTRL_EXPERT, CTRL_LOG, CTRL_EXPERT_DISCRETE = 0, 1, 2, 3, 4
 
 _fp = C.POINTER(C.c_float)
 _u8p = C.POINTER(C.c_uint8)
@@ -36,7 +36,10 @@ class WsimConfig(C.Structure):
                 ("idm_s0", C.c_float), ("idm_dq", C.c_float), ("route_h", C.c_float), ("gap_min", C.c_float),
                 ("loss_lambda", C.c_float), ("loss_tau", C.c_float), ("ckpt_every", C.c_int32),
                 ("tile_segs", C.c_int32), ("kin_amax", C.c_float), ("kin_kmax", C.c_float),
-                ("route_max_dist", C.c_float), ("route_max_rel", C.c_float)]
+                ("route_max_dist", C.c_float), ("route_max_rel", C.c_float),
+                ("disc_a_max", C.c_float), ("disc_k_max", C.c_float), ("disc_d_max", C.c_float),
+                ("disc_t_max", C.c_float), ("disc_na", C.c_int32), ("disc_nk", C.c_int32), ("disc_nd", C.c_int32),
+                ("disc_nt", C.c_int32)]
 
 
 class WsimBatch(C.Structure):
@@ -107,6 +110,8 @@ def _load():
     lib.wsim_loss_grad.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
     lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
     lib.wsim_expert_actions.argtypes = [vp, C.c_int, C.c_int, vp, vp]
+    lib.wsim_discretize.argtypes = [vp, vp, C.c_int, vp, vp]
+    lib.wsim_decode_actions.argtypes = [vp, vp, C.c_int, vp, vp]
     lib.wsim_route_metrics.argtypes = [vp, P(WsimState), vp, vp, vp]
     lib.wsim_observe.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, vp, vp, vp, vp, vp]
     return lib
@@ -117,7 +122,7 @@ lib = _load()
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
             "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static",
             "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad", "wsim_expert_actions", "wsim_observe",
-            "wsim_route_metrics")
+            "wsim_route_metrics", "wsim_discretize", "wsim_decode_actions")
 
 
 class WsimError(RuntimeError):
@@ -307,6 +312,24 @@ class Sim:
                                 out["agents_valid"].data_ptr(), out["rg"].data_ptr(), out["rg_idx"].data_ptr(),
                                 _stream(stream)), "wsim_observe")
         return out
+
+    def discretize(self, act_seq: torch.Tensor, stream=None) -> torch.Tensor:
+        """Flat discrete action indices [T, N_tot] of act_seq [T, 3, N_tot]
+        (wsim_discretize)."""
+        T = act_seq.shape[0]
+        idx = torch.empty((T, self.batch.N_tot), dtype=torch.int32, device=act_seq.device)
+        _check(lib.wsim_discretize(self._h, act_seq.data_ptr(), T, idx.data_ptr(), _stream(stream)),
+               "wsim_discretize")
+        return idx
+
+    def decode_actions(self, idx: torch.Tensor, stream=None) -> torch.Tensor:
+        """Grid actions [T, 3, N_tot] of flat indices [T, N_tot]
+        (wsim_decode_actions)."""
+        T = idx.shape[0]
+        act = torch.empty((T, 3, self.batch.N_tot), dtype=torch.float32, device=idx.device)
+        _check(lib.wsim_decode_actions(self._h, idx.data_ptr(), T, act.data_ptr(), _stream(stream)),
+               "wsim_decode_actions")
+        return act
 
     def route_metrics(self, st: State, stream=None):
         """Route progress ratio (float32 [S], NaN when undefined) and

@@ -52,6 +52,9 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.wsim_expert_actions(None, 10, 80, None, None) == wsim.EINVAL
     assert lib.wsim_observe(None, None, None, 128, 64, None, None, None, None, None) == wsim.EINVAL
     assert lib.wsim_route_metrics(None, None, None, None, None) == wsim.EINVAL
+    assert lib.wsim_discretize(None, None, 1, None, None) == wsim.EINVAL
+    assert lib.wsim_decode_actions(None, None, 1, None, None) == wsim.EINVAL
+    assert (cfg.disc_na, cfg.disc_nk, cfg.disc_nd, cfg.disc_nt) == (13, 31, 25, 13)
     assert cfg.route_max_dist == 5.0 and cfg.route_max_rel == 2.0
     assert lib.wsim_strerror(wsim.ETIMEOUT).decode().startswith("a bounded")
 
