@@ -455,15 +455,31 @@ __device__ __forceinline__ int ctrl_of(const StepArgs& A, int g) {
     return A.ctrl ? A.ctrl[g] : WSIM_CTRL_ACTION;
 }
 
-template <int NT>
-__device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* act, int t_next, int a0, int N,
-                                 Counts& cnt) {
+// IDM agents of the transition, one warp each, taken from work[0].
+__device__ __forceinline__ void transition_idm_tasks(AgentSmem& sm, const StepArgs& A, int a0, int N, Counts& cnt) {
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) sm.work[1] = sm.work[2] = 0;  // the metrics phase starts after two barriers
     for (int i = next_agent(sm, 0, lane); i < N; i = next_agent(sm, 0, lane)) {
         if (A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i] && ctrl_of(A, a0 + i) != WSIM_CTRL_LOG)
             idm_agent(sm, A, a0, N, i, lane, cnt);
     }
+}
+
+template <int NT>
+__device__ void transition_policy(AgentSmem& sm, const StepArgs& A, const float* act, int t_next, int a0, int N);
+
+template <int NT>
+__device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* act, int t_next, int a0, int N,
+                                 Counts& cnt) {
+    if (threadIdx.x == 0) sm.work[1] = sm.work[2] = 0;  // the metrics phase starts after two barriers
+    transition_idm_tasks(sm, A, a0, N, cnt);
+    transition_policy<NT>(sm, A, act, t_next, a0, N);
+}
+
+// Every agent that is not an IDM agent on its route, one thread each: the
+// policy dynamics (given action, expert, discrete expert), log playback, or
+// a copy of the state.
+template <int NT>
+__device__ void transition_policy(AgentSmem& sm, const StepArgs& A, const float* act, int t_next, int a0, int N) {
     const Params& p = A.p;
     const bool full_log = A.log_th && A.log_vx && A.log_vy;
     const size_t row = static_cast<size_t>(t_next) * A.N_tot;
@@ -1053,6 +1069,17 @@ __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_bas
     }
 }
 
+// The warp tasks of the metrics (off-road groups from work[2], overlap rows
+// from work[1]), with the overlap culling records already in place.
+__device__ __forceinline__ void metrics_tasks(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
+                                              float4* meta_base, int N, Counts& cnt) {
+    const int lane = threadIdx.x & 31;
+    for (int g = next_agent(sm, 2, lane); 8 * g < N; g = next_agent(sm, 2, lane))
+        offroad_group(sm, V, hint_base, tl_base, meta_base, N, 8 * g, lane, cnt);
+    for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane))
+        if (sm.valid[i]) overlap_row(sm, N, i, lane, cnt);
+}
+
 // ov_i of a valid agent after phase_metrics.
 __device__ __forceinline__ float merged_ov(const AgentSmem& sm, int i) { return unukey(sm.ovk[i]); }
 
@@ -1088,6 +1115,94 @@ __device__ void phase_finish(AgentSmem& sm, const StepArgs& A, const MetricsP& m
     if (r) atomicAdd(&sm.reward, r);
     __syncthreads();
     if (threadIdx.x == 0) *reward = sm.reward;
+}
+
+// ---------------------------------------------------------------------------
+// The per-agent phase of the pipelined rollout step (thread per agent, between
+// two barriers).  For agent i, in this order: (1) finish the metrics of the
+// current state (log row t_log; metric row m; the scene's reward summed into
+// sm.reward); (2) advance to the next state (n* -> current, the
+// kinematic-infeasibility flag of that transition, the state stored to out);
+// (3) prepare the overlap culling record of the next state from the n*
+// arrays (the partner's n* is final during this phase, its current arrays
+// are not), and clear the overlap maxima.  Every read of another agent's
+// data is of arrays this phase does not write.
+// ---------------------------------------------------------------------------
+template <int NT>
+__device__ void finish_advance(AgentSmem& sm, const StepArgs& A, const MetricsP* m, int t_log, bool advance,
+                               const StateP* out, int a0, int N) {
+    const Params& p = A.p;
+    int r = 0;
+    for (int i = threadIdx.x; i < N; i += NT) {
+        const int g = a0 + i;
+        if (m) {
+            float ov = 0.f, off = 0.f, ld = 0.f;
+            uint8_t fl = 0;
+            if (sm.valid[i]) {
+                const size_t li = static_cast<size_t>(t_log) * A.N_tot + g;
+                const float dx = (sm.xh[i] - A.log_x[li]) + sm.xl[i];
+                const float dy = (sm.yh[i] - A.log_y[li]) + sm.yl[i];
+                ld = sqrtf(fmaf(dx, dx, dy * dy));
+                ov = merged_ov(sm, i);
+                off = sm.off[i];
+                fl = (ov > 0.f ? WSIM_FLAG_COLLISION : 0) | (off > 0.f ? WSIM_FLAG_OFFROAD : 0) |
+                     (sm.kin[i] ? WSIM_FLAG_KININF : 0);
+                r -= (ov > 0.f) + (off > 0.f);
+            }
+            m->ov[g] = ov;
+            m->off[g] = off;
+            m->logdiv[g] = ld;
+            m->flags[g] = fl;
+        }
+        if (!advance) continue;
+        sm.kin[i] = sm.valid[i] ? kin_infeasible(p, sm.vx[i], sm.vy[i], sm.thh[i], sm.thl[i], sm.nvx[i], sm.nvy[i])
+                                : uint8_t(0);
+        if (out) {
+            out->x[g] = sm.nxh[i];
+            out->x_lo[g] = sm.nxl[i];
+            out->y[g] = sm.nyh[i];
+            out->y_lo[g] = sm.nyl[i];
+            out->th[g] = sm.nth[i];
+            out->th_lo[g] = sm.ntl[i];
+            out->vx[g] = sm.nvx[i];
+            out->vy[g] = sm.nvy[i];
+            out->s[g] = sm.nsh[i];
+            out->s_lo[g] = sm.nsl[i];
+        }
+        sm.xh[i] = sm.nxh[i];
+        sm.xl[i] = sm.nxl[i];
+        sm.yh[i] = sm.nyh[i];
+        sm.yl[i] = sm.nyl[i];
+        sm.thh[i] = sm.nth[i];
+        sm.thl[i] = sm.ntl[i];
+        float c, s;
+        comp_sincos(sm.nth[i], sm.ntl[i], c, s);
+        sm.c[i] = c;
+        sm.s[i] = s;
+        sm.vx[i] = sm.nvx[i];
+        sm.vy[i] = sm.nvy[i];
+        sm.sh[i] = sm.nsh[i];
+        sm.sl[i] = sm.nsl[i];
+        // overlap culling record of the next state, from the n* arrays
+        float lb = -WSIM_INF;
+        const int q = (sm.pk[i] >> 8) > (kNoDepth >> 8) ? static_cast<int>(sm.pk[i] & 0xffu) : -1;
+        if (sm.valid[i] && q >= 0 && q < N && q != i && sm.valid[q]) {
+            const int a = min(i, q), b = max(i, q);
+            float ca, sa, cb, sb;
+            comp_sincos(sm.nth[a], sm.ntl[a], ca, sa);
+            comp_sincos(sm.nth[b], sm.ntl[b], cb, sb);
+            const float dx = comp_diff(sm.nxh[b], sm.nxl[b], sm.nxh[a], sm.nxl[a]);
+            const float dy = comp_diff(sm.nyh[b], sm.nyl[b], sm.nyh[a], sm.nyl[a]);
+            lb = sat_depth(dx, dy, ca, sa, sm.hl[a], sm.hw[a], cb, sb, sm.hl[b], sm.hw[b]);
+        }
+        const float R = (sm.hl[i] + sm.hw[i]) * 1.000001f + 5e-4f;
+        sm.obox[i] = sm.valid[i] ? make_float4(sm.nxh[i], sm.nyh[i], R, R - lb + 5e-4f)
+                                 : make_float4(sm.nxh[i], sm.nyh[i], -WSIM_INF, -WSIM_INF);
+        sm.ovk[i] = kNoDepth;
+        sm.pk[i] = kNoDepth;
+    }
+    if (r) atomicAdd(&sm.reward, r);
+    if (threadIdx.x == 0) sm.work[0] = sm.work[1] = sm.work[2] = 0;  // the next task phase
 }
 
 // ---------------------------------------------------------------------------

@@ -91,25 +91,40 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
                 break;
             }
         }
+        if (threadIdx.x == 0) sm.reward = 0;
         __syncthreads();
-        for (int k = 0; k < A.T; ++k) {
-            phase_transition<NT>(sm, A, A.act ? A.act + static_cast<size_t>(k) * 3 * N_tot : nullptr, A.t_log + k,
-                                 a0, N, cnt);
-            __syncthreads();
-            if (A.traj.x) {
-                const StateP tr = offset_state(A.traj, static_cast<size_t>(k) * N_tot);
-                writeback<NT>(sm, A.p, &tr, a0, N);
+        // Pipelined steps, two barriers each.  Iteration k: the task phase runs
+        // the metrics of state t0+k (k >= 1) together with the transition
+        // t0+k -> t0+k+1 (k < T): both read state t0+k and write disjoint
+        // arrays, and warps take off-road groups, overlap rows and then IDM
+        // agents from one pool (that order measured fastest).  The per-agent phase then finishes the metrics of
+        // t0+k (row k-1), makes t0+k+1 current and prepares its overlap
+        // bounds.  The reward of row k-1 is stored at the next task phase.
+        for (int k = 0; k <= A.T; ++k) {
+            if (k >= 2 && threadIdx.x == 0) {  // reward of row k-2, summed in the last per-agent phase
+                A.m.reward[static_cast<size_t>(k - 2) * A.S + s] = sm.reward;
+                sm.reward = 0;
+            }
+            if (k < A.T) {
+                if (k >= 1) metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, cnt);
+                transition_idm_tasks(sm, A, a0, N, cnt);
+                transition_policy<NT>(sm, A, A.act ? A.act + static_cast<size_t>(k) * 3 * N_tot : nullptr,
+                                      A.t_log + k, a0, N);
             } else {
-                writeback<NT>(sm, A.p, nullptr, a0, N);
+                metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, cnt);
             }
             __syncthreads();
-            phase_metrics<NT>(sm, V, sm.hint, tlist, tmeta, N, true, true, cnt);
-            __syncthreads();
-            const size_t r = static_cast<size_t>(k) * N_tot;
-            const MetricsP m{A.m.ov + r, A.m.off + r, A.m.logdiv + r, A.m.flags + r, nullptr};
-            phase_finish<NT>(sm, A, m, A.m.reward + static_cast<size_t>(k) * A.S + s, A.t_log + k, a0, N);
+            MetricsP m;
+            if (k >= 1) {
+                const size_t r = static_cast<size_t>(k - 1) * N_tot;
+                m = MetricsP{A.m.ov + r, A.m.off + r, A.m.logdiv + r, A.m.flags + r, nullptr};
+            }
+            const StateP tr = offset_state(A.traj, static_cast<size_t>(k) * N_tot);
+            finish_advance<NT>(sm, A, k >= 1 ? &m : nullptr, A.t_log + k - 1, k < A.T,
+                               (k < A.T && A.traj.x) ? &tr : nullptr, a0, N);
             __syncthreads();
         }
+        if (threadIdx.x == 0) A.m.reward[static_cast<size_t>(A.T - 1) * A.S + s] = sm.reward;
         store_state<NT>(sm, A.out, a0, N);
         __syncthreads();
     }
