@@ -88,6 +88,9 @@ def parse():
     ap.add_argument("--shape", type=int, default=None,
                     help="pin one launch shape of the scene-resident rollout instead of autotuning (profiling)")
     ap.add_argument("--bptt-only", action="store_true", help="run only the BPTT leg (profiling)")
+    ap.add_argument("--bptt-workload", type=int, default=3,
+                    help="synthetic workload of the BPTT leg (3 = 256 scenes x 64 agents; 4 = the 30k-point sweep)")
+    ap.add_argument("--bptt-scenes", type=int, default=None, help="override the BPTT leg's scene count")
     ap.add_argument("--profile", action="store_true",
                     help="time the main path only (no mode comparison, end-to-end or CPU legs)")
     return ap.parse_args()
@@ -202,7 +205,8 @@ def run_reference(args, ws, rank, pg):
     from paper_2310_08710_b300 import synth
     if rank != 0:
         return
-    b = synth.make_batch(args.workload, seed=args.seed, S=args.scenes)
+    b = synth.make_batch(args.workload, seed=args.seed, S=args.scenes,
+                         workers=gen_workers(args.scenes or synth.WORKLOADS[args.workload].S))
     import oracle
     cores = os.cpu_count() or 1
     # size each step so that the whole run stays within a few minutes
@@ -237,11 +241,14 @@ def bptt_leg(wsim, synth, torch, args, rank):
     """Gradient steps/s of the differentiable rollout (256 scenes x 64 agents x
     80 steps, bicycle agents, synthetic workload 3): one gradient step = forward rollout with the
     loss plus the reverse sweep giving dL/d(every action)."""
-    b = synth.make_batch(3, seed=args.seed + 1000 * rank)
+    b = synth.make_batch(args.bptt_workload, seed=args.seed + 1000 * rank, S=args.bptt_scenes,
+                         workers=gen_workers(args.bptt_scenes or synth.WORKLOADS[args.bptt_workload].S))
     sim = wsim.Sim(wsim.DeviceBatch(b))
     st = wsim.State.from_batch(b)
     act = torch.as_tensor(b.actions).cuda().contiguous()
-    out = {"workload": "256 scenes x 64 agents x 80 steps, loss = log divergence^2 + softplus overlap"}
+    out = {"workload": f"{b.S} scenes x up to {int(np.diff(b.agent_off).max())} agents x {b.T} steps "
+                       f"({synth.WORKLOADS[args.bptt_workload].name}), "
+                       "loss = log divergence^2 + softplus overlap"}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for name, ck, plain, reps in (("ckpt10", 10, False, 5), ("store_all", 1, False, 5), ("plain_per_scene_ckpt10", 10, True, 1)):
         sim.loss_grad(st, act, synth.T0, b.T, ck, plain=plain)
@@ -265,6 +272,11 @@ def bptt_leg(wsim, synth, torch, args, rank):
     assert sim.status() == 0
     sim.close()
     return out
+
+
+def gen_workers(scenes: int) -> int:
+    """Processes that draw the synthetic scenes (large batches only)."""
+    return min(32, os.cpu_count() or 1) if scenes >= 512 else 1
 
 
 def hbm_peak_gbs():
@@ -399,7 +411,8 @@ def main():
         if rank == 0:
             print(json.dumps({"profile": True, "bptt": out}), flush=True)
         return
-    b = synth.make_batch(args.workload, seed=args.seed + 1000 * rank, S=args.scenes)
+    b = synth.make_batch(args.workload, seed=args.seed + 1000 * rank, S=args.scenes,
+                         workers=gen_workers(args.scenes or synth.WORKLOADS[args.workload].S))
     T, N, S = b.T, b.N_tot, b.S
     main_mode = wsim.MODE_FUSED if args.mode == "fused" else wsim.MODE_GRAPH
     db = wsim.DeviceBatch(b)

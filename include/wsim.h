@@ -173,7 +173,10 @@ void wsim_default_config(wsim_config *cfg);
  * the packed road-edge segments and their culling tiles on the device and
  * the cost-ordered scene work list.  Allocates device scratch owned by the
  * context.  Synchronises `stream`.  Limits: agents per scene <=
- * WSIM_MAX_AGENTS, S >= 1, T_log >= 2. */
+ * WSIM_MAX_AGENTS, S >= 1, T_log >= 2; a scene's road-edge segments, each
+ * polyline run padded to a multiple of 16, at most 2^20 positions, and the
+ * batch's at most INT32_MAX once every scene is padded to a multiple of 16
+ * (else WSIM_ESIZE). */
 int wsim_init(wsim_ctx **out, const wsim_config *cfg, const wsim_batch *b, void *stream);
 
 /* step() of Sec. 4: state t -> t+1 for every scene, then the metrics of t+1

@@ -387,6 +387,12 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
         cudaStreamSynchronize(st) != cudaSuccess)
         return fail(WSIM_ECUDA);
     std::vector<int32_t> soff(S + 1, 0);
+    int64_t padded = 0;  // packed positions are int32 indexes; tile lists hold 16-bit tile indexes
+    for (int s = 0; s < S; ++s) {
+        padded += ((static_cast<int64_t>(cnt[s]) + kSegAlign - 1) / kSegAlign) * kSegAlign;
+        if (cnt[s] > kMaxSceneSegs) return fail(WSIM_ESIZE);
+    }
+    if (padded > INT32_MAX) return fail(WSIM_ESIZE);
     for (int s = 0; s < S; ++s) {
         off[s + 1] = off[s] + ((cnt[s] + kSegAlign - 1) / kSegAlign) * kSegAlign;
         const int nt = (cnt[s] + kTile - 1) / kTile;

@@ -13,6 +13,7 @@ constexpr int kRollShapes = WSIM_ROLL_SHAPES;  // launch shapes of the scene-res
 constexpr int kBuckets = WSIM_BUCKETS;          // scene-size buckets of the rollout work list
 constexpr int kTile = 16;               // road-edge segments per culling tile (half a warp)
 constexpr int kSegAlign = kTile;        // per-scene segment arrays start on a tile boundary
+constexpr int kMaxSceneSegs = 65536 * kTile;  // packed positions per scene (tile lists hold 16-bit tile indexes)
 constexpr int kSuper = 8;               // tiles per super-tile (first culling level)
 constexpr int kList = 32;               // tiles in an agent's cached candidate list (one per lane)
 constexpr float kSkin = 8.0f;           // extra radius of a candidate list beyond the current need (m)

@@ -363,13 +363,15 @@ class SceneBatch:
 
 def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
                N: Optional[int] = None, R: Optional[int] = None, S: Optional[int] = None,
-               T: Optional[int] = None) -> SceneBatch:
+               T: Optional[int] = None, workers: int = 1) -> SceneBatch:
     """Scenes of workload `cfg` (0-4).
 
     scenes: ids of the workload's scenes to draw (default all S); a scene's
     content depends only on (seed, id), so subsets reproduce the full batch.
     N, R: override agents / roadgraph points per scene (tests use tiny scenes).
     S: override the scene count of the workload; T: rollout length.
+    workers > 1 draws chunks of scenes in that many spawned processes and
+    concatenates them (the same arrays as one process draws).
     """
     wl = WORKLOADS[cfg]
     if S is not None:
@@ -377,6 +379,19 @@ def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
     if T is not None:
         wl = Workload(wl.name, wl.S, wl.N, wl.R, wl.driver, wl.ego_delta_half, T)
     ids = np.arange(wl.S) if scenes is None else np.asarray(scenes, dtype=np.int64)
+    if workers > 1 and len(ids) > 1:
+        import concurrent.futures
+        import multiprocessing
+        chunks = [c for c in np.array_split(ids, min(len(ids), 4 * workers)) if len(c)]
+        ctx = multiprocessing.get_context("spawn")  # safe whatever the parent has initialised
+        with concurrent.futures.ProcessPoolExecutor(max_workers=workers, mp_context=ctx) as ex:
+            got = list(ex.map(_build, [(cfg, seed, c, N, R, wl) for c in chunks]))
+        return concat(got)
+    return _build((cfg, seed, ids, N, R, wl))
+
+
+def _build(job) -> SceneBatch:
+    cfg, seed, ids, N, R, wl = job
     parts = [_scene(scene_rng(seed, int(s)), wl, int(s), N, R) for s in ids]
     Ns = np.array([p["N"] for p in parts], dtype=np.int64)
     Rs = np.array([p["R"] for p in parts], dtype=np.int64)
@@ -425,4 +440,34 @@ def make_batch(cfg: int, seed: int = 0, scenes: Optional[Sequence[int]] = None,
         path_x=(np.concatenate(px) if px else np.zeros(0)).astype(np.float32),
         path_y=(np.concatenate(py) if py else np.zeros(0)).astype(np.float32),
         path_on=(np.concatenate(pon) if pon else np.zeros(0)).astype(np.uint8),
+    )
+
+
+def concat(batches: Sequence[SceneBatch]) -> SceneBatch:
+    """One batch holding the scenes of `batches` in order (CSR offsets rebased)."""
+    b0 = batches[0]
+
+    def offs(name, base_of):
+        out, base = [np.zeros(1, np.int64)], 0
+        for b in batches:
+            o = getattr(b, name).astype(np.int64)
+            out.append(o[1:] + base)
+            base += base_of(b)
+        return np.concatenate(out).astype(np.int32)
+
+    cat = lambda name, axis=0: np.concatenate([getattr(b, name) for b in batches], axis=axis)
+    return SceneBatch(
+        cfg=b0.cfg, seed=b0.seed, scenes=cat("scenes"), S=sum(b.S for b in batches),
+        N_tot=sum(b.N_tot for b in batches), T=b0.T,
+        agent_off=offs("agent_off", lambda b: b.N_tot), rg_off=offs("rg_off", lambda b: len(b.rg_x)),
+        L=cat("L"), W=cat("W"), valid=cat("valid"), kind=cat("kind"), idm_v0=cat("idm_v0"),
+        route_off=offs("route_off", lambda b: len(b.route_x)), route_x=cat("route_x"), route_y=cat("route_y"),
+        rg_x=cat("rg_x"), rg_y=cat("rg_y"), rg_poly=cat("rg_poly"), rg_type=cat("rg_type"),
+        rg_valid=cat("rg_valid"),
+        log_x=cat("log_x", 1), log_y=cat("log_y", 1), log_th=cat("log_th", 1), log_vx=cat("log_vx", 1),
+        log_vy=cat("log_vy", 1), x=cat("x"), y=cat("y"), th=cat("th"), vx=cat("vx"), vy=cat("vy"),
+        actions=np.ascontiguousarray(cat("actions", 2)),
+        path_off=offs("path_off", lambda b: len(b.path_on)),
+        path_pt_off=offs("path_pt_off", lambda b: len(b.path_x)),
+        path_x=cat("path_x"), path_y=cat("path_y"), path_on=cat("path_on"),
     )

@@ -178,6 +178,23 @@ def test_max_agents_per_scene(wsim):
     assert e.value.code == wsim.ESIZE
 
 
+def test_max_road_edge_segments_per_scene(wsim):
+    # one straight road edge: n points give n - 1 segments in one run, padded
+    # to a multiple of 16; 2^20 packed positions is the limit of a scene
+    # (16-bit tile indexes in the candidate-tile lists)
+    for n_seg, ok in ((1 << 20, True), ((1 << 20) + 1, False)):
+        xs = np.arange(n_seg + 1, dtype=np.float64) * 0.01
+        b = tiny_batch([dict(x=5.0, y=1.0, th=0.0, v=1.0), dict(x=9000.0, y=-2.0, th=0.5, v=2.0)],
+                       roadgraph=[(np.stack([xs, np.zeros_like(xs)], 1), 1)], T=4)
+        if ok:
+            g = H.run_rollout(b, T=4)
+            H.teacher_forced(b, g, [0], range(4))
+        else:
+            with pytest.raises(wsim.WsimError) as e:
+                wsim.Sim(wsim.DeviceBatch(b))
+            assert e.value.code == wsim.ESIZE
+
+
 def test_idm_scene_with_routes_every_step(wsim):
     b = synth.make_batch(1, seed=3, S=6, R=4000)
     g = H.run_rollout(b)
