@@ -281,47 +281,54 @@ __device__ __forceinline__ void route_locate(float hi, float lo, const Params& p
 }
 
 // ---------------------------------------------------------------------------
-// IDM route following of agent i (Sec. 3.5; textbook IDM of Treiber et al.).
-// Warp-cooperative: lane k holds look-ahead sample k+1 at route parameter
-// s + L/2 + dq (k+1).  Candidate agents are found 32 at a time (one per lane)
-// by a bounding-circle test; for each candidate the warp tests all 32
-// samples against its box widened by half this agent's width, and the
-// ballot's lowest set bit is the first hit.  The lead is the hit agent with
-// the smallest bumper gap (ties: lower index).
+// IDM route following (Sec. 3.5; textbook IDM of Treiber et al.) of the
+// agents i0 .. i0+kIdmGroup-1 that follow their route, one warp per group.
+// The per-agent arithmetic (route cursor, acceleration, advance) runs one
+// lane per agent; the lead search runs warp-wide, agent by agent: lane k
+// holds look-ahead sample k+1 at route parameter s + L/2 + dq (k+1).
+// Candidate agents are found 32 at a time (one per lane) by a bounding-circle
+// test; for each candidate the warp tests all 32 samples against its box
+// widened by half this agent's width, and the ballot's lowest set bit is the
+// first hit.  The lead is the hit agent with the smallest bumper gap (ties:
+// lower index).
 // ---------------------------------------------------------------------------
-static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N, int i, int lane, Counts& cnt) {
+constexpr int kIdmGroup = 8;
+
+__device__ __forceinline__ int ctrl_of(const StepArgs& A, int g) {
+    return A.ctrl ? A.ctrl[g] : WSIM_CTRL_ACTION;
+}
+
+// Whether agent i is advanced by IDM in this transition.
+__device__ __forceinline__ bool idm_moves(const AgentSmem& sm, const StepArgs& A, int a0, int i) {
+    return A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i] && ctrl_of(A, a0 + i) != WSIM_CTRL_LOG;
+}
+
+struct IdmLead {
+    int lead;         // -1: no lead
+    float gap;        // bumper gap to the lead
+    float tlx, tly;   // route tangent at the first sample inside the lead's box
+};
+
+// Lead of agent i (warp-wide; every lane returns the same result).
+static __device__ IdmLead idm_lead(AgentSmem& sm, const StepArgs& A, int a0, int N, int i, int lane, Counts& cnt) {
     const Params& p = A.p;
     const int g = a0 + i;
     const int ro = A.route_off[g];
     const int P = A.route_off[g + 1] - ro;
     const float* rx = A.route_x + ro;
     const float* ry = A.route_y + ro;
-    const float s_hi = sm.sh[i], s_lo = sm.sl[i];
-    const float vxi = sm.vx[i], vyi = sm.vy[i];
-    const float v = sqrtf(fmaf(vxi, vxi, vyi * vyi));
     const float hli = sm.hl[i], wi = sm.hw[i];
 
     // This lane's look-ahead sample.
     float bh, bl;
-    two_sum(s_hi, fmaf(p.dq, static_cast<float>(lane + 1), hli), bh, bl);
-    bl = __fadd_rn(bl, s_lo);
+    two_sum(sm.sh[i], fmaf(p.dq, static_cast<float>(lane + 1), hli), bh, bl);
+    bl = __fadd_rn(bl, sm.sl[i]);
     int seg;
     float tau;
     route_locate(bh, bl, p, P, seg, tau);
-    // Route points near the cursor, loaded with the samples: the advance
-    // below moves the cursor by (v + v') dt / 2, a few segments at most, so
-    // its segment is almost always among them (lane k < kNear: point seg0 + k).
-    constexpr int kNear = 8;
-    int seg0;
-    float tau0;
-    route_locate(s_hi, s_lo, p, P, seg0, tau0);
-    const int kn = min(seg0 + lane, P - 1);
-    const float nxp = lane < kNear ? rx[kn] : 0.f, nyp = lane < kNear ? ry[kn] : 0.f;
     const float Px = rx[seg], Py = ry[seg];
     const float dx = rx[seg + 1] - Px, dy = ry[seg + 1] - Py;
     const float qox = tau * dx, qoy = tau * dy;
-    const float rn = rsqrtf(fmaf(dx, dx, dy * dy));
-    const float tx = dx * rn, ty = dy * rn;
 
     // Bounding circles of the four groups of 8 consecutive samples: a box
     // (widened by wi) that holds a sample of group G has its centre within
@@ -391,59 +398,63 @@ static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N
             if (h2) take(j2, h2);
         }
     }
+    const float rn = rsqrtf(fmaf(dx, dx, dy * dy));
+    const float tlx = __shfl_sync(kFull, dx * rn, lead_hit), tly = __shfl_sync(kFull, dy * rn, lead_hit);
+    return IdmLead{lead, gbest, tlx, tly};
+}
 
-    // IDM acceleration (exponent 4).
+static __device__ void idm_group(AgentSmem& sm, const StepArgs& A, int a0, int N, int i0, int lane, Counts& cnt) {
+    const Params& p = A.p;
+    const int i = i0 + lane;
+    const bool mine = lane < kIdmGroup && i < N && idm_moves(sm, A, a0, i);
+    IdmLead L{-1, WSIM_INF, 0.f, 0.f};
+    for (unsigned todo = __ballot_sync(kFull, mine); todo; todo &= todo - 1) {
+        const int k = __ffs(todo) - 1;
+        const IdmLead l = idm_lead(sm, A, a0, N, i0 + k, lane, cnt);
+        if (lane == k) L = l;
+    }
+    if (!mine) return;
+    // IDM acceleration (exponent 4), one lane per agent.
+    const int g = a0 + i;
+    const float vxi = sm.vx[i], vyi = sm.vy[i];
+    const float v = sqrtf(fmaf(vxi, vxi, vyi * vyi));
     const float r = v / A.v0[g];
     const float r2 = r * r;
     const float r4 = r2 * r2;
     float acc;
-    if (lead >= 0) {
-        const float tlx = __shfl_sync(kFull, tx, lead_hit);
-        const float tly = __shfl_sync(kFull, ty, lead_hit);
-        const float vl = fmaf(sm.vx[lead], tlx, sm.vy[lead] * tly);
+    if (L.lead >= 0) {
+        const float vl = fmaf(sm.vx[L.lead], L.tlx, sm.vy[L.lead] * L.tly);
         const float sstar = p.s0 + fmaxf(0.f, fmaf(v, p.T, v * (v - vl) / p.idm_sqrt_ab2));
-        const float q = sstar / gbest;
+        const float q = sstar / L.gap;
         acc = p.amax * (1.f - r4 - q * q);
     } else {
         acc = p.amax * (1.f - r4);
     }
     // Advance along the route by the trapezoidal distance of the new speed.
+    const int ro = A.route_off[g];
+    const int P = A.route_off[g + 1] - ro;
     const float vn = fmaxf(0.f, fmaf(acc, p.dt, v));
-    float sh = s_hi, sl = s_lo;
+    float sh = sm.sh[i], sl = sm.sl[i];
     comp_add(sh, sl, 0.5f * (v + vn) * p.dt);
     int sg;
     float ta;
     route_locate(sh, sl, p, P, sg, ta);
-    const int d = sg - seg0;  // the same in every lane
-    float Qx, Qy, Q1x, Q1y;
-    if (d >= 0 && d + 1 < kNear) {
-        Qx = __shfl_sync(kFull, nxp, d);
-        Qy = __shfl_sync(kFull, nyp, d);
-        Q1x = __shfl_sync(kFull, nxp, d + 1);
-        Q1y = __shfl_sync(kFull, nyp, d + 1);
-    } else {
-        Qx = rx[sg];
-        Qy = ry[sg];
-        Q1x = rx[sg + 1];
-        Q1y = ry[sg + 1];
-    }
-    const float ux = Q1x - Qx, uy = Q1y - Qy;
-    if (lane == 0) {
-        float xh, xe, yh, ye;
-        two_sum(Qx, ta * ux, xh, xe);
-        two_sum(Qy, ta * uy, yh, ye);
-        const float un = rsqrtf(fmaf(ux, ux, uy * uy));
-        sm.nxh[i] = xh;
-        sm.nxl[i] = xe;
-        sm.nyh[i] = yh;
-        sm.nyl[i] = ye;
-        sm.nth[i] = atan2f(uy, ux);
-        sm.ntl[i] = 0.f;
-        sm.nvx[i] = vn * ux * un;
-        sm.nvy[i] = vn * uy * un;
-        sm.nsh[i] = sh;
-        sm.nsl[i] = sl;
-    }
+    const float Qx = A.route_x[ro + sg], Qy = A.route_y[ro + sg];
+    const float ux = A.route_x[ro + sg + 1] - Qx, uy = A.route_y[ro + sg + 1] - Qy;
+    float xh, xe, yh, ye;
+    two_sum(Qx, ta * ux, xh, xe);
+    two_sum(Qy, ta * uy, yh, ye);
+    const float un = rsqrtf(fmaf(ux, ux, uy * uy));
+    sm.nxh[i] = xh;
+    sm.nxl[i] = xe;
+    sm.nyh[i] = yh;
+    sm.nyl[i] = ye;
+    sm.nth[i] = atan2f(uy, ux);
+    sm.ntl[i] = 0.f;
+    sm.nvx[i] = vn * ux * un;
+    sm.nvy[i] = vn * uy * un;
+    sm.nsh[i] = sh;
+    sm.nsl[i] = sl;
 }
 
 // ---------------------------------------------------------------------------
@@ -451,17 +462,12 @@ static __device__ void idm_agent(AgentSmem& sm, const StepArgs& A, int a0, int N
 // (null when no agent takes WSIM_CTRL_ACTION); t_next = t+1 is the log row
 // read by the expert and by log playback.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int ctrl_of(const StepArgs& A, int g) {
-    return A.ctrl ? A.ctrl[g] : WSIM_CTRL_ACTION;
-}
 
-// IDM agents of the transition, one warp each, taken from work[0].
+// IDM agents of the transition, kIdmGroup agents per warp task, taken from work[0].
 __device__ __forceinline__ void transition_idm_tasks(AgentSmem& sm, const StepArgs& A, int a0, int N, Counts& cnt) {
     const int lane = threadIdx.x & 31;
-    for (int i = next_agent(sm, 0, lane); i < N; i = next_agent(sm, 0, lane)) {
-        if (A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i] && ctrl_of(A, a0 + i) != WSIM_CTRL_LOG)
-            idm_agent(sm, A, a0, N, i, lane, cnt);
-    }
+    for (int q = next_agent(sm, 0, lane); q * kIdmGroup < N; q = next_agent(sm, 0, lane))
+        idm_group(sm, A, a0, N, q * kIdmGroup, lane, cnt);
 }
 
 template <int NT>
