@@ -470,7 +470,7 @@ __device__ __forceinline__ void transition_idm_tasks(AgentSmem& sm, const StepAr
         idm_group(sm, A, a0, N, q * kIdmGroup, lane, cnt);
 }
 
-template <int NT>
+template <int NT, bool DRIVERS = true>
 __device__ void transition_policy(AgentSmem& sm, const StepArgs& A, const float* act, int t_next, int a0, int N);
 
 template <int NT>
@@ -483,8 +483,9 @@ __device__ void phase_transition(AgentSmem& sm, const StepArgs& A, const float* 
 
 // Every agent that is not an IDM agent on its route, one thread each: the
 // policy dynamics (given action, expert, discrete expert), log playback, or
-// a copy of the state.
-template <int NT>
+// a copy of the state.  DRIVERS = false compiles the given-action driver
+// only (A.ctrl must be null), which keeps the rollout kernel's code small.
+template <int NT, bool DRIVERS>
 __device__ void transition_policy(AgentSmem& sm, const StepArgs& A, const float* act, int t_next, int a0, int N) {
     const Params& p = A.p;
     const bool full_log = A.log_th && A.log_vx && A.log_vy;
@@ -492,7 +493,7 @@ __device__ void transition_policy(AgentSmem& sm, const StepArgs& A, const float*
     for (int i = threadIdx.x; i < N; i += NT) {
         const int g = a0 + i;
         const int kind = A.kind[g];
-        const int cm = ctrl_of(A, g);
+        const int cm = DRIVERS ? ctrl_of(A, g) : WSIM_CTRL_ACTION;
         if (kind == WSIM_KIND_IDM && sm.valid[i] && cm != WSIM_CTRL_LOG) continue;
         float xh = sm.xh[i], xl = sm.xl[i], yh = sm.yh[i], yl = sm.yl[i];
         float thh = sm.thh[i], thl = sm.thl[i];

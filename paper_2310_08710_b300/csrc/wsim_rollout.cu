@@ -38,7 +38,7 @@ __device__ __forceinline__ StateP offset_state(const StateP& s, size_t k) {
                   s.th_lo + k, s.vx + k, s.vy + k, s.s + k, s.s_lo + k};
 }
 
-template <int NT, int MINB, bool STAGE>
+template <int NT, int MINB, bool STAGE, bool DRIVERS>
 __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
     extern __shared__ __align__(128) unsigned char dyn[];
     AgentSmem& sm = *reinterpret_cast<AgentSmem*>(dyn);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
             if (k < A.T) {
                 if (k >= 1) metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, cnt);
                 transition_idm_tasks(sm, A, a0, N, cnt);
-                transition_policy<NT>(sm, A, A.act ? A.act + static_cast<size_t>(k) * 3 * N_tot : nullptr,
+                transition_policy<NT, DRIVERS>(sm, A, A.act ? A.act + static_cast<size_t>(k) * 3 * N_tot : nullptr,
                                       A.t_log + k, a0, N);
             } else {
                 metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, cnt);
@@ -131,10 +131,14 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
     publish_counts(sm, A, cnt);
 }
 
+// [0]: the given-action and IDM drivers only (no per-agent driver array);
+// [1]: every driver.
 using KernelFn = void (*)(StepArgs);
-constexpr KernelFn kKernels[kRollShapes] = {k_rollout<512, 1, true>, k_rollout<256, 2, true>,
-                                            k_rollout<256, 4, false>, k_rollout<512, 2, false>,
-                                            k_rollout<512, 2, true>};
+constexpr KernelFn kKernels[2][kRollShapes] = {
+    {k_rollout<512, 1, true, false>, k_rollout<256, 2, true, false>, k_rollout<256, 4, false, false>,
+     k_rollout<512, 2, false, false>, k_rollout<512, 2, true, false>},
+    {k_rollout<512, 1, true, true>, k_rollout<256, 2, true, true>, k_rollout<256, 4, false, true>,
+     k_rollout<512, 2, false, true>, k_rollout<512, 2, true, true>}};
 
 static size_t stage_bytes(int seg_cap) {
     const size_t nt = static_cast<size_t>(seg_cap / kTile);
@@ -163,18 +167,23 @@ int shape_max_seg_cap(int shape) {
 
 cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm) {
     const size_t bytes = kAgentBytes + stage_bytes(kShapes[shape].stage ? seg_cap : 0);
-    cudaError_t e = cudaFuncSetAttribute(kKernels[shape], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(bytes));
-    if (e != cudaSuccess) return e;
-    int n = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kKernels[shape], kShapes[shape].threads, bytes);
+    int n = 1 << 30;
+    for (int d = 0; d < 2; ++d) {
+        cudaError_t e = cudaFuncSetAttribute(kKernels[d][shape], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(bytes));
+        if (e != cudaSuccess) return e;
+        int nd = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd, kKernels[d][shape], kShapes[shape].threads, bytes);
+        if (e != cudaSuccess) return e;
+        n = nd < n ? nd : n;
+    }
     *blocks_per_sm = n > 0 ? n : 1;
-    return e;
+    return cudaSuccess;
 }
 
 cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st) {
     const size_t bytes = kAgentBytes + stage_bytes(kShapes[shape].stage ? a.seg_cap : 0);
-    kKernels[shape]<<<grid, kShapes[shape].threads, bytes, st>>>(a);
+    kKernels[a.ctrl ? 1 : 0][shape]<<<grid, kShapes[shape].threads, bytes, st>>>(a);
     return cudaGetLastError();
 }
 
