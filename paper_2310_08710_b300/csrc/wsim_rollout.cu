@@ -128,11 +128,11 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
         store_state<NT>(sm, A.out, a0, N);
         __syncthreads();
     }
-    publish_counts(sm, A, cnt);
+    if (DRIVERS) publish_counts(sm, A, cnt);  // the lean kernel's counts are dead code
 }
 
-// [0]: the given-action and IDM drivers only (no per-agent driver array);
-// [1]: every driver.
+// [0]: the given-action and IDM drivers only (no per-agent driver array),
+// without work counting; [1]: every driver, counting on request.
 using KernelFn = void (*)(StepArgs);
 constexpr KernelFn kKernels[2][kRollShapes] = {
     {k_rollout<512, 1, true, false>, k_rollout<256, 2, true, false>, k_rollout<256, 4, false, false>,
@@ -183,7 +183,7 @@ cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm) {
 
 cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st) {
     const size_t bytes = kAgentBytes + stage_bytes(kShapes[shape].stage ? a.seg_cap : 0);
-    kKernels[a.ctrl ? 1 : 0][shape]<<<grid, kShapes[shape].threads, bytes, st>>>(a);
+    kKernels[a.ctrl || a.count ? 1 : 0][shape]<<<grid, kShapes[shape].threads, bytes, st>>>(a);
     return cudaGetLastError();
 }
 
