@@ -18,6 +18,7 @@ constexpr int kSuper = 8;               // tiles per super-tile (first culling l
 constexpr int kList = 32;               // tiles in an agent's cached candidate list (one per lane)
 constexpr float kSkin = 8.0f;           // extra radius of a candidate list beyond the current need (m)
 constexpr float kSkinSmall = 2.0f;      // fallback when the kSkin list would not fit in kList tiles
+constexpr float kListLook = 5.0f;       // the wide list is centred this many steps of motion ahead
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
 constexpr int kCounters = WSIM_COUNTERS;         // work counters (wsim_counters)
 

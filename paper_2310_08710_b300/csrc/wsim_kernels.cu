@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(NTs) k_step(const StepArgs A) {
         if (A.do_metrics) {
             const SegView V = global_view(A.segs, s);
             phase_metrics<NTs>(sm, V, A.hint ? A.hint + 4 * a0 : nullptr, A.tlist ? A.tlist + kList * a0 : nullptr,
-                               A.tmeta ? A.tmeta + a0 : nullptr, N, true, true, cnt);
+                               A.tmeta ? A.tmeta + a0 : nullptr, N, true, true, kListLook * A.p.dt, cnt);
             __syncthreads();
             phase_finish<NTs>(sm, A, A.m, A.m.reward + s, A.t_log, a0, N);
         }
@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(NTs) k_plain_overlap(const StepArgs A, int s) 
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
     load_state<NTs>(sm, A, A.do_transition ? as_const(A.out) : A.in, a0, N);
     __syncthreads();
-    phase_metrics<NTs>(sm, SegView{}, nullptr, nullptr, nullptr, N, true, false, cnt);
+    phase_metrics<NTs>(sm, SegView{}, nullptr, nullptr, nullptr, N, true, false, 0.f, cnt);
     __syncthreads();
     for (int i = threadIdx.x; i < N; i += NTs)
         if (sm.valid[i]) A.m.ov[a0 + i] = merged_ov(sm, i);
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(NTs) k_plain_offroad(const StepArgs A, int s) 
     __syncthreads();
     phase_metrics<NTs>(sm, global_view(A.segs, s), A.hint ? A.hint + 4 * a0 : nullptr,
                        A.tlist ? A.tlist + kList * a0 : nullptr, A.tmeta ? A.tmeta + a0 : nullptr, N, false, true,
-                       cnt);
+                       kListLook * A.p.dt, cnt);
     __syncthreads();
     for (int i = threadIdx.x; i < N; i += NTs)
         if (sm.valid[i]) A.m.off[a0 + i] = sm.off[i];

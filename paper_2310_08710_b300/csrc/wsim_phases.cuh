@@ -760,7 +760,7 @@ __device__ __forceinline__ float corner_side(const SegView& V, int e, float d2, 
 
 static __device__ float offroad_agent(const SegView& V, int lane, float xh, float xl, float yh, float yl, float c,
                                       float s, float hl, float hw, int32_t* hint, uint16_t* tl, float4* meta,
-                                      Counts& cnt, bool force_scan = false) {
+                                      Counts& cnt, bool force_scan = false, float lvx = 0.f, float lvy = 0.f) {
     if (V.E == 0) {
         if (hint && lane < 4) hint[lane] = -1;
         return -WSIM_INF;
@@ -866,12 +866,17 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
         }
     }
     if (!done) {
-        // Full search over the super-tiles; on the way, collect the tiles
-        // within R of the centre as the next candidate list.
-        // Two list radii are collected in one scan; the wider is kept when it fits.
-        const float R = ucap + rad + kSkin, Rs = ucap + rad + kSkinSmall;
+        // Full search over the super-tiles; on the way, collect the next
+        // candidate list.  Two lists are collected in one scan and the wider
+        // is kept when it fits: the tiles within R of a centre moved ahead
+        // of the agent by (lvx, lvy) (R grown by that distance, so the list
+        // covers the agent's next steps), and the tiles within Rs of the
+        // centre itself.
+        const float dl = sqrt_approx(fmaf(lvx, lvx, lvy * lvy)) * 1.000001f;
+        const float lcx = ccx + lvx, lcy = ccy + lvy;
+        const float R = ucap + rad + kSkin + dl, Rs = ucap + rad + kSkinSmall;
         const float R2 = (R + 1e-3f) * (R + 1e-3f);
-        const float slim = fmaxf(clim, R2);
+        const float slim = fmaxf(clim, (Rs + 1e-3f) * (Rs + 1e-3f));
         int nl = 0, nls = 0;
         int small_t = -1;  // the narrow list, entry n kept by lane n
         for (int sb = 0; sb < V.ns; sb += 32) {
@@ -880,7 +885,9 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
                 const float4 B = V.sup[sb + lane];
                 const float dx = fmaxf(fmaxf(B.x - ccx, ccx - B.z), 0.f);
                 const float dy = fmaxf(fmaxf(B.y - ccy, ccy - B.w), 0.f);
-                pass = fmaf(dx, dx, dy * dy) <= slim;
+                const float ex = fmaxf(fmaxf(B.x - lcx, lcx - B.z), 0.f);
+                const float ey = fmaxf(fmaxf(B.y - lcy, lcy - B.w), 0.f);
+                pass = fmaf(dx, dx, dy * dy) <= slim || fmaf(ex, ex, ey * ey) <= R2;
             }
             if (lane == 0) cnt.tiles += min(32, V.ns - sb);
             unsigned sup = __ballot_sync(kFull, pass);
@@ -896,7 +903,7 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
                     const float4 Q = V.tiles[2 * t + 1];
                     const float dc = cap_d2(C, Q.y, ccx, ccy);
                     const float rl = R + Q.x + 1e-3f, rs = Rs + Q.x + 1e-3f, rc = ucap + rad + Q.x;
-                    inl = dc <= rl * rl;
+                    inl = cap_d2(C, Q.y, lcx, lcy) <= rl * rl;
                     inls = dc <= rs * rs;
                     if (dc <= rc * rc) {
 #pragma unroll
@@ -927,13 +934,13 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
         }
         if (tl) {
             if (nl <= kList) {
-                if (lane == 0) *meta = make_float4(ccx, ccy, R, __int_as_float(nl));
+                if (lane == 0) *meta = make_float4(lcx, lcy, R, __int_as_float(nl));
             } else if (nls <= kList) {
                 __syncwarp();
                 if (lane < nls) tl[lane] = static_cast<uint16_t>(small_t);
                 if (lane == 0) *meta = make_float4(ccx, ccy, Rs, __int_as_float(nls));
             } else if (lane == 0) {
-                *meta = make_float4(ccx, ccy, R, __int_as_float(-1));
+                *meta = make_float4(lcx, lcy, R, __int_as_float(-1));
             }
         }
     }
@@ -969,7 +976,7 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
 // which also rebuilds the cache.
 // ---------------------------------------------------------------------------
 static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
-                                     float4* meta_base, int N, int g0, int lane, Counts& cnt) {
+                                     float4* meta_base, int N, int g0, int lane, float look, Counts& cnt) {
     const int a = g0 + (lane >> 2), k = lane & 3;
     const bool act = a < N && sm.valid[a];
     bool fast = false;
@@ -1050,7 +1057,7 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
         const float f = offroad_agent(V, lane, sm.xh[ai], sm.xl[ai], sm.yh[ai], sm.yl[ai], sm.c[ai], sm.s[ai],
                                       sm.hl[ai], sm.hw[ai], hint_base ? hint_base + 4 * ai : nullptr,
                                       tl_base ? tl_base + kList * ai : nullptr, tl_base ? meta_base + ai : nullptr,
-                                      cnt, true);
+                                      cnt, true, sm.vx[ai] * look, sm.vy[ai] * look);
         if (lane == 0) sm.off[ai] = f;
     }
 }
@@ -1062,7 +1069,7 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
-                              float4* meta_base, int N, bool do_ov, bool do_off, Counts& cnt) {
+                              float4* meta_base, int N, bool do_ov, bool do_off, float look, Counts& cnt) {
     const int lane = threadIdx.x & 31;
     if (do_ov) {
         overlap_bounds<NT>(sm, N);
@@ -1072,17 +1079,17 @@ __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_bas
     }
     if (do_off) {
         for (int g = next_agent(sm, 2, lane); 8 * g < N; g = next_agent(sm, 2, lane))
-            offroad_group(sm, V, hint_base, tl_base, meta_base, N, 8 * g, lane, cnt);
+            offroad_group(sm, V, hint_base, tl_base, meta_base, N, 8 * g, lane, look, cnt);
     }
 }
 
 // The warp tasks of the metrics (off-road groups from work[2], overlap rows
 // from work[1]), with the overlap culling records already in place.
 __device__ __forceinline__ void metrics_tasks(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
-                                              float4* meta_base, int N, Counts& cnt) {
+                                              float4* meta_base, int N, float look, Counts& cnt) {
     const int lane = threadIdx.x & 31;
     for (int g = next_agent(sm, 2, lane); 8 * g < N; g = next_agent(sm, 2, lane))
-        offroad_group(sm, V, hint_base, tl_base, meta_base, N, 8 * g, lane, cnt);
+        offroad_group(sm, V, hint_base, tl_base, meta_base, N, 8 * g, lane, look, cnt);
     for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane))
         if (sm.valid[i]) overlap_row(sm, N, i, lane, cnt);
 }

@@ -106,12 +106,12 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
                 sm.reward = 0;
             }
             if (k < A.T) {
-                if (k >= 1) metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, cnt);
+                if (k >= 1) metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, kListLook * A.p.dt, cnt);
                 transition_idm_tasks(sm, A, a0, N, cnt);
                 transition_policy<NT, DRIVERS>(sm, A, A.act ? A.act + static_cast<size_t>(k) * 3 * N_tot : nullptr,
                                       A.t_log + k, a0, N);
             } else {
-                metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, cnt);
+                metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, kListLook * A.p.dt, cnt);
             }
             __syncthreads();
             MetricsP m;
