@@ -1083,13 +1083,16 @@ __device__ void phase_metrics(AgentSmem& sm, const SegView& V, int32_t* hint_bas
     }
 }
 
-// The warp tasks of the metrics (off-road groups from work[2], overlap rows
-// from work[1]), with the overlap culling records already in place.
-__device__ __forceinline__ void metrics_tasks(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
+// The warp tasks of the metrics: off-road groups from work[2], and overlap
+// rows from work[1] (with the overlap culling records already in place).
+__device__ __forceinline__ void offroad_tasks(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
                                               float4* meta_base, int N, float look, Counts& cnt) {
     const int lane = threadIdx.x & 31;
     for (int g = next_agent(sm, 2, lane); 8 * g < N; g = next_agent(sm, 2, lane))
         offroad_group(sm, V, hint_base, tl_base, meta_base, N, 8 * g, lane, look, cnt);
+}
+__device__ __forceinline__ void row_tasks(AgentSmem& sm, int N, Counts& cnt) {
+    const int lane = threadIdx.x & 31;
     for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane))
         if (sm.valid[i]) overlap_row(sm, N, i, lane, cnt);
 }

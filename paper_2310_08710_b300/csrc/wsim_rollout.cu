@@ -96,22 +96,28 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
         // Pipelined steps, two barriers each.  Iteration k: the task phase runs
         // the metrics of state t0+k (k >= 1) together with the transition
         // t0+k -> t0+k+1 (k < T): both read state t0+k and write disjoint
-        // arrays, and warps take off-road groups, overlap rows and then IDM
-        // agents from one pool (that order measured fastest).  The per-agent phase then finishes the metrics of
-        // t0+k (row k-1), makes t0+k+1 current and prepares its overlap
-        // bounds.  The reward of row k-1 is stored at the next task phase.
+        // arrays.  Warps take the long tasks first (IDM groups, then off-road
+        // groups) and the short overlap rows last (that order measured
+        // fastest); the policy agents follow, one thread each.  The per-agent
+        // phase then finishes the metrics of t0+k (row k-1), makes t0+k+1
+        // current and prepares its overlap bounds.  The reward of row k-1 is
+        // stored at the next task phase.
         for (int k = 0; k <= A.T; ++k) {
             if (k >= 2 && threadIdx.x == 0) {  // reward of row k-2, summed in the last per-agent phase
                 A.m.reward[static_cast<size_t>(k - 2) * A.S + s] = sm.reward;
                 sm.reward = 0;
             }
             if (k < A.T) {
-                if (k >= 1) metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, kListLook * A.p.dt, cnt);
                 transition_idm_tasks(sm, A, a0, N, cnt);
+                if (k >= 1) {
+                    offroad_tasks(sm, V, sm.hint, tlist, tmeta, N, kListLook * A.p.dt, cnt);
+                    row_tasks(sm, N, cnt);
+                }
                 transition_policy<NT, DRIVERS>(sm, A, A.act ? A.act + static_cast<size_t>(k) * 3 * N_tot : nullptr,
                                       A.t_log + k, a0, N);
             } else {
-                metrics_tasks(sm, V, sm.hint, tlist, tmeta, N, kListLook * A.p.dt, cnt);
+                offroad_tasks(sm, V, sm.hint, tlist, tmeta, N, kListLook * A.p.dt, cnt);
+                row_tasks(sm, N, cnt);
             }
             __syncthreads();
             MetricsP m;
