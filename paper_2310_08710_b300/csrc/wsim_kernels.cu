@@ -21,6 +21,8 @@ namespace wsim {
 
 constexpr int NTs = kStepThreads;
 
+// COUNT = false: the work counts are dead code (fewer live registers).
+template <bool COUNT>
 __global__ void __launch_bounds__(NTs) k_step(const StepArgs A) {
     __shared__ AgentSmem sm;
     init_cta(sm);
@@ -49,7 +51,7 @@ __global__ void __launch_bounds__(NTs) k_step(const StepArgs A) {
         }
         __syncthreads();
     }
-    publish_counts(sm, A, cnt);
+    if (COUNT) publish_counts(sm, A, cnt);
 }
 
 // ---------------------------------------------------------------------------
@@ -414,7 +416,10 @@ cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg
 }
 
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st) {
-    k_step<<<grid, NTs, 0, st>>>(a);
+    if (a.count)
+        k_step<true><<<grid, NTs, 0, st>>>(a);
+    else
+        k_step<false><<<grid, NTs, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -430,7 +435,11 @@ cudaError_t launch_plain_scene(const StepArgs& a, int scene, cudaStream_t st) {
 
 int step_blocks_per_sm() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step, NTs, 0) != cudaSuccess) return 1;
+    int m = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_step<false>, NTs, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&m, k_step<true>, NTs, 0) != cudaSuccess)
+        return 1;
+    n = m < n ? m : n;
     return n > 0 ? n : 1;
 }
 
