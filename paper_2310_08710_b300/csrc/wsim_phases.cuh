@@ -892,13 +892,18 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
             if (lane == 0) cnt.tiles += min(32, V.ns - sb);
             unsigned sup = __ballot_sync(kFull, pass);
             while (sup) {
-                const int t0 = (sb + __ffs(sup) - 1) * kSuper;
-                sup &= sup - 1;
-                // Lanes 0..kSuper-1 test the super-tile's tiles corner by corner.
+                // Up to 32 / kSuper passing super-tiles at once, in index
+                // order: lanes kSuper q .. kSuper q + kSuper-1 test the tiles
+                // of the q-th, corner by corner (so tiles stay in increasing
+                // order across lanes, and the lists too).
+                unsigned rest = sup;
+                for (int r = 0; r < lane / kSuper && rest; ++r) rest &= rest - 1;
+                const int t = rest ? (sb + __ffs(rest) - 1) * kSuper + (lane & (kSuper - 1)) : V.nt;
+                int taken = 0;
+                for (; taken < 32 / kSuper && sup; ++taken) sup &= sup - 1;
                 unsigned cm = 0;
                 bool inl = false, inls = false;
-                const int t = t0 + lane;
-                if (lane < kSuper && t < V.nt) {
+                if (t < V.nt) {
                     const float4 C = V.tiles[2 * t];
                     const float4 Q = V.tiles[2 * t + 1];
                     const float dc = cap_d2(C, Q.y, ccx, ccy);
@@ -913,7 +918,7 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
                         }
                     }
                 }
-                if (lane == 0) cnt.tiles += kSuper;
+                if (lane == 0) cnt.tiles += kSuper * taken;
                 if (tl) {
                     const unsigned lb = __ballot_sync(kFull, inl);
                     const int pos = nl + __popc(lb & ((1u << lane) - 1u));
@@ -924,7 +929,8 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
                     while (sb2) {
                         const int l = __ffs(sb2) - 1;
                         sb2 &= sb2 - 1;
-                        if (lane == nls) small_t = t0 + l;
+                        const int tn = __shfl_sync(kFull, t, l);
+                        if (lane == nls) small_t = tn;
                         ++nls;
                     }
                 }
