@@ -592,8 +592,6 @@ static __device__ void overlap_row(AgentSmem& sm, int N, int i, int lane, Counts
     const float4 Pi = sm.obox[i];
     const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
     const float ci = sm.c[i], si = sm.s[i], hli = sm.hl[i], hwi = sm.hw[i];
-    float best = -WSIM_INF;
-    int bj = -1;
     for (int j = i + 1 + lane; j < N; j += 32) {
         const float4 Pj = sm.obox[j];  // invalid agents: R = -inf, always skipped
         cnt.bounds += 1;
@@ -603,26 +601,12 @@ static __device__ void overlap_row(AgentSmem& sm, int N, int i, int lane, Counts
         const float ddx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
         const float ddy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
         const float d = sat_depth(ddx, ddy, ci, si, hli, hwi, sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
-        if (d > best) {
-            best = d;
-            bj = j;
-        }
+        // both agents' maxima and partner keys (max is order-free)
         atomicMax(&sm.ovk[j], ukey(d));
         atomicMax(&sm.pk[j], partner_key(d, i));
+        atomicMax(&sm.ovk[i], ukey(d));
+        atomicMax(&sm.pk[i], partner_key(d, j));
         cnt.pairs += 2;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float ob = __shfl_xor_sync(kFull, best, o);
-        const int oj = __shfl_xor_sync(kFull, bj, o);
-        if (ob > best || (ob == best && oj > bj)) {
-            best = ob;
-            bj = oj;
-        }
-    }
-    if (lane == 0 && bj >= 0) {
-        atomicMax(&sm.ovk[i], ukey(best));
-        atomicMax(&sm.pk[i], partner_key(best, bj));
     }
 }
 
