@@ -191,6 +191,11 @@ __device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, 
         sm.kin[i] = 0;
         sm.ovk[i] = kNoDepth;
         sm.pk[i] = kNoDepth;
+        // culling record of the loaded state (no lower bound yet); the IDM
+        // candidate filter reads its centre and R >= hl + hw
+        const float R = (sm.hl[i] + sm.hw[i]) * 1.000001f + 5e-4f;
+        sm.obox[i] = sm.valid[i] ? make_float4(st.x[g], st.y[g], R, -WSIM_INF)
+                                 : make_float4(st.x[g], st.y[g], -WSIM_INF, -WSIM_INF);
     }
     if (threadIdx.x == 0) sm.work[0] = sm.work[1] = sm.work[2] = 0;
 }
@@ -232,6 +237,8 @@ __device__ void writeback(AgentSmem& sm, const Params& p, const StateP* out, int
         sm.vy[i] = sm.nvy[i];
         sm.sh[i] = sm.nsh[i];
         sm.sl[i] = sm.nsl[i];
+        sm.obox[i].x = sm.nxh[i];  // the culling record's centre follows the state
+        sm.obox[i].y = sm.nyh[i];
     }
 }
 
@@ -367,12 +374,17 @@ static __device__ IdmLead idm_lead(AgentSmem& sm, const StepArgs& A, int a0, int
     for (int jb = 0; jb < N; jb += 32) {
         const int jl = jb + lane;
         bool cand = false;
-        // non-candidates test a point that no circle reaches
+        // non-candidates test a point that no circle reaches; the culling
+        // record gives the centre and R >= hl + hw in one load (a wider
+        // reach only adds candidates that the box tests reject)
         float xj = WSIM_INF, yj = WSIM_INF, reach = 0.f;
-        if (jl < N && jl != i && sm.valid[jl]) {
-            xj = sm.xh[jl];
-            yj = sm.yh[jl];
-            reach = sm.hl[jl] + sm.hw[jl];
+        if (jl < N && jl != i) {
+            const float4 P = sm.obox[jl];
+            if (P.z > 0.f) {  // valid
+                xj = P.x;
+                yj = P.y;
+                reach = P.z;
+            }
         }
         cnt.filters += 4;
 #pragma unroll
