@@ -1021,7 +1021,7 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
             mask &= mask - 1;
             const int e0 = static_cast<int>(L[j]) * kTile;
             cnt.evals += kTile;
-#pragma unroll 4
+#pragma unroll 8
             for (int q = 0; q < kTile; ++q) {
                 const int e = e0 + q;
                 if (e < V.E) {
