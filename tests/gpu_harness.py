@@ -23,7 +23,7 @@ TOL_DEPTH = 2e-5    # m, overlap depth and off-road distance
 ULP_SLACK = 4       # float32 ulps of the value for large magnitudes
 
 
-def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None, tuning=None, no_actions=False):
+def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None, tuning=None, no_actions=False, count=False):
     from paper_2310_08710_b300 import wsim
     mode = wsim.MODE_FUSED if mode is None else mode
     T = b.T if T is None else T
@@ -36,14 +36,17 @@ def run_rollout(b, mode=None, T=None, ctrl=None, cfg=None, tuning=None, no_actio
     traj = wsim.State(b.N_tot, rows=T)
     m = wsim.Metrics(b.N_tot, b.S, rows=T)
     ct = None if ctrl is None else torch.as_tensor(ctrl, dtype=torch.uint8).cuda()
+    if count:
+        sim.set_counting(True)
     sim.rollout(st, act, m, synth.T0, T, mode=mode, traj=traj, ctrl=ct)
     torch.cuda.synchronize()
     status = sim.status()
+    counters = sim.counters() if count else None
     out = dict(
         traj=traj.data.cpu().numpy().reshape(10, T, b.N_tot),
         final=st.data.cpu().numpy(),
         ov=m.ov.cpu().numpy(), off=m.off.cpu().numpy(), logdiv=m.logdiv.cpu().numpy(),
-        flags=m.flags.cpu().numpy(), reward=m.reward.cpu().numpy(), status=status,
+        flags=m.flags.cpu().numpy(), reward=m.reward.cpu().numpy(), status=status, counters=counters,
     )
     sim.close()
     return out

@@ -116,6 +116,25 @@ def test_every_launch_configuration_bit_identical(wsim):
             assert np.array_equal(g[k].view(np.uint8), ref[k].view(np.uint8)), (tun, k)
 
 
+def test_lean_and_full_kernels_bit_identical(wsim):
+    # The rollout and step kernels are compiled twice: without the driver
+    # array and without work counting (the benchmark's launches), and with
+    # every driver and counting.  Both must give the same bits; the counted
+    # run must count work in every category an IDM batch exercises.
+    b = synth.make_batch(1, seed=11, S=24, R=4000, T=16)
+    ctrl = np.full(b.N_tot, wsim.CTRL_ACTION, np.uint8)
+    for mode in (wsim.MODE_FUSED, wsim.MODE_GRAPH):
+        lean = H.run_rollout(b, mode=mode)
+        counted = H.run_rollout(b, mode=mode, count=True)
+        driven = H.run_rollout(b, mode=mode, ctrl=ctrl)
+        for k in ("traj", "final", "ov", "off", "logdiv", "flags", "reward"):
+            assert np.array_equal(lean[k].view(np.uint8), counted[k].view(np.uint8)), (mode, k)
+            assert np.array_equal(lean[k].view(np.uint8), driven[k].view(np.uint8)), (mode, k)
+        c = counted["counters"]
+        print(mode, c)
+        assert c[0] > 0 and c[1] > 0 and c[3] > 0 and c[4] > 0 and c[5] > 0, c
+
+
 def test_autotune_keeps_results(wsim):
     import torch
     b = synth.make_batch(2, seed=8, S=64, T=10)
