@@ -16,7 +16,7 @@ constexpr int kSegAlign = kTile;        // per-scene segment arrays start on a t
 constexpr int kMaxSceneSegs = 65536 * kTile;  // packed positions per scene (tile lists hold 16-bit tile indexes)
 constexpr int kSuper = 8;               // tiles per super-tile (first culling level)
 constexpr int kList = 32;               // tiles in an agent's cached candidate list (one per lane)
-constexpr float kSkin = 8.0f;           // extra radius of a candidate list beyond the current need (m)
+constexpr float kSkin = 6.0f;           // extra radius of a candidate list beyond the current need (m)
 constexpr float kSkinSmall = 2.0f;      // fallback when the kSkin list would not fit in kList tiles
 constexpr float kListLook = 5.0f;       // the wide list is centred this many steps of motion ahead
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any mbarrier wait
