@@ -495,17 +495,18 @@ def main():
     # a CUDA graph of T persistent step launches, and one launch per scene
     # and phase (the plain baseline).
     modes = {}
-    for name, mode in (("graph_of_steps", wsim.MODE_GRAPH), ("plain_per_scene", wsim.MODE_PLAIN)):
+    for name, mode, reps in (("graph_of_steps", wsim.MODE_GRAPH, 3), ("plain_per_scene", wsim.MODE_PLAIN, 1)):
         st.data.copy_(st0.data)
         sim.rollout(st, act, m, synth.T0, T, mode=mode)
         torch.cuda.synchronize()
         e0.record(stream)
-        st.data.copy_(st0.data)
-        sim.rollout(st, act, m, synth.T0, T, mode=mode)
+        for _ in range(reps):
+            st.data.copy_(st0.data)
+            sim.rollout(st, act, m, synth.T0, T, mode=mode)
         e1.record(stream)
         torch.cuda.synchronize()
-        mm = e0.elapsed_time(e1)
-        modes[name] = {"value": N * T / (mm / 1e3), "unit": UNIT, "ms_per_rollout": mm}
+        mm = e0.elapsed_time(e1) / reps
+        modes[name] = {"value": N * T / (mm / 1e3), "unit": UNIT, "ms_per_rollout": mm, "rollouts_timed": reps}
     assert sim.status() == 0
 
     observe = observe_leg(wsim, synth, torch, b, sim, st0, args.steps)
