@@ -18,7 +18,7 @@
 
 namespace wsim {
 
-constexpr int NTb = 256;
+constexpr int NTb = 512;  // 16 warps per scene: the pair loops take N / 16 agents per warp
 
 struct BpttArgs {
     StepArgs A;      // batch, actions (act = [T][3][N_tot]), in = state t0, t_log = t0 + 1, T
@@ -249,10 +249,12 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int s
         }
         if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (warp == 0) {  // the step's loss in a fixed order: lane-strided sums, then a fixed shuffle tree
             float step = 0.f;
-            for (int i = 0; i < N; ++i) step += adj.part[i];
-            adj.total += static_cast<double>(step);
+            for (int i = lane; i < N; i += 32) step += adj.part[i];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) step += __shfl_xor_sync(kFull, step, o);
+            if (lane == 0) adj.total += static_cast<double>(step);
         }
     }
     __syncthreads();
