@@ -344,7 +344,8 @@ static __device__ IdmLead idm_lead(AgentSmem& sm, const StepArgs& A, int a0, int
     const float qx = Px + qox, qy = Py + qoy;
     const int gl = lane & ~7;
     const float gcx = __shfl_sync(kFull, qx, gl + 4), gcy = __shfl_sync(kFull, qy, gl + 4);
-    float gr = sqrtf((qx - gcx) * (qx - gcx) + (qy - gcy) * (qy - gcy));
+    // (approximate root rounded up: the circles only grow, a conservative filter)
+    float gr = sqrt_approx((qx - gcx) * (qx - gcx) + (qy - gcy) * (qy - gcy)) * 1.000002f + 1e-6f;
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) gr = fmaxf(gr, __shfl_xor_sync(kFull, gr, o));
     gr += 2.f * wi + 0.05f;  // lanes 8G .. 8G+7 hold circle G
@@ -675,7 +676,7 @@ __device__ __forceinline__ void scan_pair(const SegView& V, int lane, int ta, un
     const unsigned u = ma | mb;
     const int e = t * kTile + (lane & (kTile - 1));
     if (lane == 0) cnt.evals += kTile * (__popc(ma) + __popc(mb));
-    if (m && e < V.E) {
+    if (m) {  // positions up to the tile's end hold segments or far-away padding
         const float4 G = V.geo[e];
         const float iv = V.inv[e];
 #pragma unroll
@@ -1021,15 +1022,15 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
             mask &= mask - 1;
             const int e0 = static_cast<int>(L[j]) * kTile;
             cnt.evals += kTile;
+            // every position of a tile holds a segment or far-away padding
+            // (squared distance +inf, never the nearest)
 #pragma unroll 8
             for (int q = 0; q < kTile; ++q) {
                 const int e = e0 + q;
-                if (e < V.E) {
-                    const float d2 = seg_dist2(V.geo[e], V.inv[e], xh, cl, yh, dl);
-                    if (d2 < best) {
-                        best = d2;
-                        bi = e;
-                    }
+                const float d2 = seg_dist2(V.geo[e], V.inv[e], xh, cl, yh, dl);
+                if (d2 < best) {
+                    best = d2;
+                    bi = e;
                 }
             }
         }
