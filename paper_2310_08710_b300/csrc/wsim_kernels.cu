@@ -4,14 +4,18 @@
 // Per step, one CTA owns one scene at a time.  The step kernel is
 // persistent: its CTAs take scene ids from an atomic work counter over a
 // cost-ordered list, so scenes of uneven size share one launch.  Per scene:
-//   transition  (Sec. 4 step): IDM agents warp-cooperatively (one look-ahead
-//               sample per lane, Sec. 3.5), policy agents one per thread
-//               (bicycle / delta dynamics, App. A.1), compensated positions;
-//   overlap     (Sec. 3.4 collision): all pairs from shared-memory boxes,
-//               one warp per agent;
+//   transition  (Sec. 4 step): IDM agents in groups of eight per warp (the
+//               lead search warp-wide with one look-ahead sample per lane,
+//               acceleration and route advance one lane per agent, Sec. 3.5),
+//               policy agents one per thread (bicycle / delta dynamics,
+//               App. A.1), compensated positions;
+//   overlap     (Sec. 3.4 collision): pairs from shared-memory boxes, culled
+//               exactly, one warp per row;
 //   off-road    (Sec. 3.4 off-road): culled nearest-segment search per box
-//               corner, one warp per agent, segments read from global
-//               memory with a per-agent cache of the last winners;
+//               corner, eight agents per warp (one lane per corner) with
+//               per-agent candidate-tile lists and last winners, segments
+//               read from global memory, a warp-cooperative full search
+//               when the cache cannot prove the answer;
 //   finish      log divergence (Sec. 3.4), flags and the sparse reward
 //               (Sec. 5.2).
 // The plain path runs the same phases as separate one-CTA launches per scene.
