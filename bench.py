@@ -514,6 +514,7 @@ def main():
     expert = expert_leg(wsim, synth, torch, args, rank, b, args.steps)
 
     ms, ms_e2e, units = combine_ranks(pg, [ms, ms_e2e], N * T, "cuda")
+    _, valid_units = combine_ranks(pg, [ms], int(b.valid.sum()) * T, "cuda")
     if rank != 0:
         return
     value = units / (ms / 1e3)
@@ -530,6 +531,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "value_valid_agents_only": valid_units / (ms / 1e3),
         "data": "synthetic", "config": {**config_dict(args, b), "rollout_tuning": tune},
         "roofline": {"bound": "alu", "kernel": "k_rollout" if fused else "k_step", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
                      "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
