@@ -127,41 +127,67 @@ __device__ float loss_agent(const AgentSmem& sm, const StepArgs& A, int a0, int 
     return acc + fmaf(ex, ex, ey * ey);
 }
 
-// Adds dL/d(x, y, theta) of agent i's loss terms at the current state
-// (warp; all pairs with i, each taken in the canonical order).
-__device__ void loss_adjoint_agent(const AgentSmem& sm, AdjSmem& adj, const StepArgs& A, int a0, int N, int i,
-                                   int lane, float lambda, float tau, int t_log) {
-    float gx = 0.f, gy = 0.f, gth = 0.f;
-    for (int j = lane; j < N; j += 32) {
-        if (j == i || !sm.valid[j]) continue;
-        const int lo = min(i, j), hi = max(i, j);
-        const float dx = comp_diff(sm.xh[hi], sm.xl[hi], sm.xh[lo], sm.xl[lo]);
-        const float dy = comp_diff(sm.yh[hi], sm.yl[hi], sm.yh[lo], sm.yl[lo]);
-        const SatGrad G = sat_grad(dx, dy, sm.c[lo], sm.s[lo], sm.hl[lo], sm.hw[lo], sm.c[hi], sm.s[hi], sm.hl[hi],
-                                   sm.hw[hi]);
-        const float w = lambda * sigmoid_f(G.d / tau);
-        if (i == lo) {
-            gx -= w * G.ddx;
+// Adds dL/d(x, y, theta) of every valid agent's loss terms at the current
+// state (all threads).  Each pair i < j is evaluated once, by the warp that
+// owns row i (rows i = warp, warp + NWb, ...): the row agent's terms are
+// summed by a warp reduction, the partner's terms go to the warp's buffer
+// wbuf[warp] (a warp synchronises between rows), and each agent then sums
+// the NWb buffers in warp order.  Fixed order throughout, no float atomics.
+constexpr int NWb = NTb / 32;
+constexpr size_t kPairBufFloats = static_cast<size_t>(NWb) * 3 * kMaxN;
+
+__device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, const StepArgs& A, int a0, int N,
+                             int lane, int warp, float lambda, float tau, int t_log) {
+    float* bx = wbuf + static_cast<size_t>(warp) * 3 * kMaxN;
+    float* by = bx + kMaxN;
+    float* bth = by + kMaxN;
+    for (int j = lane; j < N; j += 32) bx[j] = by[j] = bth[j] = 0.f;
+    __syncwarp();
+    for (int i = warp; i < N; i += NWb) {
+        if (!sm.valid[i]) continue;
+        const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
+        const float ci = sm.c[i], si = sm.s[i], hli = sm.hl[i], hwi = sm.hw[i];
+        float gx = 0.f, gy = 0.f, gth = 0.f;
+        for (int j = i + 1 + lane; j < N; j += 32) {
+            if (!sm.valid[j]) continue;
+            const float dx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
+            const float dy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
+            const SatGrad G = sat_grad(dx, dy, ci, si, hli, hwi, sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
+            const float w = lambda * sigmoid_f(G.d / tau);
+            gx -= w * G.ddx;  // i is the first box of the pair
             gy -= w * G.ddy;
             gth += w * G.dthA;
-        } else {
-            gx += w * G.ddx;
-            gy += w * G.ddy;
-            gth += w * G.dthB;
+            bx[j] += w * G.ddx;  // j the second
+            by[j] += w * G.ddy;
+            bth[j] += w * G.dthB;
         }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        gx += __shfl_xor_sync(kFull, gx, o);
-        gy += __shfl_xor_sync(kFull, gy, o);
-        gth += __shfl_xor_sync(kFull, gth, o);
+        for (int o = 16; o > 0; o >>= 1) {
+            gx += __shfl_xor_sync(kFull, gx, o);
+            gy += __shfl_xor_sync(kFull, gy, o);
+            gth += __shfl_xor_sync(kFull, gth, o);
+        }
+        if (lane == 0) {
+            const size_t li = static_cast<size_t>(t_log) * A.N_tot + a0 + i;
+            const float ex = (xih - A.log_x[li]) + xil, ey = (yih - A.log_y[li]) + yil;
+            adj.x[i] += gx + 2.f * ex;
+            adj.y[i] += gy + 2.f * ey;
+            adj.th[i] += gth;
+        }
+        __syncwarp();  // the next row's lanes update entries of this row's lanes
     }
-    if (lane == 0) {
-        const size_t li = static_cast<size_t>(t_log) * A.N_tot + a0 + i;
-        const float ex = (sm.xh[i] - A.log_x[li]) + sm.xl[i], ey = (sm.yh[i] - A.log_y[li]) + sm.yl[i];
-        adj.x[i] += gx + 2.f * ex;
-        adj.y[i] += gy + 2.f * ey;
-        adj.th[i] += gth;
+    __syncthreads();
+    for (int j = threadIdx.x; j < N; j += NTb) {
+        float sx = 0.f, sy = 0.f, st = 0.f;
+        for (int w = 0; w < NWb; ++w) {
+            const float* b = wbuf + static_cast<size_t>(w) * 3 * kMaxN;
+            sx += b[j];
+            sy += b[kMaxN + j];
+            st += b[2 * kMaxN + j];
+        }
+        adj.x[j] += sx;
+        adj.y[j] += sy;
+        adj.th[j] += st;
     }
 }
 
@@ -224,7 +250,7 @@ __device__ void transition_adjoint(AgentSmem& sm, AdjSmem& adj, const BpttArgs& 
     }
 }
 
-__device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int s) {
+__device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttArgs& B, int s) {
     const StepArgs& A = B.A;
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -285,8 +311,7 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int s
                                              : cslot(B.segbuf, t + 1 - a, A.N_tot);
             load_state<NTb>(sm, A, nxt, a0, N);
             __syncthreads();
-            for (int i = warp; i < N; i += NW)
-                if (sm.valid[i]) loss_adjoint_agent(sm, adj, A, a0, N, i, lane, B.lambda, B.tau, A.t_log + t);
+            loss_adjoint(sm, adj, wbuf, A, a0, N, lane, warp, B.lambda, B.tau, A.t_log + t);
             const CStateP cur = (t == a) ? cslot(B.ckpt, sg, A.N_tot) : cslot(B.segbuf, t - a, A.N_tot);
             load_prev(sm, cur, a0, N);
             __syncthreads();
@@ -296,12 +321,19 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int s
     __syncthreads();
 }
 
+// Dynamic shared memory: AgentSmem, AdjSmem, then the pair buffers.
+constexpr size_t kAdjOff = (sizeof(AgentSmem) + 15) / 16 * 16;
+constexpr size_t kBufOff = (kAdjOff + sizeof(AdjSmem) + 15) / 16 * 16;
+constexpr size_t kBpttSmem = kBufOff + kPairBufFloats * sizeof(float);
+
 __global__ void __launch_bounds__(NTb, 2) k_bptt(const BpttArgs B) {
-    __shared__ AgentSmem sm;
-    __shared__ AdjSmem adj;
+    extern __shared__ __align__(16) unsigned char bdyn[];
+    AgentSmem& sm = *reinterpret_cast<AgentSmem*>(bdyn);
+    AdjSmem& adj = *reinterpret_cast<AdjSmem*>(bdyn + kAdjOff);
+    float* wbuf = reinterpret_cast<float*>(bdyn + kBufOff);
     init_cta(sm);
     if (B.scene >= 0) {
-        bptt_scene(sm, adj, B, B.scene);
+        bptt_scene(sm, adj, wbuf, B, B.scene);
         return;
     }
     for (;;) {
@@ -309,7 +341,7 @@ __global__ void __launch_bounds__(NTb, 2) k_bptt(const BpttArgs B) {
         __syncthreads();
         const int w = sm.scene;
         if (w >= B.A.n_work) break;
-        bptt_scene(sm, adj, B, B.A.order[w]);
+        bptt_scene(sm, adj, wbuf, B, B.A.order[w]);
         __syncthreads();
     }
 }
@@ -325,21 +357,29 @@ cudaError_t launch_bptt(const StepArgs& a, float* ckpt, float* segbuf, int ck, d
     B.dact = dact;
     B.lambda = lambda;
     B.tau = tau;
+    cudaError_t e = cudaFuncSetAttribute(k_bptt, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kBpttSmem));
+    if (e != cudaSuccess) return e;
     if (plain) {
         for (int s = 0; s < a.S; ++s) {
             B.scene = s;
-            k_bptt<<<1, NTb, 0, st>>>(B);
+            k_bptt<<<1, NTb, kBpttSmem, st>>>(B);
         }
     } else {
         B.scene = -1;
-        k_bptt<<<grid, NTb, 0, st>>>(B);
+        k_bptt<<<grid, NTb, kBpttSmem, st>>>(B);
     }
     return cudaGetLastError();
 }
 
 int bptt_blocks_per_sm() {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bptt, NTb, 0) != cudaSuccess) return 1;
+    if (cudaFuncSetAttribute(k_bptt, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kBpttSmem)) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bptt, NTb, kBpttSmem) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
     return n > 0 ? n : 1;
 }
 
