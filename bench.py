@@ -45,13 +45,15 @@ FLOPS_PER_FILTER = 9     # IDM lead-candidate circle test
 FLOPS_PER_IDM_STEP = 800 # IDM agent-step: 32 look-ahead samples on the route, acceleration, advance
 
 
-def source_hash() -> str:
-    """sha256 (first 16 hex digits) of the CUDA sources and the C ABI header."""
-    import glob
+ROLLOUT_SOURCES = ("wsim_rollout.cu", "wsim_phases.cuh", "wsim_device.cuh", "wsim_internal.h")
+
+
+def source_hash(names=ROLLOUT_SOURCES) -> str:
+    """sha256 (first 16 hex digits) of the sources a kernel is built from (by
+    default the scene-resident rollout kernel's) and the C ABI header."""
     import hashlib
     c = os.path.join(ROOT, "paper_2310_08710_b300", "csrc")
-    files = sorted(glob.glob(os.path.join(c, "*.cu"))) + sorted(glob.glob(os.path.join(c, "*.cuh"))) + \
-        sorted(glob.glob(os.path.join(c, "*.h"))) + [os.path.join(ROOT, "include", "wsim.h")]
+    files = [os.path.join(c, n) for n in names] + [os.path.join(ROOT, "include", "wsim.h")]
     h = hashlib.sha256()
     for f in files:
         with open(f, "rb") as fh:
