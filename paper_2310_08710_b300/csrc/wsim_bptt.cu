@@ -11,9 +11,9 @@
 // every `ck` steps (and at T).  Backward: segments from last to first; each
 // recomputes its inner states from its checkpoint with the same code (so
 // ck = 10 and ck = 1 give bit-identical results), then runs the reverse
-// sweep: the adjoint of the loss at t+1 (every agent sums its own pair terms
-// in a fixed lane order: no float atomics) and the adjoint of the transition
-// t -> t+1, which yields dL/d(actions at t).
+// sweep: the adjoint of the loss at t+1 (each pair evaluated once; the terms
+// summed in a fixed order through per-warp buffers: no float atomics) and
+// the adjoint of the transition t -> t+1, which yields dL/d(actions at t).
 #include "wsim_phases.cuh"
 
 namespace wsim {
