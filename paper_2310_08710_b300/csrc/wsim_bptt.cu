@@ -310,11 +310,13 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttA
             const CStateP nxt = (t + 1 == b) ? cslot(B.ckpt, (b + ck - 1) / ck, A.N_tot)
                                              : cslot(B.segbuf, t + 1 - a, A.N_tot);
             load_state<NTb>(sm, A, nxt, a0, N);
-            __syncthreads();
-            loss_adjoint(sm, adj, wbuf, A, a0, N, lane, warp, B.lambda, B.tau, A.t_log + t);
+            // state t into the n* arrays, which the loss adjoint does not read
             const CStateP cur = (t == a) ? cslot(B.ckpt, sg, A.N_tot) : cslot(B.segbuf, t - a, A.N_tot);
             load_prev(sm, cur, a0, N);
             __syncthreads();
+            loss_adjoint(sm, adj, wbuf, A, a0, N, lane, warp, B.lambda, B.tau, A.t_log + t);
+            // the loss adjoint ends with agent j's sum in the thread that
+            // takes agent j here: no barrier in between
             transition_adjoint(sm, adj, B, t, a0, N);
         }
     }
