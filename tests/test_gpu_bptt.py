@@ -131,6 +131,30 @@ def test_differentiable_256x64_full_size_sampled(wsim):
         assert rel_err(got, ref) <= TOL_GRAD, s
 
 
+def test_max_agents_per_scene(wsim):
+    # 256 agents: every warp owns rows and the per-warp pair buffers are full;
+    # sampled directions against the oracle, and the checkpoint interval and
+    # launch path still bit-identical
+    b = synth.make_batch(3, seed=9, S=2, N=256, T=12)
+    loss, dact = gpu_grad(wsim, b)
+    o = oracle.Oracle(b)
+    st = o.initial_state()
+    act = b.actions.astype(np.float64)
+    rng = np.random.default_rng(4)
+    for s in range(b.S):
+        lo = o.loss(s, st, act, T0, b.T)
+        assert abs(loss[s] - lo) <= TOL_LOSS * abs(lo), (s, loss[s], lo)
+        dirs = policy_dirs(b, s, b.T)
+        pick = [dirs[k] for k in rng.choice(len(dirs), 32, replace=False)]
+        ref = o.loss_grad(s, st, act, T0, b.T, pick)
+        got = np.array([dact[t, c, g] for t, c, g in pick], dtype=np.float64)
+        assert rel_err(got, ref) <= TOL_GRAD, (s, rel_err(got, ref))
+    for ck, plain in ((1, False), (10, True)):
+        l, g = gpu_grad(wsim, b, ckpt=ck, plain=plain)
+        assert np.array_equal(l.view(np.uint8), loss.view(np.uint8)), (ck, plain)
+        assert np.array_equal(g.view(np.uint8), dact.view(np.uint8)), (ck, plain)
+
+
 def test_delta_ego_and_idm_stop_gradient(wsim):
     # scene 0: delta ego, scene 1: bicycle ego; the other agents are IDM
     # (moving, constant for the derivative)
