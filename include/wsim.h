@@ -368,9 +368,14 @@ void wsim_destroy(wsim_ctx *ctx);
  * current); make that first call before any stream capture.  All calls share
  * the array and it keeps the previous call's contents, so calls that overlap
  * on the GPU (other streams, other threads) race: serialise them.  The call
- * synchronises `stream` and returns WSIM_OK or the first error found (also
- * the device-side checks of the CSR offsets and the agents-per-scene
- * limit).  Outputs are the same as wsim_metrics on the same inputs. */
+ * synchronises `stream` and returns WSIM_OK or the first error found.  The
+ * CSR offsets are device arrays: a first kernel checks them (agent_off and
+ * rg_off start at 0, end at N_tot and R_tot and never decrease; at most
+ * WSIM_MAX_AGENTS agents per scene) and the call returns WSIM_EINVAL
+ * (WSIM_ESIZE for the agent limit) before any kernel reads a scene's
+ * roadgraph range; packed segments beyond the limit return WSIM_ESIZE before
+ * any is written.  No metric is written on an error.  Outputs are the same
+ * as wsim_metrics on the same inputs. */
 int wsim_metrics_static(const wsim_config *cfg, const wsim_batch *b, const wsim_state *st,
                         const wsim_metric_buf *m, int t, void *stream);
 

@@ -136,6 +136,16 @@ __device__ float loss_agent(const AgentSmem& sm, const StepArgs& A, int a0, int 
 constexpr int NWb = NTb / 32;
 constexpr size_t kPairBufFloats = static_cast<size_t>(NWb) * 3 * kMaxN;
 
+// Agent j's per-agent work in the reverse sweep (the column sums closing
+// loss_adjoint and the whole of transition_adjoint) runs in thread
+// agent_thread(j).  Both loops iterate through this helper, so the thread
+// that finishes agent j's sums is the one that reads them next, and the two
+// need no barrier in between; load_prev writes only the n* arrays, which
+// loss_adjoint does not read.
+__device__ __forceinline__ int first_agent() { return threadIdx.x; }
+constexpr int kAgentStride = NTb;
+static_assert(kAgentStride == NTb, "one agent per thread and stride: the reverse sweep relies on it");
+
 __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, const StepArgs& A, int a0, int N,
                              int lane, int warp, float lambda, float tau, int t_log) {
     float* bx = wbuf + static_cast<size_t>(warp) * 3 * kMaxN;
@@ -177,7 +187,7 @@ __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, con
         __syncwarp();  // the next row's lanes update entries of this row's lanes
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < N; j += NTb) {
+    for (int j = first_agent(); j < N; j += kAgentStride) {  // same mapping as transition_adjoint
         float sx = 0.f, sy = 0.f, st = 0.f;
         for (int w = 0; w < NWb; ++w) {
             const float* b = wbuf + static_cast<size_t>(w) * 3 * kMaxN;
@@ -209,7 +219,7 @@ __device__ void transition_adjoint(AgentSmem& sm, AdjSmem& adj, const BpttArgs& 
     const StepArgs& A = B.A;
     const float dt = A.p.dt, hdt2 = 0.5f * dt * dt;
     const float* act = A.act + static_cast<size_t>(t) * 3 * A.N_tot;
-    for (int i = threadIdx.x; i < N; i += NTb) {
+    for (int i = first_agent(); i < N; i += kAgentStride) {  // same mapping as loss_adjoint's column sums
         const int g = a0 + i;
         const int kind = A.kind[g];
         float ga = 0.f, gk = 0.f, g2 = 0.f;

@@ -91,27 +91,34 @@ __device__ int block_excl_scan(int v, int* wsum, int* carry) {
     return incl - v;
 }
 
-// One CTA: checks the CSR offsets and the agents-per-scene limit, turns the
-// per-scene segment counts into padded segment offsets and super-tile
-// offsets, and writes the identity work order.  Violations go to the status
-// word.
-__global__ void __launch_bounds__(1024) k_static_offsets(const int32_t* agent_off, const int32_t* rg_off, int S,
-                                                         int N_tot, int64_t R_tot, StaticScratch* sc) {
+// One CTA, before any kernel reads the roadgraph: checks the CSR offsets
+// (agent_off and rg_off start at 0, end at N_tot and R_tot, never decrease)
+// and the agents-per-scene limit.  Violations go to the status word, which
+// the host reads before the first roadgraph walk.
+__global__ void __launch_bounds__(1024) k_static_check(const int32_t* agent_off, const int32_t* rg_off, int S,
+                                                       int N_tot, int64_t R_tot, StaticScratch* sc) {
+    if (threadIdx.x == 0 &&
+        (agent_off[0] != 0 || agent_off[S] != N_tot || rg_off[0] != 0 || rg_off[S] != R_tot))
+        atomicCAS(&sc->status, 0, WSIM_EINVAL);
+    for (int s = threadIdx.x; s < S; s += 1024) {
+        const int n = agent_off[s + 1] - agent_off[s];
+        if (n < 0 || rg_off[s + 1] < rg_off[s]) atomicCAS(&sc->status, 0, WSIM_EINVAL);
+        if (n > kMaxN) atomicCAS(&sc->status, 0, WSIM_ESIZE);
+    }
+}
+
+// One CTA: turns the per-scene segment counts into padded segment offsets
+// and super-tile offsets and writes the identity work order; packed
+// segments beyond the fixed arrays set WSIM_ESIZE.
+__global__ void __launch_bounds__(1024) k_static_offsets(int S, StaticScratch* sc) {
     __shared__ int32_t carry[2];
     __shared__ int32_t wsum[32];
-    if (threadIdx.x == 0) {
-        carry[0] = carry[1] = 0;
-        if (agent_off[0] != 0 || agent_off[S] != N_tot || rg_off[0] != 0 || rg_off[S] != R_tot)
-            atomicCAS(&sc->status, 0, WSIM_EINVAL);
-    }
+    if (threadIdx.x == 0) carry[0] = carry[1] = 0;
     __syncthreads();
     for (int base = 0; base < S; base += 1024) {
         const int s = base + threadIdx.x;
         int padded = 0, nsup = 0;
         if (s < S) {
-            const int n = agent_off[s + 1] - agent_off[s];
-            if (n < 0 || rg_off[s + 1] < rg_off[s]) atomicCAS(&sc->status, 0, WSIM_EINVAL);
-            if (n > kMaxN) atomicCAS(&sc->status, 0, WSIM_ESIZE);
             padded = (sc->seg_cnt[s] + kSegAlign - 1) / kSegAlign * kSegAlign;
             nsup = (padded / kTile + kSuper - 1) / kSuper;
             sc->order[s] = s;
@@ -170,12 +177,18 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
         cudaGetLastError();
         return WSIM_ECUDA;
     }
+    // The offsets live in device memory: check them on the device and stop
+    // on a violation before any kernel walks a scene's roadgraph range.
+    k_static_check<<<1, 1024, 0, s>>>(b->agent_off, b->rg_off, b->S, b->N_tot, b->R_tot, sc);
+    if (cudaGetLastError() != cudaSuccess) return WSIM_ECUDA;
+    rc = read_status(sc, s);
+    if (rc) return rc;
     if (launch_seg_count(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, b->S, sc->seg_cnt, s) !=
         cudaSuccess)
         return WSIM_ECUDA;
-    k_static_offsets<<<1, 1024, 0, s>>>(b->agent_off, b->rg_off, b->S, b->N_tot, b->R_tot, sc);
+    k_static_offsets<<<1, 1024, 0, s>>>(b->S, sc);
     if (cudaGetLastError() != cudaSuccess) return WSIM_ECUDA;
-    // The metrics kernel relies on the checks above: stop here on a violation.
+    // The packing kernels rely on the padded total fitting the fixed arrays.
     rc = read_status(sc, s);
     if (rc) return rc;
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, b->S, sc->seg_off,
