@@ -97,6 +97,12 @@ def lib():
         _lib.oracle_loss.restype = C.c_double
         _lib.oracle_loss_grad.argtypes = [P(ObParams), P(ObBatch), C.c_int, P(ObState), _dp, C.c_int,
                                           C.c_int, C.c_double, C.c_double, C.c_int, _i32p, _i32p, _i32p, _dp]
+        _lib.oracle_objective.argtypes = [P(ObParams), P(ObBatch), C.c_int, P(ObState), _dp, C.c_int, C.c_int,
+                                          C.c_double, C.c_double, C.c_double, _dp, _dp, _dp]
+        _lib.oracle_objective.restype = C.c_double
+        _lib.oracle_objective_grad.argtypes = [P(ObParams), P(ObBatch), C.c_int, P(ObState), _dp, C.c_int,
+                                               C.c_int, C.c_double, C.c_double, C.c_double, _dp, _dp, _dp,
+                                               C.c_int, _i32p, _i32p, _i32p, _i32p, _dp]
     return _lib
 
 
@@ -368,6 +374,46 @@ class Oracle:
                                     _ptr(dg, _i32p), _ptr(out, _dp))
         if rc:
             raise RuntimeError("oracle_loss_grad failed")
+        return out
+
+
+    @staticmethod
+    def _weights(w, T, N):
+        if w is None:
+            return None, None
+        a = _f64(w).reshape(T, N)
+        return a, _ptr(a, _dp)
+
+    def objective(self, scene: int, st0: dict, act_seq: np.ndarray, t0: int, T: int, w_loss: float = 0.0,
+                  g_logdiv=None, g_ov=None, g_off=None, lam: float = 1.0, tau: float = 0.25) -> float:
+        """J = w_loss * loss + sum of the weighted per-step metrics (weights
+        [T][N_tot] or None) of the scene's T-step rollout (oracle_objective)."""
+        st = {k: _f64(st0[k]) for k in STATE_KEYS}
+        act = _f64(act_seq)
+        N = self.b.N_tot
+        keep = [self._weights(w, T, N) for w in (g_logdiv, g_ov, g_off)]
+        return lib().oracle_objective(C.byref(self._cp), C.byref(self._batch), scene, C.byref(self._cstate(st)),
+                                      _ptr(act, _dp), t0, T, lam, tau, w_loss, *[k[1] for k in keep])
+
+    def objective_grad(self, scene: int, st0: dict, act_seq: np.ndarray, t0: int, T: int, dirs,
+                       w_loss: float = 0.0, g_logdiv=None, g_ov=None, g_off=None, lam: float = 1.0,
+                       tau: float = 0.25) -> np.ndarray:
+        """dJ/d(direction) by dual numbers for dirs = iterable of (kind, t, c,
+        g): kind 0 = act_seq[t][c][g]; kind 1 = component c (x, y, theta, vx,
+        vy) of agent g's initial state."""
+        d = np.asarray(list(dirs), dtype=np.int32).reshape(-1, 4)
+        dk, dt_, dc, dg = (np.ascontiguousarray(d[:, i]) for i in range(4))
+        out = np.zeros(len(d))
+        st = {k: _f64(st0[k]) for k in STATE_KEYS}
+        act = _f64(act_seq)
+        N = self.b.N_tot
+        keep = [self._weights(w, T, N) for w in (g_logdiv, g_ov, g_off)]
+        rc = lib().oracle_objective_grad(C.byref(self._cp), C.byref(self._batch), scene,
+                                         C.byref(self._cstate(st)), _ptr(act, _dp), t0, T, lam, tau, w_loss,
+                                         *[k[1] for k in keep], len(d), _ptr(dk, _i32p), _ptr(dt_, _i32p),
+                                         _ptr(dc, _i32p), _ptr(dg, _i32p), _ptr(out, _dp))
+        if rc:
+            raise RuntimeError("oracle_objective_grad failed")
         return out
 
 

@@ -577,23 +577,60 @@ void metrics_scene(const ob_params* p, const ob_batch* b, int s, const ob_state*
     reward[s] = r;
 }
 
-// The differentiable loss of one scene, generic in the scalar type.  IDM
-// agents move as in oracle_transition but are constants for
-// differentiation (their updates use the values only): the gradient flows
-// through the policy agents' dynamics and every loss term.
-template <class T, class ActFn>
-T scene_loss(const ob_params* p, const ob_batch* b, int s, const ob_state* st0, ActFn act,
-             int t0, int nsteps, double lambda, double tau) {
+// Signed distance of a point whose coordinates may carry derivatives
+// (Sec. 3.4 off-road).  The nearest segment and the side are decided on the
+// values, exactly as point_sd decides them (exhaustive scan, ties to the
+// lower index, vertex rule); the distance from the point to that segment's
+// nearest point (the projection parameter clamped to [0, 1]) carries the
+// derivative.
+template <class T> T point_sd_t(const std::vector<Seg>& g, T px, T py) {
+    int idx = -1;
+    point_sd(g, val(px), val(py), 0.0, nullptr, &idx);
+    if (idx < 0) return T(-kInf);
+    const Seg& e = g[idx];
+    double traw;
+    seg_d2(e, val(px), val(py), &traw);
+    const bool on = on_road_side(g, idx, traw, val(px), val(py));
+    T wx = px - e.ax, wy = py - e.ay;
+    T t = (wx * e.ux + wy * e.uy) / (e.ux * e.ux + e.uy * e.uy);
+    t = tmin(tmax(t, T(0.0)), T(1.0));
+    T ex = wx - t * e.ux, ey = wy - t * e.uy;
+    T d = sqrt(ex * ex + ey * ey);
+    return on ? -d : d;
+}
+
+// Weights of the per-step metrics in a differentiable objective: element
+// [k * N_tot + g] weighs agent g's metric at time t0+k+1; NULL = all 0.
+struct MetricWeights { const double *logdiv, *ov, *off; };
+
+template <class T> struct Objective { T loss, metrics; };
+
+// The differentiable objective of one scene over nsteps steps, generic in
+// the scalar type: the loss (squared log divergence plus the softplus
+// overlap penalty) and, separately, the weighted sum of the per-step metrics
+// of oracle_metrics (log divergence; overlap depth, the largest SAT depth
+// against another valid agent; off-road distance, the largest signed
+// distance over the box corners).  A metric of weight 0 is not evaluated; a
+// metric of -inf (no other agent, no road edge) adds nothing.  IDM agents
+// move as in oracle_transition but are constants for differentiation (their
+// updates use the values only): the derivative flows through the policy
+// agents' dynamics and every term.  st(g, c) gives component c (x, y,
+// theta, vx, vy) of agent g's initial state.
+template <class T, class ActFn, class StFn>
+Objective<T> scene_objective(const ob_params* p, const ob_batch* b, int s, const ob_state* st0, StFn st,
+                             ActFn act, int t0, int nsteps, double lambda, double tau, const MetricWeights* w) {
     const int a0 = b->agent_off[s], a1 = b->agent_off[s + 1], n = a1 - a0, N = b->N_tot;
     std::vector<St<T>> cur(n);
     std::vector<double> vals(6 * (size_t)n + 6);
     ob_state vs = {vals.data(), vals.data() + n, vals.data() + 2 * n, vals.data() + 3 * n,
                    vals.data() + 4 * n, vals.data() + 5 * n};
     for (int g = a0; g < a1; ++g) {
-        cur[g - a0] = {T(st0->x[g]), T(st0->y[g]), T(st0->th[g]), T(st0->vx[g]), T(st0->vy[g])};
+        cur[g - a0] = {st(g, 0), st(g, 1), st(g, 2), st(g, 3), st(g, 4)};
         vs.s[g - a0] = st0->s[g];
     }
-    T loss = T(0.0);
+    const bool with_metrics = w && (w->logdiv || w->ov || w->off);
+    const std::vector<Seg> segs = with_metrics && w->off ? scene_segments(b, s) : std::vector<Seg>();
+    T loss = T(0.0), metrics = T(0.0);
     std::vector<Box<T>> box(n);
     for (int k = 0; k < nsteps; ++k) {
         for (int g = a0; g < a1; ++g) {  // values of state t for the IDM agents
@@ -633,8 +670,49 @@ T scene_loss(const ob_params* p, const ob_batch* b, int s, const ob_state* st0, 
                 loss += lambda * tau * softplus(d / tau);
             }
         }
+        if (!with_metrics) continue;
+        for (int g = a0; g < a1; ++g) {
+            if (!b->valid[g]) continue;
+            const size_t wi = (size_t)k * N + g;
+            if (w->logdiv && w->logdiv[wi] != 0) {
+                T dx = cur[g - a0].x - b->log_x[(size_t)tl * N + g];
+                T dy = cur[g - a0].y - b->log_y[(size_t)tl * N + g];
+                metrics += w->logdiv[wi] * sqrt(dx * dx + dy * dy);
+            }
+            if (w->ov && w->ov[wi] != 0) {
+                T o = T(-kInf);
+                for (int j = a0; j < a1; ++j) {
+                    if (j == g || !b->valid[j]) continue;
+                    const int lo = std::min(g, j), hi = std::max(g, j);
+                    o = tmax(o, sat_depth(box[lo - a0], box[hi - a0]));
+                }
+                if (val(o) > -kInf) metrics += w->ov[wi] * o;
+            }
+            if (w->off && w->off[wi] != 0) {
+                const Box<T>& B = box[g - a0];
+                const double sl[4] = {1, 1, -1, -1}, sw[4] = {1, -1, -1, 1};
+                T f = T(-kInf);
+                for (int c = 0; c < 4; ++c) {
+                    T px = B.cx + sl[c] * B.hl * B.c - sw[c] * B.hw * B.s;
+                    T py = B.cy + sl[c] * B.hl * B.s + sw[c] * B.hw * B.c;
+                    f = tmax(f, point_sd_t(segs, px, py));
+                }
+                if (val(f) > -kInf) metrics += w->off[wi] * f;
+            }
+        }
     }
-    return loss;
+    return {loss, metrics};
+}
+
+// The BPTT loss alone (no metric terms), from the initial state's values.
+template <class T, class ActFn>
+T scene_loss(const ob_params* p, const ob_batch* b, int s, const ob_state* st0, ActFn act,
+             int t0, int nsteps, double lambda, double tau) {
+    auto st = [&](int g, int c) {
+        const double* f[5] = {st0->x, st0->y, st0->th, st0->vx, st0->vy};
+        return T(f[c][g]);
+    };
+    return scene_objective<T>(p, b, s, st0, st, act, t0, nsteps, lambda, tau, nullptr).loss;
 }
 
 bool scene_differentiable(const ob_batch* b, int s) {
@@ -920,6 +998,46 @@ int oracle_loss_grad(const ob_params* p, const ob_batch* b, int s, const ob_stat
             return Dual(v, (k == tq && c == cq && g == gq) ? 1.0 : 0.0);
         };
         grad[q] = scene_loss<Dual>(p, b, s, st0, act, t0, T, lambda, tau).d;
+    }
+    return 0;
+}
+
+double oracle_objective(const ob_params* p, const ob_batch* b, int s, const ob_state* st0,
+                        const double* act_seq, int t0, int T, double lambda, double tau, double w_loss,
+                        const double* g_logdiv, const double* g_ov, const double* g_off) {
+    if (!scene_differentiable(b, s) || t0 < 0 || t0 + T > b->T_log - 1) return std::nan("");
+    const int N = b->N_tot;
+    auto act = [&](int k, int c, int g) { return act_seq[((size_t)k * 3 + c) * N + g]; };
+    auto st = [&](int g, int c) {
+        const double* f[5] = {st0->x, st0->y, st0->th, st0->vx, st0->vy};
+        return f[c][g];
+    };
+    const MetricWeights w = {g_logdiv, g_ov, g_off};
+    const Objective<double> o = scene_objective<double>(p, b, s, st0, st, act, t0, T, lambda, tau, &w);
+    return w_loss * o.loss + o.metrics;
+}
+
+int oracle_objective_grad(const ob_params* p, const ob_batch* b, int s, const ob_state* st0,
+                          const double* act_seq, int t0, int T, double lambda, double tau, double w_loss,
+                          const double* g_logdiv, const double* g_ov, const double* g_off, int n,
+                          const int32_t* dir_kind, const int32_t* dir_t, const int32_t* dir_c,
+                          const int32_t* dir_g, double* grad) {
+    if (!scene_differentiable(b, s) || t0 < 0 || t0 + T > b->T_log - 1) return -1;
+    const int N = b->N_tot;
+    const MetricWeights w = {g_logdiv, g_ov, g_off};
+    for (int q = 0; q < n; ++q) {
+        const int kq = dir_kind[q], tq = dir_t[q], cq = dir_c[q], gq = dir_g[q];
+        if (kq < 0 || kq > 1 || cq < 0 || cq > (kq == 0 ? 2 : 4) || gq < 0 || gq >= N) return -1;
+        auto act = [&](int k, int c, int g) {
+            const double v = act_seq[((size_t)k * 3 + c) * N + g];
+            return Dual(v, (kq == 0 && k == tq && c == cq && g == gq) ? 1.0 : 0.0);
+        };
+        auto st = [&](int g, int c) {
+            const double* f[5] = {st0->x, st0->y, st0->th, st0->vx, st0->vy};
+            return Dual(f[c][g], (kq == 1 && g == gq && c == cq) ? 1.0 : 0.0);
+        };
+        const Objective<Dual> o = scene_objective<Dual>(p, b, s, st0, st, act, t0, T, lambda, tau, &w);
+        grad[q] = w_loss * o.loss.d + o.metrics.d;
     }
     return 0;
 }

@@ -215,6 +215,34 @@ int oracle_loss_grad(const ob_params *p, const ob_batch *b, int s,
                      double lambda, double tau, int n, const int32_t *dir_t,
                      const int32_t *dir_c, const int32_t *dir_g, double *grad);
 
+/* Differentiable objective of one scene over T steps (the objective whose
+ * gradient the differentiable rollout returns):
+ *   J = w_loss * L + sum_k sum_g ( g_logdiv[k][g] * d_g(t0+k+1)
+ *                                + g_ov[k][g] * ov_g(t0+k+1) + g_off[k][g] * off_g(t0+k+1) )
+ * with L the loss of oracle_loss and d, ov, off the metrics of oracle_metrics
+ * (log divergence, largest SAT depth against another valid agent, largest
+ * signed distance of a box corner to the road edges) of the rollout's states.
+ * Weight arrays are [T][N_tot] (element k * N_tot + g), each may be NULL
+ * (all 0); a metric of weight 0 is not evaluated and a metric of -inf adds
+ * nothing.  The max over partners and corners keeps the first maximum
+ * (lowest partner index, corner order of oracle_metrics); the nearest road
+ * edge and its side are decided on the values.  IDM agents move but are
+ * constants for differentiation. */
+double oracle_objective(const ob_params *p, const ob_batch *b, int s, const ob_state *st0,
+                        const double *act_seq, int t0, int T, double lambda, double tau, double w_loss,
+                        const double *g_logdiv, const double *g_ov, const double *g_off);
+
+/* dJ/d(direction) for n directions by forward-mode dual numbers (one pass
+ * each): dir_kind 0 = act_seq[dir_t][dir_c][dir_g] (dir_c 0..2); dir_kind 1 =
+ * component dir_c (0 x, 1 y, 2 theta, 3 vx, 4 vy) of agent dir_g's initial
+ * state (dir_t unused).  Returns 0, or -1 for a bad direction or a scene
+ * that cannot be rolled out. */
+int oracle_objective_grad(const ob_params *p, const ob_batch *b, int s, const ob_state *st0,
+                          const double *act_seq, int t0, int T, double lambda, double tau, double w_loss,
+                          const double *g_logdiv, const double *g_ov, const double *g_off, int n,
+                          const int32_t *dir_kind, const int32_t *dir_t, const int32_t *dir_c,
+                          const int32_t *dir_g, double *grad);
+
 #ifdef __cplusplus
 }
 #endif
