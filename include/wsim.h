@@ -332,6 +332,53 @@ int wsim_get_tuning(wsim_ctx *ctx, wsim_tuning *out);
 int wsim_loss_grad(wsim_ctx *ctx, const wsim_state *st0, const float *act_seq, int t0, int T, int ckpt_every,
                    int flags, double *loss, float *dact, void *stream);
 
+/* Differentiable rollout (the differentiable simulation of Sec. 6), forward
+ * half.  Runs the T-step rollout from st0 (not modified) with every policy
+ * agent taking act_seq ([T][3][N_tot], as wsim_rollout with ctrl NULL; IDM
+ * agents follow their routes) and keeps a record of it in the context: the
+ * state every ckpt_every steps and, when mseq is given, the indices that
+ * decided each step's metrics: per valid agent the partner of its deepest
+ * overlap (exact maximum, ties to the lower index) and the corner, road-edge
+ * segment and side of its largest off-road distance (ties to the lower
+ * corner).  mseq (may be NULL: no metrics) receives the metric rows exactly
+ * as wsim_rollout writes them (bit for bit); loss (device float64 [S], may be
+ * NULL) the scene losses of wsim_loss_grad; st_T (may be NULL, must not alias
+ * st0) the state at t0+T.  A context holds one record: a new call replaces
+ * it.  The record's scratch grows on first use and when T grows (the call
+ * then synchronises `stream`); otherwise asynchronous. */
+int wsim_rollout_record(wsim_ctx *ctx, const wsim_state *st0, const float *act_seq, int t0, int T, int ckpt_every,
+                        const wsim_metric_buf *mseq, double *loss, wsim_state *st_T, void *stream);
+
+/* Weights of the per-step metrics in the objective of wsim_rollout_backward:
+ * device float32 [T][N_tot] arrays, row k for time t0+k+1 (the rows of the
+ * recorded rollout's mseq); NULL = all 0. */
+typedef struct {
+    const float *logdiv, *ov, *off;
+} wsim_metric_grad;
+
+/* Differentiable rollout, reverse half: the gradient of
+ *   J = sum_s loss_w[s] L_s
+ *     + sum_k sum_g ( gm.logdiv[k][g] logdiv_g + gm.ov[k][g] ov_g + gm.off[k][g] off_g )
+ * over the recorded rollout, with respect to its actions and its initial
+ * state.  L_s is the loss of wsim_loss_grad; logdiv, ov and off are the
+ * metric rows of the recorded rollout (App. A.1 dynamics, Sec. 3.4 metrics).
+ * ov and off are maxima: their derivative is that of the recorded deciding
+ * pair or corner (the nearest point on the recorded segment, the side fixed);
+ * a metric of -inf (no other valid agent, no road edge) and every metric of
+ * an invalid agent add nothing.  IDM agents move but are constants for the
+ * derivative.  act_seq: the recorded rollout's actions, unchanged.  loss_w
+ * (device float64 [S], may be NULL = no loss term); gm may be NULL (no metric
+ * term).  dact ([T][3][N_tot], may be NULL) receives dJ/dact as
+ * wsim_loss_grad writes it; dst0 (may be NULL, not both) receives dJ/d(state
+ * t0): x and x_lo both hold dJ/dx of x = x + x_lo (likewise y, th), vx and vy
+ * their derivatives, s and s_lo 0.  The segments between checkpoints are
+ * recomputed with the forward's code, so results do not depend on
+ * ckpt_every; no float atomics (deterministic).  WSIM_ESTATE without a
+ * record, or with metric weights for a record made without mseq.
+ * Asynchronous on `stream`. */
+int wsim_rollout_backward(wsim_ctx *ctx, const float *act_seq, const wsim_metric_grad *gm, const double *loss_w,
+                          float *dact, wsim_state *dst0, void *stream);
+
 /* Sticky device status: synchronises `stream`, writes the first device error
  * code recorded since the last call (WSIM_OK if none) to *device_status and
  * clears it. */

@@ -53,6 +53,13 @@ struct wsim_ctx {
     float* ckpt = nullptr;    // BPTT checkpoints
     float* segbuf = nullptr;  // BPTT recomputed segment states
     size_t ckpt_len = 0, seg_len = 0;
+    // record of the differentiable rollout (wsim_rollout_record)
+    float* rckpt = nullptr;     // its checkpoints
+    int16_t* rec_ov = nullptr;  // [T][N_tot] deepest-overlap partners
+    int32_t* rec_off = nullptr; // [T][N_tot] off-road records
+    size_t rckpt_len = 0, rec_ov_len = 0, rec_off_len = 0;
+    int rec_T = 0, rec_t0 = 0, rec_ck = 0, rec_metrics = 0;
+    bool recorded = false;
     // captured rollout
     cudaStream_t cap = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -737,6 +744,98 @@ int wsim_get_tuning(wsim_ctx* c, wsim_tuning* out) {
     return WSIM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Grows a scratch array of the context to at least `need` elements
+// (synchronises the stream first: a kernel may still use the old one).
+template <class T> int grow(T** p, size_t* len, size_t need, cudaStream_t s) {
+    if (need <= *len) return WSIM_OK;
+    CK(cudaStreamSynchronize(s));
+    cudaFree(*p);
+    *p = nullptr;
+    *len = 0;
+    int rc = dalloc(p, need);
+    if (rc) return rc;
+    *len = need;
+    return WSIM_OK;
+}
+
+int bptt_grid(const wsim_ctx* c, int which) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return std::min(c->S, sms * bptt_blocks_per_sm(which));
+}
+
+}  // namespace
+
+extern "C" {
+
+int wsim_rollout_record(wsim_ctx* c, const wsim_state* st0, const float* act_seq, int t0, int T, int ckpt_every,
+                        const wsim_metric_buf* mseq, double* loss, wsim_state* st_T, void* stream) {
+    if (!c || !state_ok(st0) || !act_seq || (mseq && !metrics_ok(mseq)) || (st_T && !state_ok(st_T)))
+        return WSIM_EINVAL;
+    if (st_T && st_T->x == st0->x) return WSIM_EINVAL;
+    if (T < 1 || t0 < 0 || t0 + T >= c->b.T_log || ckpt_every < 1) return WSIM_ESIZE;
+    cudaStream_t s = S_(stream);
+    c->last = s;
+    c->recorded = false;
+    const int ck = std::min(ckpt_every, T);
+    const size_t per = 10 * static_cast<size_t>(c->N_tot);
+    const size_t rows = static_cast<size_t>(T) * static_cast<size_t>(c->N_tot);
+    int rc = grow(&c->rckpt, &c->rckpt_len, static_cast<size_t>((T + ck - 1) / ck + 1) * per, s);
+    if (rc) return rc;
+    if (mseq && ((rc = grow(&c->rec_ov, &c->rec_ov_len, rows, s)) || (rc = grow(&c->rec_off, &c->rec_off_len, rows, s))))
+        return rc;
+    StepArgs a = base_args(c);
+    a.in = cstate(st0);
+    if (st_T) a.out = mstate(st_T);
+    a.act = act_seq;
+    a.t_log = t0 + 1;
+    a.T = T;
+    a.queue = c->queue;
+    a.do_transition = 1;
+    a.do_metrics = mseq != nullptr;
+    if (mseq) a.m = MetricsP{mseq->ov, mseq->off, mseq->logdiv, mseq->flags, mseq->reward};
+    CK(cudaMemsetAsync(c->queue, 0, sizeof(int32_t), s));
+    CK(launch_record(a, c->rckpt, ck, loss, mseq != nullptr, c->rec_ov, c->rec_off, c->cfg.loss_lambda,
+                     c->cfg.loss_tau, bptt_grid(c, 1), s));
+    c->rec_T = T;
+    c->rec_t0 = t0;
+    c->rec_ck = ck;
+    c->rec_metrics = mseq != nullptr;
+    c->recorded = true;
+    return WSIM_OK;
+}
+
+int wsim_rollout_backward(wsim_ctx* c, const float* act_seq, const wsim_metric_grad* gm, const double* loss_w,
+                          float* dact, wsim_state* dst0, void* stream) {
+    if (!c || !act_seq || (!dact && !dst0) || (dst0 && !state_ok(dst0))) return WSIM_EINVAL;
+    if (!c->recorded) return WSIM_ESTATE;
+    const bool metrics = gm && (gm->logdiv || gm->ov || gm->off);
+    if (metrics && !c->rec_metrics) return WSIM_ESTATE;
+    cudaStream_t s = S_(stream);
+    c->last = s;
+    const int T = c->rec_T, ck = c->rec_ck;
+    int rc = grow(&c->segbuf, &c->seg_len, static_cast<size_t>(ck + 1) * 10 * static_cast<size_t>(c->N_tot), s);
+    if (rc) return rc;
+    StepArgs a = base_args(c);
+    a.act = act_seq;
+    a.t_log = c->rec_t0 + 1;
+    a.T = T;
+    a.queue = c->queue;
+    a.do_transition = 1;
+    StateP d{};
+    if (dst0) d = mstate(dst0);
+    CK(cudaMemsetAsync(c->queue, 0, sizeof(int32_t), s));
+    CK(launch_backward(a, c->rckpt, c->segbuf, ck, c->rec_ov, c->rec_off, metrics ? gm->logdiv : nullptr,
+                       metrics ? gm->ov : nullptr, metrics ? gm->off : nullptr, loss_w, dact, d, c->cfg.loss_lambda,
+                       c->cfg.loss_tau, bptt_grid(c, 0), s));
+    return WSIM_OK;
+}
+
 int wsim_loss_grad(wsim_ctx* c, const wsim_state* st0, const float* act_seq, int t0, int T, int ckpt_every,
                    int flags, double* loss, float* dact, void* stream) {
     if (!c || !state_ok(st0) || !act_seq || !loss) return WSIM_EINVAL;
@@ -842,6 +941,9 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->tmp);
     cudaFree(c->ckpt);
     cudaFree(c->segbuf);
+    cudaFree(c->rckpt);
+    cudaFree(c->rec_ov);
+    cudaFree(c->rec_off);
     cudaFree(c->seg_geo);
     cudaFree(c->seg_inv);
     cudaFree(c->seg_flags);

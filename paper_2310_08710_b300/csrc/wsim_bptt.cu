@@ -14,6 +14,8 @@
 // sweep: the adjoint of the loss at t+1 (each pair evaluated once; the terms
 // summed in a fixed order through per-warp buffers: no float atomics) and
 // the adjoint of the transition t -> t+1, which yields dL/d(actions at t).
+#include <cstring>
+
 #include "wsim_phases.cuh"
 
 namespace wsim {
@@ -25,15 +27,24 @@ struct BpttArgs {
     float* ckpt;     // [n_ckpt][10][N_tot]
     float* segbuf;   // [ck + 1][10][N_tot]
     int ck;
-    double* loss;    // [S]
-    float* dact;     // [T][3][N_tot] (may be null: loss only)
+    double* loss;    // [S] (may be null in the recording forward)
+    float* dact;     // [T][3][N_tot] (may be null)
     float lambda, tau;
     int scene;       // >= 0: this scene only (plain path); -1: persistent over the work list
+    // Recording forward and the backward of a weighted objective.
+    int metrics;                           // recording forward: metric rows (A.m) and records
+    int16_t* rec_ov;                       // [T][N_tot] partner of the deepest overlap (-1: none)
+    int32_t* rec_off;                      // [T][N_tot] off-road record (offroad_code, -1: none)
+    const float *g_logdiv, *g_ov, *g_off;  // [T][N_tot] weights of the metric rows (may be null)
+    const double* loss_w;                  // [S] weight of each scene's loss (null: 1)
+    StateP dst0;                           // dL/d(state t0) (x == nullptr: not wanted)
 };
 
 struct AdjSmem {
     float x[kMaxN], y[kMaxN], th[kMaxN], vx[kMaxN], vy[kMaxN];
     float part[kMaxN];
+    float cx[kMaxN], cy[kMaxN], cth[kMaxN];  // an agent's overlap term, partner's share
+    int16_t pidx[kMaxN];                     // ... and the partner (-1: none)
     double total;
 };
 
@@ -146,8 +157,10 @@ __device__ __forceinline__ int first_agent() { return threadIdx.x; }
 constexpr int kAgentStride = NTb;
 static_assert(kAgentStride == NTb, "one agent per thread and stride: the reverse sweep relies on it");
 
+// wl weighs the whole term (the scene's loss weight; 1 gives the loss's own
+// gradient bit for bit).
 __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, const StepArgs& A, int a0, int N,
-                             int lane, int warp, float lambda, float tau, int t_log) {
+                             int lane, int warp, float lambda, float tau, int t_log, float wl) {
     float* bx = wbuf + static_cast<size_t>(warp) * 3 * kMaxN;
     float* by = bx + kMaxN;
     float* bth = by + kMaxN;
@@ -180,9 +193,9 @@ __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, con
         if (lane == 0) {
             const size_t li = static_cast<size_t>(t_log) * A.N_tot + a0 + i;
             const float ex = (xih - A.log_x[li]) + xil, ey = (yih - A.log_y[li]) + yil;
-            adj.x[i] += gx + 2.f * ex;
-            adj.y[i] += gy + 2.f * ey;
-            adj.th[i] += gth;
+            adj.x[i] += wl * (gx + 2.f * ex);
+            adj.y[i] += wl * (gy + 2.f * ey);
+            adj.th[i] += wl * gth;
         }
         __syncwarp();  // the next row's lanes update entries of this row's lanes
     }
@@ -194,6 +207,95 @@ __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, con
             sx += b[j];
             sy += b[kMaxN + j];
             st += b[2 * kMaxN + j];
+        }
+        adj.x[j] += wl * sx;
+        adj.y[j] += wl * sy;
+        adj.th[j] += wl * st;
+    }
+}
+
+// Adds the derivative of the weighted metric row of the current state
+// (metric row t, time t0+t+1) to adj (all threads; agent j's sums in thread
+// agent_thread(j)):
+//   log divergence d = |p - log|: (p - log) / d;
+//   off-road off = +-|corner - q| (q the nearest point of the recorded
+//     segment, + off road): +-(corner - q) / |corner - q|, through the
+//     corner c + R(theta) (a, b) also into theta;
+//   overlap ov_i = d_ij of the recorded partner j: the SAT depth's partial
+//     derivatives (active axis) for both agents; the partner's share goes
+//     through adj.c* and is summed by the partner's thread in index order.
+__device__ void metric_adjoint(const AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, const SegView& V, int t,
+                               int a0, int N) {
+    const StepArgs& A = B.A;
+    const size_t row = static_cast<size_t>(t) * A.N_tot;
+    const size_t lrow = static_cast<size_t>(A.t_log + t) * A.N_tot;
+    for (int i = first_agent(); i < N; i += kAgentStride) {
+        const int g = a0 + i;
+        adj.pidx[i] = -1;
+        if (!sm.valid[i]) continue;
+        float gx = 0.f, gy = 0.f, gth = 0.f;
+        const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
+        const float w_ld = B.g_logdiv ? B.g_logdiv[row + g] : 0.f;
+        if (w_ld != 0.f) {
+            const float ex = (xih - A.log_x[lrow + g]) + xil, ey = (yih - A.log_y[lrow + g]) + yil;
+            const float ld = sqrtf(fmaf(ex, ex, ey * ey));
+            if (ld > 0.f) {
+                gx += w_ld * ex / ld;
+                gy += w_ld * ey / ld;
+            }
+        }
+        const float w_off = B.g_off ? B.g_off[row + g] : 0.f;
+        const int code = w_off != 0.f ? B.rec_off[row + g] : -1;
+        if (code >= 0) {
+            const int e = code >> 3, k = (code >> 1) & 3;
+            const float sgn = (code & 1) ? 1.f : -1.f;
+            const float a = (k < 2 ? 1.f : -1.f) * sm.hl[i];
+            const float b = (k == 0 || k == 3 ? 1.f : -1.f) * sm.hw[i];
+            const float c = sm.c[i], s = sm.s[i];
+            const float cl = xil + fmaf(a, c, -b * s), dl = yil + fmaf(a, s, b * c);
+            const float4 G = V.geo[e];
+            const float wx = (xih - G.x) + cl, wy = (yih - G.y) + dl;
+            const float tq = __saturatef(fmaf(wx, G.z, wy * G.w) * V.inv[e]);
+            const float ex = fmaf(-tq, G.z, wx), ey = fmaf(-tq, G.w, wy);
+            const float d = sqrtf(fmaf(ex, ex, ey * ey));
+            if (d > 0.f) {
+                const float px = w_off * sgn * ex / d, py = w_off * sgn * ey / d;
+                gx += px;
+                gy += py;
+                gth += px * fmaf(-a, s, -b * c) + py * fmaf(a, c, -b * s);  // d corner / d theta
+            }
+        }
+        const float w_ov = B.g_ov ? B.g_ov[row + g] : 0.f;
+        const int j = w_ov != 0.f ? B.rec_ov[row + g] : -1;
+        if (j >= 0) {
+            const int ia = min(i, j), ib = max(i, j);
+            const float dx = comp_diff(sm.xh[ib], sm.xl[ib], sm.xh[ia], sm.xl[ia]);
+            const float dy = comp_diff(sm.yh[ib], sm.yl[ib], sm.yh[ia], sm.yl[ia]);
+            const SatGrad G = sat_grad(dx, dy, sm.c[ia], sm.s[ia], sm.hl[ia], sm.hw[ia], sm.c[ib], sm.s[ib],
+                                       sm.hl[ib], sm.hw[ib]);
+            // d d_ab: -(ddx, ddy) and dthA for a, +(ddx, ddy) and dthB for b
+            const float sx = i == ia ? -1.f : 1.f;
+            gx += sx * w_ov * G.ddx;
+            gy += sx * w_ov * G.ddy;
+            gth += w_ov * (i == ia ? G.dthA : G.dthB);
+            adj.cx[i] = -sx * w_ov * G.ddx;
+            adj.cy[i] = -sx * w_ov * G.ddy;
+            adj.cth[i] = w_ov * (i == ia ? G.dthB : G.dthA);
+            adj.pidx[i] = static_cast<int16_t>(j);
+        }
+        adj.x[i] += gx;
+        adj.y[i] += gy;
+        adj.th[i] += gth;
+    }
+    __syncthreads();
+    for (int j = first_agent(); j < N; j += kAgentStride) {  // same mapping as transition_adjoint
+        float sx = 0.f, sy = 0.f, st = 0.f;
+        for (int i = 0; i < N; ++i) {
+            if (adj.pidx[i] == j) {
+                sx += adj.cx[i];
+                sy += adj.cy[i];
+                st += adj.cth[i];
+            }
         }
         adj.x[j] += sx;
         adj.y[j] += sy;
@@ -260,45 +362,46 @@ __device__ void transition_adjoint(AgentSmem& sm, AdjSmem& adj, const BpttArgs& 
     }
 }
 
-__device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttArgs& B, int s) {
+// One step's loss of the current state (all threads): each warp's rows into
+// adj.part, then (after the caller's barrier) warp 0 adds them in a fixed
+// order; see loss_sum.
+__device__ __forceinline__ void loss_rows(const AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int a0, int N,
+                                          int t_log) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = warp; i < N; i += NWb) {
+        const float v = sm.valid[i] ? loss_agent(sm, B.A, a0, N, i, lane, B.lambda, B.tau, t_log) : 0.f;
+        if (lane == 0) adj.part[i] = v;
+    }
+}
+// The step's loss in a fixed order: lane-strided sums, then a fixed shuffle tree.
+__device__ __forceinline__ void loss_sum(AdjSmem& adj, int N) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+        float step = 0.f;
+        for (int i = lane; i < N; i += 32) step += adj.part[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) step += __shfl_xor_sync(kFull, step, o);
+        if (lane == 0) adj.total += static_cast<double>(step);
+    }
+}
+
+// Reverse sweep over the checkpointed rollout of scene s: segments from last
+// to first, each recomputed from its checkpoint with the forward's code (so
+// the checkpoint interval does not change a bit), then, step by step from
+// the last, the adjoint of the loss at t+1 weighted by wl (skipped for wl =
+// 0), the adjoint of the weighted metric row t (when metric weights are
+// given), and the adjoint of the transition t -> t+1, which writes
+// dL/d(actions at t).  dL/d(state t0) remains in adj and goes to B.dst0.
+__device__ void reverse_sweep(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttArgs& B, int s, float wl) {
     const StepArgs& A = B.A;
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = NTb / 32;
     Counts cnt;
     const int T = A.T, ck = B.ck;
     const int nseg = (T + ck - 1) / ck;
-
-    // Forward.
-    load_state<NTb>(sm, A, A.in, a0, N);
-    __syncthreads();
-    store_state<NTb>(sm, slot_state(B.ckpt, 0, A.N_tot), a0, N);
-    if (threadIdx.x == 0) adj.total = 0.0;
-    for (int k = 0; k < T; ++k) {
-        phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(k) * 3 * A.N_tot, A.t_log + k, a0, N, cnt);
-        __syncthreads();
-        writeback<NTb>(sm, A.p, nullptr, a0, N);
-        __syncthreads();
-        for (int i = warp; i < N; i += NW) {
-            const float v = sm.valid[i] ? loss_agent(sm, A, a0, N, i, lane, B.lambda, B.tau, A.t_log + k) : 0.f;
-            if (lane == 0) adj.part[i] = v;
-        }
-        if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
-        __syncthreads();
-        if (warp == 0) {  // the step's loss in a fixed order: lane-strided sums, then a fixed shuffle tree
-            float step = 0.f;
-            for (int i = lane; i < N; i += 32) step += adj.part[i];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) step += __shfl_xor_sync(kFull, step, o);
-            if (lane == 0) adj.total += static_cast<double>(step);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) B.loss[s] = adj.total;
-    if (!B.dact) return;
-
-    // Backward.
-    for (int i = threadIdx.x; i < N; i += NTb) adj.x[i] = adj.y[i] = adj.th[i] = adj.vx[i] = adj.vy[i] = 0.f;
+    const bool metrics = B.g_logdiv || B.g_ov || B.g_off;
+    const SegView V = global_view(A.segs, s);
+    for (int i = first_agent(); i < N; i += kAgentStride) adj.x[i] = adj.y[i] = adj.th[i] = adj.vx[i] = adj.vy[i] = 0.f;
     for (int sg = nseg - 1; sg >= 0; --sg) {
         const int a = sg * ck, b = min(a + ck, T);
         // Recompute the inner states a+1 .. b-1 of the segment.
@@ -320,16 +423,117 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttA
             const CStateP nxt = (t + 1 == b) ? cslot(B.ckpt, (b + ck - 1) / ck, A.N_tot)
                                              : cslot(B.segbuf, t + 1 - a, A.N_tot);
             load_state<NTb>(sm, A, nxt, a0, N);
-            // state t into the n* arrays, which the loss adjoint does not read
+            // state t into the n* arrays, which the loss and metric adjoints do not read
             const CStateP cur = (t == a) ? cslot(B.ckpt, sg, A.N_tot) : cslot(B.segbuf, t - a, A.N_tot);
             load_prev(sm, cur, a0, N);
             __syncthreads();
-            loss_adjoint(sm, adj, wbuf, A, a0, N, lane, warp, B.lambda, B.tau, A.t_log + t);
-            // the loss adjoint ends with agent j's sum in the thread that
-            // takes agent j here: no barrier in between
+            if (wl != 0.f) loss_adjoint(sm, adj, wbuf, A, a0, N, lane, warp, B.lambda, B.tau, A.t_log + t, wl);
+            if (metrics) metric_adjoint(sm, adj, B, V, t, a0, N);
+            // both adjoints end with agent j's sums in the thread that takes
+            // agent j here: no barrier in between
             transition_adjoint(sm, adj, B, t, a0, N);
         }
     }
+    if (B.dst0.x) {
+        // x = x_hi + x_lo: both words get dL/dx (likewise theta); the route
+        // parameter of IDM agents is a constant
+        const StateP& d = B.dst0;
+        for (int i = first_agent(); i < N; i += kAgentStride) {
+            const int g = a0 + i;
+            d.x[g] = d.x_lo[g] = adj.x[i];
+            d.y[g] = d.y_lo[g] = adj.y[i];
+            d.th[g] = d.th_lo[g] = adj.th[i];
+            d.vx[g] = adj.vx[i];
+            d.vy[g] = adj.vy[i];
+            d.s[g] = d.s_lo[g] = 0.f;
+        }
+    }
+    __syncthreads();
+}
+
+// Forward with the loss and checkpoints, then (dact given) the reverse sweep
+// of the loss alone.
+__device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttArgs& B, int s) {
+    const StepArgs& A = B.A;
+    const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
+    Counts cnt;
+    const int T = A.T, ck = B.ck;
+
+    // Forward.
+    load_state<NTb>(sm, A, A.in, a0, N);
+    __syncthreads();
+    store_state<NTb>(sm, slot_state(B.ckpt, 0, A.N_tot), a0, N);
+    if (threadIdx.x == 0) adj.total = 0.0;
+    for (int k = 0; k < T; ++k) {
+        phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(k) * 3 * A.N_tot, A.t_log + k, a0, N, cnt);
+        __syncthreads();
+        writeback<NTb>(sm, A.p, nullptr, a0, N);
+        __syncthreads();
+        loss_rows(sm, adj, B, a0, N, A.t_log + k);
+        if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
+        __syncthreads();
+        loss_sum(adj, N);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) B.loss[s] = adj.total;
+    if (!B.dact) return;
+    reverse_sweep(sm, adj, wbuf, B, s, 1.f);
+}
+
+// Recording forward of scene s: the rollout (every policy agent takes its
+// action) with checkpoints every ck steps, the loss (B.loss given) and, with
+// B.metrics, every step's metric row (A.m, as wsim_rollout writes it) and
+// the records of its deciding indices: the partner of each agent's deepest
+// overlap (exact maximum, ties to the lower index) and the corner, segment
+// and side of its largest off-road distance (ties to the lower corner).
+// tlist / tmeta: the scene's candidate-tile caches of the off-road search.
+__device__ void record_scene(AgentSmem& sm, AdjSmem& adj, unsigned long long* k64, uint16_t* tlist, float4* tmeta,
+                             const BpttArgs& B, int s) {
+    const StepArgs& A = B.A;
+    const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
+    const int lane = threadIdx.x & 31;
+    Counts cnt;
+    const int T = A.T, ck = B.ck;
+    const size_t N_tot = static_cast<size_t>(A.N_tot);
+    const SegView V = global_view(A.segs, s);
+    load_state<NTb>(sm, A, A.in, a0, N);
+    for (int j = threadIdx.x; j < 4 * N; j += NTb) sm.hint[j] = -1;
+    for (int j = threadIdx.x; j < N; j += NTb) tmeta[j] = make_float4(0.f, 0.f, 0.f, __int_as_float(-1));
+    __syncthreads();
+    store_state<NTb>(sm, slot_state(B.ckpt, 0, A.N_tot), a0, N);
+    if (threadIdx.x == 0) adj.total = 0.0;
+    for (int k = 0; k < T; ++k) {
+        phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(k) * 3 * N_tot, A.t_log + k, a0, N, cnt);
+        __syncthreads();
+        writeback<NTb>(sm, A.p, nullptr, a0, N);
+        __syncthreads();
+        if (B.metrics) {
+            const size_t row = static_cast<size_t>(k) * N_tot;
+            overlap_bounds<NTb>(sm, N);
+            for (int j = threadIdx.x; j < N; j += NTb) k64[j] = 0ull;
+            __syncthreads();
+            int32_t* orec = B.rec_off + row + a0;
+            for (int q = next_agent(sm, 2, lane); 8 * q < N; q = next_agent(sm, 2, lane))
+                offroad_group<true>(sm, V, sm.hint, tlist, tmeta, N, 8 * q, lane, kListLook * A.p.dt, cnt, orec);
+            for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane))
+                if (sm.valid[i]) overlap_row<true>(sm, N, i, lane, cnt, k64);
+            __syncthreads();
+            const MetricsP m{A.m.ov + row, A.m.off + row, A.m.logdiv + row, A.m.flags + row, nullptr};
+            phase_finish<NTb>(sm, A, m, A.m.reward + static_cast<size_t>(k) * A.S + s, A.t_log + k, a0, N);
+            for (int i = threadIdx.x; i < N; i += NTb) {
+                const bool v = sm.valid[i];
+                B.rec_ov[row + a0 + i] = static_cast<int16_t>(v ? argmax_partner(k64[i]) : -1);
+                if (!v) orec[i] = -1;
+            }
+        }
+        if (B.loss) loss_rows(sm, adj, B, a0, N, A.t_log + k);
+        if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
+        __syncthreads();
+        if (B.loss) loss_sum(adj, N);
+    }
+    __syncthreads();
+    if (B.loss && threadIdx.x == 0) B.loss[s] = adj.total;
+    if (A.out.x) store_state<NTb>(sm, A.out, a0, N);
     __syncthreads();
 }
 
@@ -337,6 +541,20 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttA
 constexpr size_t kAdjOff = (sizeof(AgentSmem) + 15) / 16 * 16;
 constexpr size_t kBufOff = (kAdjOff + sizeof(AdjSmem) + 15) / 16 * 16;
 constexpr size_t kBpttSmem = kBufOff + kPairBufFloats * sizeof(float);
+// Recording forward: AgentSmem, AdjSmem, argmax keys, then the off-road
+// candidate-tile caches (list metadata, lists).
+constexpr size_t kK64Off = kBufOff;
+constexpr size_t kMetaOff = kK64Off + kMaxN * sizeof(unsigned long long);
+constexpr size_t kListOff = kMetaOff + kMaxN * sizeof(float4);
+constexpr size_t kRecordSmem = kListOff + static_cast<size_t>(kMaxN) * kList * sizeof(uint16_t);
+
+// Next scene of the persistent work list (-1: none left).
+__device__ __forceinline__ int next_scene(AgentSmem& sm, const StepArgs& A) {
+    if (threadIdx.x == 0) sm.scene = atomicAdd(A.queue, 1);
+    __syncthreads();
+    const int w = sm.scene;
+    return w < A.n_work ? A.order[w] : -1;
+}
 
 __global__ void __launch_bounds__(NTb, 2) k_bptt(const BpttArgs B) {
     extern __shared__ __align__(16) unsigned char bdyn[];
@@ -348,27 +566,56 @@ __global__ void __launch_bounds__(NTb, 2) k_bptt(const BpttArgs B) {
         bptt_scene(sm, adj, wbuf, B, B.scene);
         return;
     }
-    for (;;) {
-        if (threadIdx.x == 0) sm.scene = atomicAdd(B.A.queue, 1);
-        __syncthreads();
-        const int w = sm.scene;
-        if (w >= B.A.n_work) break;
-        bptt_scene(sm, adj, wbuf, B, B.A.order[w]);
+    for (int s = next_scene(sm, B.A); s >= 0; s = next_scene(sm, B.A)) {
+        bptt_scene(sm, adj, wbuf, B, s);
         __syncthreads();
     }
 }
 
-cudaError_t launch_bptt(const StepArgs& a, float* ckpt, float* segbuf, int ck, double* loss, float* dact,
-                        float lambda, float tau, int grid, bool plain, cudaStream_t st) {
+__global__ void __launch_bounds__(NTb, 2) k_record(const BpttArgs B) {
+    extern __shared__ __align__(16) unsigned char rdyn[];
+    AgentSmem& sm = *reinterpret_cast<AgentSmem*>(rdyn);
+    AdjSmem& adj = *reinterpret_cast<AdjSmem*>(rdyn + kAdjOff);
+    unsigned long long* k64 = reinterpret_cast<unsigned long long*>(rdyn + kK64Off);
+    float4* tmeta = reinterpret_cast<float4*>(rdyn + kMetaOff);
+    uint16_t* tlist = reinterpret_cast<uint16_t*>(rdyn + kListOff);
+    init_cta(sm);
+    for (int s = next_scene(sm, B.A); s >= 0; s = next_scene(sm, B.A)) {
+        record_scene(sm, adj, k64, tlist, tmeta, B, s);
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(NTb, 2) k_backward(const BpttArgs B) {
+    extern __shared__ __align__(16) unsigned char bdyn[];
+    AgentSmem& sm = *reinterpret_cast<AgentSmem*>(bdyn);
+    AdjSmem& adj = *reinterpret_cast<AdjSmem*>(bdyn + kAdjOff);
+    float* wbuf = reinterpret_cast<float*>(bdyn + kBufOff);
+    init_cta(sm);
+    for (int s = next_scene(sm, B.A); s >= 0; s = next_scene(sm, B.A)) {
+        reverse_sweep(sm, adj, wbuf, B, s, B.loss_w ? static_cast<float>(B.loss_w[s]) : 0.f);
+        __syncthreads();
+    }
+}
+
+static BpttArgs bptt_args(const StepArgs& a, float* ckpt, float* segbuf, int ck, float lambda, float tau) {
     BpttArgs B;
+    std::memset(&B, 0, sizeof(B));
     B.A = a;
     B.ckpt = ckpt;
     B.segbuf = segbuf;
     B.ck = ck;
-    B.loss = loss;
-    B.dact = dact;
     B.lambda = lambda;
     B.tau = tau;
+    B.scene = -1;
+    return B;
+}
+
+cudaError_t launch_bptt(const StepArgs& a, float* ckpt, float* segbuf, int ck, double* loss, float* dact,
+                        float lambda, float tau, int grid, bool plain, cudaStream_t st) {
+    BpttArgs B = bptt_args(a, ckpt, segbuf, ck, lambda, tau);
+    B.loss = loss;
+    B.dact = dact;
     cudaError_t e = cudaFuncSetAttribute(k_bptt, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(kBpttSmem));
     if (e != cudaSuccess) return e;
@@ -378,17 +625,53 @@ cudaError_t launch_bptt(const StepArgs& a, float* ckpt, float* segbuf, int ck, d
             k_bptt<<<1, NTb, kBpttSmem, st>>>(B);
         }
     } else {
-        B.scene = -1;
         k_bptt<<<grid, NTb, kBpttSmem, st>>>(B);
     }
     return cudaGetLastError();
 }
 
-int bptt_blocks_per_sm() {
+cudaError_t launch_record(const StepArgs& a, float* ckpt, int ck, double* loss, int metrics, int16_t* rec_ov,
+                          int32_t* rec_off, float lambda, float tau, int grid, cudaStream_t st) {
+    BpttArgs B = bptt_args(a, ckpt, nullptr, ck, lambda, tau);
+    B.loss = loss;
+    B.metrics = metrics;
+    B.rec_ov = rec_ov;
+    B.rec_off = rec_off;
+    cudaError_t e = cudaFuncSetAttribute(k_record, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kRecordSmem));
+    if (e != cudaSuccess) return e;
+    k_record<<<grid, NTb, kRecordSmem, st>>>(B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward(const StepArgs& a, float* ckpt, float* segbuf, int ck, const int16_t* rec_ov,
+                            const int32_t* rec_off, const float* g_logdiv, const float* g_ov, const float* g_off,
+                            const double* loss_w, float* dact, const StateP& dst0, float lambda, float tau, int grid,
+                            cudaStream_t st) {
+    BpttArgs B = bptt_args(a, ckpt, segbuf, ck, lambda, tau);
+    B.rec_ov = const_cast<int16_t*>(rec_ov);
+    B.rec_off = const_cast<int32_t*>(rec_off);
+    B.g_logdiv = g_logdiv;
+    B.g_ov = g_ov;
+    B.g_off = g_off;
+    B.loss_w = loss_w;
+    B.dact = dact;
+    B.dst0 = dst0;
+    cudaError_t e = cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kBpttSmem));
+    if (e != cudaSuccess) return e;
+    k_backward<<<grid, NTb, kBpttSmem, st>>>(B);
+    return cudaGetLastError();
+}
+
+// Resident CTAs per SM of the BPTT kernels (which = 0: k_bptt and
+// k_backward; 1: k_record).
+int bptt_blocks_per_sm(int which) {
     int n = 0;
-    if (cudaFuncSetAttribute(k_bptt, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kBpttSmem)) !=
-            cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_bptt, NTb, kBpttSmem) != cudaSuccess) {
+    const void* f = which == 1 ? reinterpret_cast<const void*>(k_record) : reinterpret_cast<const void*>(k_bptt);
+    const size_t smem = which == 1 ? kRecordSmem : kBpttSmem;
+    if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, f, NTb, smem) != cudaSuccess) {
         cudaGetLastError();
         return 1;
     }

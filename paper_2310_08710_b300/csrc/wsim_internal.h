@@ -138,6 +138,14 @@ cudaError_t launch_route(const StepArgs& a, const int32_t* path_off, const int32
 // Backpropagation through the rollout (wsim_bptt.cu).
 cudaError_t launch_bptt(const StepArgs& a, float* ckpt, float* segbuf, int ck, double* loss, float* dact,
                         float lambda, float tau, int grid, bool plain, cudaStream_t st);
-int bptt_blocks_per_sm();
+// Recording forward (checkpoints, loss, metric rows and their deciding
+// indices) and the backward of a weighted objective of its metrics and loss.
+cudaError_t launch_record(const StepArgs& a, float* ckpt, int ck, double* loss, int metrics, int16_t* rec_ov,
+                          int32_t* rec_off, float lambda, float tau, int grid, cudaStream_t st);
+cudaError_t launch_backward(const StepArgs& a, float* ckpt, float* segbuf, int ck, const int16_t* rec_ov,
+                            const int32_t* rec_off, const float* g_logdiv, const float* g_ov, const float* g_off,
+                            const double* loss_w, float* dact, const StateP& dst0, float lambda, float tau, int grid,
+                            cudaStream_t st);
+int bptt_blocks_per_sm(int which = 0);
 
 }  // namespace wsim

@@ -601,7 +601,22 @@ __device__ void transition_policy(AgentSmem& sm, const StepArgs& A, const float*
 // lb_i and lb_j changes neither maximum and is skipped (1.5 mm of slack for
 // the float32 bound and the hi words used).
 // ---------------------------------------------------------------------------
-static __device__ void overlap_row(AgentSmem& sm, int N, int i, int lane, Counts& cnt) {
+// Exact argmax key of a pair depth for agent records: the depth's ordered
+// key above the partner's index complement, so that the maximum key names
+// the deepest partner, ties to the lower index.  0 = no partner.
+__device__ __forceinline__ unsigned long long argmax_key(float d, int j) {
+    return (static_cast<unsigned long long>(ukey(d)) << 32) | static_cast<unsigned long long>(0xffffu - j);
+}
+__device__ __forceinline__ int argmax_partner(unsigned long long k) {
+    return k ? static_cast<int>(0xffffu - static_cast<unsigned>(k & 0xffffu)) : -1;
+}
+
+// REC: also folds argmax_key into k64[] of both agents (records of the
+// differentiable rollout; a culled pair cannot be a maximum, so the recorded
+// partner is the exhaustive argmax).
+template <bool REC = false>
+static __device__ void overlap_row(AgentSmem& sm, int N, int i, int lane, Counts& cnt,
+                                   unsigned long long* k64 = nullptr) {
     const float4 Pi = sm.obox[i];
     const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
     const float ci = sm.c[i], si = sm.s[i], hli = sm.hl[i], hwi = sm.hw[i];
@@ -619,6 +634,10 @@ static __device__ void overlap_row(AgentSmem& sm, int N, int i, int lane, Counts
         atomicMax(&sm.pk[j], partner_key(d, i));
         atomicMax(&sm.ovk[i], ukey(d));
         atomicMax(&sm.pk[i], partner_key(d, j));
+        if (REC) {
+            atomicMax(&k64[j], argmax_key(d, i));
+            atomicMax(&k64[i], argmax_key(d, j));
+        }
         cnt.pairs += 2;
     }
 }
@@ -755,11 +774,38 @@ __device__ __forceinline__ float corner_side(const SegView& V, int e, float d2, 
     return on ? -d : d;
 }
 
+// Record of an agent's off-road distance for the differentiable rollout:
+// (segment << 3) | (corner << 1) | (1 if off road), -1 without a segment.
+__device__ __forceinline__ int offroad_code(int e, int k, float sd) {
+    return e >= 0 ? (e << 3) | (k << 1) | (sd > 0.f ? 1 : 0) : -1;
+}
+
+// The record of the corner holding the largest signed distance among the
+// four lanes 4q .. 4q+3 (lane 4q+k: corner k), ties to the lower corner.
+__device__ __forceinline__ int quad_argmax_code(float sd, int code, int lane) {
+    int bk = lane & 3;
+#pragma unroll
+    for (int o = 1; o <= 2; o <<= 1) {
+        const float os = __shfl_xor_sync(kFull, sd, o);
+        const int ok = __shfl_xor_sync(kFull, bk, o), oc = __shfl_xor_sync(kFull, code, o);
+        if (os > sd || (os == sd && ok < bk)) {
+            sd = os;
+            bk = ok;
+            code = oc;
+        }
+    }
+    return code;
+}
+
+// REC: *orec (lane 0) receives the agent's offroad_code.
+template <bool REC = false>
 static __device__ float offroad_agent(const SegView& V, int lane, float xh, float xl, float yh, float yl, float c,
                                       float s, float hl, float hw, int32_t* hint, uint16_t* tl, float4* meta,
-                                      Counts& cnt, bool force_scan = false, float lvx = 0.f, float lvy = 0.f) {
+                                      Counts& cnt, bool force_scan = false, float lvx = 0.f, float lvy = 0.f,
+                                      int32_t* orec = nullptr) {
     if (V.E == 0) {
         if (hint && lane < 4) hint[lane] = -1;
+        if (REC && lane == 0) *orec = -1;
         return -WSIM_INF;
     }
     float cxl[4], cyl[4], px[4], py[4];
@@ -959,10 +1005,16 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
     }
     // Side of the nearest feature (lane k: corner k).
     float sd = -WSIM_INF;
+    int code = -1;
     if (lane < 4) {
         const int e = pick4(bi, lane);
         if (e >= 0) sd = corner_side(V, e, pick4(bd, lane), xh, pick4(cxl, lane), yh, pick4(cyl, lane));
         if (hint) hint[lane] = e;
+        if (REC) code = offroad_code(e, lane, sd);
+    }
+    if (REC) {
+        code = quad_argmax_code(sd, code, lane);
+        if (lane == 0) *orec = code;
     }
     sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 1));
     sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 2));
@@ -978,8 +1030,11 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
 // hints fail any corner take the warp-cooperative search (offroad_agent),
 // which also rebuilds the cache.
 // ---------------------------------------------------------------------------
+// REC: orec[a] receives agent a's offroad_code.
+template <bool REC = false>
 static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* hint_base, uint16_t* tl_base,
-                                     float4* meta_base, int N, int g0, int lane, float look, Counts& cnt) {
+                                     float4* meta_base, int N, int g0, int lane, float look, Counts& cnt,
+                                     int32_t* orec = nullptr) {
     const int a = g0 + (lane >> 2), k = lane & 3;
     const bool act = a < N && sm.valid[a];
     bool fast = false;
@@ -1049,6 +1104,10 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
         sd = corner_side(V, bi, best, xh, cl, yh, dl);
         hint_base[4 * a + k] = bi;
     }
+    if (REC) {
+        const int code = quad_argmax_code(sd, ok ? offroad_code(bi, k, sd) : -1, lane);
+        if (ok && k == 0) orec[a] = code;
+    }
     sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 1));
     sd = fmaxf(sd, __shfl_xor_sync(kFull, sd, 2));
     if (ok && k == 0) sm.off[a] = sd;
@@ -1057,10 +1116,11 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
     while (need) {
         const int ai = g0 + ((__ffs(need) - 1) >> 2);
         need &= need - 1;
-        const float f = offroad_agent(V, lane, sm.xh[ai], sm.xl[ai], sm.yh[ai], sm.yl[ai], sm.c[ai], sm.s[ai],
-                                      sm.hl[ai], sm.hw[ai], hint_base ? hint_base + 4 * ai : nullptr,
-                                      tl_base ? tl_base + kList * ai : nullptr, tl_base ? meta_base + ai : nullptr,
-                                      cnt, true, sm.vx[ai] * look, sm.vy[ai] * look);
+        const float f = offroad_agent<REC>(V, lane, sm.xh[ai], sm.xl[ai], sm.yh[ai], sm.yl[ai], sm.c[ai], sm.s[ai],
+                                           sm.hl[ai], sm.hw[ai], hint_base ? hint_base + 4 * ai : nullptr,
+                                           tl_base ? tl_base + kList * ai : nullptr,
+                                           tl_base ? meta_base + ai : nullptr, cnt, true, sm.vx[ai] * look,
+                                           sm.vy[ai] * look, REC ? orec + ai : nullptr);
         if (lane == 0) sm.off[ai] = f;
     }
 }

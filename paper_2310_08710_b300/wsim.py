@@ -84,6 +84,10 @@ class WsimMetricBuf(C.Structure):
                 ("reward", C.c_void_p)]
 
 
+class WsimMetricGrad(C.Structure):
+    _fields_ = [("logdiv", C.c_void_p), ("ov", C.c_void_p), ("off", C.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libwsim.so is not built ({LIB_PATH}); run paper_2310_08710_b300.build.build()")
@@ -108,6 +112,9 @@ def _load():
     lib.wsim_set_tuning.argtypes = [vp, P(WsimTuning)]
     lib.wsim_get_tuning.argtypes = [vp, P(WsimTuning)]
     lib.wsim_loss_grad.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp]
+    lib.wsim_rollout_record.argtypes = [vp, P(WsimState), vp, C.c_int, C.c_int, C.c_int, P(WsimMetricBuf), vp,
+                                        P(WsimState), vp]
+    lib.wsim_rollout_backward.argtypes = [vp, vp, P(WsimMetricGrad), vp, vp, P(WsimState), vp]
     lib.wsim_metrics_static.argtypes = [P(WsimConfig), P(WsimBatch), P(WsimState), P(WsimMetricBuf), C.c_int, vp]
     lib.wsim_expert_actions.argtypes = [vp, C.c_int, C.c_int, vp, vp]
     lib.wsim_discretize.argtypes = [vp, vp, C.c_int, vp, vp]
@@ -121,7 +128,8 @@ lib = _load()
 
 EXPORTED = ("wsim_default_config", "wsim_init", "wsim_step", "wsim_metrics", "wsim_rollout", "wsim_status",
             "wsim_set_counting", "wsim_counters", "wsim_strerror", "wsim_destroy", "wsim_metrics_static",
-            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad", "wsim_expert_actions", "wsim_observe",
+            "wsim_autotune", "wsim_set_tuning", "wsim_get_tuning", "wsim_loss_grad", "wsim_rollout_record",
+            "wsim_rollout_backward", "wsim_expert_actions", "wsim_observe",
             "wsim_route_metrics", "wsim_discretize", "wsim_decode_actions")
 
 
@@ -297,6 +305,44 @@ class Sim:
                "wsim_loss_grad")
         return loss, dact
 
+    def rollout_record(self, st0: State, act_seq: torch.Tensor, mseq: Optional[Metrics] = None, t0: int = 10,
+                       T: Optional[int] = None, ckpt_every: int = 10, loss: bool = True,
+                       st_T: Optional[State] = None, stream=None) -> Optional[torch.Tensor]:
+        """Differentiable rollout, forward half (wsim_rollout_record): the
+        T-step rollout from st0 with its checkpoints and, with mseq, its
+        metric rows and their deciding indices kept in the context for
+        rollout_backward.  Returns the scene losses (float64 [S]) or None."""
+        T = act_seq.shape[0] if T is None else T
+        out = torch.empty(self.batch.S, dtype=torch.float64, device=act_seq.device) if loss else None
+        mc = mseq.c() if mseq is not None else None
+        sc = st_T.c() if st_T is not None else None
+        _check(lib.wsim_rollout_record(self._h, C.byref(st0.c()), act_seq.data_ptr(), t0, T, ckpt_every,
+                                       C.byref(mc) if mc is not None else None, _ptr(out),
+                                       C.byref(sc) if sc is not None else None, _stream(stream)),
+               "wsim_rollout_record")
+        self.record_id = getattr(self, "record_id", 0) + 1
+        return out
+
+    def rollout_backward(self, act_seq: torch.Tensor, g_logdiv: Optional[torch.Tensor] = None,
+                         g_ov: Optional[torch.Tensor] = None, g_off: Optional[torch.Tensor] = None,
+                         loss_w: Optional[torch.Tensor] = None, dact: bool = True, dst0: bool = True, stream=None):
+        """Differentiable rollout, reverse half (wsim_rollout_backward): dJ/dact
+        ([T, 3, N_tot]) and dJ/d(initial state) (a State) of J = sum loss_w *
+        loss + the metric rows weighted by g_* ([T, N_tot] float32 each)."""
+        T, dev = act_seq.shape[0], act_seq.device
+        N = self.batch.N_tot
+        f = lambda t: None if t is None else t.detach().to(torch.float32).contiguous()
+        g_logdiv, g_ov, g_off = f(g_logdiv), f(g_ov), f(g_off)
+        lw = None if loss_w is None else loss_w.detach().to(torch.float64).contiguous()
+        gm = WsimMetricGrad(_ptr(g_logdiv), _ptr(g_ov), _ptr(g_off))
+        da = torch.empty((T, 3, N), dtype=torch.float32, device=dev) if dact else None
+        ds = State(N, device=dev) if dst0 else None
+        dc = ds.c() if ds is not None else None
+        _check(lib.wsim_rollout_backward(self._h, act_seq.data_ptr(), C.byref(gm), _ptr(lw), _ptr(da),
+                                         C.byref(dc) if dc is not None else None, _stream(stream)),
+               "wsim_rollout_backward")
+        return da, ds
+
     def observe(self, st: State, M: int, K: int, observers: Optional[torch.Tensor] = None, out: Optional[dict] = None,
                 stream=None) -> dict:
         """Observation (wsim_observe): agents [N_tot, M, 5], agents_valid
@@ -375,25 +421,64 @@ def metrics_static(batch: DeviceBatch, st: State, m: Metrics, t: int, cfg: Optio
                                    _stream(stream)), "wsim_metrics_static")
 
 
+class RolloutFn(torch.autograd.Function):
+    """Differentiable rollout through the recorded forward and its backward:
+
+        logdiv, ov, off, loss = RolloutFn.apply(actions, state0, sim, t0, ckpt_every)
+
+    actions [T, 3, N_tot] and state0 (a State's [10, N_tot] data) are the
+    differentiable inputs; the outputs are the metric rows [T, N_tot] of the
+    T-step rollout (wsim_rollout's logdiv, ov, off) and the per-scene loss of
+    wsim_loss_grad (float64 [S]).  The forward records the rollout in the
+    context (wsim_rollout_record); backward runs wsim_rollout_backward with
+    the incoming gradients as metric and loss weights.  A context holds one
+    record: backward refuses a graph whose forward record was replaced.
+    Entries of ov and off that are -inf (no other agent, no road edge) and
+    the metrics of invalid agents carry no derivative."""
+
+    @staticmethod
+    def forward(ctx, actions: torch.Tensor, state0: torch.Tensor, sim: "Sim", t0: int = 10, ckpt_every: int = 10):
+        act = actions.detach().contiguous()
+        st0 = State(sim.batch.N_tot, data=state0.detach().contiguous())
+        T = act.shape[0]
+        m = Metrics(sim.batch.N_tot, sim.batch.S, rows=T, device=act.device)
+        loss = sim.rollout_record(st0, act, m, t0, T, ckpt_every, loss=True)
+        ctx.sim, ctx.record_id = sim, sim.record_id
+        ctx.save_for_backward(act)
+        return m.logdiv, m.ov, m.off, loss
+
+    @staticmethod
+    def backward(ctx, g_logdiv, g_ov, g_off, g_loss):
+        (act,) = ctx.saved_tensors
+        sim = ctx.sim
+        if sim.record_id != ctx.record_id:
+            raise RuntimeError("RolloutFn.backward: the context recorded another rollout since this forward")
+        da, ds = sim.rollout_backward(act, g_logdiv, g_ov, g_off, g_loss, dact=ctx.needs_input_grad[0],
+                                      dst0=ctx.needs_input_grad[1])
+        return da, (ds.data if ds is not None else None), None, None, None
+
+
 class RolloutLoss(torch.autograd.Function):
     """Differentiable rollout loss: forward returns the per-scene BPTT loss
-    (float64 [S]) of a T-step rollout driven by `actions` ([T, 3, N_tot]);
-    backward returns grad_output[scene] * dL_scene/dactions.  The gradient is
-    computed with the loss (one scene-resident kernel, checkpointed), so the
-    forward costs the whole BPTT pass."""
+    (float64 [S]) of a T-step rollout driven by `actions` ([T, 3, N_tot]) and
+    records the rollout's checkpoints in the context (wsim_rollout_record,
+    without metrics); backward runs the reverse sweep (wsim_rollout_backward)
+    with grad_output as the scenes' loss weights.  A forward under no_grad is
+    the recording forward alone."""
 
     @staticmethod
     def forward(ctx, actions: torch.Tensor, sim: "Sim", st0: State, t0: int = 10, ckpt_every: int = 10):
         act = actions.detach().contiguous()
-        loss, dact = sim.loss_grad(st0, act, t0, act.shape[0], ckpt_every, grad=True)
-        ctx.save_for_backward(dact)
-        ctx.agent_scene = torch.repeat_interleave(
-            torch.arange(sim.batch.S, device=act.device),
-            (sim.batch.agent_off[1:] - sim.batch.agent_off[:-1]).long())
+        loss = sim.rollout_record(st0, act, None, t0, act.shape[0], ckpt_every, loss=True)
+        ctx.sim, ctx.record_id = sim, sim.record_id
+        ctx.save_for_backward(act)
         return loss
 
     @staticmethod
     def backward(ctx, grad_loss):
-        (dact,) = ctx.saved_tensors
-        w = grad_loss.to(dact.dtype)[ctx.agent_scene]  # per agent, its scene's weight
-        return dact * w[None, None, :], None, None, None, None
+        (act,) = ctx.saved_tensors
+        sim = ctx.sim
+        if sim.record_id != ctx.record_id:
+            raise RuntimeError("RolloutLoss.backward: the context recorded another rollout since this forward")
+        da, _ = sim.rollout_backward(act, loss_w=grad_loss, dact=True, dst0=False)
+        return da, None, None, None, None

@@ -52,6 +52,8 @@ def test_host_side_argument_checks_without_gpu():
     assert lib.wsim_expert_actions(None, 10, 80, None, None) == wsim.EINVAL
     assert lib.wsim_observe(None, None, None, 128, 64, None, None, None, None, None) == wsim.EINVAL
     assert lib.wsim_route_metrics(None, None, None, None, None) == wsim.EINVAL
+    assert lib.wsim_rollout_record(None, None, None, 10, 80, 10, None, None, None, None) == wsim.EINVAL
+    assert lib.wsim_rollout_backward(None, None, None, None, None, None, None) == wsim.EINVAL
     assert lib.wsim_discretize(None, None, 1, None, None) == wsim.EINVAL
     assert lib.wsim_decode_actions(None, None, 1, None, None) == wsim.EINVAL
     assert (cfg.disc_na, cfg.disc_nk, cfg.disc_nd, cfg.disc_nt) == (13, 31, 25, 13)
