@@ -323,7 +323,7 @@ __device__ void transition_adjoint(AgentSmem& sm, AdjSmem& adj, const BpttArgs& 
     const float* act = A.act + static_cast<size_t>(t) * 3 * A.N_tot;
     for (int i = first_agent(); i < N; i += kAgentStride) {  // same mapping as loss_adjoint's column sums
         const int g = a0 + i;
-        const int kind = A.kind[g];
+        const int kind = sm.kind[i];
         float ga = 0.f, gk = 0.f, g2 = 0.f;
         if (!sm.valid[i]) {
             // held state: the adjoint passes through unchanged

@@ -25,6 +25,9 @@ struct __align__(16) AgentSmem {
     uint32_t pk[kMaxN];       // the same with its low 8 bits replaced by the pair's other agent
     float4 obox[kMaxN];       // overlap culling record: (x, y, R, R - lower bound of ov)
     int32_t hint[4 * kMaxN];  // scene-resident nearest-segment cache
+    int32_t ro[kMaxN + 1];    // the scene's route offsets (route_off of its agents and the end)
+    float v0[kMaxN];          // IDM desired speeds
+    uint8_t kind[kMaxN];
     uint8_t valid[kMaxN];
     uint8_t kin[kMaxN];       // kinematically infeasible transition into the current state
     int scene;
@@ -188,6 +191,11 @@ __device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, 
         sm.sh[i] = st.s[g];
         sm.sl[i] = st.s_lo[g];
         sm.valid[i] = A.valid[g];
+        // per-agent constants the transitions read every step (absent in a
+        // metrics-only batch)
+        sm.kind[i] = A.kind ? A.kind[g] : static_cast<uint8_t>(WSIM_KIND_BICYCLE);
+        sm.v0[i] = A.v0 ? A.v0[g] : 0.f;
+        sm.ro[i] = A.route_off ? A.route_off[g] : 0;
         sm.kin[i] = 0;
         sm.ovk[i] = kNoDepth;
         sm.pk[i] = kNoDepth;
@@ -197,7 +205,10 @@ __device__ void load_state(AgentSmem& sm, const StepArgs& A, const CStateP& st, 
         sm.obox[i] = sm.valid[i] ? make_float4(st.x[g], st.y[g], R, -WSIM_INF)
                                  : make_float4(st.x[g], st.y[g], -WSIM_INF, -WSIM_INF);
     }
-    if (threadIdx.x == 0) sm.work[0] = sm.work[1] = sm.work[2] = 0;
+    if (threadIdx.x == 0) {
+        sm.work[0] = sm.work[1] = sm.work[2] = 0;
+        sm.ro[N] = A.route_off ? A.route_off[a0 + N] : 0;
+    }
 }
 
 // Make the next state current (after flagging a kinematically infeasible
@@ -307,7 +318,7 @@ __device__ __forceinline__ int ctrl_of(const StepArgs& A, int g) {
 
 // Whether agent i is advanced by IDM in this transition.
 __device__ __forceinline__ bool idm_moves(const AgentSmem& sm, const StepArgs& A, int a0, int i) {
-    return A.kind[a0 + i] == WSIM_KIND_IDM && sm.valid[i] && ctrl_of(A, a0 + i) != WSIM_CTRL_LOG;
+    return sm.kind[i] == WSIM_KIND_IDM && sm.valid[i] && ctrl_of(A, a0 + i) != WSIM_CTRL_LOG;
 }
 
 struct IdmLead {
@@ -316,26 +327,62 @@ struct IdmLead {
     float tlx, tly;   // route tangent at the first sample inside the lead's box
 };
 
+// Look-ahead sample k (0-based; at route parameter s + L/2 + dq (k+1)) of an
+// IDM agent with route cursor (sh, sl) and half length hl: the route point
+// (Px, Py) starting its segment, the segment vector (dx, dy) and the offset
+// (qox, qoy) = tau (dx, dy) of the sample along it.
+struct IdmSample {
+    float Px, Py, dx, dy, qox, qoy;
+};
+__device__ __forceinline__ IdmSample idm_sample(const Params& p, const float* rx, const float* ry, int P, float sh,
+                                                float sl, float hl, int k) {
+    float bh, bl;
+    two_sum(sh, fmaf(p.dq, static_cast<float>(k + 1), hl), bh, bl);
+    bl = __fadd_rn(bl, sl);
+    int seg;
+    float tau;
+    route_locate(bh, bl, p, P, seg, tau);
+    IdmSample q;
+    q.Px = rx[seg];
+    q.Py = ry[seg];
+    q.dx = rx[seg + 1] - q.Px;
+    q.dy = ry[seg + 1] - q.Py;
+    q.qox = tau * q.dx;
+    q.qoy = tau * q.dy;
+    return q;
+}
+
+// Whether look-ahead sample (P + qo) lies in agent j's box widened by wi
+// (half the follower's width) on both axes.
+__device__ __forceinline__ bool idm_in_box(const AgentSmem& sm, int j, float Px, float Py, float qox, float qoy,
+                                           float wi) {
+    const float rxq = (Px - sm.xh[j]) + (qox - sm.xl[j]);
+    const float ryq = (Py - sm.yh[j]) + (qoy - sm.yl[j]);
+    const float cj = sm.c[j], sj = sm.s[j];
+    const float pu = fabsf(fmaf(rxq, cj, ryq * sj));
+    const float pn = fabsf(fmaf(-rxq, sj, ryq * cj));
+    return fminf(sm.hl[j] + wi - pu, sm.hw[j] + wi - pn) >= 0.f;
+}
+
+// Bumper gap between follower i and agent j (clamped below at gap_min).
+__device__ __forceinline__ float idm_gap(const AgentSmem& sm, const Params& p, int i, int j) {
+    const float ddx = comp_diff(sm.xh[j], sm.xl[j], sm.xh[i], sm.xl[i]);
+    const float ddy = comp_diff(sm.yh[j], sm.yl[j], sm.yh[i], sm.yl[i]);
+    return fmaxf(p.gap_min, sqrtf(fmaf(ddx, ddx, ddy * ddy)) - (sm.hl[i] + sm.hl[j]));
+}
+
 // Lead of agent i (warp-wide; every lane returns the same result).
 static __device__ IdmLead idm_lead(AgentSmem& sm, const StepArgs& A, int a0, int N, int i, int lane, Counts& cnt) {
     const Params& p = A.p;
-    const int g = a0 + i;
-    const int ro = A.route_off[g];
-    const int P = A.route_off[g + 1] - ro;
+    const int ro = sm.ro[i];
+    const int P = sm.ro[i + 1] - ro;
     const float* rx = A.route_x + ro;
     const float* ry = A.route_y + ro;
     const float hli = sm.hl[i], wi = sm.hw[i];
 
     // This lane's look-ahead sample.
-    float bh, bl;
-    two_sum(sm.sh[i], fmaf(p.dq, static_cast<float>(lane + 1), hli), bh, bl);
-    bl = __fadd_rn(bl, sm.sl[i]);
-    int seg;
-    float tau;
-    route_locate(bh, bl, p, P, seg, tau);
-    const float Px = rx[seg], Py = ry[seg];
-    const float dx = rx[seg + 1] - Px, dy = ry[seg + 1] - Py;
-    const float qox = tau * dx, qoy = tau * dy;
+    const IdmSample smp = idm_sample(p, rx, ry, P, sm.sh[i], sm.sl[i], hli, lane);
+    const float Px = smp.Px, Py = smp.Py, dx = smp.dx, dy = smp.dy, qox = smp.qox, qoy = smp.qoy;
 
     // Bounding circles of the four groups of 8 consecutive samples: a box
     // (widened by wi) that holds a sample of group G has its centre within
@@ -349,23 +396,20 @@ static __device__ IdmLead idm_lead(AgentSmem& sm, const StepArgs& A, int a0, int
 #pragma unroll
     for (int o = 4; o > 0; o >>= 1) gr = fmaxf(gr, __shfl_xor_sync(kFull, gr, o));
     gr += 2.f * wi + 0.05f;  // lanes 8G .. 8G+7 hold circle G
+    float cxs[4], cys[4], crs[4];  // the four circles in every lane
+#pragma unroll
+    for (int G = 0; G < 4; ++G) {
+        cxs[G] = __shfl_sync(kFull, gcx, 8 * G);
+        cys[G] = __shfl_sync(kFull, gcy, 8 * G);
+        crs[G] = __shfl_sync(kFull, gr, 8 * G);
+    }
 
-    const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
     int lead = -1, lead_hit = 0;
     float gbest = WSIM_INF;
     // Samples in the widened box of agent j (one ballot bit per sample).
-    auto box_hits = [&](int j) {
-        const float rxq = (Px - sm.xh[j]) + (qox - sm.xl[j]);
-        const float ryq = (Py - sm.yh[j]) + (qoy - sm.yl[j]);
-        const float cj = sm.c[j], sj = sm.s[j];
-        const float pu = fabsf(fmaf(rxq, cj, ryq * sj));
-        const float pn = fabsf(fmaf(-rxq, sj, ryq * cj));
-        return fminf(sm.hl[j] + wi - pu, sm.hw[j] + wi - pn) >= 0.f;
-    };
+    auto box_hits = [&](int j) { return idm_in_box(sm, j, Px, Py, qox, qoy, wi); };
     auto take = [&](int j, unsigned hits) {
-        const float ddx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
-        const float ddy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
-        const float gap = fmaxf(p.gap_min, sqrtf(fmaf(ddx, ddx, ddy * ddy)) - (hli + sm.hl[j]));
+        const float gap = idm_gap(sm, p, i, j);
         if (gap < gbest) {
             gbest = gap;
             lead = j;
@@ -390,8 +434,8 @@ static __device__ IdmLead idm_lead(AgentSmem& sm, const StepArgs& A, int a0, int
         cnt.filters += 4;
 #pragma unroll
         for (int G = 0; G < 4; ++G) {
-            const float ex = xj - __shfl_sync(kFull, gcx, 8 * G), ey = yj - __shfl_sync(kFull, gcy, 8 * G);
-            const float rr = __shfl_sync(kFull, gr, 8 * G) + reach;
+            const float ex = xj - cxs[G], ey = yj - cys[G];
+            const float rr = crs[G] + reach;
             cand = cand || fmaf(ex, ex, ey * ey) <= rr * rr;
         }
         unsigned cm = __ballot_sync(kFull, cand);
@@ -416,27 +460,19 @@ static __device__ IdmLead idm_lead(AgentSmem& sm, const StepArgs& A, int a0, int
     return IdmLead{lead, gbest, tlx, tly};
 }
 
-static __device__ void idm_group(AgentSmem& sm, const StepArgs& A, int a0, int N, int i0, int lane, Counts& cnt) {
+// IDM acceleration (exponent 4) of agent i with lead L (the lead's velocity
+// (lvx, lvy) at t), then the advance along its route into the n* arrays.
+static __device__ void idm_accel_advance(AgentSmem& sm, const StepArgs& A, int a0, int i, const IdmLead& L, float lvx,
+                                         float lvy) {
     const Params& p = A.p;
-    const int i = i0 + lane;
-    const bool mine = lane < kIdmGroup && i < N && idm_moves(sm, A, a0, i);
-    IdmLead L{-1, WSIM_INF, 0.f, 0.f};
-    for (unsigned todo = __ballot_sync(kFull, mine); todo; todo &= todo - 1) {
-        const int k = __ffs(todo) - 1;
-        const IdmLead l = idm_lead(sm, A, a0, N, i0 + k, lane, cnt);
-        if (lane == k) L = l;
-    }
-    if (!mine) return;
-    // IDM acceleration (exponent 4), one lane per agent.
-    const int g = a0 + i;
     const float vxi = sm.vx[i], vyi = sm.vy[i];
     const float v = sqrtf(fmaf(vxi, vxi, vyi * vyi));
-    const float r = v / A.v0[g];
+    const float r = v / sm.v0[i];
     const float r2 = r * r;
     const float r4 = r2 * r2;
     float acc;
     if (L.lead >= 0) {
-        const float vl = fmaf(sm.vx[L.lead], L.tlx, sm.vy[L.lead] * L.tly);
+        const float vl = fmaf(lvx, L.tlx, lvy * L.tly);
         const float sstar = p.s0 + fmaxf(0.f, fmaf(v, p.T, v * (v - vl) / p.idm_sqrt_ab2));
         const float q = sstar / L.gap;
         acc = p.amax * (1.f - r4 - q * q);
@@ -444,8 +480,8 @@ static __device__ void idm_group(AgentSmem& sm, const StepArgs& A, int a0, int N
         acc = p.amax * (1.f - r4);
     }
     // Advance along the route by the trapezoidal distance of the new speed.
-    const int ro = A.route_off[g];
-    const int P = A.route_off[g + 1] - ro;
+    const int ro = sm.ro[i];
+    const int P = sm.ro[i + 1] - ro;
     const float vn = fmaxf(0.f, fmaf(acc, p.dt, v));
     float sh = sm.sh[i], sl = sm.sl[i];
     comp_add(sh, sl, 0.5f * (v + vn) * p.dt);
@@ -468,6 +504,19 @@ static __device__ void idm_group(AgentSmem& sm, const StepArgs& A, int a0, int N
     sm.nvy[i] = vn * uy * un;
     sm.nsh[i] = sh;
     sm.nsl[i] = sl;
+}
+
+static __device__ void idm_group(AgentSmem& sm, const StepArgs& A, int a0, int N, int i0, int lane, Counts& cnt) {
+    const int i = i0 + lane;
+    const bool mine = lane < kIdmGroup && i < N && idm_moves(sm, A, a0, i);
+    IdmLead L{-1, WSIM_INF, 0.f, 0.f};
+    for (unsigned todo = __ballot_sync(kFull, mine); todo; todo &= todo - 1) {
+        const int k = __ffs(todo) - 1;
+        const IdmLead l = idm_lead(sm, A, a0, N, i0 + k, lane, cnt);
+        if (lane == k) L = l;
+    }
+    if (!mine) return;
+    idm_accel_advance(sm, A, a0, i, L, L.lead >= 0 ? sm.vx[L.lead] : 0.f, L.lead >= 0 ? sm.vy[L.lead] : 0.f);
 }
 
 // ---------------------------------------------------------------------------
@@ -505,7 +554,7 @@ __device__ void transition_policy(AgentSmem& sm, const StepArgs& A, const float*
     const size_t row = static_cast<size_t>(t_next) * A.N_tot;
     for (int i = threadIdx.x; i < N; i += NT) {
         const int g = a0 + i;
-        const int kind = A.kind[g];
+        const int kind = sm.kind[i];
         const int cm = DRIVERS ? ctrl_of(A, g) : WSIM_CTRL_ACTION;
         if (kind == WSIM_KIND_IDM && sm.valid[i] && cm != WSIM_CTRL_LOG) continue;
         float xh = sm.xh[i], xl = sm.xl[i], yh = sm.yh[i], yl = sm.yl[i];
