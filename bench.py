@@ -115,6 +115,7 @@ def parse():
     ap.add_argument("--bptt-scenes", type=int, default=None, help="override the --bptt-only leg's scene count")
     ap.add_argument("--profile", action="store_true",
                     help="time the main path only (no mode comparison, end-to-end or CPU legs)")
+    ap.add_argument("--expert-only", action="store_true", help="run only the expert leg on the workload (profiling)")
     return ap.parse_args()
 
 
@@ -464,6 +465,19 @@ def bptt_leg(wsim, synth, torch, b, plain, reps=5):
         stc.data.copy_(st.data)
         sim.rollout(stc, act, mf, synth.T0, T, mode=wsim.MODE_FUSED)
     out["forward_rollout_ms"] = timed(torch, fwd, reps, warm=1)
+    # The general differentiable rollout: recorded forward (metric rows, their
+    # deciding indices, checkpoints every 10 steps, the loss) and the backward
+    # of a weighted sum of every metric row and the loss, to the actions and
+    # the initial state (wsim_rollout_record + wsim_rollout_backward).
+    g = torch.Generator(device="cuda").manual_seed(7)
+    wts = [torch.randn((T, b.N_tot), device="cuda", generator=g) for _ in range(3)]
+    lw = torch.ones(b.S, dtype=torch.float64, device="cuda")
+    ms_rec = timed(torch, lambda: sim.rollout_record(st, act, mf, synth.T0, T, 10), reps, warm=1)
+    ms_bwd = timed(torch, lambda: sim.rollout_backward(act, *wts, loss_w=lw), reps, warm=1)
+    out["metric_grad_ckpt10"] = {"grad_steps_per_s": 1e3 / (ms_rec + ms_bwd), "ms": ms_rec + ms_bwd,
+                                 "record_ms": ms_rec, "backward_ms": ms_bwd,
+                                 "objective": "loss + random weights on every log divergence, overlap and "
+                                              "off-road row; gradients to actions and initial state"}
     assert sim.status() == 0
     sim.close()
     return out
@@ -560,13 +574,18 @@ def main():
     seed = args.seed + 1000 * rank
     if args.bptt_only:
         b = make(synth, args.bptt_workload, seed + 1, S=args.bptt_scenes)
-        out = bptt_leg(wsim, synth, torch, b, plain=False)
+        out = bptt_leg(wsim, synth, torch, b, plain=False, reps=args.steps)
         if rank == 0:
             print(json.dumps({"profile": True, "bptt": out}), flush=True)
         return
     b = make(synth, args.workload, seed, S=args.scenes)
     T, N, S = b.T, b.N_tot, b.S
     R = Rollout(wsim, synth, torch, b, args.mode, args.shape)
+    if args.expert_only:
+        out = expert_leg(wsim, synth, torch, R, args.steps)
+        if rank == 0:
+            print(json.dumps({"profile": True, "expert": out}), flush=True)
+        return
     cnt = R.counts()  # work counters of one (untimed) rollout: the roofline numerator
     for _ in range(max(3, args.warmup)):
         R.run()

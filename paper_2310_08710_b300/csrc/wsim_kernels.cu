@@ -128,13 +128,15 @@ __global__ void __launch_bounds__(NTs) k_plain_finish(const StepArgs A, int s) {
 // agent g's action space (App. A.1) from log row t0+k to row t0+k+1.  A
 // thread takes one agent and a chunk of kExpertChunk steps: it loads the
 // chunk's kExpertChunk+1 log rows of that agent first (all loads in flight
-// together), then writes the chunk's actions.  Consecutive threads take
+// together), then writes the chunk's actions.  The bicycle inverse (two
+// divisions, atan2, square roots) makes the kernel issue-bound; chunks of 4
+// (more warps in flight, fewer registers) measured faster than 2 or 8.  Consecutive threads take
 // consecutive agents, so every load and store of a warp is one coalesced row
 // segment.  HBM-bound: per policy agent-step 12 B of log read (heading and
 // velocity for bicycle agents, position and heading for delta agents), per
 // agent-step 12 B of action written; the first row of a chunk is read twice.
 // ---------------------------------------------------------------------------
-constexpr int kExpertChunk = 8;
+constexpr int kExpertChunk = 4;
 
 __global__ void __launch_bounds__(256) k_expert_actions(const StepArgs A, int t0, int T, float* __restrict__ act) {
     const int g = blockIdx.x * 256 + threadIdx.x;
@@ -160,13 +162,17 @@ __global__ void __launch_bounds__(256) k_expert_actions(const StepArgs A, int t0
             }
         }
     }
+    // speed of each logged row, once (each serves two consecutive actions)
+    float sp[kExpertChunk + 1];
+#pragma unroll
+    for (int j = 0; j <= kExpertChunk; ++j) sp[j] = (bic && j <= m) ? sqrtf(fmaf(r0[j], r0[j], r1[j] * r1[j])) : 0.f;
     float* out = act + static_cast<size_t>(k0) * 3 * n + g;
 #pragma unroll
     for (int j = 0; j < kExpertChunk; ++j) {
         if (j < m) {
             float u0 = 0.f, u1 = 0.f, u2 = 0.f;
             if (bic) {
-                const BicycleInv r = bicycle_inverse(A.p, r0[j], r1[j], r2[j], 0.f, r0[j + 1], r1[j + 1]);
+                const BicycleInv r = bicycle_inverse_v(A.p, sp[j], sp[j + 1], r2[j], 0.f, r0[j + 1], r1[j + 1]);
                 u0 = r.a;
                 u1 = r.kappa;
             } else if (del) {

@@ -105,16 +105,21 @@ struct BicycleInv {
     float a, kappa, turn, dist;
 };
 
-__device__ __forceinline__ BicycleInv bicycle_inverse(const Params& p, float vx, float vy, float thh, float thl,
-                                                      float nvx, float nvy) {
+// The same from the two speeds v = |(vx, vy)| and vn = |(nvx, nvy)| (callers
+// that already hold them).
+__device__ __forceinline__ BicycleInv bicycle_inverse_v(const Params& p, float v, float vn, float thh, float thl,
+                                                        float nvx, float nvy) {
     BicycleInv r;
-    const float v = sqrtf(fmaf(vx, vx, vy * vy));
-    const float vn = sqrtf(fmaf(nvx, nvx, nvy * nvy));
     r.a = (vn - v) / p.dt;
     r.turn = (nvx != 0.f || nvy != 0.f) ? turn_from(atan2f(nvy, nvx), thh, thl) : 0.f;
     r.dist = fmaf(v, p.dt, r.a * (0.5f * p.dt * p.dt));
     r.kappa = r.dist > 0.f ? r.turn / r.dist : 0.f;
     return r;
+}
+
+__device__ __forceinline__ BicycleInv bicycle_inverse(const Params& p, float vx, float vy, float thh, float thl,
+                                                      float nvx, float nvy) {
+    return bicycle_inverse_v(p, sqrtf(fmaf(vx, vx, vy * vy)), sqrtf(fmaf(nvx, nvx, nvy * nvy)), thh, thl, nvx, nvy);
 }
 
 // Discrete action grids (Sec. 5.2): n values over [-max, max], centred on 0
