@@ -83,10 +83,10 @@ def recorded_traffic(kernel: str, workload: str):
     workload, if it is of this build (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-            rec = json.load(f).get(kernel)
-    except (OSError, ValueError):
+            rec = json.load(f).get(kernel, {}).get(workload)
+    except (OSError, ValueError, AttributeError):
         return None
-    if not rec or rec.get("source_sha256_16") != source_hash() or rec.get("workload_key") != workload:
+    if not rec or rec.get("source_sha256_16") != source_hash():
         return None
     return rec.get("dram_bytes_per_launch")
 
