@@ -44,9 +44,21 @@ struct AdjSmem {
     float x[kMaxN], y[kMaxN], th[kMaxN], vx[kMaxN], vy[kMaxN];
     float part[kMaxN];
     float cx[kMaxN], cy[kMaxN], cth[kMaxN];  // an agent's overlap term, partner's share
+    float lx[kMaxN], ly[kMaxN];              // the current step's logged positions
     int16_t pidx[kMaxN];                     // ... and the partner (-1: none)
     double total;
 };
+
+// The logged positions of log row t_log into adj.lx / adj.ly (thread per
+// agent, in a per-agent phase): the loss and its adjoint read them in their
+// pair loops, one parallel round trip to memory per step.
+__device__ __forceinline__ void load_log_row(AdjSmem& adj, const StepArgs& A, int a0, int N, int t_log) {
+    const size_t row = static_cast<size_t>(t_log) * A.N_tot + a0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        adj.lx[i] = A.log_x[row + i];
+        adj.ly[i] = A.log_y[row + i];
+    }
+}
 
 __device__ __forceinline__ StateP slot_state(float* base, int slot, int N_tot) {
     float* p = base + static_cast<size_t>(slot) * 10 * N_tot;
@@ -120,8 +132,8 @@ __device__ __forceinline__ SatGrad sat_grad(float dx, float dy, float cA, float 
 
 // Loss terms of the current state of agent i (warp): d_i^2 plus the
 // penalty of its pairs with j > i.  Same value in every lane.
-__device__ float loss_agent(const AgentSmem& sm, const StepArgs& A, int a0, int N, int i, int lane, float lambda,
-                            float tau, int t_log) {
+__device__ float loss_agent(const AgentSmem& sm, const AdjSmem& adj, int N, int i, int lane, float lambda,
+                            float tau) {
     float acc = 0.f;
     const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
     for (int j = i + 1 + lane; j < N; j += 32) {
@@ -133,8 +145,7 @@ __device__ float loss_agent(const AgentSmem& sm, const StepArgs& A, int a0, int 
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    const size_t li = static_cast<size_t>(t_log) * A.N_tot + a0 + i;
-    const float ex = (xih - A.log_x[li]) + xil, ey = (yih - A.log_y[li]) + yil;
+    const float ex = (xih - adj.lx[i]) + xil, ey = (yih - adj.ly[i]) + yil;
     return acc + fmaf(ex, ex, ey * ey);
 }
 
@@ -159,8 +170,8 @@ static_assert(kAgentStride == NTb, "one agent per thread and stride: the reverse
 
 // wl weighs the whole term (the scene's loss weight; 1 gives the loss's own
 // gradient bit for bit).
-__device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, const StepArgs& A, int a0, int N,
-                             int lane, int warp, float lambda, float tau, int t_log, float wl) {
+__device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, int N, int lane, int warp, float lambda,
+                             float tau, float wl) {
     float* bx = wbuf + static_cast<size_t>(warp) * 3 * kMaxN;
     float* by = bx + kMaxN;
     float* bth = by + kMaxN;
@@ -191,8 +202,7 @@ __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, con
             gth += __shfl_xor_sync(kFull, gth, o);
         }
         if (lane == 0) {
-            const size_t li = static_cast<size_t>(t_log) * A.N_tot + a0 + i;
-            const float ex = (xih - A.log_x[li]) + xil, ey = (yih - A.log_y[li]) + yil;
+            const float ex = (xih - adj.lx[i]) + xil, ey = (yih - adj.ly[i]) + yil;
             adj.x[i] += wl * (gx + 2.f * ex);
             adj.y[i] += wl * (gy + 2.f * ey);
             adj.th[i] += wl * gth;
@@ -228,7 +238,6 @@ __device__ void metric_adjoint(const AgentSmem& sm, AdjSmem& adj, const BpttArgs
                                int a0, int N) {
     const StepArgs& A = B.A;
     const size_t row = static_cast<size_t>(t) * A.N_tot;
-    const size_t lrow = static_cast<size_t>(A.t_log + t) * A.N_tot;
     for (int i = first_agent(); i < N; i += kAgentStride) {
         const int g = a0 + i;
         adj.pidx[i] = -1;
@@ -237,7 +246,7 @@ __device__ void metric_adjoint(const AgentSmem& sm, AdjSmem& adj, const BpttArgs
         const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
         const float w_ld = B.g_logdiv ? B.g_logdiv[row + g] : 0.f;
         if (w_ld != 0.f) {
-            const float ex = (xih - A.log_x[lrow + g]) + xil, ey = (yih - A.log_y[lrow + g]) + yil;
+            const float ex = (xih - adj.lx[i]) + xil, ey = (yih - adj.ly[i]) + yil;
             const float ld = sqrtf(fmaf(ex, ex, ey * ey));
             if (ld > 0.f) {
                 gx += w_ld * ex / ld;
@@ -362,14 +371,13 @@ __device__ void transition_adjoint(AgentSmem& sm, AdjSmem& adj, const BpttArgs& 
     }
 }
 
-// One step's loss of the current state (all threads): each warp's rows into
-// adj.part, then (after the caller's barrier) warp 0 adds them in a fixed
-// order; see loss_sum.
-__device__ __forceinline__ void loss_rows(const AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int a0, int N,
-                                          int t_log) {
+// One step's loss of the current state (all threads; the logged positions
+// in adj.lx / adj.ly): each warp's rows into adj.part, then (after the
+// caller's barrier) warp 0 adds them in a fixed order; see loss_sum.
+__device__ __forceinline__ void loss_rows(const AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int N) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < N; i += NWb) {
-        const float v = sm.valid[i] ? loss_agent(sm, B.A, a0, N, i, lane, B.lambda, B.tau, t_log) : 0.f;
+        const float v = sm.valid[i] ? loss_agent(sm, adj, N, i, lane, B.lambda, B.tau) : 0.f;
         if (lane == 0) adj.part[i] = v;
     }
 }
@@ -426,8 +434,9 @@ __device__ void reverse_sweep(AgentSmem& sm, AdjSmem& adj, float* wbuf, const Bp
             // state t into the n* arrays, which the loss and metric adjoints do not read
             const CStateP cur = (t == a) ? cslot(B.ckpt, sg, A.N_tot) : cslot(B.segbuf, t - a, A.N_tot);
             load_prev(sm, cur, a0, N);
+            load_log_row(adj, A, a0, N, A.t_log + t);
             __syncthreads();
-            if (wl != 0.f) loss_adjoint(sm, adj, wbuf, A, a0, N, lane, warp, B.lambda, B.tau, A.t_log + t, wl);
+            if (wl != 0.f) loss_adjoint(sm, adj, wbuf, N, lane, warp, B.lambda, B.tau, wl);
             if (metrics) metric_adjoint(sm, adj, B, V, t, a0, N);
             // both adjoints end with agent j's sums in the thread that takes
             // agent j here: no barrier in between
@@ -468,8 +477,9 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttA
         phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(k) * 3 * A.N_tot, A.t_log + k, a0, N, cnt);
         __syncthreads();
         writeback<NTb>(sm, A.p, nullptr, a0, N);
+        load_log_row(adj, A, a0, N, A.t_log + k);
         __syncthreads();
-        loss_rows(sm, adj, B, a0, N, A.t_log + k);
+        loss_rows(sm, adj, B, N);
         if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
         __syncthreads();
         loss_sum(adj, N);
@@ -506,6 +516,7 @@ __device__ void record_scene(AgentSmem& sm, AdjSmem& adj, unsigned long long* k6
         phase_transition<NTb>(sm, A, A.act + static_cast<size_t>(k) * 3 * N_tot, A.t_log + k, a0, N, cnt);
         __syncthreads();
         writeback<NTb>(sm, A.p, nullptr, a0, N);
+        if (B.loss) load_log_row(adj, A, a0, N, A.t_log + k);
         __syncthreads();
         if (B.metrics) {
             const size_t row = static_cast<size_t>(k) * N_tot;
@@ -526,7 +537,7 @@ __device__ void record_scene(AgentSmem& sm, AdjSmem& adj, unsigned long long* k6
                 if (!v) orec[i] = -1;
             }
         }
-        if (B.loss) loss_rows(sm, adj, B, a0, N, A.t_log + k);
+        if (B.loss) loss_rows(sm, adj, B, N);
         if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
         __syncthreads();
         if (B.loss) loss_sum(adj, N);
