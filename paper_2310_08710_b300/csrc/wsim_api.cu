@@ -41,6 +41,7 @@ struct wsim_ctx {
     float4* seg_tiles = nullptr;
     int32_t* seg_soff = nullptr;
     float4* seg_sup = nullptr;
+    uint16_t* seg_tperm = nullptr;  // tiles in super-tile order, per scene
     int32_t* hint = nullptr;  // [N_tot][4] nearest-segment cache of the per-step kernels
     uint16_t* tlist = nullptr;  // [N_tot][kList] candidate-tile lists of the per-step kernels
     float4* tmeta = nullptr;    // [N_tot] their centre, radius and count
@@ -131,7 +132,8 @@ StepArgs base_args(const wsim_ctx* c) {
     a.log_th = b.log_th;
     a.log_vx = b.log_vx;
     a.log_vy = b.log_vy;
-    a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags, c->seg_tiles, c->seg_soff, c->seg_sup};
+    a.segs = Segs{c->seg_off, c->seg_cnt, c->seg_geo, c->seg_inv, c->seg_flags, c->seg_tiles, c->seg_soff, c->seg_sup,
+              c->seg_tperm};
     a.n_work = b.S;
     a.hint = c->hint;
     a.tlist = c->tlist;
@@ -408,7 +410,8 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     const size_t E = static_cast<size_t>(off[S]);
     if ((rc = dalloc(&c->seg_geo, E)) || (rc = dalloc(&c->seg_inv, E)) || (rc = dalloc(&c->seg_flags, E)) ||
         (rc = dalloc(&c->seg_tiles, 2 * (E / kTile))) || (rc = dalloc(&c->seg_soff, S + 1)) ||
-        (rc = dalloc(&c->seg_sup, static_cast<size_t>(soff[S]))))
+        (rc = dalloc(&c->seg_sup, static_cast<size_t>(soff[S]))) ||
+        (rc = dalloc(&c->seg_tperm, std::max<size_t>(E / kTile, 1))))
         return fail(rc);
     if (cudaMemcpyAsync(c->seg_soff, soff.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, st) !=
         cudaSuccess)
@@ -421,7 +424,9 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, S, c->seg_off, c->seg_geo,
                         c->seg_inv, c->seg_flags, st) != cudaSuccess ||
         launch_tile_build(S, c->seg_off, c->seg_cnt, c->seg_geo, c->seg_flags, c->seg_tiles, st) != cudaSuccess ||
-        launch_super_build(S, c->seg_off, c->seg_cnt, c->seg_soff, c->seg_tiles, c->seg_sup, st) != cudaSuccess)
+        launch_tile_order(S, c->seg_off, c->seg_cnt, c->seg_tiles, c->seg_tperm, st) != cudaSuccess ||
+        launch_super_build(S, c->seg_off, c->seg_cnt, c->seg_soff, c->seg_tiles, c->seg_tperm, c->seg_sup, st) !=
+            cudaSuccess)
         return fail(WSIM_ECUDA);
 
     // Scene work list, most expensive first (longest-processing-time order).
@@ -950,6 +955,7 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->seg_tiles);
     cudaFree(c->seg_soff);
     cudaFree(c->seg_sup);
+    cudaFree(c->seg_tperm);
     cudaFree(c->hint);
     cudaFree(c->tlist);
     cudaFree(c->tmeta);

@@ -39,7 +39,11 @@ struct Segs {
                            // bit2: a segment (0: padding between runs, far away, never nearest)
     const float4* tiles;   // [2 * tiles]
     const int32_t* soff;   // [S+1] first super-tile of each scene
-    const float4* sup;     // super-tile bounding boxes: super-tile j of scene s covers its tiles 8j .. 8j+7
+    const float4* sup;     // super-tile bounding boxes: super-tile j of scene s covers its tiles
+                           // tperm[8j .. 8j+7]
+    const uint16_t* tperm; // [tiles] per scene: its tiles in super-tile order (scene-relative indexes,
+                           // sorted along a Morton curve of the tile centres so that a super-tile is
+                           // compact); null: identity
 };
 
 struct StateP {
@@ -104,8 +108,13 @@ cudaError_t launch_seg_pack(const int32_t* rg_off, const float* rg_x, const floa
                             float4* geo, float* inv, uint8_t* flags, cudaStream_t st);
 cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const float4* geo,
                               const uint8_t* flags, float4* tiles, cudaStream_t st);
+// Super-tile order of each scene's tiles (Morton order of the tile centres;
+// the identity for scenes of more than kOrderMaxTiles tiles).
+constexpr int kOrderMaxTiles = 4096;
+cudaError_t launch_tile_order(int S, const int32_t* seg_off, const int32_t* seg_cnt, const float4* tiles,
+                              uint16_t* tperm, cudaStream_t st);
 cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const int32_t* soff,
-                               const float4* tiles, float4* sup, cudaStream_t st);
+                               const float4* tiles, const uint16_t* tperm, float4* sup, cudaStream_t st);
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);
 // Discrete actions: continuous [T][3][N_tot] <-> flat grid indices [T][N_tot].
 cudaError_t launch_discretize(const StepArgs& a, const float* act, int T, int32_t* idx, cudaStream_t st);

@@ -372,16 +372,113 @@ __global__ void __launch_bounds__(256) k_tile_build(const int32_t* seg_off, cons
     }
 }
 
-// Per super-tile: bounding box of its kSuper tiles' capsules.
+// Super-tile order of one scene's tiles: the tiles sorted by the Morton code
+// of their chord midpoints (8 bits per axis over the scene's extent; ties by
+// tile index, so the order is unique), one CTA per scene, bitonic sort of
+// (code << 16 | tile) keys in shared memory.  Consecutive tiles in this
+// order lie close together, so kSuper of them make a compact super-tile
+// whatever the roadgraph's polyline order is.
+__device__ __forceinline__ uint32_t spread8(uint32_t v) {  // bits 0..7 -> even bits 0..14
+    v &= 0xffu;
+    v = (v | (v << 4)) & 0x0f0fu;
+    v = (v | (v << 2)) & 0x3333u;
+    v = (v | (v << 1)) & 0x5555u;
+    return v;
+}
+
+constexpr int kOrderThreads = 1024;
+
+__global__ void __launch_bounds__(kOrderThreads) k_tile_order(const int32_t* seg_off, const int32_t* seg_cnt,
+                                                              const float4* tiles, uint16_t* tperm) {
+    __shared__ uint32_t key[kOrderMaxTiles];
+    __shared__ float red[4][kOrderThreads / 32];
+    const int s = blockIdx.x;
+    const int e0 = seg_off[s], E = seg_cnt[s];
+    const int nt = (E + kTile - 1) / kTile;
+    const size_t tb = static_cast<size_t>(e0 / kTile);
+    if (nt > kOrderMaxTiles) {  // identity
+        for (int t = threadIdx.x; t < nt; t += kOrderThreads) tperm[tb + t] = static_cast<uint16_t>(t);
+        return;
+    }
+    // extent of the chord midpoints (fminf / fmaxf ignore NaN)
+    float lo_x = WSIM_INF, lo_y = WSIM_INF, hi_x = -WSIM_INF, hi_y = -WSIM_INF;
+    for (int t = threadIdx.x; t < nt; t += kOrderThreads) {
+        const float4 C = tiles[2 * (tb + t)];
+        const float mx = fmaf(0.5f, C.z, C.x), my = fmaf(0.5f, C.w, C.y);
+        lo_x = fminf(lo_x, mx);
+        lo_y = fminf(lo_y, my);
+        hi_x = fmaxf(hi_x, mx);
+        hi_y = fmaxf(hi_y, my);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo_x = fminf(lo_x, __shfl_xor_sync(0xffffffffu, lo_x, o));
+        lo_y = fminf(lo_y, __shfl_xor_sync(0xffffffffu, lo_y, o));
+        hi_x = fmaxf(hi_x, __shfl_xor_sync(0xffffffffu, hi_x, o));
+        hi_y = fmaxf(hi_y, __shfl_xor_sync(0xffffffffu, hi_y, o));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][warp] = lo_x;
+        red[1][warp] = lo_y;
+        red[2][warp] = hi_x;
+        red[3][warp] = hi_y;
+    }
+    __syncthreads();
+    lo_x = lo_y = WSIM_INF;
+    hi_x = hi_y = -WSIM_INF;
+    for (int w = 0; w < kOrderThreads / 32; ++w) {
+        lo_x = fminf(lo_x, red[0][w]);
+        lo_y = fminf(lo_y, red[1][w]);
+        hi_x = fmaxf(hi_x, red[2][w]);
+        hi_y = fmaxf(hi_y, red[3][w]);
+    }
+    const float sx = hi_x > lo_x ? 255.f / (hi_x - lo_x) : 0.f;
+    const float sy = hi_y > lo_y ? 255.f / (hi_y - lo_y) : 0.f;
+    int n2 = 1;
+    while (n2 < nt) n2 <<= 1;
+    for (int t = threadIdx.x; t < n2; t += kOrderThreads) {
+        uint32_t k = 0xffffffffu;  // padding sorts last
+        if (t < nt) {
+            const float4 C = tiles[2 * (tb + t)];
+            const float mx = fmaf(0.5f, C.z, C.x), my = fmaf(0.5f, C.w, C.y);
+            // clamped cell coordinates (a NaN or infinite extent gives cell 0)
+            const uint32_t qx = static_cast<uint32_t>(fminf(255.f, fmaxf(0.f, (mx - lo_x) * sx)));
+            const uint32_t qy = static_cast<uint32_t>(fminf(255.f, fmaxf(0.f, (my - lo_y) * sy)));
+            k = ((spread8(qx) | (spread8(qy) << 1)) << 16) | static_cast<uint32_t>(t);
+        }
+        key[t] = k;
+    }
+    __syncthreads();
+    for (int k = 2; k <= n2; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2; i += kOrderThreads) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const uint32_t a = key[i], b = key[l];
+                    if (((i & k) == 0) == (a > b)) {
+                        key[i] = b;
+                        key[l] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < nt; t += kOrderThreads) tperm[tb + t] = static_cast<uint16_t>(key[t] & 0xffffu);
+}
+
+// Per super-tile: bounding box of the capsules of its kSuper tiles (in
+// super-tile order).
 __global__ void __launch_bounds__(256) k_super_build(const int32_t* seg_off, const int32_t* seg_cnt,
-                                                     const int32_t* soff, const float4* tiles, float4* sup) {
+                                                     const int32_t* soff, const float4* tiles,
+                                                     const uint16_t* tperm, float4* sup) {
     const int s = blockIdx.x;
     const int e0 = seg_off[s], E = seg_cnt[s];
     const int nt = (E + kTile - 1) / kTile;
     const int ns = (nt + kSuper - 1) / kSuper;
     for (int j = threadIdx.x; j < ns; j += 256) {
         float x0 = WSIM_INF, y0 = WSIM_INF, x1 = -WSIM_INF, y1 = -WSIM_INF;
-        for (int t = j * kSuper; t < min(nt, (j + 1) * kSuper); ++t) {
+        for (int q = j * kSuper; q < min(nt, (j + 1) * kSuper); ++q) {
+            const int t = tperm ? tperm[e0 / kTile + q] : q;
             const size_t ti = static_cast<size_t>(e0 / kTile) + t;
             const float4 C = tiles[2 * ti];
             const float r = tiles[2 * ti + 1].x;
@@ -419,9 +516,15 @@ cudaError_t launch_tile_build(int S, const int32_t* seg_off, const int32_t* seg_
     return cudaGetLastError();
 }
 
+cudaError_t launch_tile_order(int S, const int32_t* seg_off, const int32_t* seg_cnt, const float4* tiles,
+                              uint16_t* tperm, cudaStream_t st) {
+    k_tile_order<<<S, kOrderThreads, 0, st>>>(seg_off, seg_cnt, tiles, tperm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const int32_t* soff,
-                               const float4* tiles, float4* sup, cudaStream_t st) {
-    k_super_build<<<S, 256, 0, st>>>(seg_off, seg_cnt, soff, tiles, sup);
+                               const float4* tiles, const uint16_t* tperm, float4* sup, cudaStream_t st) {
+    k_super_build<<<S, 256, 0, st>>>(seg_off, seg_cnt, soff, tiles, tperm, sup);
     return cudaGetLastError();
 }
 

@@ -49,6 +49,7 @@ struct SegView {
     const float4* tiles;  // 2 per tile: capsule (start, chord), (radius, 1/|chord|^2)
     const float4* sup;    // bounding box per super-tile of kSuper tiles
     int E, nt, ns;
+    const uint16_t* perm;  // the tiles in super-tile order (null: identity); lists stay in index order
 };
 
 
@@ -740,6 +741,9 @@ __device__ __forceinline__ float seg_dist2(float4 G, float iv, float cxh, float 
 
 // Scan two tiles at once (lanes 0-15: tile ta, lanes 16-31: tile tb) for the
 // corners in their masks, updating each lane's (distance, index) minima.
+// TIE: the tiles may come in any order, so equal distances compare indexes
+// (otherwise they come in increasing index order and the first one stays).
+template <bool TIE = false>
 __device__ __forceinline__ void scan_pair(const SegView& V, int lane, int ta, unsigned ma, int tb, unsigned mb,
                                           float xh, float yh, const float (&cxl)[4], const float (&cyl)[4],
                                           float (&bd)[4], int (&bi)[4], Counts& cnt) {
@@ -756,7 +760,7 @@ __device__ __forceinline__ void scan_pair(const SegView& V, int lane, int ta, un
         for (int k = 0; k < 4; ++k) {
             if ((u >> k) & 1u) {
                 const float d2 = seg_dist2(G, iv, xh, cxl[k], yh, cyl[k]);
-                if (((m >> k) & 1u) && d2 < bd[k]) {
+                if (((m >> k) & 1u) && (d2 < bd[k] || (TIE && d2 == bd[k] && e < bi[k]))) {
                     bd[k] = d2;
                     bi[k] = e;
                 }
@@ -767,6 +771,7 @@ __device__ __forceinline__ void scan_pair(const SegView& V, int lane, int ta, un
 
 // Takes up to two tiles from the ballot `want` (lane l's tile and corner mask
 // in t_l, cm_l) and scans them.
+template <bool TIE = false>
 __device__ __forceinline__ void scan_next_two(const SegView& V, int lane, unsigned& want, int tl_lane,
                                               unsigned cm_lane, float xh, float yh, const float (&cxl)[4],
                                               const float (&cyl)[4], float (&bd)[4], int (&bi)[4], Counts& cnt) {
@@ -779,7 +784,20 @@ __device__ __forceinline__ void scan_next_two(const SegView& V, int lane, unsign
     const int t1 = __shfl_sync(kFull, tl_lane, l1);
     const unsigned m2 = __shfl_sync(kFull, cm_lane, l2);
     const int t2 = __shfl_sync(kFull, tl_lane, l2);
-    scan_pair(V, lane, t1, m1, t2, two ? m2 : 0u, xh, yh, cxl, cyl, bd, bi, cnt);
+    scan_pair<TIE>(V, lane, t1, m1, t2, two ? m2 : 0u, xh, yh, cxl, cyl, bd, bi, cnt);
+}
+
+// Ascending sort of one value per lane (bitonic network over the warp).
+__device__ __forceinline__ unsigned warp_sort_asc(unsigned v, int lane) {
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const unsigned o = __shfl_xor_sync(kFull, v, j);
+            const bool take_min = ((lane & j) == 0) == ((lane & k) == 0);
+            v = take_min ? min(v, o) : max(v, o);
+        }
+    return v;
 }
 
 
@@ -995,7 +1013,8 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
                 // order across lanes, and the lists too).
                 unsigned rest = sup;
                 for (int r = 0; r < lane / kSuper && rest; ++r) rest &= rest - 1;
-                const int t = rest ? (sb + __ffs(rest) - 1) * kSuper + (lane & (kSuper - 1)) : V.nt;
+                const int q = rest ? (sb + __ffs(rest) - 1) * kSuper + (lane & (kSuper - 1)) : V.nt;
+                const int t = q < V.nt ? (V.perm ? static_cast<int>(V.perm[q]) : q) : V.nt;
                 int taken = 0;
                 for (; taken < 32 / kSuper && sup; ++taken) sup &= sup - 1;
                 unsigned cm = 0;
@@ -1032,15 +1051,23 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
                     }
                 }
                 unsigned want = __ballot_sync(kFull, cm != 0);
-                while (want) scan_next_two(V, lane, want, t, cm, xh, yh, cxl, cyl, bd, bi, cnt);
+                while (want) scan_next_two<true>(V, lane, want, t, cm, xh, yh, cxl, cyl, bd, bi, cnt);
             }
         }
         if (tl) {
+            // Lists are kept in increasing tile order (super-tiles come in
+            // any order), so that their scans meet equal distances in
+            // increasing index order.
             if (nl <= kList) {
+                __syncwarp();
+                const unsigned v = warp_sort_asc(lane < nl ? static_cast<unsigned>(tl[lane]) : 0xffffffffu, lane);
+                __syncwarp();
+                if (lane < nl) tl[lane] = static_cast<uint16_t>(v);
                 if (lane == 0) *meta = make_float4(lcx, lcy, R, __int_as_float(nl));
             } else if (nls <= kList) {
+                const unsigned v = warp_sort_asc(lane < nls ? static_cast<unsigned>(small_t) : 0xffffffffu, lane);
                 __syncwarp();
-                if (lane < nls) tl[lane] = static_cast<uint16_t>(small_t);
+                if (lane < nls) tl[lane] = static_cast<uint16_t>(v);
                 if (lane == 0) *meta = make_float4(ccx, ccy, Rs, __int_as_float(nls));
             } else if (lane == 0) {
                 *meta = make_float4(lcx, lcy, R, __int_as_float(-1));
@@ -1371,7 +1398,7 @@ __device__ __forceinline__ SegView global_view(const Segs& G, int s) {
     const int E = G.cnt[s];
     const int nt = (E + kTile - 1) / kTile;
     return SegView{G.geo + e0, G.inv + e0, G.flags + e0, G.tiles + 2 * (e0 / kTile), G.sup + G.soff[s],
-                   E, nt, (nt + kSuper - 1) / kSuper};
+                   E, nt, (nt + kSuper - 1) / kSuper, G.tperm ? G.tperm + e0 / kTile : nullptr};
 }
 
 }  // namespace wsim

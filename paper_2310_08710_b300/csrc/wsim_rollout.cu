@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
                 bulk_g2s(tiles, A.segs.tiles + 2 * (e0 / kTile), bt, &sm.bar[0]);
                 bulk_g2s(sup, A.segs.sup + A.segs.soff[s], bs, &sm.bar[0]);
             }
-            V = SegView{geo, inv, fl, tiles, sup, V.E, V.nt, V.ns};
+            V = SegView{geo, inv, fl, tiles, sup, V.E, V.nt, V.ns, V.perm};  // the order stays in global memory
         }
         load_state<NT>(sm, A, A.in, a0, N);
         for (int j = threadIdx.x; j < 4 * N; j += NT) sm.hint[j] = -1;

@@ -27,6 +27,7 @@ struct StaticScratch {
     uint8_t flags[kStaticMaxSegs];
     float4 tiles[2 * (kStaticMaxSegs / kTile)];
     float4 sup[kStaticMaxSegs / kTile / kSuper + kStaticMaxScenes];
+    uint16_t tperm[kStaticMaxSegs / kTile];
     int32_t seg_off[kStaticMaxScenes + 1];
     int32_t soff[kStaticMaxScenes + 1];
     int32_t seg_cnt[kStaticMaxScenes];
@@ -194,7 +195,8 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
     if (launch_seg_pack(b->rg_off, b->rg_x, b->rg_y, b->rg_poly, b->rg_type, b->rg_valid, b->S, sc->seg_off,
                         sc->geo, sc->inv, sc->flags, s) != cudaSuccess ||
         launch_tile_build(b->S, sc->seg_off, sc->seg_cnt, sc->geo, sc->flags, sc->tiles, s) != cudaSuccess ||
-        launch_super_build(b->S, sc->seg_off, sc->seg_cnt, sc->soff, sc->tiles, sc->sup, s) != cudaSuccess)
+        launch_tile_order(b->S, sc->seg_off, sc->seg_cnt, sc->tiles, sc->tperm, s) != cudaSuccess ||
+        launch_super_build(b->S, sc->seg_off, sc->seg_cnt, sc->soff, sc->tiles, sc->tperm, sc->sup, s) != cudaSuccess)
         return WSIM_ECUDA;
 
     StepArgs a;
@@ -209,7 +211,7 @@ extern "C" int wsim_metrics_static(const wsim_config* cfg, const wsim_batch* b, 
     a.valid = b->valid;
     a.log_x = b->log_x;
     a.log_y = b->log_y;
-    a.segs = Segs{sc->seg_off, sc->seg_cnt, sc->geo, sc->inv, sc->flags, sc->tiles, sc->soff, sc->sup};
+    a.segs = Segs{sc->seg_off, sc->seg_cnt, sc->geo, sc->inv, sc->flags, sc->tiles, sc->soff, sc->sup, sc->tperm};
     a.hint = nullptr;  // no nearest-segment cache: bounds come from the tiles
     a.in = CStateP{st->x, st->y, st->x_lo, st->y_lo, st->th, st->th_lo, st->vx, st->vy, st->s, st->s_lo};
     a.m = MetricsP{m->ov, m->off, m->logdiv, m->flags, m->reward};

@@ -97,6 +97,72 @@ def test_roadgraph_gaps_and_short_runs(wsim):
     print("gaps and short runs", c)
 
 
+def _fan_scene(seed, fans=60, T=4):
+    """Road edges in fans: three polylines start at one point P and leave it
+    at angles a, a + 45, a + 90 degrees; the polylines of all fans are
+    shuffled, so their index order has nothing to do with where they lie.
+    One parked agent per fan sits in the quadrant behind the fan, where
+    every corner's nearest point on all three polylines is P itself: exact
+    ties between segments of different polylines, whose sides differ
+    (the lowest index decides, Sec. 3.4 road-edge side)."""
+    rng = np.random.default_rng(seed)
+    polys, agents = [], []
+    side = int(np.ceil(np.sqrt(fans)))
+    for f in range(fans):
+        P = np.array([25.0 * (f % side), 25.0 * (f // side)]) + rng.uniform(-3, 3, 2)
+        a = rng.uniform(-np.pi, np.pi)
+        for d in (0.0, np.pi / 4, np.pi / 2):
+            n = int(rng.integers(17, 41))
+            k = np.arange(n)[:, None]
+            polys.append((P + 0.5 * k * np.array([np.cos(a + d), np.sin(a + d)]), 1))
+        phi = a + 1.25 * np.pi
+        c = P + 3.6 * np.array([np.cos(phi), np.sin(phi)])
+        agents.append(dict(x=c[0], y=c[1], th=phi, v=0.0, L=4.5, W=2.0))
+    order = rng.permutation(len(polys))
+    return tiny_batch(agents, roadgraph=[polys[i] for i in order], T=T)
+
+
+def _tied_corners(b):
+    """Corners (float64, at t0) whose nearest distance to the road edges is
+    reached by segments of two or more polylines."""
+    e = (b.rg_type == 1)
+    same = e[:-1] & e[1:] & (b.rg_poly[:-1] == b.rg_poly[1:])
+    a = np.stack([b.rg_x[:-1], b.rg_y[:-1]], 1)[same].astype(np.float64)
+    z = np.stack([b.rg_x[1:], b.rg_y[1:]], 1)[same].astype(np.float64)
+    pid = b.rg_poly[:-1][same]
+    n = 0
+    for i in range(b.N_tot):
+        c, s = np.cos(float(b.th[i])), np.sin(float(b.th[i]))
+        for u, v in ((1, 1), (1, -1), (-1, -1), (-1, 1)):
+            px = float(b.x[i]) + u * 0.5 * float(b.L[i]) * c - v * 0.5 * float(b.W[i]) * s
+            py = float(b.y[i]) + u * 0.5 * float(b.L[i]) * s + v * 0.5 * float(b.W[i]) * c
+            d = z - a
+            t = np.clip(((px - a[:, 0]) * d[:, 0] + (py - a[:, 1]) * d[:, 1]) / (d * d).sum(1), 0, 1)
+            dist = np.hypot(a[:, 0] + t * d[:, 0] - px, a[:, 1] + t * d[:, 1] - py)
+            n += len(set(pid[dist == dist.min()].tolist())) > 1
+    return n
+
+
+def test_ties_across_polylines_go_to_the_lower_index(wsim):
+    # The off-road search visits super-tiles in spatial order, not index
+    # order; equal distances must still resolve to the lowest segment index
+    # in every launch path, as in the oracle's exhaustive scan.
+    b = _fan_scene(3)
+    assert _tied_corners(b) >= 200
+    g = H.run_rollout(b)
+    assert g["status"] == 0
+    off = g["off"][0]
+    assert (off > 0).sum() >= 10 and (off < 0).sum() >= 10  # both sides won ties
+    for shape in range(SHAPES):
+        p = H.run_rollout(b, tuning=dict(single_shape=shape))
+        assert np.array_equal(g["off"].view(np.uint8), p["off"].view(np.uint8)), shape
+    for mode in (wsim.MODE_GRAPH, wsim.MODE_PLAIN):
+        p = H.run_rollout(b, mode=mode)
+        assert np.array_equal(g["off"].view(np.uint8), p["off"].view(np.uint8)), mode
+    c = H.teacher_forced(b, g, [0], range(b.T))
+    print("ties across polylines", c)
+
+
 def test_every_launch_configuration_bit_identical(wsim):
     # Uneven scenes span the three size buckets; every single launch shape
     # and every split configuration of the scene-resident rollout must give
