@@ -364,7 +364,7 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     c->h_agent_off = ao;
     c->p = Params{cfg->dt,     cfg->idm_amax,         cfg->idm_b,  cfg->idm_T,
                   cfg->idm_s0, cfg->idm_dq,           cfg->route_h, 1.0f / cfg->route_h,
-                  cfg->gap_min, 2.0f * sqrtf(cfg->idm_amax * cfg->idm_b), cfg->kin_amax, cfg->kin_kmax,
+                  cfg->gap_min, 2.0f * sqrtf(cfg->idm_amax * cfg->idm_b), 1.0f / cfg->dt, cfg->kin_amax, cfg->kin_kmax,
                   cfg->disc_a_max, cfg->disc_k_max, cfg->disc_d_max, cfg->disc_t_max,
                   cfg->disc_na, cfg->disc_nk, cfg->disc_nd, cfg->disc_nt};
     int rc = WSIM_OK;

@@ -61,6 +61,7 @@ struct MetricsP {
 
 struct Params {
     float dt, amax, b, T, s0, dq, h, inv_h, gap_min, idm_sqrt_ab2;  // 2 sqrt(a b)
+    float inv_dt;                      // 1 / dt, rounded once
     float kin_amax, kin_kmax;  // kinematic infeasibility limits
     float da_max, dk_max, dd_max, dt_max;  // discrete action grids (ranges)
     int na, nk, nd, nt;                    // ... and values per component

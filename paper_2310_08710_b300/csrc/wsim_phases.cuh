@@ -81,12 +81,15 @@ template <class T> __device__ __forceinline__ T pick4(const T (&a)[4], int k) {
 
 // ---------------------------------------------------------------------------
 // Inverse kinematics of the bicycle action space (App. A.1) from two
-// consecutive states: a = (|v'| - |v|) / dt; the direction of travel turns
-// from the old heading to atan2(vy', vx') (the paper prints arctan(vx'/vy'):
-// components swapped, quadrant lost), reduced modulo 2 pi; a state with zero
-// velocity has no direction (turn 0); kappa = turn / (v dt + a dt^2 / 2),
-// 0 when no distance is travelled.  dist is formed exactly as the forward
-// model forms it, so an expert action turns the heading by `turn`.
+// consecutive states: a = (|v'| - |v|) / dt (a product with 1/dt, within an
+// ulp of the quotient); the direction of travel turns from the old heading
+// to atan2(vy', vx') (the paper prints arctan(vx'/vy'): components swapped,
+// quadrant lost), reduced modulo 2 pi; a state with zero velocity has no
+// direction (turn 0); kappa = turn / (v dt + a dt^2 / 2), 0 when no
+// distance is travelled.  dist is formed exactly as the forward model forms
+// it, so an expert action turns the heading by `turn` to a few ulps.  The
+// float32 atan2 and quotients are the fast forms (atan2_poly, 2-ulp
+// division): the inverse is most of the open-loop expert kernel's issue.
 // ---------------------------------------------------------------------------
 constexpr float kTwoPiHi = 6.28318548202514648f;      // float nearest 2 pi
 constexpr float kTwoPiLo = -1.74845553146951715e-7f;  // 2 pi - kTwoPiHi
@@ -102,6 +105,33 @@ __device__ __forceinline__ float turn_from(float phi, float thh, float thl) {
     return fmaf(-k, kTwoPiLo, r) + dl;
 }
 
+// atan2(y, x) in float32 for finite arguments: the octant reduction t =
+// min(|x|, |y|) / max(|x|, |y|) in [0, 1], atan(t) = t P(t^2) with P of
+// degree 7 (coefficients fitted by Lawson's iteratively reweighted least
+// squares for the smallest largest relative error on [0, 1], 1e-7;
+// gen_atan_poly.py beside this file), then atan(1/t) = pi/2 - atan(t),
+// atan2(y, -x) = pi - atan2(y, x) and the sign of y.  Within 4e-7 rad of
+// the exact angle (the quotient is an approximate division, 2 ulps);
+// (0, 0) gives 0 and (+-0, x < 0) +-pi.
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+    const float ax = fabsf(x), ay = fabsf(y);
+    const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+    const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+    const float s = t * t;
+    float q = -4.693275783e-03f;
+    q = fmaf(q, s, 2.425240166e-02f);
+    q = fmaf(q, s, -5.948639289e-02f);
+    q = fmaf(q, s, 9.914292395e-02f);
+    q = fmaf(q, s, -1.401948035e-01f);
+    q = fmaf(q, s, 1.996972412e-01f);
+    q = fmaf(q, s, -3.333199024e-01f);
+    q = fmaf(q, s, 9.999998808e-01f);
+    float r = t * q;
+    r = ay > ax ? 1.57079637f - r : r;   // float nearest pi/2
+    r = x < 0.f ? 3.14159274f - r : r;   // float nearest pi
+    return copysignf(r, y);
+}
+
 struct BicycleInv {
     float a, kappa, turn, dist;
 };
@@ -111,10 +141,10 @@ struct BicycleInv {
 __device__ __forceinline__ BicycleInv bicycle_inverse_v(const Params& p, float v, float vn, float thh, float thl,
                                                         float nvx, float nvy) {
     BicycleInv r;
-    r.a = (vn - v) / p.dt;
-    r.turn = (nvx != 0.f || nvy != 0.f) ? turn_from(atan2f(nvy, nvx), thh, thl) : 0.f;
+    r.a = (vn - v) * p.inv_dt;
+    r.turn = (nvx != 0.f || nvy != 0.f) ? turn_from(atan2_poly(nvy, nvx), thh, thl) : 0.f;
     r.dist = fmaf(v, p.dt, r.a * (0.5f * p.dt * p.dt));
-    r.kappa = r.dist > 0.f ? r.turn / r.dist : 0.f;
+    r.kappa = r.dist > 0.f ? __fdividef(r.turn, r.dist) : 0.f;  // 2 ulps
     return r;
 }
 

@@ -116,6 +116,47 @@ def test_expert_actions_parity(wsim):
         np.abs(got[:, 0, bic] - ex[:, 0, bic]).max(), np.abs(got[:, 1, bic] - ex[:, 1, bic]).max(), d.max()))
 
 
+def test_expert_turn_in_every_direction(wsim):
+    # The expert's turn comes from a float32 atan2 of its own (octant
+    # reduction and a fitted polynomial): logged velocities in every
+    # direction, on the octant boundaries and next to them, +-0 components,
+    # speeds from 1 cm/s to 100 m/s and standing still; headings zero, so
+    # the turn is the direction itself.
+    b = mixed_batch(seed=5, S=2, N=64, R=1000)
+    b.kind = np.full_like(b.kind, synth.KIND_BICYCLE)
+    b.valid = np.ones_like(b.valid)
+    rng = np.random.default_rng(5)
+    rows, n = synth.T_LOG, b.N_tot
+    base = np.arange(-4, 5) * (np.pi / 4)
+    ang = np.concatenate([base, base + 1e-6, base - 1e-6, rng.uniform(-np.pi, np.pi, 64)])
+    phi = rng.choice(ang, (rows, n))
+    spd = 10.0 ** rng.uniform(-2, 2, (rows, n))
+    spd[rng.random((rows, n)) < 0.05] = 0.0
+    vx = (spd * np.cos(phi)).astype(np.float32)
+    vy = (spd * np.sin(phi)).astype(np.float32)
+    # exact axes and diagonals with signed zeros
+    ex = [(1, 0), (1, 1), (0, 1), (-1, 1), (-1, 0), (-1, -1), (0, -1), (1, -1),
+          (-1, -0.0), (1, -0.0), (0.0, 1), (-0.0, -1)]
+    for j, (a, c) in enumerate(ex):
+        vx[T0 + 1 + j, :] = np.float32(a) * np.float32(3.0)
+        vy[T0 + 1 + j, :] = np.float32(c) * np.float32(3.0)
+    b.log_vx, b.log_vy = vx, vy
+    b.log_th = np.zeros((rows, n), np.float32)
+    sim = wsim.Sim(wsim.DeviceBatch(b))
+    got = sim.expert_actions(T0, b.T).cpu().numpy().astype(np.float64)
+    assert sim.status() == 0
+    sim.close()
+    exo = oracle.Oracle(b).expert_actions(T0, b.T)
+    assert (np.abs(got[:, 0] - exo[:, 0]) <= _a_tol(b, b.T)).all()
+    assert (np.abs(got[:, 1] - exo[:, 1]) <= _kappa_tol(b, exo, b.T)).all()
+    # the exact directions: turn = kappa * dist within 4e-7 rad of atan2
+    v0 = np.hypot(vx[T0:T0 + 12].astype(np.float64), vy[T0:T0 + 12].astype(np.float64))
+    v1 = np.hypot(vx[T0 + 1:T0 + 13].astype(np.float64), vy[T0 + 1:T0 + 13].astype(np.float64))
+    turn = got[:12, 1] * 0.1 * 0.5 * (v0 + v1)
+    want = np.arctan2(vy[T0 + 1:T0 + 13].astype(np.float64), vx[T0 + 1:T0 + 13].astype(np.float64))
+    assert np.abs(turn - want).max() <= 4e-7 + 1e-6 * np.abs(want).max(), np.abs(turn - want).max()
+
+
 def test_expert_actions_full_size_sampled(wsim):
     # 1024 scenes x 128 agents x 80 steps in one launch; every policy agent's
     # fitted actions checked on 16 sampled scenes, the others must be zero.

@@ -163,6 +163,23 @@ def test_ties_across_polylines_go_to_the_lower_index(wsim):
     print("ties across polylines", c)
 
 
+def test_idm_far_from_origin_scene_resident_equals_per_step(wsim):
+    # Far from the origin (float32 spacing 2-4 mm) the culling bounds of the
+    # off-road, overlap and IDM searches work with large coordinates; the
+    # scene-resident rollout and the per-step kernels must still give the
+    # same bits.
+    import copy
+    b = copy.copy(synth.make_batch(1, seed=4, S=48, R=3000, T=24))
+    for k, d in (("x", 3.1e4), ("y", -2.3e4)):
+        for f in (k, "rg_" + k, "route_" + k, "log_" + k):
+            setattr(b, f, (getattr(b, f).astype(np.float64) + d).astype(np.float32))
+    g = H.run_rollout(b, mode=wsim.MODE_FUSED)
+    assert g["status"] == 0
+    gg = H.run_rollout(b, mode=wsim.MODE_GRAPH)
+    for k in ("traj", "final", "ov", "off", "logdiv", "flags", "reward"):
+        assert np.array_equal(g[k].view(np.uint8), gg[k].view(np.uint8)), k
+
+
 def test_every_launch_configuration_bit_identical(wsim):
     # Uneven scenes span the three size buckets; every single launch shape
     # and every split configuration of the scene-resident rollout must give
