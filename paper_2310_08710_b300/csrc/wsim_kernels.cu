@@ -128,9 +128,11 @@ __global__ void __launch_bounds__(NTs) k_plain_finish(const StepArgs A, int s) {
 // agent g's action space (App. A.1) from log row t0+k to row t0+k+1.  A
 // thread takes one agent and a chunk of kExpertChunk steps: it loads the
 // chunk's kExpertChunk+1 log rows of that agent first (all loads in flight
-// together), then writes the chunk's actions.  The bicycle inverse (two
-// divisions, atan2, square roots) makes the kernel issue-bound; chunks of 4
-// (more warps in flight, fewer registers) measured faster than 2 or 8.  Consecutive threads take
+// together), then writes the chunk's actions.  The bicycle inverse (atan2,
+// square roots, quotients) keeps the kernel issue-bound; chunks of 4 (more
+// warps in flight, fewer registers) measured faster than 2 or 8, than the
+// chunk index fastest in the grid, and than a rolling window of prefetched
+// rows that reads each row once.  Consecutive threads take
 // consecutive agents, so every load and store of a warp is one coalesced row
 // segment.  HBM-bound: per policy agent-step 12 B of log read (heading and
 // velocity for bicycle agents, position and heading for delta agents), per
