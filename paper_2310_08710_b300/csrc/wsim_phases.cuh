@@ -1171,7 +1171,8 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
             fast = true;
             const float U = sqrt_approx(seg_dist2(V.geo[eh], V.inv[eh], xh, cl, yh, dl)) * 1.000001f + 2e-3f;
             L = tl_base + kList * a;
-            for (int j = 0; j < n; ++j) {
+#pragma unroll 4
+            for (int j = 0; j < n; ++j) {  // unrolled: four tiles' loads in flight
                 const int t = L[j];
                 const float4 C = V.tiles[2 * t];
                 const float4 Q = V.tiles[2 * t + 1];
