@@ -1266,10 +1266,38 @@ __device__ __forceinline__ void offroad_tasks(AgentSmem& sm, const SegView& V, i
     for (int g = next_agent(sm, 2, lane); 8 * g < N; g = next_agent(sm, 2, lane))
         offroad_group(sm, V, hint_base, tl_base, meta_base, N, 8 * g, lane, look, cnt);
 }
+// Rows q and N-1-q of the pair triangle as one warp task of the
+// scene-resident rollout: N-1 pairs for every q, so the lanes stay full
+// (single rows left a quarter of the lanes idle on average); an invalid
+// agent's record fails every bound test, as an absent partner's does.  The
+// same pairs and maxima as overlap_row (max is order-free).
+static __device__ void overlap_rows2(AgentSmem& sm, int N, int q, int lane, Counts& cnt) {
+    const int ia = q, ib = N - 1 - q;
+    const int na = N - 1 - ia, nb = ib > ia ? N - 1 - ib : 0;
+    for (int u = lane; u < na + nb; u += 32) {
+        const bool in_a = u < na;
+        const int i = in_a ? ia : ib;
+        const int j = in_a ? ia + 1 + u : ib + 1 + (u - na);
+        const float4 Pi = sm.obox[i];
+        const float4 Pj = sm.obox[j];  // invalid agents: R = -inf, always skipped
+        cnt.bounds += 1;
+        const float dx = Pj.x - Pi.x, dy = Pj.y - Pi.y;
+        const float t = fmaxf(Pi.w + Pj.z, Pi.z + Pj.w);  // |dc| / sqrt(2) above this: skip
+        if (!(t >= 0.f) || fmaf(dx, dx, dy * dy) > 2.f * t * t) continue;
+        const float ddx = comp_diff(sm.xh[j], sm.xl[j], sm.xh[i], sm.xl[i]);
+        const float ddy = comp_diff(sm.yh[j], sm.yl[j], sm.yh[i], sm.yl[i]);
+        const float d = sat_depth(ddx, ddy, sm.c[i], sm.s[i], sm.hl[i], sm.hw[i], sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
+        atomicMax(&sm.ovk[j], ukey(d));
+        atomicMax(&sm.pk[j], partner_key(d, i));
+        atomicMax(&sm.ovk[i], ukey(d));
+        atomicMax(&sm.pk[i], partner_key(d, j));
+        cnt.pairs += 2;
+    }
+}
+
 __device__ __forceinline__ void row_tasks(AgentSmem& sm, int N, Counts& cnt) {
     const int lane = threadIdx.x & 31;
-    for (int i = next_agent(sm, 1, lane); i < N; i = next_agent(sm, 1, lane))
-        if (sm.valid[i]) overlap_row(sm, N, i, lane, cnt);
+    for (int q = next_agent(sm, 1, lane); 2 * q < N; q = next_agent(sm, 1, lane)) overlap_rows2(sm, N, q, lane, cnt);
 }
 
 // ov_i of a valid agent after phase_metrics.

@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
         // the metrics of state t0+k (k >= 1) together with the transition
         // t0+k -> t0+k+1 (k < T): both read state t0+k and write disjoint
         // arrays.  Warps take the long tasks first (IDM groups, then off-road
-        // groups) and the short overlap rows last (that order measured
+        // groups) and the short overlap row pairs last (that order measured
         // fastest); the policy agents follow, one thread each.  The per-agent
         // phase then finishes the metrics of t0+k (row k-1), makes t0+k+1
         // current and prepares its overlap bounds.  The reward of row k-1 is
