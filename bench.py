@@ -446,6 +446,14 @@ def bptt_leg(wsim, synth, torch, b, plain, reps=5):
                        "loss = log divergence^2 + softplus overlap"}
     pairs, T = bptt_pairs(b), b.T
     agents = int(b.valid.sum())
+    # Pairs the kernel evaluates: those not ruled out by the exact cut (a
+    # pair whose depth bound lies below -120 tau adds exactly 0); counted
+    # once, forward and adjoint evaluate the same pairs (2 per pair each).
+    sim.set_counting(True)
+    sim.loss_grad(st, act, synth.T0, T, 10)
+    evaluated = [int(x) for x in sim.counters()][2] // 4
+    sim.set_counting(False)
+    out["pairs_x_steps"] = {"valid": pairs * T, "evaluated": evaluated}
     legs = [("ckpt10", 10, False, reps), ("store_all", 1, False, reps)]
     if plain:
         legs.append(("plain_per_scene_ckpt10", 10, True, 1))
@@ -453,11 +461,11 @@ def bptt_leg(wsim, synth, torch, b, plain, reps=5):
         ms = timed(torch, lambda: sim.loss_grad(st, act, synth.T0, T, ck, plain=pl), n, warm=1)
         out[name] = {"grad_steps_per_s": 1e3 / ms, "ms": ms, "agent_steps_per_s": b.N_tot * T / (ms / 1e3)}
         if not pl:
-            flops = (pairs * T * (BPTT_PAIR_FWD + BPTT_PAIR_ADJ)
+            flops = (evaluated * (BPTT_PAIR_FWD + BPTT_PAIR_ADJ)
                      + agents * T * (BPTT_AGENT_FWD + BPTT_AGENT_LOSS + BPTT_AGENT_ADJ
                                      + BPTT_AGENT_FWD * (ck - 1) / ck))
             out[name]["roofline"] = alu_roofline("k_bptt", float(flops), ms, traffic=None,
-                                                 counted={"valid_pairs_x_steps": pairs * T,
+                                                 counted={"evaluated_pairs_x_steps": evaluated,
                                                           "valid_agent_steps": agents * T})
     stc, mf = st.clone(), wsim.Metrics(b.N_tot, b.S, rows=T)
 

@@ -384,12 +384,13 @@ int wsim_rollout_backward(wsim_ctx *ctx, const float *act_seq, const wsim_metric
  * clears it. */
 int wsim_status(wsim_ctx *ctx, int *device_status, void *stream);
 
-/* Work counters of the last rollout (for roofline accounting; 0 unless
- * wsim_set_counting(ctx, 1) was called before it): [0] corner-segment
+/* Work counters summed over the launches since wsim_set_counting(ctx, 1)
+ * (for roofline accounting; 0 when counting is off): [0] corner-segment
  * distance evaluations, [1] culling-tile bound tests, [2] SAT pair
- * evaluations (each unordered pair counts 2), [3] IDM look-ahead sample-box
- * tests, [4] overlap pair bound tests, [5] IDM lead-candidate circle tests.
- * Synchronises. */
+ * evaluations (each unordered pair counts 2; in wsim_loss_grad and
+ * wsim_rollout_backward those of the loss and its adjoint), [3] IDM
+ * look-ahead sample-box tests, [4] overlap pair bound tests, [5] IDM
+ * lead-candidate circle tests.  Synchronises. */
 #define WSIM_COUNTERS 6
 int wsim_set_counting(wsim_ctx *ctx, int on);
 int wsim_counters(wsim_ctx *ctx, int64_t out[WSIM_COUNTERS], void *stream);

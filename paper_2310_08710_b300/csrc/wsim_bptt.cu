@@ -21,6 +21,7 @@
 namespace wsim {
 
 constexpr int NTb = 512;  // 16 warps per scene: the pair loops take N / 16 agents per warp
+constexpr int NWb = NTb / 32;
 
 struct BpttArgs {
     StepArgs A;      // batch, actions (act = [T][3][N_tot]), in = state t0, t_log = t0 + 1, T
@@ -46,6 +47,7 @@ struct AdjSmem {
     float cx[kMaxN], cy[kMaxN], cth[kMaxN];  // an agent's overlap term, partner's share
     float lx[kMaxN], ly[kMaxN];              // the current step's logged positions
     int16_t pidx[kMaxN];                     // ... and the partner (-1: none)
+    uint8_t plist[NWb][kMaxN];               // each warp's list of a row's partners (row_partners)
     double total;
 };
 
@@ -130,14 +132,48 @@ __device__ __forceinline__ SatGrad sat_grad(float dx, float dy, float cA, float 
     return g;
 }
 
+// Pairs that add exactly nothing: softplus(d/tau) and sigmoid(d/tau) are 0
+// in float32 once d/tau < -104 (e^(d/tau) underflows), so a pair whose SAT
+// depth bound R_i + R_j - |c_j - c_i| / sqrt(2) (the overlap culling bound)
+// lies below -120 tau contributes 0 to the loss and to its gradient and is
+// not evaluated.  cut = 120 tau, or -1 (no culling) unless 0 < tau < inf;
+// the 1 cm and relative slack cover the float32 centres (high words).
+__device__ __forceinline__ float pair_cut(float tau) { return (tau > 0.f && tau < WSIM_INF) ? 120.f * tau : -1.f; }
+__device__ __forceinline__ bool pair_far(const AgentSmem& sm, int i, int j, float cut) {
+    const float dx = sm.xh[j] - sm.xh[i], dy = sm.yh[j] - sm.yh[i];
+    // R_i + R_j with R = hl + hw rounded up
+    const float rr = (sm.hl[i] + sm.hw[i] + sm.hl[j] + sm.hw[j]) * 1.000001f + 1e-3f;
+    const float r = rr + cut + 0.01f + 1e-6f * (fabsf(sm.xh[i]) + fabsf(sm.yh[i]) + fabsf(sm.xh[j]) + fabsf(sm.yh[j]));
+    return cut > 0.f && fmaf(dx, dx, dy * dy) > 2.f * r * r;
+}
+
+// The valid partners j > i of row i that pair_far does not rule out, in
+// increasing order, into list (warp; returns their count, same in every
+// lane).  The pair loops then run over full lanes.
+__device__ __forceinline__ int row_partners(const AgentSmem& sm, int N, int i, int lane, float cut, uint8_t* list) {
+    int n = 0;
+    for (int jb = i + 1; jb < N; jb += 32) {
+        const int j = jb + lane;
+        const bool keep = j < N && sm.valid[j] && !pair_far(sm, i, j, cut);
+        const unsigned m = __ballot_sync(kFull, keep);
+        if (keep) list[n + __popc(m & ((1u << lane) - 1u))] = static_cast<uint8_t>(j);
+        n += __popc(m);
+    }
+    __syncwarp();
+    return n;
+}
+
 // Loss terms of the current state of agent i (warp): d_i^2 plus the
-// penalty of its pairs with j > i.  Same value in every lane.
+// penalty of its pairs with j > i.  Same value in every lane.  list: the
+// warp's partner list.
 __device__ float loss_agent(const AgentSmem& sm, const AdjSmem& adj, int N, int i, int lane, float lambda,
-                            float tau) {
+                            float tau, uint8_t* list, Counts& cnt) {
     float acc = 0.f;
     const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
-    for (int j = i + 1 + lane; j < N; j += 32) {
-        if (!sm.valid[j]) continue;
+    const int np = row_partners(sm, N, i, lane, pair_cut(tau), list);
+    if (lane == 0) cnt.pairs += 2 * np;  // SAT evaluations, two per pair as in the overlap rows
+    for (int q = lane; q < np; q += 32) {
+        const int j = list[q];
         const float dx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
         const float dy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
         const float d = sat_depth(dx, dy, sm.c[i], sm.s[i], sm.hl[i], sm.hw[i], sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
@@ -145,6 +181,7 @@ __device__ float loss_agent(const AgentSmem& sm, const AdjSmem& adj, int N, int 
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+    __syncwarp();  // the list is rewritten by the warp's next row
     const float ex = (xih - adj.lx[i]) + xil, ey = (yih - adj.ly[i]) + yil;
     return acc + fmaf(ex, ex, ey * ey);
 }
@@ -155,7 +192,6 @@ __device__ float loss_agent(const AgentSmem& sm, const AdjSmem& adj, int N, int 
 // summed by a warp reduction, the partner's terms go to the warp's buffer
 // wbuf[warp] (a warp synchronises between rows), and each agent then sums
 // the NWb buffers in warp order.  Fixed order throughout, no float atomics.
-constexpr int NWb = NTb / 32;
 constexpr size_t kPairBufFloats = static_cast<size_t>(NWb) * 3 * kMaxN;
 
 // Agent j's per-agent work in the reverse sweep (the column sums closing
@@ -171,10 +207,12 @@ static_assert(kAgentStride == NTb, "one agent per thread and stride: the reverse
 // wl weighs the whole term (the scene's loss weight; 1 gives the loss's own
 // gradient bit for bit).
 __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, int N, int lane, int warp, float lambda,
-                             float tau, float wl) {
+                             float tau, float wl, Counts& cnt) {
     float* bx = wbuf + static_cast<size_t>(warp) * 3 * kMaxN;
     float* by = bx + kMaxN;
     float* bth = by + kMaxN;
+    uint8_t* list = adj.plist[warp];
+    const float cut = pair_cut(tau);
     for (int j = lane; j < N; j += 32) bx[j] = by[j] = bth[j] = 0.f;
     __syncwarp();
     for (int i = warp; i < N; i += NWb) {
@@ -182,8 +220,10 @@ __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, int
         const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
         const float ci = sm.c[i], si = sm.s[i], hli = sm.hl[i], hwi = sm.hw[i];
         float gx = 0.f, gy = 0.f, gth = 0.f;
-        for (int j = i + 1 + lane; j < N; j += 32) {
-            if (!sm.valid[j]) continue;
+        const int np = row_partners(sm, N, i, lane, cut, list);
+        if (lane == 0) cnt.pairs += 2 * np;
+        for (int q = lane; q < np; q += 32) {
+            const int j = list[q];
             const float dx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
             const float dy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
             const SatGrad G = sat_grad(dx, dy, ci, si, hli, hwi, sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
@@ -374,10 +414,10 @@ __device__ void transition_adjoint(AgentSmem& sm, AdjSmem& adj, const BpttArgs& 
 // One step's loss of the current state (all threads; the logged positions
 // in adj.lx / adj.ly): each warp's rows into adj.part, then (after the
 // caller's barrier) warp 0 adds them in a fixed order; see loss_sum.
-__device__ __forceinline__ void loss_rows(const AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int N) {
+__device__ __forceinline__ void loss_rows(const AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int N, Counts& cnt) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = warp; i < N; i += NWb) {
-        const float v = sm.valid[i] ? loss_agent(sm, adj, N, i, lane, B.lambda, B.tau) : 0.f;
+        const float v = sm.valid[i] ? loss_agent(sm, adj, N, i, lane, B.lambda, B.tau, adj.plist[warp], cnt) : 0.f;
         if (lane == 0) adj.part[i] = v;
     }
 }
@@ -400,11 +440,11 @@ __device__ __forceinline__ void loss_sum(AdjSmem& adj, int N) {
 // 0), the adjoint of the weighted metric row t (when metric weights are
 // given), and the adjoint of the transition t -> t+1, which writes
 // dL/d(actions at t).  dL/d(state t0) remains in adj and goes to B.dst0.
-__device__ void reverse_sweep(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttArgs& B, int s, float wl) {
+__device__ void reverse_sweep(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttArgs& B, int s, float wl,
+                              Counts& cnt) {
     const StepArgs& A = B.A;
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    Counts cnt;
     const int T = A.T, ck = B.ck;
     const int nseg = (T + ck - 1) / ck;
     const bool metrics = B.g_logdiv || B.g_ov || B.g_off;
@@ -436,7 +476,7 @@ __device__ void reverse_sweep(AgentSmem& sm, AdjSmem& adj, float* wbuf, const Bp
             load_prev(sm, cur, a0, N);
             load_log_row(adj, A, a0, N, A.t_log + t);
             __syncthreads();
-            if (wl != 0.f) loss_adjoint(sm, adj, wbuf, N, lane, warp, B.lambda, B.tau, wl);
+            if (wl != 0.f) loss_adjoint(sm, adj, wbuf, N, lane, warp, B.lambda, B.tau, wl, cnt);
             if (metrics) metric_adjoint(sm, adj, B, V, t, a0, N);
             // both adjoints end with agent j's sums in the thread that takes
             // agent j here: no barrier in between
@@ -462,10 +502,9 @@ __device__ void reverse_sweep(AgentSmem& sm, AdjSmem& adj, float* wbuf, const Bp
 
 // Forward with the loss and checkpoints, then (dact given) the reverse sweep
 // of the loss alone.
-__device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttArgs& B, int s) {
+__device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttArgs& B, int s, Counts& cnt) {
     const StepArgs& A = B.A;
     const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
-    Counts cnt;
     const int T = A.T, ck = B.ck;
 
     // Forward.
@@ -479,7 +518,7 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttA
         writeback<NTb>(sm, A.p, nullptr, a0, N);
         load_log_row(adj, A, a0, N, A.t_log + k);
         __syncthreads();
-        loss_rows(sm, adj, B, N);
+        loss_rows(sm, adj, B, N, cnt);
         if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
         __syncthreads();
         loss_sum(adj, N);
@@ -487,7 +526,7 @@ __device__ void bptt_scene(AgentSmem& sm, AdjSmem& adj, float* wbuf, const BpttA
     __syncthreads();
     if (threadIdx.x == 0) B.loss[s] = adj.total;
     if (!B.dact) return;
-    reverse_sweep(sm, adj, wbuf, B, s, 1.f);
+    reverse_sweep(sm, adj, wbuf, B, s, 1.f, cnt);
 }
 
 // Recording forward of scene s: the rollout (every policy agent takes its
@@ -537,7 +576,7 @@ __device__ void record_scene(AgentSmem& sm, AdjSmem& adj, unsigned long long* k6
                 if (!v) orec[i] = -1;
             }
         }
-        if (B.loss) loss_rows(sm, adj, B, N);
+        if (B.loss) loss_rows(sm, adj, B, N, cnt);
         if ((k + 1) % ck == 0 || k + 1 == T) store_state<NTb>(sm, slot_state(B.ckpt, (k + 1 + ck - 1) / ck, A.N_tot), a0, N);
         __syncthreads();
         if (B.loss) loss_sum(adj, N);
@@ -573,14 +612,16 @@ __global__ void __launch_bounds__(NTb, 2) k_bptt(const BpttArgs B) {
     AdjSmem& adj = *reinterpret_cast<AdjSmem*>(bdyn + kAdjOff);
     float* wbuf = reinterpret_cast<float*>(bdyn + kBufOff);
     init_cta(sm);
+    Counts cnt;  // published on request (wsim_set_counting): the loss's SAT pair evaluations, the IDM tests
     if (B.scene >= 0) {
-        bptt_scene(sm, adj, wbuf, B, B.scene);
-        return;
+        bptt_scene(sm, adj, wbuf, B, B.scene, cnt);
+    } else {
+        for (int s = next_scene(sm, B.A); s >= 0; s = next_scene(sm, B.A)) {
+            bptt_scene(sm, adj, wbuf, B, s, cnt);
+            __syncthreads();
+        }
     }
-    for (int s = next_scene(sm, B.A); s >= 0; s = next_scene(sm, B.A)) {
-        bptt_scene(sm, adj, wbuf, B, s);
-        __syncthreads();
-    }
+    publish_counts(sm, B.A, cnt);
 }
 
 __global__ void __launch_bounds__(NTb, 2) k_record(const BpttArgs B) {
@@ -603,10 +644,12 @@ __global__ void __launch_bounds__(NTb, 2) k_backward(const BpttArgs B) {
     AdjSmem& adj = *reinterpret_cast<AdjSmem*>(bdyn + kAdjOff);
     float* wbuf = reinterpret_cast<float*>(bdyn + kBufOff);
     init_cta(sm);
+    Counts cnt;
     for (int s = next_scene(sm, B.A); s >= 0; s = next_scene(sm, B.A)) {
-        reverse_sweep(sm, adj, wbuf, B, s, B.loss_w ? static_cast<float>(B.loss_w[s]) : 0.f);
+        reverse_sweep(sm, adj, wbuf, B, s, B.loss_w ? static_cast<float>(B.loss_w[s]) : 0.f, cnt);
         __syncthreads();
     }
+    publish_counts(sm, B.A, cnt);
 }
 
 static BpttArgs bptt_args(const StepArgs& a, float* ckpt, float* segbuf, int ck, float lambda, float tau) {

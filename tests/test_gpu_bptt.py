@@ -74,6 +74,40 @@ def test_gradient_matches_oracle_duals_8x8(wsim):
     print("grad rel err (8 scenes x 8 agents, all components):", worst)
 
 
+@pytest.mark.parametrize("tau", [0.05, 0.25, 2.0])
+def test_pair_culling_exact_at_every_tau(wsim, tau):
+    # Pairs whose SAT depth bound lies below -120 tau are skipped (their
+    # softplus and sigmoid are exactly 0 in float32).  Agents packed into a
+    # 30 m square (overlapping and near pairs) and spread over 200 m, at a
+    # tau that culls almost nothing (2 m), the default and a small one:
+    # loss and gradient against the oracle's FP64 sum over every pair.
+    b = synth.make_batch(3, seed=6, S=4, N=24, T=30)
+    for s in range(2):  # the first two scenes packed, the others as drawn
+        a0, a1 = b.agent_off[s], b.agent_off[s + 1]
+        for k in ("x", "y"):
+            v = getattr(b, k)
+            v[a0:a1] = (100.0 + 0.15 * (v[a0:a1].astype(np.float64) - 100.0)).astype(np.float32)
+            lg = getattr(b, "log_" + k)
+            lg[:, a0:a1] = (100.0 + 0.15 * (lg[:, a0:a1].astype(np.float64) - 100.0)).astype(np.float32)
+    cfg = wsim.default_config(loss_tau=tau)
+    sim = wsim.Sim(wsim.DeviceBatch(b), cfg)
+    loss, dact = sim.loss_grad(wsim.State.from_batch(b), torch.as_tensor(b.actions).cuda().contiguous(), T0, b.T)
+    torch.cuda.synchronize()
+    assert sim.status() == 0
+    sim.close()
+    loss, dact = loss.cpu().numpy(), dact.cpu().numpy()
+    o = oracle.Oracle(b)
+    st = o.initial_state()
+    act = b.actions.astype(np.float64)
+    for s in range(b.S):
+        lo = o.loss(s, st, act, T0, b.T, tau=tau)
+        assert abs(loss[s] - lo) <= TOL_LOSS * abs(lo), (s, loss[s], lo)
+        dirs = policy_dirs(b, s, b.T)
+        ref = o.loss_grad(s, st, act, T0, b.T, dirs, tau=tau)
+        got = np.array([dact[t, c, g] for t, c, g in dirs], dtype=np.float64)
+        assert rel_err(got, ref) <= TOL_GRAD, (s, tau, rel_err(got, ref))
+
+
 def test_gradient_matches_central_differences(wsim):
     b = synth.make_batch(3, seed=1, S=8, N=8)
     _, dact = gpu_grad(wsim, b)
