@@ -26,8 +26,10 @@ namespace wsim {
 constexpr int NTs = kStepThreads;
 
 // COUNT = false: the work counts are dead code (fewer live registers).
+// Both instantiations are held to 64 registers (4 CTAs of 256 per SM): the
+// graph path sizes its grid by the smaller occupancy of the two.
 template <bool COUNT>
-__global__ void __launch_bounds__(NTs) k_step(const StepArgs A) {
+__global__ void __launch_bounds__(NTs, 4) k_step(const StepArgs A) {
     __shared__ AgentSmem sm;
     init_cta(sm);
     Counts cnt;
