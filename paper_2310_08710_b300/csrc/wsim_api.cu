@@ -23,6 +23,7 @@ struct wsim_ctx {
     int S = 0, N_tot = 0, grid = 1, count = 0;
     // scene-resident rollout: scenes in size buckets, each with a launch shape
     int shape_cap[kRollShapes] = {};   // staged segments per shape
+    int cache_n = 32;                  // the largest scene's agents rounded up to a warp
     int shape_grid[kRollShapes] = {};  // persistent grid per shape
     int bucket_n[kBuckets] = {};       // scenes per bucket
     int bucket_at[kBuckets] = {};      // first entry of the bucket in border
@@ -142,6 +143,7 @@ StepArgs base_args(const wsim_ctx* c) {
     a.status = c->status;
     a.counters = c->counters;
     a.count = c->count;
+    a.cache_n = c->cache_n;
     a.p = c->p;
     return a;
 }
@@ -448,22 +450,26 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
     c->grid = std::min(S, sms * step_blocks_per_sm());
     // Scene-resident rollout.  Buckets by staged size: 0 = fits the small
     // stage (shapes 1 and 4), 1 = fits the large stage (shape 0), 2 = neither.
-    int need = 0;
-    for (int s = 0; s < S; ++s) need = std::max(need, off[s + 1] - off[s]);
-    for (int sh = 0; sh < kRollShapes; ++sh) c->shape_cap[sh] = std::min(need, shape_max_seg_cap(sh));
+    int need = 0, nmax = 1;
+    for (int s = 0; s < S; ++s) {
+        need = std::max(need, off[s + 1] - off[s]);
+        nmax = std::max(nmax, ao[s + 1] - ao[s]);
+    }
+    c->cache_n = std::min(kMaxN, (nmax + 31) / 32 * 32);
+    for (int sh = 0; sh < kRollShapes; ++sh) c->shape_cap[sh] = std::min(need, shape_max_seg_cap(sh, c->cache_n));
     std::vector<int32_t> border;
     for (int bk = 0; bk < kBuckets; ++bk) {
         c->bucket_at[bk] = static_cast<int>(border.size());
         for (int w = 0; w < S; ++w) {
             const int s = order[w], segs = off[s + 1] - off[s];
-            const int b = segs <= shape_max_seg_cap(1) ? 0 : (segs <= shape_max_seg_cap(0) ? 1 : 2);
+            const int b = segs <= shape_max_seg_cap(1, c->cache_n) ? 0 : (segs <= shape_max_seg_cap(0, c->cache_n) ? 1 : 2);
             if (b == bk) border.push_back(s);
         }
         c->bucket_n[bk] = static_cast<int>(border.size()) - c->bucket_at[bk];
     }
     for (int sh = 0; sh < kRollShapes; ++sh) {
         int bps = 1;
-        if (shape_prepare(sh, c->shape_cap[sh], &bps) != cudaSuccess) return fail(WSIM_ECUDA);
+        if (shape_prepare(sh, c->shape_cap[sh], c->cache_n, &bps) != cudaSuccess) return fail(WSIM_ECUDA);
         c->shape_grid[sh] = sms * bps;
     }
     if (cudaMemcpyAsync(c->border, border.data(), sizeof(int32_t) * S, cudaMemcpyHostToDevice, st) != cudaSuccess ||

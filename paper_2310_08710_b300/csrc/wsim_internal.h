@@ -97,6 +97,7 @@ struct StepArgs {
     unsigned long long* counters;  // [kCounters] work counters (when count != 0)
     int count;
     int seg_cap;           // rollout: segments that fit in the shared-memory stage
+    int cache_n;           // rollout: agents of the per-CTA candidate-tile caches (>= every scene's N)
     Params p;
 };
 
@@ -128,8 +129,9 @@ int step_blocks_per_sm();
 // 512 x 1 large stage, 1 256 x 2 small stage, 2 256 x 4 no stage, 3 512 x 2
 // no stage, 4 512 x 2 small stage.  seg_cap: staged segments (a.seg_cap at
 // launch).
-int shape_max_seg_cap(int shape);
-cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm);
+// cache_n: agents of the per-CTA candidate-tile caches (a.cache_n at launch).
+int shape_max_seg_cap(int shape, int cache_n);
+cudaError_t shape_prepare(int shape, int seg_cap, int cache_n, int* blocks_per_sm);
 cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st);
 // Observation (wsim_observe.cu): roadgraph point tiles of kPtTile consecutive
 // points per scene, and the per-observer kernel.

@@ -21,8 +21,14 @@
 
 namespace wsim {
 
-constexpr size_t kCacheBytes = kMaxN * (kList * sizeof(uint16_t) + sizeof(float4));  // candidate-tile lists
-constexpr size_t kAgentBytes = (sizeof(AgentSmem) + kCacheBytes + 127) / 128 * 128;
+// Per-CTA bytes before the stage: the agent block, then the candidate-tile
+// caches (list metadata and lists) for cache_n agents, the batch's largest
+// scene rounded up to a warp: a batch of small scenes leaves room for more
+// resident CTAs.
+constexpr size_t kCacheOff = (sizeof(AgentSmem) + 15) / 16 * 16;
+__host__ __device__ constexpr size_t agent_bytes(int cache_n) {
+    return (kCacheOff + static_cast<size_t>(cache_n) * (kList * sizeof(uint16_t) + sizeof(float4)) + 127) / 128 * 128;
+}
 constexpr size_t kBytesPerTile = kTile * (16 + 4 + 1) + 32;  // geo + inv + flags + tile records
 constexpr size_t kBytesPerSuper = 16;
 
@@ -42,9 +48,9 @@ template <int NT, int MINB, bool STAGE, bool DRIVERS>
 __global__ void __launch_bounds__(NT, MINB) k_rollout(const StepArgs A) {
     extern __shared__ __align__(128) unsigned char dyn[];
     AgentSmem& sm = *reinterpret_cast<AgentSmem*>(dyn);
-    float4* tmeta = reinterpret_cast<float4*>(dyn + (sizeof(AgentSmem) + 15) / 16 * 16);
-    uint16_t* tlist = reinterpret_cast<uint16_t*>(tmeta + kMaxN);
-    unsigned char* stage = dyn + kAgentBytes;
+    float4* tmeta = reinterpret_cast<float4*>(dyn + kCacheOff);
+    uint16_t* tlist = reinterpret_cast<uint16_t*>(tmeta + A.cache_n);
+    unsigned char* stage = dyn + agent_bytes(A.cache_n);
     init_cta(sm);
     Counts cnt;
     uint32_t parity = 0;
@@ -152,7 +158,7 @@ static size_t stage_bytes(int seg_cap) {
 }
 
 // Largest stage (in segments, a multiple of kTile) of a shape on this device.
-int shape_max_seg_cap(int shape) {
+int shape_max_seg_cap(int shape, int cache_n) {
     if (!kShapes[shape].stage) return 0;
     int dev = 0, per_sm = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -165,14 +171,15 @@ int shape_max_seg_cap(int shape) {
     size_t budget = static_cast<size_t>(per_sm) / kShapes[shape].min_blocks;
     budget = budget > 1024 ? budget - 1024 : 0;
     if (budget > static_cast<size_t>(optin)) budget = static_cast<size_t>(optin);
-    if (budget <= kAgentBytes + kBytesPerSuper) return 0;
-    size_t nt = (budget - kAgentBytes - kBytesPerSuper) / (kBytesPerTile + kBytesPerSuper / kSuper);
-    while (nt > 0 && kAgentBytes + stage_bytes(static_cast<int>(nt * kTile)) > budget) --nt;
+    const size_t ab = agent_bytes(cache_n);
+    if (budget <= ab + kBytesPerSuper) return 0;
+    size_t nt = (budget - ab - kBytesPerSuper) / (kBytesPerTile + kBytesPerSuper / kSuper);
+    while (nt > 0 && ab + stage_bytes(static_cast<int>(nt * kTile)) > budget) --nt;
     return static_cast<int>(nt) * kTile;
 }
 
-cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm) {
-    const size_t bytes = kAgentBytes + stage_bytes(kShapes[shape].stage ? seg_cap : 0);
+cudaError_t shape_prepare(int shape, int seg_cap, int cache_n, int* blocks_per_sm) {
+    const size_t bytes = agent_bytes(cache_n) + stage_bytes(kShapes[shape].stage ? seg_cap : 0);
     int n = 1 << 30;
     for (int d = 0; d < 2; ++d) {
         cudaError_t e = cudaFuncSetAttribute(kKernels[d][shape], cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -188,7 +195,7 @@ cudaError_t shape_prepare(int shape, int seg_cap, int* blocks_per_sm) {
 }
 
 cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st) {
-    const size_t bytes = kAgentBytes + stage_bytes(kShapes[shape].stage ? a.seg_cap : 0);
+    const size_t bytes = agent_bytes(a.cache_n) + stage_bytes(kShapes[shape].stage ? a.seg_cap : 0);
     kKernels[a.ctrl || a.count ? 1 : 0][shape]<<<grid, kShapes[shape].threads, bytes, st>>>(a);
     return cudaGetLastError();
 }
