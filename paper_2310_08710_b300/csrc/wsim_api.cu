@@ -46,6 +46,7 @@ struct wsim_ctx {
     int32_t* hint = nullptr;  // [N_tot][4] nearest-segment cache of the per-step kernels
     uint16_t* tlist = nullptr;  // [N_tot][kList] candidate-tile lists of the per-step kernels
     float4* tmeta = nullptr;    // [N_tot] their centre, radius and count
+    float* route_rf = nullptr;  // [N_tot] each route's largest segment length over route_h
     unsigned long long* counters = nullptr;
     // observation: roadgraph point tiles, observer list, agent -> scene (built on first use)
     int32_t *pt_tile_off = nullptr, *pt_cnt = nullptr, *obs_list = nullptr, *obs_count = nullptr,
@@ -128,6 +129,7 @@ StepArgs base_args(const wsim_ctx* c) {
     a.route_off = b.route_off;
     a.route_x = b.route_x;
     a.route_y = b.route_y;
+    a.route_rf = c->route_rf;
     a.log_x = b.log_x;
     a.log_y = b.log_y;
     a.log_th = b.log_th;
@@ -379,8 +381,12 @@ int wsim_init(wsim_ctx** out, const wsim_config* cfg, const wsim_batch* b, void*
         (rc = dalloc(&c->status, 1)) || (rc = dalloc(&c->counters, kCounters)) ||
         (rc = dalloc(&c->tmp, static_cast<size_t>(N) * 10)) || (rc = ensure_queue(c, 128)) ||
         (rc = dalloc(&c->hint, static_cast<size_t>(N) * 4)) ||
-        (rc = dalloc(&c->tlist, static_cast<size_t>(N) * kList)) || (rc = dalloc(&c->tmeta, static_cast<size_t>(N))))
+        (rc = dalloc(&c->tlist, static_cast<size_t>(N) * kList)) || (rc = dalloc(&c->tmeta, static_cast<size_t>(N))) ||
+        (rc = dalloc(&c->route_rf, static_cast<size_t>(N))))
         return fail(rc);
+    if (launch_route_speed(b->route_off, b->route_x, b->route_y, N, 1.0f / cfg->route_h, c->route_rf, st) !=
+        cudaSuccess)
+        return fail(WSIM_ECUDA);
     // all-ones: no nearest segment known, list count -1 (no list yet)
     if (cudaMemsetAsync(c->hint, 0xff, std::max<size_t>(N, 1) * 4 * sizeof(int32_t), st) != cudaSuccess ||
         cudaMemsetAsync(c->tmeta, 0xff, std::max<size_t>(N, 1) * sizeof(float4), st) != cudaSuccess)
@@ -965,6 +971,7 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->hint);
     cudaFree(c->tlist);
     cudaFree(c->tmeta);
+    cudaFree(c->route_rf);
     delete c;
 }
 

@@ -76,6 +76,7 @@ struct StepArgs {
     const uint8_t *valid, *kind;
     const int32_t* route_off;
     const float *route_x, *route_y;
+    const float* route_rf;  // per agent: its route's largest segment length over route_h (+inf if not finite)
     const float *log_x, *log_y;
     const float *log_th, *log_vx, *log_vy;  // may be null (no expert, no log playback)
     Segs segs;
@@ -118,6 +119,10 @@ cudaError_t launch_tile_order(int S, const int32_t* seg_off, const int32_t* seg_
 cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg_cnt, const int32_t* soff,
                                const float4* tiles, const uint16_t* tperm, float4* sup, cudaStream_t st);
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st);
+// route_rf[g] = (largest segment length of agent g's route) / route_h,
+// rounded up; +inf when a segment length is not finite; 0 without segments.
+cudaError_t launch_route_speed(const int32_t* route_off, const float* rx, const float* ry, int N, float inv_h,
+                               float* rf, cudaStream_t st);
 // Discrete actions: continuous [T][3][N_tot] <-> flat grid indices [T][N_tot].
 cudaError_t launch_discretize(const StepArgs& a, const float* act, int T, int32_t* idx, cudaStream_t st);
 cudaError_t launch_decode_actions(const StepArgs& a, const int32_t* idx, int T, float* act, cudaStream_t st);

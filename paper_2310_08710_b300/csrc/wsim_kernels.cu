@@ -532,6 +532,29 @@ cudaError_t launch_super_build(int S, const int32_t* seg_off, const int32_t* seg
     return cudaGetLastError();
 }
 
+// Largest route-point spacing per route parameter, one thread per agent: a
+// sample moves at most rf metres per metre of route parameter, so samples
+// k dq apart lie within k dq rf of each other (the IDM lead search's group
+// circles).
+__global__ void __launch_bounds__(256) k_route_speed(const int32_t* route_off, const float* rx, const float* ry,
+                                                     int N, float inv_h, float* rf) {
+    const int g = blockIdx.x * 256 + threadIdx.x;
+    if (g >= N) return;
+    float m = 0.f;
+    for (int k = route_off[g]; k + 1 < route_off[g + 1]; ++k) {
+        const float d = hypotf(rx[k + 1] - rx[k], ry[k + 1] - ry[k]);
+        m = d < WSIM_INF ? fmaxf(m, d) : WSIM_INF;  // NaN or inf: no bound
+    }
+    rf[g] = m < WSIM_INF ? m * inv_h * 1.00001f : WSIM_INF;
+}
+
+cudaError_t launch_route_speed(const int32_t* route_off, const float* rx, const float* ry, int N, float inv_h,
+                               float* rf, cudaStream_t st) {
+    if (N == 0) return cudaSuccess;
+    k_route_speed<<<(N + 255) / 256, 256, 0, st>>>(route_off, rx, ry, N, inv_h, rf);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(const StepArgs& a, int grid, cudaStream_t st) {
     if (a.count)
         k_step<true><<<grid, NTs, 0, st>>>(a);

@@ -420,24 +420,24 @@ static __device__ IdmLead idm_lead(AgentSmem& sm, const StepArgs& A, int a0, int
     const IdmSample smp = idm_sample(p, rx, ry, P, sm.sh[i], sm.sl[i], hli, lane);
     const float Px = smp.Px, Py = smp.Py, dx = smp.dx, dy = smp.dy, qox = smp.qox, qoy = smp.qoy;
 
-    // Bounding circles of the four groups of 8 consecutive samples: a box
-    // (widened by wi) that holds a sample of group G has its centre within
-    // r_G + hl + hw + 2 wi of the circle's centre (5 cm of slack for the
+    // Bounding circles of the four groups of 8 consecutive samples, centred
+    // on each group's fifth sample: the samples of a group lie within 4 dq
+    // of route parameter of it, so within 4 dq rf in the plane (rf: the
+    // route's largest segment length per route parameter); a box (widened
+    // by wi) that holds a sample of group G has its centre within that
+    // radius + hl + hw + 2 wi of the circle's centre (5 cm of slack for the
     // float32 positions).
     const float qx = Px + qox, qy = Py + qoy;
-    const int gl = lane & ~7;
-    const float gcx = __shfl_sync(kFull, qx, gl + 4), gcy = __shfl_sync(kFull, qy, gl + 4);
-    // (approximate root rounded up: the circles only grow, a conservative filter)
-    float gr = sqrt_approx((qx - gcx) * (qx - gcx) + (qy - gcy) * (qy - gcy)) * 1.000002f + 1e-6f;
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) gr = fmaxf(gr, __shfl_xor_sync(kFull, gr, o));
-    gr += 2.f * wi + 0.05f;  // lanes 8G .. 8G+7 hold circle G
+    // (read from global memory beside the route loads: a per-agent array in
+    // shared memory would cost a four-CTA shape its shared-memory carve-out)
+    const float rf = A.route_rf ? A.route_rf[a0 + i] : WSIM_INF;
+    const float gr = fmaf(4.f * p.dq, rf, 2.f * wi + 0.05f);
     float cxs[4], cys[4], crs[4];  // the four circles in every lane
 #pragma unroll
     for (int G = 0; G < 4; ++G) {
-        cxs[G] = __shfl_sync(kFull, gcx, 8 * G);
-        cys[G] = __shfl_sync(kFull, gcy, 8 * G);
-        crs[G] = __shfl_sync(kFull, gr, 8 * G);
+        cxs[G] = __shfl_sync(kFull, qx, 8 * G + 4);
+        cys[G] = __shfl_sync(kFull, qy, 8 * G + 4);
+        crs[G] = gr;
     }
 
     int lead = -1, lead_hit = 0;

@@ -305,6 +305,32 @@ def test_idm_scene_with_routes_every_step(wsim):
     assert c["band_idm"] <= 0.02 * c["agent_steps"]
 
 
+def test_idm_routes_with_uneven_point_spacing(wsim):
+    # The lead search bounds each group of look-ahead samples by the route's
+    # largest segment length per route parameter (computed at init): routes
+    # whose segments are stretched 0.4x to 4x (the parameter still counts
+    # 0.5 m per segment) must give the oracle's leads.
+    b = synth.make_batch(1, seed=8, S=6, R=4000)
+    rng = np.random.default_rng(8)
+    for g in range(b.N_tot):
+        r0, r1 = b.route_off[g], b.route_off[g + 1]
+        if r1 - r0 < 2:
+            continue
+        x = b.route_x[r0:r1].astype(np.float64)
+        y = b.route_y[r0:r1].astype(np.float64)
+        f = rng.uniform(0.4, 4.0, r1 - r0 - 1)
+        b.route_x[r0 + 1:r1] = (x[0] + np.cumsum(np.diff(x) * f)).astype(np.float32)
+        b.route_y[r0 + 1:r1] = (y[0] + np.cumsum(np.diff(y) * f)).astype(np.float32)
+    g = H.run_rollout(b)
+    assert g["status"] == 0
+    gg = H.run_rollout(b, mode=wsim.MODE_GRAPH)
+    for k in ("traj", "ov", "off", "flags"):
+        assert np.array_equal(g[k].view(np.uint8), gg[k].view(np.uint8)), k
+    c = H.teacher_forced(b, g, list(range(b.S)), range(b.T))
+    print("idm, stretched routes", c)
+    assert c["band_idm"] <= 0.02 * c["agent_steps"]
+
+
 def test_ctrl_mask_and_nonfinite_status(wsim):
     b = synth.make_batch(0, seed=5)
     ctrl = (np.arange(b.N_tot) % 3 != 0).astype(np.uint8)
