@@ -249,7 +249,9 @@ int wsim_decode_actions(wsim_ctx *ctx, const int32_t *idx, int T, float *act, vo
  * (device, caller-owned) row k receives the action that takes log row
  * t0+k to log row t0+k+1: (a, kappa, 0) for bicycle agents by the inverse
  * kinematics, (dx, dy, dtheta) for delta agents, 0 for IDM and invalid
- * agents.  Requires log_th/log_vx/log_vy (else WSIM_EINVAL), 0 <= t0,
+ * agents.  Float32: the direction within 4e-7 rad (the library's own
+ * atan2), a within an ulp of (|v'| - |v|) / dt, kappa = turn / distance
+ * within 2 ulps.  Requires log_th/log_vx/log_vy (else WSIM_EINVAL), 0 <= t0,
  * T >= 0 and t0+T < T_log (else WSIM_ESIZE).  Asynchronous on `stream`. */
 int wsim_expert_actions(wsim_ctx *ctx, int t0, int T, float *act_out, void *stream);
 
