@@ -1134,10 +1134,11 @@ static __device__ float offroad_agent(const SegView& V, int lane, float xh, floa
 
 // ---------------------------------------------------------------------------
 // Off-road of eight agents (warp; lane 4a+k = corner k of agent a).  Fast
-// path, lane by lane: the bound U from the corner's previous nearest
-// segment, the agent's cached candidate tiles whose capsule lies within U,
-// a scan of those tiles, and the cache condition best + |p - c0| <= r0 - 1 mm
-// (then the result is the exact nearest segment).  Agents whose cache or
+// path: the bound U from each corner's previous nearest segment, the
+// agent's cached candidate tiles whose capsule lies within U (the agent's
+// four lanes split the list and test each tile for all four corners), a
+// scan of each corner's tiles, and the cache condition best + |p - c0| <=
+// r0 - 1 mm (then the result is the exact nearest segment).  Agents whose cache or
 // hints fail any corner take the warp-cooperative search (offroad_agent),
 // which also rebuilds the cache.
 // ---------------------------------------------------------------------------
@@ -1155,6 +1156,8 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
     float4 M = make_float4(0.f, 0.f, 0.f, 0.f);
     unsigned mask = 0;
     const uint16_t* L = nullptr;
+    float U = WSIM_INF;
+    int n = -1;
     if (act && V.E > 0 && hint_base && tl_base) {
         const float hl = (k < 2 ? 1.f : -1.f) * sm.hl[a], hw = (k == 0 || k == 3 ? 1.f : -1.f) * sm.hw[a];
         const float c = sm.c[a], s = sm.s[a];
@@ -1165,23 +1168,49 @@ static __device__ void offroad_group(AgentSmem& sm, const SegView& V, int32_t* h
         px = xh + cl;
         py = yh + dl;
         M = meta_base[a];
-        const int n = __float_as_int(M.w);
+        n = __float_as_int(M.w);
         const int eh = hint_base[4 * a + k];
         if (n >= 0 && eh >= 0 && eh < V.E) {
             fast = true;
-            const float U = sqrt_approx(seg_dist2(V.geo[eh], V.inv[eh], xh, cl, yh, dl)) * 1.000001f + 2e-3f;
-            L = tl_base + kList * a;
-#pragma unroll 4
-            for (int j = 0; j < n; ++j) {  // unrolled: four tiles' loads in flight
-                const int t = L[j];
-                const float4 C = V.tiles[2 * t];
-                const float4 Q = V.tiles[2 * t + 1];
-                const float l = U + Q.x;
-                if (cap_d2(C, Q.y, px, py) <= l * l) mask |= 1u << j;
-            }
-            cnt.tiles += n;
+            U = sqrt_approx(seg_dist2(V.geo[eh], V.inv[eh], xh, cl, yh, dl)) * 1.000001f + 2e-3f;
         }
     }
+    // The agent's four lanes split its list (lane k takes entries k, k+4,
+    // ...) and test each tile against all four corners; the corner masks
+    // are then gathered per lane.  Only agents whose four corners all have a
+    // bound take the fast path.
+    const unsigned qm = 0xfu << (lane & ~3);
+    const bool qfast = (__ballot_sync(kFull, fast) & qm) == qm;
+    float pxs[4], pys[4], us[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        pxs[c] = __shfl_sync(kFull, px, (lane & ~3) | c);
+        pys[c] = __shfl_sync(kFull, py, (lane & ~3) | c);
+        us[c] = __shfl_sync(kFull, U, (lane & ~3) | c);
+    }
+    unsigned mc[4] = {0u, 0u, 0u, 0u};
+    if (qfast) {
+        L = tl_base + kList * a;
+        for (int j = k; j < n; j += 4) {
+            const int t = L[j];
+            const float4 C = V.tiles[2 * t];
+            const float4 Q = V.tiles[2 * t + 1];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float l = us[c] + Q.x;
+                if (cap_d2(C, Q.y, pxs[c], pys[c]) <= l * l) mc[c] |= 1u << j;
+            }
+        }
+        cnt.tiles += n;
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        unsigned v = mc[c];
+        v |= __shfl_xor_sync(kFull, v, 1);
+        v |= __shfl_xor_sync(kFull, v, 2);
+        if (c == k) mask = v;
+    }
+    fast = qfast;
     // Scan each lane's passing tiles (lanes with fewer tiles idle).
     while (__any_sync(kFull, mask != 0)) {
         if (mask) {
