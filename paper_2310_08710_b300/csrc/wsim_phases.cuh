@@ -1371,11 +1371,12 @@ __device__ void phase_finish(AgentSmem& sm, const StepArgs& A, const MetricsP& m
 // two barriers).  For agent i, in this order: (1) finish the metrics of the
 // current state (log row t_log; metric row m; the scene's reward summed into
 // sm.reward); (2) advance to the next state (n* -> current, the
-// kinematic-infeasibility flag of that transition, the state stored to out);
-// (3) prepare the overlap culling record of the next state from the n*
-// arrays (the partner's n* is final during this phase, its current arrays
-// are not), and clear the overlap maxima.  Every read of another agent's
-// data is of arrays this phase does not write.
+// kinematic-infeasibility flag of that transition, the state stored to out,
+// the cos / sin of its heading); then, after a barrier, (3) prepare the
+// overlap culling record of the next state from the current arrays (the
+// partner's heading cos / sin is not computed a second time) and clear the
+// overlap maxima.  Before the barrier every read of another agent's data is
+// of arrays the pass does not write.
 // ---------------------------------------------------------------------------
 template <int NT>
 __device__ void finish_advance(AgentSmem& sm, const StepArgs& A, const MetricsP* m, int t_log, bool advance,
@@ -1432,26 +1433,30 @@ __device__ void finish_advance(AgentSmem& sm, const StepArgs& A, const MetricsP*
         sm.vy[i] = sm.nvy[i];
         sm.sh[i] = sm.nsh[i];
         sm.sl[i] = sm.nsl[i];
-        // overlap culling record of the next state, from the n* arrays
+    }
+    if (r) atomicAdd(&sm.reward, r);
+    if (threadIdx.x == 0) sm.work[0] = sm.work[1] = sm.work[2] = 0;  // the next task phase
+    if (!advance) return;
+    // Overlap culling record of the new state, once every agent's new state
+    // (and its heading's cos / sin) is in the current arrays: the depth
+    // against the deepest partner of the step just measured, a lower bound
+    // of the new maximum; then the maxima are cleared.
+    __syncthreads();
+    for (int i = threadIdx.x; i < N; i += NT) {
         float lb = -WSIM_INF;
         const int q = (sm.pk[i] >> 8) > (kNoDepth >> 8) ? static_cast<int>(sm.pk[i] & 0xffu) : -1;
         if (sm.valid[i] && q >= 0 && q < N && q != i && sm.valid[q]) {
             const int a = min(i, q), b = max(i, q);
-            float ca, sa, cb, sb;
-            comp_sincos(sm.nth[a], sm.ntl[a], ca, sa);
-            comp_sincos(sm.nth[b], sm.ntl[b], cb, sb);
-            const float dx = comp_diff(sm.nxh[b], sm.nxl[b], sm.nxh[a], sm.nxl[a]);
-            const float dy = comp_diff(sm.nyh[b], sm.nyl[b], sm.nyh[a], sm.nyl[a]);
-            lb = sat_depth(dx, dy, ca, sa, sm.hl[a], sm.hw[a], cb, sb, sm.hl[b], sm.hw[b]);
+            const float dx = comp_diff(sm.xh[b], sm.xl[b], sm.xh[a], sm.xl[a]);
+            const float dy = comp_diff(sm.yh[b], sm.yl[b], sm.yh[a], sm.yl[a]);
+            lb = sat_depth(dx, dy, sm.c[a], sm.s[a], sm.hl[a], sm.hw[a], sm.c[b], sm.s[b], sm.hl[b], sm.hw[b]);
         }
         const float R = (sm.hl[i] + sm.hw[i]) * 1.000001f + 5e-4f;
-        sm.obox[i] = sm.valid[i] ? make_float4(sm.nxh[i], sm.nyh[i], R, R - lb + 5e-4f)
-                                 : make_float4(sm.nxh[i], sm.nyh[i], -WSIM_INF, -WSIM_INF);
+        sm.obox[i] = sm.valid[i] ? make_float4(sm.xh[i], sm.yh[i], R, R - lb + 5e-4f)
+                                 : make_float4(sm.xh[i], sm.yh[i], -WSIM_INF, -WSIM_INF);
         sm.ovk[i] = kNoDepth;
         sm.pk[i] = kNoDepth;
     }
-    if (r) atomicAdd(&sm.reward, r);
-    if (threadIdx.x == 0) sm.work[0] = sm.work[1] = sm.work[2] = 0;  // the next task phase
 }
 
 // ---------------------------------------------------------------------------
