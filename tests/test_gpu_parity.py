@@ -180,6 +180,34 @@ def test_idm_far_from_origin_scene_resident_equals_per_step(wsim):
         assert np.array_equal(g[k].view(np.uint8), gg[k].view(np.uint8)), k
 
 
+def test_scene_beyond_the_tile_order_limit(wsim):
+    # A scene of more than 4,096 culling tiles (70,000 road-edge points in
+    # short polylines) keeps its tiles in index order for the super-tiles;
+    # its neighbour scene is ordered.  Both against the oracle, and the
+    # scene-resident rollout against the per-step kernels bit for bit.
+    rng = np.random.default_rng(12)
+    polys = []
+    for p in range(3500):
+        n = 20
+        start = rng.uniform(0.0, 400.0, 2)
+        h = rng.uniform(-np.pi, np.pi)
+        k = np.arange(n)[:, None]
+        polys.append((start + 0.5 * k * np.array([np.cos(h), np.sin(h)]), 1))
+    agents = [dict(x=float(x), y=float(y), th=float(t), v=float(v))
+              for x, y, t, v in zip(rng.uniform(50, 350, 12), rng.uniform(50, 350, 12),
+                                   rng.uniform(-np.pi, np.pi, 12), rng.uniform(0, 10, 12))]
+    big = tiny_batch(agents, roadgraph=polys, T=6)
+    small = synth.make_batch(0, seed=12, S=1, N=12, R=3000, T=6)
+    b = _concat([big, small], 6)
+    g = H.run_rollout(b)
+    assert g["status"] == 0
+    gg = H.run_rollout(b, mode=wsim.MODE_GRAPH)
+    for k in ("traj", "ov", "off", "flags", "reward"):
+        assert np.array_equal(g[k].view(np.uint8), gg[k].view(np.uint8)), k
+    c = H.teacher_forced(b, g, [0, 1], range(b.T))
+    print("scene beyond the tile order limit", c)
+
+
 def test_every_launch_configuration_bit_identical(wsim):
     # Uneven scenes span the three size buckets; every single launch shape
     # and every split configuration of the scene-resident rollout must give
