@@ -384,9 +384,15 @@ class Rollout:
         return cnt
 
     def e2e(self, reps):
-        """The same rollout through the public API with the step's inputs
-        copied from pinned host memory and its result read back."""
-        torch, b = self.torch, self.b
+        """The same rollout through the public API with every step's inputs
+        copied from pinned host memory and its result (reward and flags
+        rows) read back, all inside the timed region.  Streamed: two sets of
+        device buffers; on a second stream the next step's inputs go up and
+        the last step's results come down while the current rollout runs
+        (a step waits for its inputs, a buffer is reused only after the
+        copies that read it).  Returns (ms per step streamed, ms per step
+        with copy, rollout and read-back in series, bytes up, bytes down)."""
+        torch, b, wsim = self.torch, self.b, self.wsim
         h_act = torch.as_tensor(b.actions).pin_memory()
         h_st = self.st0.data.cpu().pin_memory()
         h_rew = torch.empty((b.T, b.S), dtype=torch.int32).pin_memory()
@@ -398,8 +404,52 @@ class Rollout:
             self.sim.rollout(self.st, self.act, self.m, self.synth.T0, b.T, mode=self.mode)
             h_rew.copy_(self.m.reward, non_blocking=True)
             h_flags.copy_(self.m.flags, non_blocking=True)
-        ms = timed(torch, step, reps, warm=2)
-        return ms, h_act.numel() * 4 + h_st.numel() * 4, h_rew.numel() * 4 + h_flags.numel()
+        ms_serial = timed(torch, step, reps, warm=2)
+
+        acts = [self.act, torch.empty_like(self.act)]
+        sts = [self.st, self.st.clone()]
+        ms_ = [self.m, wsim.Metrics(b.N_tot, b.S, rows=b.T)]
+        comp, copy = torch.cuda.current_stream(), torch.cuda.Stream()
+        ev = lambda: torch.cuda.Event()
+        inputs_in, compute_done, results_out = [ev(), ev()], [ev(), ev()], [ev(), ev()]
+
+        def upload(k):  # inputs of step k into buffer k % 2, on the copy stream
+            q = k % 2
+            with torch.cuda.stream(copy):
+                copy.wait_event(compute_done[q])  # the rollout that read this buffer is done
+                acts[q].copy_(h_act, non_blocking=True)
+                sts[q].data.copy_(h_st, non_blocking=True)
+                inputs_in[q].record(copy)
+
+        def run(n):
+            upload(0)
+            for k in range(n):
+                q = k % 2
+                if k + 1 < n:
+                    upload(k + 1)
+                comp.wait_event(inputs_in[q])
+                comp.wait_event(results_out[q])  # the metric rows of step k-2 have been read
+                self.sim.rollout(sts[q], acts[q], ms_[q], self.synth.T0, b.T, mode=self.mode)
+                compute_done[q].record(comp)
+                with torch.cuda.stream(copy):
+                    copy.wait_event(compute_done[q])
+                    h_rew.copy_(ms_[q].reward, non_blocking=True)
+                    h_flags.copy_(ms_[q].flags, non_blocking=True)
+                    results_out[q].record(copy)
+            comp.wait_stream(copy)  # the last read-back inside the timed region
+
+        for q in range(2):  # events start recorded
+            compute_done[q].record(comp)
+            results_out[q].record(comp)
+        run(2)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(comp)
+        run(reps)
+        e1.record(comp)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        return ms, ms_serial, h_act.numel() * 4 + h_st.numel() * 4, h_rew.numel() * 4 + h_flags.numel()
 
     def close(self):
         assert self.sim.status() == 0
@@ -624,7 +674,7 @@ def main():
                               "value": N * T / (ms / 1e3), "counts": cnt}), flush=True)
         return
 
-    ms_e2e, h2d, d2h = R.e2e(args.steps)
+    ms_e2e, ms_e2e_serial, h2d, d2h = R.e2e(args.steps)
     modes = modes_leg(wsim, synth, torch, R, plain_scenes=256)
     # the batched result: the scene-resident rollout against the per-step
     # paths on the same B300, as ratios of agent-steps/s
@@ -661,7 +711,7 @@ def main():
                             / md1["plain_per_scene"]["value"]}
         R1.close()
 
-    ms, ms_e2e, units = combine_ranks(pg, [ms, ms_e2e], N * T, "cuda")
+    ms, ms_e2e, ms_e2e_serial, units = combine_ranks(pg, [ms, ms_e2e, ms_e2e_serial], N * T, "cuda")
     _, valid_units = combine_ranks(pg, [ms], int(b.valid.sum()) * T, "cuda")
     if rank != 0:
         return
@@ -673,7 +723,10 @@ def main():
         "data": "synthetic", "config": {**workload_config(synth, args.workload, S, b), "rollout_tuning": tune},
         "roofline": roof,
         "e2e": {"value": units / (ms_e2e / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                "d2h_bytes_per_step": int(d2h)},
+                "d2h_bytes_per_step": int(d2h),
+                "streamed": "next step's inputs up and last step's reward and flags down on a second stream "
+                            "during the rollout (two buffer sets)",
+                "serial_value": units / (ms_e2e_serial / 1e3)},
         "gpu_launches": args.steps * launches,
         "modes": modes,
         "bptt": bptt,
