@@ -116,6 +116,8 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="time the main path only (no mode comparison, end-to-end or CPU legs)")
     ap.add_argument("--expert-only", action="store_true", help="run only the expert leg on the workload (profiling)")
+    ap.add_argument("--observe-only", action="store_true",
+                    help="run only the observation and route-metric leg on the workload (profiling)")
     return ap.parse_args()
 
 
@@ -643,6 +645,11 @@ def main():
         out = expert_leg(wsim, synth, torch, R, args.steps)
         if rank == 0:
             print(json.dumps({"profile": True, "expert": out}), flush=True)
+        return
+    if args.observe_only:
+        out = observe_leg(wsim, synth, torch, R, args.steps)
+        if rank == 0:
+            print(json.dumps({"profile": True, "observe": out}), flush=True)
         return
     cnt = R.counts()  # work counters of one (untimed) rollout: the roofline numerator
     for _ in range(max(3, args.warmup)):
