@@ -611,7 +611,7 @@ int wsim_observe(wsim_ctx* c, const wsim_state* st, const uint8_t* observers, in
             for (int g = c->h_agent_off[i]; g < c->h_agent_off[i + 1]; ++g) sc[g] = i;
         int rc = WSIM_OK;
         if ((rc = dalloc(&c->pt_tile_off, S + 1)) || (rc = dalloc(&c->pt_cnt, toff[S])) ||
-            (rc = dalloc(&c->pt_box, toff[S])) || (rc = dalloc(&c->obs_list, N)) || (rc = dalloc(&c->obs_count, 1)) ||
+            (rc = dalloc(&c->pt_box, toff[S])) || (rc = dalloc(&c->obs_list, 2 * N)) || (rc = dalloc(&c->obs_count, 3)) ||
             (rc = dalloc(&c->scene_of, N))) {
             cudaFree(c->pt_tile_off);
             cudaFree(c->pt_cnt);

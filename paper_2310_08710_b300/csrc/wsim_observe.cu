@@ -11,7 +11,9 @@
 //
 // Roadgraph points are grouped in tiles of kPtTile consecutive points of a
 // scene (the roadgraph's own order, invalid points skipped in the box and
-// the count), built once per context.  Per observer one CTA:
+// the count), built once per context.  Per observer (one warp of
+// k_observe_warp when there are at least as many observers as that kernel
+// keeps warps resident and K <= kObwMaxK; else one CTA of k_observe):
 //   1. writes the other agents in the observer's frame;
 //   2. bounds the K-th key from above: a histogram of the tiles' upper bounds
 //      gives a key below which whole tiles already hold K points, and a
@@ -22,6 +24,8 @@
 //      list, the bound is lowered by bisection over the gathered tiles);
 //   4. sorts the (key, index) pairs (bitonic, shared memory) and writes the
 //      first K in the observer's frame.
+#include <climits>
+
 #include "wsim_phases.cuh"
 
 namespace wsim {
@@ -59,11 +63,17 @@ __global__ void __launch_bounds__(256) k_pt_tiles(const int32_t* rg_off, const i
     }
 }
 
-// Observers in a list (any order: every observer's output is its own).
+// Observers in a list, ascending within each warp's 32 agents (consecutive
+// entries mostly share a scene and its roadgraph in L1).
 __global__ void k_obs_list(const uint8_t* observers, const uint8_t* valid, int N_tot, int32_t* list, int32_t* count) {
-    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < N_tot; g += gridDim.x * blockDim.x) {
-        const bool obs = observers ? observers[g] != 0 : valid[g] != 0;
-        if (obs) list[atomicAdd(count, 1)] = g;
+    for (int base = blockIdx.x * blockDim.x; base < N_tot; base += gridDim.x * blockDim.x) {
+        const int g = base + threadIdx.x, lane = threadIdx.x & 31;
+        const bool obs = g < N_tot && (observers ? observers[g] != 0 : valid[g] != 0);
+        const unsigned bal = __ballot_sync(0xffffffffu, obs);
+        int pos = 0;
+        if (lane == 0 && bal) pos = atomicAdd(count, __popc(bal));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (obs) list[pos + __popc(bal & ((1u << lane) - 1u))] = g;
     }
 }
 
@@ -222,16 +232,70 @@ __device__ int count_points_within(const float4* box, const int32_t* cnt, int t0
     return block_sum(c, sm);
 }
 
+// The other agents of the observer's scene in its frame (position, heading
+// difference, velocity); slots j >= N, the observer itself and invalid agents
+// are zero and flagged invalid.  Threads j0, j0 + stride, ... of the caller.
+__device__ __forceinline__ void agents_in_frame(const StepArgs& A, int g, int a0, int N, int M, float xh, float xl,
+                                                float yh, float yl, float th, float tl, float c, float sn, int j0,
+                                                int stride, float* agents, uint8_t* agents_valid) {
+    for (int j = j0; j < M; j += stride) {
+        const int gj = a0 + j;
+        const bool ok = j < N && gj != g && A.valid[gj];
+        const size_t o = static_cast<size_t>(g) * M + j;
+        float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+        if (ok) {
+            const float dx = comp_diff(A.in.x[gj], A.in.x_lo[gj], xh, xl);
+            const float dy = comp_diff(A.in.y[gj], A.in.y_lo[gj], yh, yl);
+            v[0] = fmaf(c, dx, sn * dy);
+            v[1] = fmaf(-sn, dx, c * dy);
+            v[2] = turn_from(A.in.th[gj], th, tl - A.in.th_lo[gj]);  // heading difference mod 2 pi
+            const float vx = A.in.vx[gj], vy = A.in.vy[gj];
+            v[3] = fmaf(c, vx, sn * vy);
+            v[4] = fmaf(-sn, vx, c * vy);
+        }
+        agents_valid[o] = ok;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) agents[o * 5 + k] = v[k];
+    }
+}
+
+// The first `have` sorted items as the observer's K points in its frame;
+// slots k >= have get index -1.  Threads k0, k0 + stride, ... of the caller.
+__device__ __forceinline__ void write_points(const unsigned long long* item, int g, int K, int have, const float* rg_x,
+                                             const float* rg_y, float xh, float xl, float yh, float yl, float c,
+                                             float sn, int k0, int stride, float* rg_out, int32_t* rg_idx) {
+    for (int k = k0; k < K; k += stride) {
+        const size_t o = static_cast<size_t>(g) * K + k;
+        float ox = 0.f, oy = 0.f;
+        int idx = -1;
+        if (k < have) {
+            idx = static_cast<int>(item[k] & 0xffffffffull);
+            const float dx = comp_diff(rg_x[idx], 0.f, xh, xl);
+            const float dy = comp_diff(rg_y[idx], 0.f, yh, yl);
+            ox = fmaf(c, dx, sn * dy);
+            oy = fmaf(-sn, dx, c * dy);
+        }
+        rg_out[2 * o] = ox;
+        rg_out[2 * o + 1] = oy;
+        rg_idx[o] = idx;
+    }
+}
+
 __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const int32_t* list, const int32_t* count,
                                                          const int32_t* rg_off, const float* rg_x, const float* rg_y,
                                                          const uint8_t* rg_valid, const int32_t* tile_off,
                                                          const float4* box, const int32_t* cnt, int M, int K,
                                                          float* agents, uint8_t* agents_valid, float* rg_out,
-                                                         int32_t* rg_idx, const int32_t* scene_of) {
+                                                         int32_t* rg_idx, const int32_t* scene_of, int N_tot,
+                                                         int warp_min) {
     __shared__ ObsSmem sm;
-    const int n_obs = *count;
+    // Below warp_min observers this kernel observes them all; else only the
+    // warp kernel's overflow list (list + N_tot, count[2]).
+    const bool all = count[0] < warp_min;
+    const int n_obs = all ? count[0] : count[2];
+    const int32_t* obs_list = all ? list : list + N_tot;
     for (int q = blockIdx.x; q < n_obs; q += gridDim.x) {
-        const int g = list[q];
+        const int g = obs_list[q];
         const int s = scene_of[g];
         const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
         const float xh = A.in.x[g], xl = A.in.x_lo[g], yh = A.in.y[g], yl = A.in.y_lo[g];
@@ -239,25 +303,7 @@ __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const
         float c, sn;
         comp_sincos(th, tl, c, sn);
         // 1. Other agents in the observer's frame.
-        for (int j = threadIdx.x; j < M; j += kObsThreads) {
-            const int gj = a0 + j;
-            const bool ok = j < N && gj != g && A.valid[gj];
-            const size_t o = static_cast<size_t>(g) * M + j;
-            float v[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-            if (ok) {
-                const float dx = comp_diff(A.in.x[gj], A.in.x_lo[gj], xh, xl);
-                const float dy = comp_diff(A.in.y[gj], A.in.y_lo[gj], yh, yl);
-                v[0] = fmaf(c, dx, sn * dy);
-                v[1] = fmaf(-sn, dx, c * dy);
-                v[2] = turn_from(A.in.th[gj], th, tl - A.in.th_lo[gj]);  // heading difference mod 2 pi
-                const float vx = A.in.vx[gj], vy = A.in.vy[gj];
-                v[3] = fmaf(c, vx, sn * vy);
-                v[4] = fmaf(-sn, vx, c * vy);
-            }
-            agents_valid[o] = ok;
-#pragma unroll
-            for (int k = 0; k < 5; ++k) agents[o * 5 + k] = v[k];
-        }
+        agents_in_frame(A, g, a0, N, M, xh, xl, yh, yl, th, tl, c, sn, threadIdx.x, kObsThreads, agents, agents_valid);
         // 2. Upper bound of the K-th key from the tiles.
         const int r0 = rg_off[s], r1 = rg_off[s + 1];
         const int t0 = tile_off[s], nt = tile_off[s + 1] - t0;
@@ -352,22 +398,264 @@ __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const
                 __syncthreads();
             }
         }
-        for (int k = threadIdx.x; k < K; k += kObsThreads) {
-            const size_t o = static_cast<size_t>(g) * K + k;
-            float ox = 0.f, oy = 0.f;
-            int idx = -1;
-            if (k < want && k < n) {
-                idx = static_cast<int>(sm.item[k] & 0xffffffffull);
-                const float dx = comp_diff(rg_x[idx], 0.f, xh, xl);
-                const float dy = comp_diff(rg_y[idx], 0.f, yh, yl);
-                ox = fmaf(c, dx, sn * dy);
-                oy = fmaf(-sn, dx, c * dy);
-            }
-            rg_out[2 * o] = ox;
-            rg_out[2 * o + 1] = oy;
-            rg_idx[o] = idx;
-        }
+        write_points(sm.item, g, K, min(want, n), rg_x, rg_y, xh, xl, yh, yl, c, sn, threadIdx.x, kObsThreads, rg_out,
+                     rg_idx);
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Warp per observer (K <= kObwMaxK, at least as many observers as the
+// kernel has resident warps): the same four steps with a histogram, tile list
+// and point list private to each warp, so that no step waits at a block
+// barrier.  Warps take chunks of kObwChunk consecutive list entries from a
+// counter.  An observer whose gathered points would exceed kObwCap goes to the
+// block kernel's overflow list instead, which then observes it from the start.
+// The tile and point passes take four tiles per iteration (their loads in
+// flight together: one warp's chain of dependent loads is the cost).
+constexpr int kObwWarps = 8;
+constexpr int kObwCap = 512;    // gathered points per warp
+constexpr int kObwList = 128;   // candidate tiles per warp (more: every tile is re-tested)
+constexpr int kObwChunk = 1;   // observers taken from the counter at a time (larger chunks left a longer tail)
+constexpr int kObwMaxK = kObwCap / 2;
+constexpr int kObwU = 4;         // tiles whose loads a pass issues together
+static_assert(kObwCap * 2 >= (1 << kHistBits), "the key histogram shares the point list");
+
+struct ObwSmem {
+    unsigned long long item[kObwWarps][kObwCap];
+    int list[kObwWarps][kObwList];
+};
+
+// The top of key-histogram bucket b (the largest float bit pattern in it).
+__device__ __forceinline__ float bucket_top(int b) {
+    return __uint_as_float(((static_cast<uint32_t>(b) + 1u) << (32 - kHistBits)) - 1u);
+}
+
+__device__ __forceinline__ void warp_clear_hist(int* hist, int lane) {
+    int4* h4 = reinterpret_cast<int4*>(hist);
+#pragma unroll
+    for (int i = 0; i < (1 << kHistBits) / 128; ++i) h4[i * 32 + lane] = make_int4(0, 0, 0, 0);
+    __syncwarp();
+}
+
+// The first bucket of hist at which the running total reaches want > 0 (-1
+// if it never does); *upto = the total through that bucket.
+__device__ __forceinline__ int warp_crossing(const int* hist, int want, int lane, int* upto) {
+    constexpr int per = (1 << kHistBits) / 32;
+    const int4* h4 = reinterpret_cast<const int4*>(hist + lane * per);
+    int local = 0;
+#pragma unroll
+    for (int k = 0; k < per / 4; ++k) {
+        const int4 v = h4[k];
+        local += (v.x + v.y) + (v.z + v.w);
+    }
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned hit = __ballot_sync(kFull, incl >= want);
+    if (!hit) {
+        *upto = 0;
+        return -1;
+    }
+    const int src = __ffs(hit) - 1;
+    int b = 0, run = 0;
+    if (lane == src) {
+        run = incl - local;
+        b = lane * per;
+        while (run + hist[b] < want) run += hist[b++];
+        run += hist[b];
+    }
+    *upto = __shfl_sync(kFull, run, src);
+    return __shfl_sync(kFull, b, src);
+}
+
+// Visits the points of the candidate tiles (nl >= 0: the nl listed ones,
+// four tiles' loads in flight at a time; else every tile whose box can hold a
+// point with key <= tau): f(ok, key, r) on every lane for every tile, ok =
+// the lane's point exists and is valid (warp-uniform calls: f may use warp
+// votes).
+template <class F>
+__device__ __forceinline__ void warp_points(const int* tl, int nl, int nt, const float4* box, const int32_t* cnt,
+                                            int t0, int r0, int r1, const float* rg_x, const float* rg_y,
+                                            const uint8_t* rg_valid, float cx, float cy, float tau, int lane, F f) {
+    if (nl >= 0) {
+        for (int q = 0; q < nl; q += kObwU) {
+            float x[kObwU], y[kObwU];
+            bool ok[kObwU];
+            int r[kObwU];
+#pragma unroll
+            for (int u = 0; u < kObwU; ++u) {
+                const int t = q + u < nl ? tl[q + u] : -1;
+                r[u] = r0 + t * kPtTile + lane;
+                const bool in = t >= 0 && r[u] < r1;
+                const int rr = in ? r[u] : r0;  // a listed tile exists, so r0 < r1
+                x[u] = rg_x[rr];
+                y[u] = rg_y[rr];
+                const uint8_t v = rg_valid[rr];
+                ok[u] = in && v;
+            }
+#pragma unroll
+            for (int u = 0; u < kObwU; ++u) f(ok[u], obs_key(x[u], y[u], cx, cy), r[u]);
+        }
+    } else {
+        for (int t = 0; t < nt; ++t) {
+            if (cnt[t0 + t] == 0 || tile_lower(box[t0 + t], cx, cy) > tau) continue;
+            const int r = r0 + t * kPtTile + lane;
+            const bool ok = r < r1 && rg_valid[r];
+            f(ok, ok ? obs_key(rg_x[r], rg_y[r], cx, cy) : 0.f, r);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kObwWarps * 32, 5)
+    k_observe_warp(const StepArgs A, const int32_t* list, int32_t* count, int warp_min, const int32_t* rg_off,
+                   const float* rg_x, const float* rg_y, const uint8_t* rg_valid, const int32_t* tile_off,
+                   const float4* box, const int32_t* cnt, int M, int K, float* agents, uint8_t* agents_valid,
+                   float* rg_out, int32_t* rg_idx, const int32_t* scene_of) {
+    static_assert(kPtTile == 32, "a tile's points are the warp's lanes");
+    __shared__ ObwSmem sm;
+    const int n_obs = count[0];
+    if (n_obs < warp_min) return;  // the block kernel observes them all
+    int32_t* ovf_list = const_cast<int32_t*>(list) + A.N_tot;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long* item = sm.item[w];
+    int* hist = reinterpret_cast<int*>(item);  // free until the gather
+    int* tl = sm.list[w];
+    const unsigned below = (1u << lane) - 1u;
+    const int nchunks = (n_obs + kObwChunk - 1) / kObwChunk;
+    for (;;) {
+        int ch = 0;
+        if (lane == 0) ch = atomicAdd(count + 1, 1);
+        ch = __shfl_sync(kFull, ch, 0);
+        if (ch >= nchunks) break;
+        const int e0 = ch * kObwChunk, e1 = min(n_obs, e0 + kObwChunk);
+        for (int e = e0; e < e1; ++e) {
+            const int g = list[e];
+            const int s = scene_of[g];
+            const int a0 = A.agent_off[s], N = A.agent_off[s + 1] - a0;
+            const float xh = A.in.x[g], xl = A.in.x_lo[g], yh = A.in.y[g], yl = A.in.y_lo[g];
+            const float th = A.in.th[g], tlo = A.in.th_lo[g];
+            float c, sn;
+            comp_sincos(th, tlo, c, sn);
+            // 1. Other agents in the observer's frame.
+            agents_in_frame(A, g, a0, N, M, xh, xl, yh, yl, th, tlo, c, sn, lane, 32, agents, agents_valid);
+            // 2. Upper bound of the K-th key from the tiles, and the valid-point total.
+            const int r0 = rg_off[s], r1 = rg_off[s + 1];
+            const int t0 = tile_off[s], nt = tile_off[s + 1] - t0;
+            const float cx = __fadd_rn(xh, xl), cy = __fadd_rn(yh, yl);
+            warp_clear_hist(hist, lane);
+            int total = 0;
+            for (int tb = 0; tb < nt; tb += kObwU * 32) {
+                int n[kObwU];
+                float4 B[kObwU];
+#pragma unroll
+                for (int u = 0; u < kObwU; ++u) {
+                    const int t = min(tb + 32 * u + lane, nt - 1);
+                    n[u] = cnt[t0 + t];
+                    B[u] = box[t0 + t];
+                }
+#pragma unroll
+                for (int u = 0; u < kObwU; ++u) {
+                    if (tb + 32 * u + lane >= nt) n[u] = 0;
+                    total += n[u];
+                    if (n[u] > 0) {
+                        const float up = tile_upper(B[u], cx, cy);
+                        if (up < WSIM_INF) atomicAdd(&hist[__float_as_uint(up) >> (32 - kHistBits)], n[u]);
+                    }
+                }
+            }
+            total = __reduce_add_sync(kFull, total);
+            __syncwarp();
+            const int want = min(K, total);
+            int n = 0;
+            if (want > 0) {
+                int upto;
+                const int b = warp_crossing(hist, want, lane, &upto);
+                float tau = b < 0 ? WSIM_INF : bucket_top(b);
+                // 3. The tiles that can hold a point below tau (nl = -1: more than fit).
+                int nl = 0;
+                for (int tb = 0; tb < nt; tb += kObwU * 32) {
+                    bool in[kObwU];
+#pragma unroll
+                    for (int u = 0; u < kObwU; ++u) {
+                        const int t = min(tb + 32 * u + lane, nt - 1);
+                        const int c1 = cnt[t0 + t];
+                        const float4 B = box[t0 + t];
+                        in[u] = tb + 32 * u + lane < nt && c1 > 0 && tile_lower(B, cx, cy) <= tau;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kObwU; ++u) {
+                        const unsigned bal = __ballot_sync(kFull, in[u]);
+                        const int q = nl + __popc(bal & below);
+                        if (in[u] && q < kObwList) tl[q] = tb + 32 * u + lane;
+                        nl += __popc(bal);
+                    }
+                }
+                if (nl > kObwList) nl = -1;
+                __syncwarp();
+                // 4. A histogram of the candidate points' keys tightens tau.
+                warp_clear_hist(hist, lane);
+                warp_points(tl, nl, nt, box, cnt, t0, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
+                            [&](bool ok, float key, int) {
+                                if (ok && key <= tau && key < WSIM_INF)
+                                    atomicAdd(&hist[__float_as_uint(key) >> (32 - kHistBits)], 1);
+                            });
+                __syncwarp();
+                const int b2 = warp_crossing(hist, want, lane, &n);
+                __syncwarp();  // the histogram is read before the gather overwrites it
+                if (b2 >= 0) {
+                    tau = fminf(tau, bucket_top(b2));
+                } else {  // fewer finite keys than wanted below tau: keep tau
+                    int c1 = 0;
+                    warp_points(tl, nl, nt, box, cnt, t0, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
+                                [&](bool ok, float key, int) { c1 += ok && key <= tau; });
+                    n = __reduce_add_sync(kFull, c1);
+                }
+                if (n > kObwCap) {  // the block kernel observes this one
+                    if (lane == 0) ovf_list[atomicAdd(count + 2, 1)] = g;
+                    continue;
+                }
+                // 5. Gather the points with key <= tau (exactly n of them).
+                int base = 0;
+                warp_points(tl, nl, nt, box, cnt, t0, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
+                            [&](bool ok, float key, int r) {
+                                const bool in = ok && key <= tau;
+                                const unsigned bal = __ballot_sync(kFull, in);
+                                const int pos = base + __popc(bal & below);
+                                if (in && pos < kObwCap)
+                                    item[pos] = (static_cast<unsigned long long>(__float_as_uint(key)) << 32) |
+                                                static_cast<uint32_t>(r);
+                                base += __popc(bal);
+                            });
+                n = min(base, kObwCap);
+                // 6. Bitonic sort of (key, index), padded to a power of two.
+                int p2 = 1;
+                while (p2 < n) p2 <<= 1;
+                for (int i = n + lane; i < p2; i += 32) item[i] = ~0ull;
+                __syncwarp();
+                for (int size = 2; size <= p2; size <<= 1) {
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        for (int i = lane; i < p2 / 2; i += 32) {
+                            const int lo = 2 * i - (i & (stride - 1));
+                            const int hi = lo + stride;
+                            const bool up = (lo & size) == 0;
+                            const unsigned long long a = item[lo], bb = item[hi];
+                            if ((a > bb) == up) {
+                                item[lo] = bb;
+                                item[hi] = a;
+                            }
+                        }
+                        __syncwarp();
+                    }
+                }
+            }
+            // 7. The first K in the observer's frame.
+            write_points(item, g, K, min(want, n), rg_x, rg_y, xh, xl, yh, yl, c, sn, lane, 32, rg_out, rg_idx);
+            __syncwarp();
+        }
     }
 }
 
@@ -382,17 +670,29 @@ cudaError_t launch_observe(const StepArgs& a, const uint8_t* observers, int32_t*
                            const int32_t* tile_off, const float4* box, const int32_t* cnt, const int32_t* scene_of,
                            int M, int K, float* agents, uint8_t* agents_valid, float* rg, int32_t* rg_idx,
                            cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(int32_t), st);
+    // list[0, N): the observers, count[0] of them; count[1]: the warp kernel's
+    // chunk counter; list[N, 2N) and count[2]: its overflow to the block kernel.
+    cudaError_t e = cudaMemsetAsync(count, 0, 3 * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
-    const int nb = std::min((a.N_tot + 255) / 256, 4096);
-    if (a.N_tot > 0) k_obs_list<<<std::max(nb, 1), 256, 0, st>>>(observers, a.valid, a.N_tot, list, count);
-    int dev = 0, sms = 148, per = 1;
+    if (a.N_tot == 0) return cudaSuccess;
+    int dev = 0, sms = 148, per = 1, perw = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int nb = std::min((a.N_tot + 255) / 256, 4096);
+    k_obs_list<<<std::max(nb, 1), 256, 0, st>>>(observers, a.valid, a.N_tot, list, count);
+    // The warp kernel takes over from as many observers as it has resident warps.
+    int warp_min = INT_MAX;
+    if (K <= kObwMaxK) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perw, k_observe_warp, kObwWarps * 32, 0);
+        warp_min = sms * std::max(perw, 1) * kObwWarps;
+        k_observe_warp<<<sms * std::max(perw, 1), kObwWarps * 32, 0, st>>>(
+            a, list, count, warp_min, rg_off, rg_x, rg_y, rg_valid, tile_off, box, cnt, M, K, agents, agents_valid,
+            rg, rg_idx, scene_of);
+    }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_observe, kObsThreads, 0);
-    const int grid = sms * std::max(per, 1);
-    k_observe<<<grid, kObsThreads, 0, st>>>(a, list, count, rg_off, rg_x, rg_y, rg_valid, tile_off, box, cnt, M, K,
-                                             agents, agents_valid, rg, rg_idx, scene_of);
+    k_observe<<<sms * std::max(per, 1), kObsThreads, 0, st>>>(a, list, count, rg_off, rg_x, rg_y, rg_valid, tile_off,
+                                                              box, cnt, M, K, agents, agents_valid, rg, rg_idx,
+                                                              scene_of, a.N_tot, warp_min);
     return cudaGetLastError();
 }
 

@@ -4,7 +4,10 @@ Agents in the observer's frame within float32 tolerances; the K nearest
 roadgraph point indices bit-exact (both sides rank by the same float32 key,
 ties to the lower index) and their coordinates in the observer's frame
 within tolerance; every agent observing and an observer subset; K above a
-scene's point count; the 1024-scene batch sampled.
+scene's point count; the 1024-scene batch sampled; batches with more
+observers than the warp-per-observer kernel has resident warps (that kernel
+then observes them), with a dense cluster of tied points beyond a warp's
+point list and more candidate tiles than a warp lists.
 """
 import numpy as np
 import pytest
@@ -114,6 +117,53 @@ def test_batch_1024x128_sampled_observers(wsim):
     oo["rg_idx"] = np.where(oo["rg_idx"] >= 0, rg_map[np.maximum(oo["rg_idx"], 0)], -1)
     go_sub = {k: v[ag] for k, v in go.items()}
     _check(go_sub, oo, np.nonzero(sub_obs)[0], 128, 256)
+
+
+def _sampled_check(go, b, rows, scenes, M, K, observers=None):
+    sub = b.subset(scenes)
+    ag = np.concatenate([np.arange(b.agent_off[s], b.agent_off[s + 1]) for s in scenes])
+    sub_obs = None if observers is None else observers[ag]
+    oo = oracle.Oracle(sub).observe(state64(rows, ag), M, K, sub_obs)
+    rg_map = np.concatenate([np.arange(b.rg_off[s], b.rg_off[s + 1]) for s in scenes])
+    oo["rg_idx"] = np.where(oo["rg_idx"] >= 0, rg_map[np.maximum(oo["rg_idx"], 0)], -1)
+    go_sub = {k: v[ag] for k, v in go.items()}
+    obs = np.nonzero(sub.valid if sub_obs is None else sub_obs)[0]
+    return _check(go_sub, oo, obs, M, K)
+
+
+def test_every_agent_of_64_scenes_warp_per_observer(wsim):
+    # 64 scenes x 128 agents, 20k-point roadgraphs: ~7,400 observers, more than
+    # the warp kernel's resident warps.  Scene 0: 600 points stacked 0.5 m
+    # ahead of its ego (the K-th key shared by more points than a warp
+    # gathers: that observer goes to the block kernel).  Scene 1: one point of
+    # each of 200 tiles within 0.3-0.5 m of its ego (more candidate tiles than a
+    # warp lists: every tile re-tested).
+    b = synth.make_batch(1, seed=7, scenes=range(64))
+    for s in (0, 1):
+        g0 = b.agent_off[s]
+        assert b.valid[g0]
+    xe, ye = float(b.x[b.agent_off[0]]), float(b.y[b.agent_off[0]])
+    r0 = int(b.rg_off[0])
+    b.rg_x[r0 + 100:r0 + 700] = np.float32(xe + 0.5)
+    b.rg_y[r0 + 100:r0 + 700] = np.float32(ye)
+    b.rg_valid[r0 + 100:r0 + 700] = 1
+    xe1, ye1 = float(b.x[b.agent_off[1]]), float(b.y[b.agent_off[1]])
+    r1 = int(b.rg_off[1])
+    for t in range(200):
+        ang, rad = 2 * np.pi * t / 200, 0.3 + 0.001 * t
+        b.rg_x[r1 + 32 * t] = np.float32(xe1 + rad * np.cos(ang))
+        b.rg_y[r1 + 32 * t] = np.float32(ye1 + rad * np.sin(ang))
+        b.rg_valid[r1 + 32 * t] = 1
+    rows = np.zeros((10, b.N_tot), np.float32)
+    rows[0], rows[1], rows[4], rows[6], rows[7] = b.x, b.y, b.th, b.vx, b.vy
+    assert b.valid.sum() > 148 * 40  # more observers than the warp kernel keeps resident (5 x 8 warps per SM)
+    for K in (64, 256):
+        go = _gpu_observe(wsim, b, rows, 128, K)
+        # the ego of scene 0 sees the first K of the 600 tied points
+        assert np.array_equal(go["rg_idx"][b.agent_off[0]][:K], np.arange(r0 + 100, r0 + 100 + K))
+        err = _sampled_check(go, b, rows, [0, 1, 17, 63], 128, K)
+        print("K", K, "max point error", err)
+        assert (go["rg_idx"][b.valid == 0] == -1).all()
 
 
 def test_observe_argument_limits(wsim):
