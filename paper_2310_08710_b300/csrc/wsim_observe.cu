@@ -12,8 +12,8 @@
 // Roadgraph points are grouped in tiles of kPtTile consecutive points of a
 // scene (the roadgraph's own order, invalid points skipped in the box and
 // the count), built once per context.  Per observer (one warp of
-// k_observe_warp when there are at least as many observers as that kernel
-// keeps warps resident and K <= kObwMaxK; else one CTA of k_observe):
+// k_observe_warp when K <= kObwMaxK and the observers number at least a few
+// per warp that kernel keeps resident; else one CTA of k_observe):
 //   1. writes the other agents in the observer's frame;
 //   2. bounds the K-th key from above: a histogram of the tiles' upper bounds
 //      gives a key below which whole tiles already hold K points, and a
@@ -405,8 +405,8 @@ __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const
 }
 
 // ---------------------------------------------------------------------------
-// Warp per observer (K <= kObwMaxK, at least as many observers as the
-// kernel has resident warps): the same four steps with a histogram, tile list
+// Warp per observer (K <= kObwMaxK, at least 4 to 11 observers per resident
+// warp, growing with K): the same four steps with a histogram, tile list
 // and point list private to each warp, so that no step waits at a block
 // barrier.  Warps take chunks of kObwChunk consecutive list entries from a
 // counter.  An observer whose gathered points would exceed kObwCap goes to the
@@ -680,11 +680,14 @@ cudaError_t launch_observe(const StepArgs& a, const uint8_t* observers, int32_t*
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nb = std::min((a.N_tot + 255) / 256, 4096);
     k_obs_list<<<std::max(nb, 1), 256, 0, st>>>(observers, a.valid, a.N_tot, list, count);
-    // The warp kernel takes over from as many observers as it has resident warps.
+    // The warp kernel takes over from a few observers per resident warp: each
+    // warp's observer is a long serial chain, so with fewer the block kernel's
+    // finer grain wins.  Measured crossovers on 30k-point scenes: about 4
+    // observers per warp at K = 64 and 11 at K = 256 (linear in between).
     int warp_min = INT_MAX;
     if (K <= kObwMaxK) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perw, k_observe_warp, kObwWarps * 32, 0);
-        warp_min = sms * std::max(perw, 1) * kObwWarps;
+        warp_min = sms * std::max(perw, 1) * kObwWarps * (4 + std::max(0, K - 64) * 7 / 192);
         k_observe_warp<<<sms * std::max(perw, 1), kObwWarps * 32, 0, st>>>(
             a, list, count, warp_min, rg_off, rg_x, rg_y, rg_valid, tile_off, box, cnt, M, K, agents, agents_valid,
             rg, rg_idx, scene_of);

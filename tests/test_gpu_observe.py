@@ -131,17 +131,17 @@ def _sampled_check(go, b, rows, scenes, M, K, observers=None):
     return _check(go_sub, oo, obs, M, K)
 
 
-def test_every_agent_of_64_scenes_warp_per_observer(wsim):
-    # 64 scenes x 128 agents, 20k-point roadgraphs: ~7,400 observers, more than
-    # the warp kernel's resident warps.  Scene 0: 600 points stacked 0.5 m
-    # ahead of its ego (the K-th key shared by more points than a warp
+def test_every_agent_of_640_scenes_warp_per_observer(wsim):
+    # 640 scenes x 128 agents, 20k-point roadgraphs: ~74,000 observers, more
+    # than the warp kernel's threshold at K = 64 and 256 (4 and 11 observers
+    # per resident warp, 5 x 8 warps per SM).  Scene 0: 600 points stacked
+    # 0.5 m ahead of its ego (the K-th key shared by more points than a warp
     # gathers: that observer goes to the block kernel).  Scene 1: one point of
     # each of 200 tiles within 0.3-0.5 m of its ego (more candidate tiles than a
     # warp lists: every tile re-tested).
-    b = synth.make_batch(1, seed=7, scenes=range(64))
+    b = synth.make_batch(1, seed=7, scenes=range(640))
     for s in (0, 1):
-        g0 = b.agent_off[s]
-        assert b.valid[g0]
+        assert b.valid[b.agent_off[s]]
     xe, ye = float(b.x[b.agent_off[0]]), float(b.y[b.agent_off[0]])
     r0 = int(b.rg_off[0])
     b.rg_x[r0 + 100:r0 + 700] = np.float32(xe + 0.5)
@@ -156,12 +156,12 @@ def test_every_agent_of_64_scenes_warp_per_observer(wsim):
         b.rg_valid[r1 + 32 * t] = 1
     rows = np.zeros((10, b.N_tot), np.float32)
     rows[0], rows[1], rows[4], rows[6], rows[7] = b.x, b.y, b.th, b.vx, b.vy
-    assert b.valid.sum() > 148 * 40  # more observers than the warp kernel keeps resident (5 x 8 warps per SM)
+    assert b.valid.sum() > 148 * 40 * 11
     for K in (64, 256):
         go = _gpu_observe(wsim, b, rows, 128, K)
         # the ego of scene 0 sees the first K of the 600 tied points
         assert np.array_equal(go["rg_idx"][b.agent_off[0]][:K], np.arange(r0 + 100, r0 + 100 + K))
-        err = _sampled_check(go, b, rows, [0, 1, 17, 63], 128, K)
+        err = _sampled_check(go, b, rows, [0, 1, 17, 639], 128, K)
         print("K", K, "max point error", err)
         assert (go["rg_idx"][b.valid == 0] == -1).all()
 
