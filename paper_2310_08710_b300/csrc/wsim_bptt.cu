@@ -47,7 +47,7 @@ struct AdjSmem {
     float cx[kMaxN], cy[kMaxN], cth[kMaxN];  // an agent's overlap term, partner's share
     float lx[kMaxN], ly[kMaxN];              // the current step's logged positions
     int16_t pidx[kMaxN];                     // ... and the partner (-1: none)
-    uint8_t plist[NWb][kMaxN];               // each warp's list of a row's partners (row_partners)
+    uint8_t pli[NWb][kMaxN + 32], plj[NWb][kMaxN + 32];  // each warp's pending pairs (PairQueue)
     double total;
 };
 
@@ -147,43 +147,98 @@ __device__ __forceinline__ bool pair_far(const AgentSmem& sm, int i, int j, floa
     return cut > 0.f && fmaf(dx, dx, dy * dy) > 2.f * r * r;
 }
 
-// The valid partners j > i of row i that pair_far does not rule out, in
-// increasing order, into list (warp; returns their count, same in every
-// lane).  The pair loops then run over full lanes.
-__device__ __forceinline__ int row_partners(const AgentSmem& sm, int N, int i, int lane, float cut, uint8_t* list) {
-    int n = 0;
+// A warp's pending pairs (i, j), j > i, in row order and increasing j within
+// a row: the valid partners that pair_far does not rule out of each of the
+// warp's rows, appended row by row and evaluated 32 at a time, so that the
+// pair loops run over full lanes however few partners a row has.  At most
+// 31 pairs wait when a row is appended, so kMaxN + 32 entries hold them.
+struct PairQueue {
+    uint8_t* pi;
+    uint8_t* pj;
+    int n;
+};
+
+__device__ __forceinline__ void append_row(const AgentSmem& sm, int N, int i, int lane, float cut, PairQueue& q,
+                                           Counts& cnt) {
+    const int n0 = q.n;
     for (int jb = i + 1; jb < N; jb += 32) {
         const int j = jb + lane;
         const bool keep = j < N && sm.valid[j] && !pair_far(sm, i, j, cut);
         const unsigned m = __ballot_sync(kFull, keep);
-        if (keep) list[n + __popc(m & ((1u << lane) - 1u))] = static_cast<uint8_t>(j);
-        n += __popc(m);
+        if (keep) {
+            const int k = q.n + __popc(m & ((1u << lane) - 1u));
+            q.pi[k] = static_cast<uint8_t>(i);
+            q.pj[k] = static_cast<uint8_t>(j);
+        }
+        q.n += __popc(m);
     }
+    if (lane == 0) cnt.pairs += 2 * (q.n - n0);  // SAT evaluations, two per pair as in the overlap rows
     __syncwarp();
-    return n;
 }
 
-// Loss terms of the current state of agent i (warp): d_i^2 plus the
-// penalty of its pairs with j > i.  Same value in every lane.  list: the
-// warp's partner list.
-__device__ float loss_agent(const AgentSmem& sm, const AdjSmem& adj, int N, int i, int lane, float lambda,
-                            float tau, uint8_t* list, Counts& cnt) {
-    float acc = 0.f;
-    const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
-    const int np = row_partners(sm, N, i, lane, pair_cut(tau), list);
-    if (lane == 0) cnt.pairs += 2 * np;  // SAT evaluations, two per pair as in the overlap rows
-    for (int q = lane; q < np; q += 32) {
-        const int j = list[q];
-        const float dx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
-        const float dy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
-        const float d = sat_depth(dx, dy, sm.c[i], sm.s[i], sm.hl[i], sm.hw[i], sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
-        acc += lambda * tau * softplus_f(d / tau);
+// Drops the first 32 pairs (after they were evaluated).
+__device__ __forceinline__ void pop32(PairQueue& q, int lane) {
+    for (int k = lane; k < q.n - 32; k += 32) {  // lane l moves entries l + 32 c in increasing c
+        q.pi[k] = q.pi[k + 32];
+        q.pj[k] = q.pj[k + 32];
     }
+    q.n -= 32;
+    __syncwarp();
+}
+
+// Sum of v over the lanes of one row's run [k0, k1) of a batch (fixed
+// shuffle tree; lanes outside the run give 0); the run ends at *k1.
+__device__ __forceinline__ float run_sum(float v, bool in_run) {
+    v = in_run ? v : 0.f;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
-    __syncwarp();  // the list is rewritten by the warp's next row
-    const float ex = (xih - adj.lx[i]) + xil, ey = (yih - adj.ly[i]) + yil;
-    return acc + fmaf(ex, ex, ey * ey);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// Loss terms of the current state (warp per row, rows warp, warp + NWb, ...):
+// adj.part[i] = d_i^2 plus the penalty of i's pairs with j > i, the pairs
+// evaluated in batches of 32 of the warp's queue and each batch's share of
+// a row added to adj.part[i] by one row-run sum (a fixed order).
+__device__ void loss_rows_warp(const AgentSmem& sm, AdjSmem& adj, int N, int lane, int warp, float lambda, float tau,
+                               Counts& cnt) {
+    PairQueue q{adj.pli[warp], adj.plj[warp], 0};
+    const float cut = pair_cut(tau);
+    auto flush = [&](int m) {
+        const int k = lane < m ? lane : 0;
+        const int i = q.pi[k], j = q.pj[k];
+        float term = 0.f;
+        if (lane < m) {
+            const float dx = comp_diff(sm.xh[j], sm.xl[j], sm.xh[i], sm.xl[i]);
+            const float dy = comp_diff(sm.yh[j], sm.yl[j], sm.yh[i], sm.yl[i]);
+            const float d = sat_depth(dx, dy, sm.c[i], sm.s[i], sm.hl[i], sm.hw[i], sm.c[j], sm.s[j], sm.hl[j],
+                                      sm.hw[j]);
+            term = lambda * tau * softplus_f(d / tau);
+        }
+        for (int k0 = 0; k0 < m;) {  // one run of equal rows at a time
+            const int r = __shfl_sync(kFull, i, k0);
+            const unsigned run = __ballot_sync(kFull, lane < m && i == r);
+            const float v = run_sum(term, (run >> lane) & 1u);
+            if (lane == 0) adj.part[r] += v;
+            k0 = 32 - __clz(run);
+        }
+        __syncwarp();
+    };
+    for (int i = warp; i < N; i += NWb) {
+        if (!sm.valid[i]) {
+            if (lane == 0) adj.part[i] = 0.f;
+            continue;
+        }
+        if (lane == 0) {
+            const float ex = (sm.xh[i] - adj.lx[i]) + sm.xl[i], ey = (sm.yh[i] - adj.ly[i]) + sm.yl[i];
+            adj.part[i] = fmaf(ex, ex, ey * ey);
+        }
+        append_row(sm, N, i, lane, cut, q, cnt);
+        while (q.n >= 32) {
+            flush(32);
+            pop32(q, lane);
+        }
+    }
+    if (q.n > 0) flush(q.n);
 }
 
 // Adds dL/d(x, y, theta) of every valid agent's loss terms at the current
@@ -211,44 +266,57 @@ __device__ void loss_adjoint(const AgentSmem& sm, AdjSmem& adj, float* wbuf, int
     float* bx = wbuf + static_cast<size_t>(warp) * 3 * kMaxN;
     float* by = bx + kMaxN;
     float* bth = by + kMaxN;
-    uint8_t* list = adj.plist[warp];
+    PairQueue q{adj.pli[warp], adj.plj[warp], 0};
     const float cut = pair_cut(tau);
     for (int j = lane; j < N; j += 32) bx[j] = by[j] = bth[j] = 0.f;
     __syncwarp();
+    // A batch of m queued pairs: lane k evaluates pair k; the partner's terms
+    // go to the warp's buffer one row run after another (a run's partners
+    // are distinct), the row's by a run sum into adj (lane 0).
+    auto flush = [&](int m) {
+        const int k = lane < m ? lane : 0;
+        const int i = q.pi[k], j = q.pj[k];
+        float w = 0.f;
+        SatGrad G{};
+        if (lane < m) {
+            const float dx = comp_diff(sm.xh[j], sm.xl[j], sm.xh[i], sm.xl[i]);
+            const float dy = comp_diff(sm.yh[j], sm.yl[j], sm.yh[i], sm.yl[i]);
+            G = sat_grad(dx, dy, sm.c[i], sm.s[i], sm.hl[i], sm.hw[i], sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
+            w = lambda * sigmoid_f(G.d / tau);
+        }
+        for (int k0 = 0; k0 < m;) {
+            const int r = __shfl_sync(kFull, i, k0);
+            const unsigned run = __ballot_sync(kFull, lane < m && i == r);
+            const bool in = (run >> lane) & 1u;
+            if (in) {  // j is the second box of the pair
+                bx[j] += w * G.ddx;
+                by[j] += w * G.ddy;
+                bth[j] += w * G.dthB;
+            }
+            const float gx = run_sum(-w * G.ddx, in), gy = run_sum(-w * G.ddy, in), gth = run_sum(w * G.dthA, in);
+            if (lane == 0) {  // i the first
+                adj.x[r] += wl * gx;
+                adj.y[r] += wl * gy;
+                adj.th[r] += wl * gth;
+            }
+            k0 = 32 - __clz(run);
+            __syncwarp();  // the next run may update the same partners
+        }
+    };
     for (int i = warp; i < N; i += NWb) {
         if (!sm.valid[i]) continue;
-        const float xih = sm.xh[i], xil = sm.xl[i], yih = sm.yh[i], yil = sm.yl[i];
-        const float ci = sm.c[i], si = sm.s[i], hli = sm.hl[i], hwi = sm.hw[i];
-        float gx = 0.f, gy = 0.f, gth = 0.f;
-        const int np = row_partners(sm, N, i, lane, cut, list);
-        if (lane == 0) cnt.pairs += 2 * np;
-        for (int q = lane; q < np; q += 32) {
-            const int j = list[q];
-            const float dx = comp_diff(sm.xh[j], sm.xl[j], xih, xil);
-            const float dy = comp_diff(sm.yh[j], sm.yl[j], yih, yil);
-            const SatGrad G = sat_grad(dx, dy, ci, si, hli, hwi, sm.c[j], sm.s[j], sm.hl[j], sm.hw[j]);
-            const float w = lambda * sigmoid_f(G.d / tau);
-            gx -= w * G.ddx;  // i is the first box of the pair
-            gy -= w * G.ddy;
-            gth += w * G.dthA;
-            bx[j] += w * G.ddx;  // j the second
-            by[j] += w * G.ddy;
-            bth[j] += w * G.dthB;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            gx += __shfl_xor_sync(kFull, gx, o);
-            gy += __shfl_xor_sync(kFull, gy, o);
-            gth += __shfl_xor_sync(kFull, gth, o);
-        }
         if (lane == 0) {
-            const float ex = (xih - adj.lx[i]) + xil, ey = (yih - adj.ly[i]) + yil;
-            adj.x[i] += wl * (gx + 2.f * ex);
-            adj.y[i] += wl * (gy + 2.f * ey);
-            adj.th[i] += wl * gth;
+            const float ex = (sm.xh[i] - adj.lx[i]) + sm.xl[i], ey = (sm.yh[i] - adj.ly[i]) + sm.yl[i];
+            adj.x[i] += wl * (2.f * ex);
+            adj.y[i] += wl * (2.f * ey);
         }
-        __syncwarp();  // the next row's lanes update entries of this row's lanes
+        append_row(sm, N, i, lane, cut, q, cnt);
+        while (q.n >= 32) {
+            flush(32);
+            pop32(q, lane);
+        }
     }
+    if (q.n > 0) flush(q.n);
     __syncthreads();
     for (int j = first_agent(); j < N; j += kAgentStride) {  // same mapping as transition_adjoint
         float sx = 0.f, sy = 0.f, st = 0.f;
@@ -415,11 +483,7 @@ __device__ void transition_adjoint(AgentSmem& sm, AdjSmem& adj, const BpttArgs& 
 // in adj.lx / adj.ly): each warp's rows into adj.part, then (after the
 // caller's barrier) warp 0 adds them in a fixed order; see loss_sum.
 __device__ __forceinline__ void loss_rows(const AgentSmem& sm, AdjSmem& adj, const BpttArgs& B, int N, Counts& cnt) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int i = warp; i < N; i += NWb) {
-        const float v = sm.valid[i] ? loss_agent(sm, adj, N, i, lane, B.lambda, B.tau, adj.plist[warp], cnt) : 0.f;
-        if (lane == 0) adj.part[i] = v;
-    }
+    loss_rows_warp(sm, adj, N, threadIdx.x & 31, threadIdx.x >> 5, B.lambda, B.tau, cnt);
 }
 // The step's loss in a fixed order: lane-strided sums, then a fixed shuffle tree.
 __device__ __forceinline__ void loss_sum(AdjSmem& adj, int N) {
