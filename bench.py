@@ -80,7 +80,7 @@ def source_hash(names=ROLLOUT_SOURCES) -> str:
 
 def recorded_traffic(kernel: str, workload: str):
     """DRAM bytes per launch from the last ncu capture of this kernel on this
-    workload, if it is of this build (else None)."""
+    workload, if it was taken on the current kernel sources (else None)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel, {}).get(workload)
