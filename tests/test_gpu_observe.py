@@ -138,7 +138,8 @@ def test_every_agent_of_640_scenes_warp_per_observer(wsim):
     # 0.5 m ahead of its ego (the K-th key shared by more points than a warp
     # gathers: that observer goes to the block kernel).  Scene 1: one point of
     # each of 200 tiles within 0.3-0.5 m of its ego (more candidate tiles than a
-    # warp lists: every tile re-tested).
+    # warp lists: every tile re-tested).  Scenes 2 and 3: no valid point, and
+    # fewer valid points than K.
     b = synth.make_batch(1, seed=7, scenes=range(640))
     for s in (0, 1):
         assert b.valid[b.agent_off[s]]
@@ -154,6 +155,12 @@ def test_every_agent_of_640_scenes_warp_per_observer(wsim):
         b.rg_x[r1 + 32 * t] = np.float32(xe1 + rad * np.cos(ang))
         b.rg_y[r1 + 32 * t] = np.float32(ye1 + rad * np.sin(ang))
         b.rg_valid[r1 + 32 * t] = 1
+    # Scene 2: no valid roadgraph point (every slot -1).  Scene 3: 40 valid
+    # points, fewer than K (the rest of the slots -1).
+    b.rg_valid[b.rg_off[2]:b.rg_off[3]] = 0
+    r3 = int(b.rg_off[3])
+    b.rg_valid[r3 + 40:b.rg_off[4]] = 0
+    b.rg_valid[r3:r3 + 40] = 1
     rows = np.zeros((10, b.N_tot), np.float32)
     rows[0], rows[1], rows[4], rows[6], rows[7] = b.x, b.y, b.th, b.vx, b.vy
     assert b.valid.sum() > 148 * 40 * 11
@@ -161,7 +168,12 @@ def test_every_agent_of_640_scenes_warp_per_observer(wsim):
         go = _gpu_observe(wsim, b, rows, 128, K)
         # the ego of scene 0 sees the first K of the 600 tied points
         assert np.array_equal(go["rg_idx"][b.agent_off[0]][:K], np.arange(r0 + 100, r0 + 100 + K))
-        err = _sampled_check(go, b, rows, [0, 1, 17, 639], 128, K)
+        obs2 = np.arange(b.agent_off[2], b.agent_off[3])[b.valid[b.agent_off[2]:b.agent_off[3]] != 0]
+        assert (go["rg_idx"][obs2] == -1).all()
+        obs3 = np.arange(b.agent_off[3], b.agent_off[4])[b.valid[b.agent_off[3]:b.agent_off[4]] != 0]
+        assert (np.sort(go["rg_idx"][obs3][:, :40], axis=1) == np.arange(r3, r3 + 40)).all()
+        assert (go["rg_idx"][obs3][:, 40:] == -1).all()
+        err = _sampled_check(go, b, rows, [0, 1, 2, 3, 17, 639], 128, K)
         print("K", K, "max point error", err)
         assert (go["rg_idx"][b.valid == 0] == -1).all()
 
