@@ -49,7 +49,7 @@ struct wsim_ctx {
     float* route_rf = nullptr;  // [N_tot] each route's largest segment length over route_h
     unsigned long long* counters = nullptr;
     // observation: roadgraph point tiles, observer list, agent -> scene (built on first use)
-    int32_t *pt_tile_off = nullptr, *pt_cnt = nullptr, *obs_list = nullptr, *obs_count = nullptr,
+    int32_t *pt_tile_off = nullptr, *pt_start = nullptr, *pt_cnt = nullptr, *obs_list = nullptr, *obs_count = nullptr,
             *scene_of = nullptr;
     float4* pt_box = nullptr;
     float* tmp = nullptr;  // ping-pong state, 10 x N_tot
@@ -603,36 +603,43 @@ int wsim_observe(wsim_ctx* c, const wsim_state* st, const uint8_t* observers, in
     c->last = s;
     if (!c->pt_box) {  // first call: point tiles and the agent -> scene map
         const int S = c->S, N = c->N_tot;
-        std::vector<int32_t> ro(S + 1), toff(S + 1, 0), sc(std::max(N, 1));
-        CK(cudaMemcpyAsync(ro.data(), c->b.rg_off, sizeof(int32_t) * (S + 1), cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        for (int i = 0; i < S; ++i) toff[i + 1] = toff[i] + (ro[i + 1] - ro[i] + kPtTile - 1) / kPtTile;
+        std::vector<int32_t> cnt(S), toff(S + 1, 0), sc(std::max(N, 1));
+        int32_t* dcnt = nullptr;
+        int rc = dalloc(&dcnt, S);
+        if (rc) return rc;
+        // tiles per scene (runs of one polyline, at most kPtTile points each)
+        cudaError_t e = launch_pt_count(c->b.rg_off, c->b.rg_poly, S, dcnt, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(cnt.data(), dcnt, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(dcnt);
+        CK(e);
+        for (int i = 0; i < S; ++i) toff[i + 1] = toff[i] + cnt[i];
         for (int i = 0; i < S; ++i)
             for (int g = c->h_agent_off[i]; g < c->h_agent_off[i + 1]; ++g) sc[g] = i;
-        int rc = WSIM_OK;
-        if ((rc = dalloc(&c->pt_tile_off, S + 1)) || (rc = dalloc(&c->pt_cnt, toff[S])) ||
-            (rc = dalloc(&c->pt_box, toff[S])) || (rc = dalloc(&c->obs_list, 2 * N)) || (rc = dalloc(&c->obs_count, 3)) ||
-            (rc = dalloc(&c->scene_of, N))) {
+        if ((rc = dalloc(&c->pt_tile_off, S + 1)) || (rc = dalloc(&c->pt_start, toff[S] + 1)) ||
+            (rc = dalloc(&c->pt_cnt, toff[S])) || (rc = dalloc(&c->pt_box, toff[S])) ||
+            (rc = dalloc(&c->obs_list, 2 * N)) || (rc = dalloc(&c->obs_count, 3)) || (rc = dalloc(&c->scene_of, N))) {
             cudaFree(c->pt_tile_off);
+            cudaFree(c->pt_start);
             cudaFree(c->pt_cnt);
             cudaFree(c->pt_box);
             cudaFree(c->obs_list);
             cudaFree(c->obs_count);
             cudaFree(c->scene_of);
-            c->pt_tile_off = c->pt_cnt = c->obs_list = c->obs_count = c->scene_of = nullptr;
+            c->pt_tile_off = c->pt_start = c->pt_cnt = c->obs_list = c->obs_count = c->scene_of = nullptr;
             c->pt_box = nullptr;
             return rc;
         }
         CK(cudaMemcpyAsync(c->pt_tile_off, toff.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, s));
         CK(cudaMemcpyAsync(c->scene_of, sc.data(), sizeof(int32_t) * N, cudaMemcpyHostToDevice, s));
-        CK(launch_pt_tiles(c->b.rg_off, c->pt_tile_off, c->b.rg_x, c->b.rg_y, c->b.rg_valid, S, c->pt_box, c->pt_cnt,
-                           s));
+        CK(launch_pt_tiles(c->b.rg_off, c->b.rg_poly, c->pt_tile_off, c->b.rg_x, c->b.rg_y, c->b.rg_valid, S,
+                           c->pt_start, c->pt_box, c->pt_cnt, s));
         CK(cudaStreamSynchronize(s));
     }
     StepArgs a = base_args(c);
     a.in = cstate(st);
-    CK(launch_observe(a, observers, c->obs_list, c->obs_count, c->b.rg_off, c->b.rg_x, c->b.rg_y, c->b.rg_valid,
-                      c->pt_tile_off, c->pt_box, c->pt_cnt, c->scene_of, M, K, agents, agents_valid, rg, rg_idx, s));
+    CK(launch_observe(a, observers, c->obs_list, c->obs_count, c->b.rg_x, c->b.rg_y, c->b.rg_valid, c->pt_tile_off,
+                      c->pt_start, c->pt_box, c->pt_cnt, c->scene_of, M, K, agents, agents_valid, rg, rg_idx, s));
     return WSIM_OK;
 }
 
@@ -950,6 +957,7 @@ void wsim_destroy(wsim_ctx* c) {
     cudaFree(c->status);
     cudaFree(c->counters);
     cudaFree(c->pt_tile_off);
+    cudaFree(c->pt_start);
     cudaFree(c->pt_cnt);
     cudaFree(c->pt_box);
     cudaFree(c->obs_list);

@@ -138,14 +138,19 @@ int step_blocks_per_sm();
 int shape_max_seg_cap(int shape, int cache_n);
 cudaError_t shape_prepare(int shape, int seg_cap, int cache_n, int* blocks_per_sm);
 cudaError_t launch_rollout(int shape, const StepArgs& a, int grid, cudaStream_t st);
-// Observation (wsim_observe.cu): roadgraph point tiles of kPtTile consecutive
-// points per scene, and the per-observer kernel.
+// Observation (wsim_observe.cu): roadgraph point tiles of at most kPtTile
+// consecutive points of one polyline run per scene (counted per scene, then
+// their starts written; tile t holds points pt_start[t] .. pt_start[t+1]-1),
+// their boxes, and the per-observer kernels.
 constexpr int kPtTile = 32;
-cudaError_t launch_pt_tiles(const int32_t* rg_off, const int32_t* tile_off, const float* rg_x, const float* rg_y,
-                            const uint8_t* rg_valid, int S, float4* box, int32_t* cnt, cudaStream_t st);
+cudaError_t launch_pt_count(const int32_t* rg_off, const int32_t* rg_poly, int S, int32_t* tiles_per_scene,
+                            cudaStream_t st);
+cudaError_t launch_pt_tiles(const int32_t* rg_off, const int32_t* rg_poly, const int32_t* tile_off, const float* rg_x,
+                            const float* rg_y, const uint8_t* rg_valid, int S, int32_t* pt_start, float4* box,
+                            int32_t* cnt, cudaStream_t st);
 cudaError_t launch_observe(const StepArgs& a, const uint8_t* observers, int32_t* list, int32_t* count,
-                           const int32_t* rg_off, const float* rg_x, const float* rg_y, const uint8_t* rg_valid,
-                           const int32_t* tile_off, const float4* box, const int32_t* cnt, const int32_t* scene_of,
+                           const float* rg_x, const float* rg_y, const uint8_t* rg_valid, const int32_t* tile_off,
+                           const int32_t* pt_start, const float4* box, const int32_t* cnt, const int32_t* scene_of,
                            int M, int K, float* agents, uint8_t* agents_valid, float* rg, int32_t* rg_idx,
                            cudaStream_t st);
 // Route metrics (wsim_route.cu).

@@ -9,9 +9,9 @@
 // (or away from) c gives an exact lower (upper) bound of every key in the
 // tile, with no slack.
 //
-// Roadgraph points are grouped in tiles of kPtTile consecutive points of a
-// scene (the roadgraph's own order, invalid points skipped in the box and
-// the count), built once per context.  Per observer (one warp of
+// Roadgraph points are grouped in tiles of at most kPtTile consecutive
+// points of one polyline (the roadgraph's own order, invalid points skipped
+// in the box and the count), built once per context.  Per observer (one warp of
 // k_observe_warp when K <= kObwMaxK and the observers number at least a few
 // per warp that kernel keeps resident; else one CTA of k_observe):
 //   1. writes the other agents in the observer's frame;
@@ -38,17 +38,86 @@ __device__ __forceinline__ float obs_key(float px, float py, float cx, float cy)
     return fmaf(dx, dx, dy * dy);
 }
 
+// Tile starts of one scene.  A polyline run (consecutive points with the
+// same polyline id) of L points gives ceil(L / kPtTile) tiles of consecutive
+// points, so no tile spans two polylines (a tile across a gap between
+// polylines has a box as large as the gap, whose lower bound then lets it
+// into every nearby observer's candidates).  One CTA per scene walks its
+// points in chunks: run_start(i) is the largest run start <= i (a block
+// max-scan, carried across chunks), and point i starts a tile when
+// i - run_start(i) is a multiple of kPtTile.  WRITE = false counts the tiles
+// into out[s]; WRITE = true writes their starts to out[tile_off[s] + k] (a
+// block sum-scan of the start flags) and, in the last scene, the end of the
+// last tile to out[tile_off[S]].
+constexpr int kPtThreads = 1024;
+
+template <bool MAX>
+__device__ __forceinline__ int block_scan(int v, int* wtot) {  // inclusive, kPtThreads threads
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v = MAX ? max(v, u) : v + u;
+    }
+    if (lane == 31) wtot[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int x = wtot[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x = MAX ? max(x, u) : x + u;
+        }
+        wtot[lane] = x;
+    }
+    __syncthreads();
+    const int before = w > 0 ? wtot[w - 1] : (MAX ? -1 : 0);
+    return MAX ? max(v, before) : v + before;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(kPtThreads) k_pt_starts(const int32_t* rg_off, const int32_t* rg_poly,
+                                                          const int32_t* tile_off, int S, int32_t* out) {
+    __shared__ int wmax[32], wsum[32];
+    __shared__ int carry_rs, carry_n;
+    const int s = blockIdx.x;
+    const int r0 = rg_off[s], r1 = rg_off[s + 1];
+    if (threadIdx.x == 0) {
+        carry_rs = r0;
+        carry_n = 0;
+    }
+    __syncthreads();
+    for (int base = r0; base < r1; base += kPtThreads) {
+        const int i = base + threadIdx.x;
+        const bool in = i < r1;
+        const bool rs = in && (i == r0 || rg_poly[i] != rg_poly[i - 1]);
+        const int run_start = max(carry_rs, block_scan<true>(rs ? i : -1, wmax));
+        const int st = in && (i - run_start) % kPtTile == 0;
+        const int incl = block_scan<false>(st, wsum) + carry_n;
+        if (WRITE && st) out[tile_off[s] + incl - 1] = i;
+        __syncthreads();  // every thread has read the carries
+        if (threadIdx.x == kPtThreads - 1) {
+            carry_rs = run_start;
+            carry_n = incl;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (!WRITE) out[s] = carry_n;
+        if (WRITE && s == S - 1) out[tile_off[S]] = r1;
+    }
+}
+
 // Tile boxes: (xmin, ymin, xmax, ymax) of the valid points and their count.
-__global__ void __launch_bounds__(256) k_pt_tiles(const int32_t* rg_off, const int32_t* tile_off, const float* rg_x,
+__global__ void __launch_bounds__(256) k_pt_tiles(const int32_t* tile_off, const int32_t* pt_start, const float* rg_x,
                                                   const float* rg_y, const uint8_t* rg_valid, int S, float4* box,
                                                   int32_t* cnt) {
     const int s = blockIdx.x;
-    const int r0 = rg_off[s], r1 = rg_off[s + 1];
     const int t0 = tile_off[s], nt = tile_off[s + 1] - t0;
     for (int t = threadIdx.x; t < nt; t += 256) {
         float x0 = WSIM_INF, y0 = WSIM_INF, x1 = -WSIM_INF, y1 = -WSIM_INF;
         int n = 0;
-        const int a = r0 + t * kPtTile, b = min(r1, a + kPtTile);
+        const int a = pt_start[t0 + t], b = pt_start[t0 + t + 1];
         for (int r = a; r < b; ++r) {
             if (!rg_valid[r]) continue;
             const float x = rg_x[r], y = rg_y[r];
@@ -156,7 +225,7 @@ __device__ int hist_crossing(const int* hist, int want, ObsSmem& sm, int* upto) 
 // A tighter bound from the points themselves: a histogram of the keys of
 // every point in the tiles that can hold one below tau gives the top of the
 // bucket holding the want-th key; *n = the points at or below it.
-__device__ float point_bound(const float4* box, const int32_t* cnt, int t0, int nt, int r0, int r1, const float* rg_x,
+__device__ float point_bound(const float4* box, const int32_t* cnt, int t0, int nt, const int32_t* ps, const float* rg_x,
                              const float* rg_y, const uint8_t* rg_valid, float cx, float cy, float tau, int want,
                              ObsSmem& sm, int* n) {
     int* hist = reinterpret_cast<int*>(sm.item);
@@ -168,8 +237,8 @@ __device__ float point_bound(const float4* box, const int32_t* cnt, int t0, int 
     for (int q = warp; q < m; q += kObsThreads / 32) {
         const int t = nl >= 0 ? sm.list[q] : q;
         if (nl < 0 && (cnt[t0 + t] == 0 || tile_lower(box[t0 + t], cx, cy) > tau)) continue;
-        const int r = r0 + t * kPtTile + lane;
-        if (r < r1 && rg_valid[r]) {
+        const int r = ps[t] + lane;
+        if (r < ps[t + 1] && rg_valid[r]) {
             const float key = obs_key(rg_x[r], rg_y[r], cx, cy);
             if (key <= tau && key < WSIM_INF) atomicAdd(&hist[__float_as_uint(key) >> (32 - kHistBits)], 1);
         }
@@ -217,7 +286,7 @@ __device__ float tile_bound(const float4* box, const int32_t* cnt, int t0, int n
 
 
 // Points with key <= tau in the tiles that can hold one.
-__device__ int count_points_within(const float4* box, const int32_t* cnt, int t0, int nt, int r0, int r1,
+__device__ int count_points_within(const float4* box, const int32_t* cnt, int t0, int nt, const int32_t* ps,
                                    const float* rg_x, const float* rg_y, const uint8_t* rg_valid, float cx, float cy,
                                    float tau, ObsSmem& sm) {
     int c = 0;
@@ -226,8 +295,8 @@ __device__ int count_points_within(const float4* box, const int32_t* cnt, int t0
     for (int q = warp; q < m; q += kObsThreads / 32) {
         const int t = nl >= 0 ? sm.list[q] : q;
         if (nl < 0 && (cnt[t0 + t] == 0 || tile_lower(box[t0 + t], cx, cy) > tau)) continue;
-        const int r = r0 + t * kPtTile + lane;
-        if (r < r1 && rg_valid[r] && obs_key(rg_x[r], rg_y[r], cx, cy) <= tau) ++c;
+        const int r = ps[t] + lane;
+        if (r < ps[t + 1] && rg_valid[r] && obs_key(rg_x[r], rg_y[r], cx, cy) <= tau) ++c;
     }
     return block_sum(c, sm);
 }
@@ -282,9 +351,10 @@ __device__ __forceinline__ void write_points(const unsigned long long* item, int
 }
 
 __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const int32_t* list, const int32_t* count,
-                                                         const int32_t* rg_off, const float* rg_x, const float* rg_y,
+                                                         const float* rg_x, const float* rg_y,
                                                          const uint8_t* rg_valid, const int32_t* tile_off,
-                                                         const float4* box, const int32_t* cnt, int M, int K,
+                                                         const int32_t* pt_start, const float4* box,
+                                                         const int32_t* cnt, int M, int K,
                                                          float* agents, uint8_t* agents_valid, float* rg_out,
                                                          int32_t* rg_idx, const int32_t* scene_of, int N_tot,
                                                          int warp_min) {
@@ -305,8 +375,8 @@ __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const
         // 1. Other agents in the observer's frame.
         agents_in_frame(A, g, a0, N, M, xh, xl, yh, yl, th, tl, c, sn, threadIdx.x, kObsThreads, agents, agents_valid);
         // 2. Upper bound of the K-th key from the tiles.
-        const int r0 = rg_off[s], r1 = rg_off[s + 1];
         const int t0 = tile_off[s], nt = tile_off[s + 1] - t0;
+        const int32_t* ps = pt_start + t0;  // tile t: points ps[t] .. ps[t+1]-1
         const float cx = __fadd_rn(xh, xl), cy = __fadd_rn(yh, yl);
         int total = 0;
         for (int t = threadIdx.x; t < nt; t += kObsThreads) {
@@ -337,21 +407,21 @@ __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const
         // 3. Gather (lowering tau while the list would overflow).
         int n = 0;
         if (want > 0) {
-            tau = point_bound(box, cnt, t0, nt, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, want, sm, &n);
-            if (n < 0) n = count_points_within(box, cnt, t0, nt, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, sm);
+            tau = point_bound(box, cnt, t0, nt, ps, rg_x, rg_y, rg_valid, cx, cy, tau, want, sm, &n);
+            if (n < 0) n = count_points_within(box, cnt, t0, nt, ps, rg_x, rg_y, rg_valid, cx, cy, tau, sm);
         }
         if (n > kObsCap) {
             uint32_t lo = 0, hi = __float_as_uint(tau);
             while (lo < hi) {  // smallest tau' with at least `want` points
                 const uint32_t mid = lo + (hi - lo) / 2;
-                if (count_points_within(box, cnt, t0, nt, r0, r1, rg_x, rg_y, rg_valid, cx, cy, __uint_as_float(mid),
+                if (count_points_within(box, cnt, t0, nt, ps, rg_x, rg_y, rg_valid, cx, cy, __uint_as_float(mid),
                                         sm) >= want)
                     hi = mid;
                 else
                     lo = mid + 1;
             }
             tau = __uint_as_float(lo);
-            n = count_points_within(box, cnt, t0, nt, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, sm);
+            n = count_points_within(box, cnt, t0, nt, ps, rg_x, rg_y, rg_valid, cx, cy, tau, sm);
             if (n > kObsCap) {  // more than kObsCap points share the K-th key
                 if (threadIdx.x == 0) set_status(A.status, WSIM_ESIZE);
                 n = 0;
@@ -365,9 +435,9 @@ __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const
             for (int qq = warp; qq < m; qq += kObsThreads / 32) {
                 const int t = nl >= 0 ? sm.list[qq] : qq;
                 if (nl < 0 && (cnt[t0 + t] == 0 || tile_lower(box[t0 + t], cx, cy) > tau)) continue;
-                const int r = r0 + t * kPtTile + lane;
+                const int r = ps[t] + lane;
                 float key = 0.f;
-                const bool in = r < r1 && rg_valid[r] && (key = obs_key(rg_x[r], rg_y[r], cx, cy)) <= tau;
+                const bool in = r < ps[t + 1] && rg_valid[r] && (key = obs_key(rg_x[r], rg_y[r], cx, cy)) <= tau;
                 const unsigned bal = __ballot_sync(kFull, in);
                 int base = 0;
                 if (lane == 0 && bal) base = atomicAdd(&sm.n, __popc(bal));
@@ -423,7 +493,8 @@ static_assert(kObwCap * 2 >= (1 << kHistBits), "the key histogram shares the poi
 
 struct ObwSmem {
     unsigned long long item[kObwWarps][kObwCap];
-    int list[kObwWarps][kObwList];
+    int start[kObwWarps][kObwList];      // candidate tiles: first point
+    uint8_t len[kObwWarps][kObwList];    // ... and point count (<= kPtTile)
 };
 
 // The top of key-histogram bucket b (the largest float bit pattern in it).
@@ -473,14 +544,16 @@ __device__ __forceinline__ int warp_crossing(const int* hist, int want, int lane
 }
 
 // Visits the points of the candidate tiles (nl >= 0: the nl listed ones,
-// four tiles' loads in flight at a time; else every tile whose box can hold a
-// point with key <= tau): f(ok, key, r) on every lane for every tile, ok =
-// the lane's point exists and is valid (warp-uniform calls: f may use warp
-// votes).
+// tile q's points ts[q] .. ts[q] + tn[q] - 1, four tiles' loads in flight at
+// a time; else every tile whose box can hold a point with key <= tau, tile
+// t's points ps[t] .. ps[t+1]-1): f(ok, key, r) on every lane for every
+// tile, ok = the lane's point exists and is valid (warp-uniform calls: f may
+// use warp votes).
 template <class F>
-__device__ __forceinline__ void warp_points(const int* tl, int nl, int nt, const float4* box, const int32_t* cnt,
-                                            int t0, int r0, int r1, const float* rg_x, const float* rg_y,
-                                            const uint8_t* rg_valid, float cx, float cy, float tau, int lane, F f) {
+__device__ __forceinline__ void warp_points(const int* ts, const uint8_t* tn, int nl, int nt, const float4* box,
+                                            const int32_t* cnt, int t0, const int32_t* ps, const float* rg_x,
+                                            const float* rg_y, const uint8_t* rg_valid, float cx, float cy, float tau,
+                                            int lane, F f) {
     if (nl >= 0) {
         for (int q = 0; q < nl; q += kObwU) {
             float x[kObwU], y[kObwU];
@@ -488,10 +561,10 @@ __device__ __forceinline__ void warp_points(const int* tl, int nl, int nt, const
             int r[kObwU];
 #pragma unroll
             for (int u = 0; u < kObwU; ++u) {
-                const int t = q + u < nl ? tl[q + u] : -1;
-                r[u] = r0 + t * kPtTile + lane;
-                const bool in = t >= 0 && r[u] < r1;
-                const int rr = in ? r[u] : r0;  // a listed tile exists, so r0 < r1
+                const bool has = q + u < nl;
+                r[u] = (has ? ts[q + u] : ts[0]) + lane;
+                const bool in = has && lane < tn[q + u];
+                const int rr = in ? r[u] : ts[0];  // a listed tile's first point (nl > 0 here)
                 x[u] = rg_x[rr];
                 y[u] = rg_y[rr];
                 const uint8_t v = rg_valid[rr];
@@ -503,16 +576,17 @@ __device__ __forceinline__ void warp_points(const int* tl, int nl, int nt, const
     } else {
         for (int t = 0; t < nt; ++t) {
             if (cnt[t0 + t] == 0 || tile_lower(box[t0 + t], cx, cy) > tau) continue;
-            const int r = r0 + t * kPtTile + lane;
-            const bool ok = r < r1 && rg_valid[r];
+            const int r = ps[t] + lane;
+            const bool ok = r < ps[t + 1] && rg_valid[r];
             f(ok, ok ? obs_key(rg_x[r], rg_y[r], cx, cy) : 0.f, r);
         }
     }
 }
 
 __global__ void __launch_bounds__(kObwWarps * 32, 5)
-    k_observe_warp(const StepArgs A, const int32_t* list, int32_t* count, int warp_min, const int32_t* rg_off,
+    k_observe_warp(const StepArgs A, const int32_t* list, int32_t* count, int warp_min,
                    const float* rg_x, const float* rg_y, const uint8_t* rg_valid, const int32_t* tile_off,
+                   const int32_t* pt_start,
                    const float4* box, const int32_t* cnt, int M, int K, float* agents, uint8_t* agents_valid,
                    float* rg_out, int32_t* rg_idx, const int32_t* scene_of) {
     static_assert(kPtTile == 32, "a tile's points are the warp's lanes");
@@ -523,7 +597,8 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     unsigned long long* item = sm.item[w];
     int* hist = reinterpret_cast<int*>(item);  // free until the gather
-    int* tl = sm.list[w];
+    int* ts = sm.start[w];
+    uint8_t* tn = sm.len[w];
     const unsigned below = (1u << lane) - 1u;
     const int nchunks = (n_obs + kObwChunk - 1) / kObwChunk;
     for (;;) {
@@ -543,8 +618,8 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
             // 1. Other agents in the observer's frame.
             agents_in_frame(A, g, a0, N, M, xh, xl, yh, yl, th, tlo, c, sn, lane, 32, agents, agents_valid);
             // 2. Upper bound of the K-th key from the tiles, and the valid-point total.
-            const int r0 = rg_off[s], r1 = rg_off[s + 1];
             const int t0 = tile_off[s], nt = tile_off[s + 1] - t0;
+            const int32_t* ps = pt_start + t0;  // tile t: points ps[t] .. ps[t+1]-1
             const float cx = __fadd_rn(xh, xl), cy = __fadd_rn(yh, yl);
             warp_clear_hist(hist, lane);
             int total = 0;
@@ -590,7 +665,11 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
                     for (int u = 0; u < kObwU; ++u) {
                         const unsigned bal = __ballot_sync(kFull, in[u]);
                         const int q = nl + __popc(bal & below);
-                        if (in[u] && q < kObwList) tl[q] = tb + 32 * u + lane;
+                        if (in[u] && q < kObwList) {
+                            const int t = tb + 32 * u + lane;
+                            ts[q] = ps[t];
+                            tn[q] = static_cast<uint8_t>(ps[t + 1] - ps[t]);
+                        }
                         nl += __popc(bal);
                     }
                 }
@@ -598,7 +677,7 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
                 __syncwarp();
                 // 4. A histogram of the candidate points' keys tightens tau.
                 warp_clear_hist(hist, lane);
-                warp_points(tl, nl, nt, box, cnt, t0, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
+                warp_points(ts, tn, nl, nt, box, cnt, t0, ps, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
                             [&](bool ok, float key, int) {
                                 if (ok && key <= tau && key < WSIM_INF)
                                     atomicAdd(&hist[__float_as_uint(key) >> (32 - kHistBits)], 1);
@@ -610,7 +689,7 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
                     tau = fminf(tau, bucket_top(b2));
                 } else {  // fewer finite keys than wanted below tau: keep tau
                     int c1 = 0;
-                    warp_points(tl, nl, nt, box, cnt, t0, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
+                    warp_points(ts, tn, nl, nt, box, cnt, t0, ps, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
                                 [&](bool ok, float key, int) { c1 += ok && key <= tau; });
                     n = __reduce_add_sync(kFull, c1);
                 }
@@ -620,7 +699,7 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
                 }
                 // 5. Gather the points with key <= tau (exactly n of them).
                 int base = 0;
-                warp_points(tl, nl, nt, box, cnt, t0, r0, r1, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
+                warp_points(ts, tn, nl, nt, box, cnt, t0, ps, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
                             [&](bool ok, float key, int r) {
                                 const bool in = ok && key <= tau;
                                 const unsigned bal = __ballot_sync(kFull, in);
@@ -659,15 +738,23 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
     }
 }
 
-cudaError_t launch_pt_tiles(const int32_t* rg_off, const int32_t* tile_off, const float* rg_x, const float* rg_y,
-                            const uint8_t* rg_valid, int S, float4* box, int32_t* cnt, cudaStream_t st) {
-    k_pt_tiles<<<S, 256, 0, st>>>(rg_off, tile_off, rg_x, rg_y, rg_valid, S, box, cnt);
+cudaError_t launch_pt_count(const int32_t* rg_off, const int32_t* rg_poly, int S, int32_t* tiles_per_scene,
+                            cudaStream_t st) {
+    k_pt_starts<false><<<S, kPtThreads, 0, st>>>(rg_off, rg_poly, nullptr, S, tiles_per_scene);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pt_tiles(const int32_t* rg_off, const int32_t* rg_poly, const int32_t* tile_off, const float* rg_x,
+                            const float* rg_y, const uint8_t* rg_valid, int S, int32_t* pt_start, float4* box,
+                            int32_t* cnt, cudaStream_t st) {
+    k_pt_starts<true><<<S, kPtThreads, 0, st>>>(rg_off, rg_poly, tile_off, S, pt_start);
+    k_pt_tiles<<<S, 256, 0, st>>>(tile_off, pt_start, rg_x, rg_y, rg_valid, S, box, cnt);
     return cudaGetLastError();
 }
 
 cudaError_t launch_observe(const StepArgs& a, const uint8_t* observers, int32_t* list, int32_t* count,
-                           const int32_t* rg_off, const float* rg_x, const float* rg_y, const uint8_t* rg_valid,
-                           const int32_t* tile_off, const float4* box, const int32_t* cnt, const int32_t* scene_of,
+                           const float* rg_x, const float* rg_y, const uint8_t* rg_valid, const int32_t* tile_off,
+                           const int32_t* pt_start, const float4* box, const int32_t* cnt, const int32_t* scene_of,
                            int M, int K, float* agents, uint8_t* agents_valid, float* rg, int32_t* rg_idx,
                            cudaStream_t st) {
     // list[0, N): the observers, count[0] of them; count[1]: the warp kernel's
@@ -689,13 +776,13 @@ cudaError_t launch_observe(const StepArgs& a, const uint8_t* observers, int32_t*
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perw, k_observe_warp, kObwWarps * 32, 0);
         warp_min = sms * std::max(perw, 1) * kObwWarps * (4 + std::max(0, K - 64) * 7 / 192);
         k_observe_warp<<<sms * std::max(perw, 1), kObwWarps * 32, 0, st>>>(
-            a, list, count, warp_min, rg_off, rg_x, rg_y, rg_valid, tile_off, box, cnt, M, K, agents, agents_valid,
-            rg, rg_idx, scene_of);
+            a, list, count, warp_min, rg_x, rg_y, rg_valid, tile_off, pt_start, box, cnt, M, K, agents,
+            agents_valid, rg, rg_idx, scene_of);
     }
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_observe, kObsThreads, 0);
-    k_observe<<<sms * std::max(per, 1), kObsThreads, 0, st>>>(a, list, count, rg_off, rg_x, rg_y, rg_valid, tile_off,
-                                                              box, cnt, M, K, agents, agents_valid, rg, rg_idx,
-                                                              scene_of, a.N_tot, warp_min);
+    k_observe<<<sms * std::max(per, 1), kObsThreads, 0, st>>>(a, list, count, rg_x, rg_y, rg_valid, tile_off,
+                                                              pt_start, box, cnt, M, K, agents, agents_valid, rg,
+                                                              rg_idx, scene_of, a.N_tot, warp_min);
     return cudaGetLastError();
 }
 
