@@ -493,7 +493,8 @@ static_assert(kObwCap * 2 >= (1 << kHistBits), "the key histogram shares the poi
 
 struct ObwSmem {
     unsigned long long item[kObwWarps][kObwCap];
-    int start[kObwWarps][kObwList];      // candidate tiles: first point
+    int start[kObwWarps][kObwList];      // candidate tiles: first point,
+    float lower[kObwWarps][kObwList];    // ... lower bound of their keys
     uint8_t len[kObwWarps][kObwList];    // ... and point count (<= kPtTile)
 };
 
@@ -598,6 +599,7 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
     unsigned long long* item = sm.item[w];
     int* hist = reinterpret_cast<int*>(item);  // free until the gather
     int* ts = sm.start[w];
+    float* tlb = sm.lower[w];
     uint8_t* tn = sm.len[w];
     const unsigned below = (1u << lane) - 1u;
     const int nchunks = (n_obs + kObwChunk - 1) / kObwChunk;
@@ -654,12 +656,14 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
                 int nl = 0;
                 for (int tb = 0; tb < nt; tb += kObwU * 32) {
                     bool in[kObwU];
+                    float lo[kObwU];
 #pragma unroll
                     for (int u = 0; u < kObwU; ++u) {
                         const int t = min(tb + 32 * u + lane, nt - 1);
                         const int c1 = cnt[t0 + t];
                         const float4 B = box[t0 + t];
-                        in[u] = tb + 32 * u + lane < nt && c1 > 0 && tile_lower(B, cx, cy) <= tau;
+                        lo[u] = tile_lower(B, cx, cy);
+                        in[u] = tb + 32 * u + lane < nt && c1 > 0 && lo[u] <= tau;
                     }
 #pragma unroll
                     for (int u = 0; u < kObwU; ++u) {
@@ -669,6 +673,7 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
                             const int t = tb + 32 * u + lane;
                             ts[q] = ps[t];
                             tn[q] = static_cast<uint8_t>(ps[t + 1] - ps[t]);
+                            tlb[q] = lo[u];
                         }
                         nl += __popc(bal);
                     }
@@ -687,6 +692,29 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
                 __syncwarp();  // the histogram is read before the gather overwrites it
                 if (b2 >= 0) {
                     tau = fminf(tau, bucket_top(b2));
+                    // keep the listed tiles that can still hold a point below the
+                    // tightened tau (in place: a round reads before it writes)
+                    if (nl > 0) {
+                        int nk = 0;
+                        for (int qb = 0; qb < nl; qb += 32) {
+                            const int qq = qb + lane;
+                            const bool keep = qq < nl && tlb[qq] <= tau;
+                            const int a1 = keep ? ts[qq] : 0;
+                            const float l1 = keep ? tlb[qq] : 0.f;
+                            const uint8_t n1 = keep ? tn[qq] : 0;
+                            const unsigned bal = __ballot_sync(kFull, keep);
+                            const int d = nk + __popc(bal & below);
+                            __syncwarp();  // the round's entries are read before any is overwritten
+                            if (keep) {
+                                ts[d] = a1;
+                                tlb[d] = l1;
+                                tn[d] = n1;
+                            }
+                            nk += __popc(bal);
+                            __syncwarp();
+                        }
+                        nl = nk;
+                    }
                 } else {  // fewer finite keys than wanted below tau: keep tau
                     int c1 = 0;
                     warp_points(ts, tn, nl, nt, box, cnt, t0, ps, rg_x, rg_y, rg_valid, cx, cy, tau, lane,
