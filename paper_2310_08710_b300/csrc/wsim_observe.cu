@@ -475,8 +475,8 @@ __global__ void __launch_bounds__(kObsThreads) k_observe(const StepArgs A, const
 }
 
 // ---------------------------------------------------------------------------
-// Warp per observer (K <= kObwMaxK, at least 4 to 11 observers per resident
-// warp, growing with K): the same four steps with a histogram, tile list
+// Warp per observer (K <= kObwMaxK, at least one observer per resident
+// warp): the same four steps with a histogram, tile list
 // and point list private to each warp, so that no step waits at a block
 // barrier.  Warps take chunks of kObwChunk consecutive list entries from a
 // counter.  An observer whose gathered points would exceed kObwCap goes to the
@@ -795,14 +795,15 @@ cudaError_t launch_observe(const StepArgs& a, const uint8_t* observers, int32_t*
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int nb = std::min((a.N_tot + 255) / 256, 4096);
     k_obs_list<<<std::max(nb, 1), 256, 0, st>>>(observers, a.valid, a.N_tot, list, count);
-    // The warp kernel takes over from a few observers per resident warp: each
-    // warp's observer is a long serial chain, so with fewer the block kernel's
-    // finer grain wins.  Measured crossovers on 30k-point scenes: about 4
-    // observers per warp at K = 64 and 11 at K = 256 (linear in between).
+    // The warp kernel takes over from one observer per resident warp: each
+    // warp's observer is a serial chain, so with fewer observers than warps
+    // the block kernel's finer grain wins (30k-point scenes, K = 256: 2,048
+    // observers 0.15 ms on the block kernel against 0.18 on the warp kernel;
+    // 16,384 observers 0.77 against 0.49 ms).
     int warp_min = INT_MAX;
     if (K <= kObwMaxK) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&perw, k_observe_warp, kObwWarps * 32, 0);
-        warp_min = sms * std::max(perw, 1) * kObwWarps * (4 + std::max(0, K - 64) * 7 / 192);
+        warp_min = sms * std::max(perw, 1) * kObwWarps;
         k_observe_warp<<<sms * std::max(perw, 1), kObwWarps * 32, 0, st>>>(
             a, list, count, warp_min, rg_x, rg_y, rg_valid, tile_off, pt_start, box, cnt, M, K, agents,
             agents_valid, rg, rg_idx, scene_of);

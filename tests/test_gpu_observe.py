@@ -132,9 +132,9 @@ def _sampled_check(go, b, rows, scenes, M, K, observers=None):
 
 
 def test_every_agent_of_640_scenes_warp_per_observer(wsim):
-    # 640 scenes x 128 agents, 20k-point roadgraphs: ~74,000 observers, more
-    # than the warp kernel's threshold at K = 64 and 256 (4 and 11 observers
-    # per resident warp, 5 x 8 warps per SM).  Scene 0: 600 points stacked
+    # 640 scenes x 128 agents, 20k-point roadgraphs: ~74,000 observers, well
+    # above the warp kernel's threshold (one observer per resident warp, 5 x 8
+    # warps per SM).  Scene 0: 600 points stacked
     # 0.5 m ahead of its ego (the K-th key shared by more points than a warp
     # gathers: that observer goes to the block kernel).  Scene 1: one point of
     # each of 200 tiles within 0.3-0.5 m of its ego (more candidate tiles than a
