@@ -584,6 +584,80 @@ __device__ __forceinline__ void warp_points(const int* ts, const uint8_t* tn, in
     }
 }
 
+// One compare-exchange stage of the bitonic network over item[0, p2) (the
+// rule of the block kernel's sort: pair (lo, lo + stride), ascending where
+// lo & size is 0).
+__device__ __forceinline__ void bitonic_stage(unsigned long long* item, int p2, int size, int stride, int lane) {
+    for (int i = lane; i < p2 / 2; i += 32) {
+        const int lo = 2 * i - (i & (stride - 1));
+        const int hi = lo + stride;
+        const bool up = (lo & size) == 0;
+        const unsigned long long a = item[lo], b = item[hi];
+        if ((a > b) == up) {
+            item[lo] = b;
+            item[hi] = a;
+        }
+    }
+    __syncwarp();
+}
+
+// The stages of strides below kSortChunk act within aligned chunks of
+// kSortChunk items, so a lane runs them on a chunk held in registers: the
+// chunk sort (sizes 2 .. kSortChunk) and, after each larger size's
+// shared-memory stages, its last three strides.  28 shared-memory round
+// trips instead of 45 for 512 items; the same network, so the same order.
+constexpr int kSortChunk = 8;
+__device__ __forceinline__ void cswap(unsigned long long& a, unsigned long long& b, bool up) {
+    const unsigned long long x = a, y = b;
+    const bool sw = (x > y) == up;
+    a = sw ? y : x;
+    b = sw ? x : y;
+}
+
+// Sorts item[0, p2) ascending (p2 a power of two, <= kObwCap), warp-wide.
+__device__ void warp_bitonic(unsigned long long* item, int p2, int lane) {
+    if (p2 < kSortChunk) {
+        for (int size = 2; size <= p2; size <<= 1)
+            for (int stride = size >> 1; stride > 0; stride >>= 1) bitonic_stage(item, p2, size, stride, lane);
+        return;
+    }
+    const int nc = p2 / kSortChunk;
+    for (int ch = lane; ch < nc; ch += 32) {  // chunk sort, directions of the whole network
+        unsigned long long v[kSortChunk];
+        const int base = ch * kSortChunk;
+#pragma unroll
+        for (int k = 0; k < kSortChunk; ++k) v[k] = item[base + k];
+#pragma unroll
+        for (int size = 2; size <= kSortChunk; size <<= 1)
+#pragma unroll
+            for (int st = size >> 1; st > 0; st >>= 1)
+#pragma unroll
+                for (int k = 0; k < kSortChunk; ++k)
+                    if (!(k & st)) cswap(v[k], v[k + st], ((base + k) & size) == 0);
+#pragma unroll
+        for (int k = 0; k < kSortChunk; ++k) item[base + k] = v[k];
+    }
+    __syncwarp();
+    for (int size = 2 * kSortChunk; size <= p2; size <<= 1) {
+        for (int stride = size >> 1; stride >= kSortChunk; stride >>= 1) bitonic_stage(item, p2, size, stride, lane);
+        for (int ch = lane; ch < nc; ch += 32) {  // strides 4, 2, 1: one direction per chunk
+            unsigned long long v[kSortChunk];
+            const int base = ch * kSortChunk;
+            const bool up = (base & size) == 0;
+#pragma unroll
+            for (int k = 0; k < kSortChunk; ++k) v[k] = item[base + k];
+#pragma unroll
+            for (int st = kSortChunk / 2; st > 0; st >>= 1)
+#pragma unroll
+                for (int k = 0; k < kSortChunk; ++k)
+                    if (!(k & st)) cswap(v[k], v[k + st], up);
+#pragma unroll
+            for (int k = 0; k < kSortChunk; ++k) item[base + k] = v[k];
+        }
+        __syncwarp();
+    }
+}
+
 __global__ void __launch_bounds__(kObwWarps * 32, 5)
     k_observe_warp(const StepArgs A, const int32_t* list, int32_t* count, int warp_min,
                    const float* rg_x, const float* rg_y, const uint8_t* rg_valid, const int32_t* tile_off,
@@ -743,21 +817,7 @@ __global__ void __launch_bounds__(kObwWarps * 32, 5)
                 while (p2 < n) p2 <<= 1;
                 for (int i = n + lane; i < p2; i += 32) item[i] = ~0ull;
                 __syncwarp();
-                for (int size = 2; size <= p2; size <<= 1) {
-                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                        for (int i = lane; i < p2 / 2; i += 32) {
-                            const int lo = 2 * i - (i & (stride - 1));
-                            const int hi = lo + stride;
-                            const bool up = (lo & size) == 0;
-                            const unsigned long long a = item[lo], bb = item[hi];
-                            if ((a > bb) == up) {
-                                item[lo] = bb;
-                                item[hi] = a;
-                            }
-                        }
-                        __syncwarp();
-                    }
-                }
+                warp_bitonic(item, p2, lane);
             }
             // 7. The first K in the observer's frame.
             write_points(item, g, K, min(want, n), rg_x, rg_y, xh, xl, yh, yl, c, sn, lane, 32, rg_out, rg_idx);
